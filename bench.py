@@ -1,0 +1,346 @@
+"""Throughput bench for the batched Voice render.
+
+Workload: the Voice, batch 128 x 4 s at 44.1 kHz, FP32 out; consecutive
+batches with seed = batch index (synth1B1-style generation), K batches per
+timed region captured in one CUDA graph. A step is one batch through the
+whole render path. Metric: audio MHz = samples rendered per second / 1e6.
+
+Our arm (default) times the fused persistent kernel (and, beside it, the
+plain unfused module-by-module form on the same GPU). ``--impl reference``
+times the FP64 CPU oracle as it stands on the host cores.
+
+Under torchrun (N > 1) every rank renders its own batches (batch indices
+rank, rank + N, ...): voices are independent, so there is no collective on
+the data path; the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BATCH = 128
+SECONDS = 4.0
+SR = 44100.0
+N_SAMPLES = int(SECONDS * SR)
+METRIC = "audio MHz (samples/s) at batch 128×4 s: fused vs plain GPU form; % roofline"
+PAPER_MHZ = 714.0  # Abstract: 714 MHz on a single V100 (context only)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1024)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax or None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_oracle_baseline(budget_s: float):
+    """The FP64 oracle as it stands on this host's cores: batches of 128 x 4 s
+    voices (seed = batch index) until about budget_s of wall time is spent."""
+    import oracle
+    cfg = oracle.default_config(seconds=SECONDS)
+    cores = oracle.hardware_threads()
+    t0 = time.perf_counter()
+    done = 0
+    b = 0
+    while True:
+        oracle.render_batch(cfg, b, b, BATCH, threads=cores)
+        done += 1
+        b += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or el / done * (done + 1) > 1.5 * budget_s:
+            break
+    el = time.perf_counter() - t0
+    mhz = done * BATCH * N_SAMPLES / el / 1e6
+    return {"value": mhz, "unit": "MHz", "cores": cores, "kind": "oracle",
+            "sample": f"{done} batch(es) of {BATCH} voices x {SECONDS:g} s (seed = batch index), "
+                      f"{el:.1f} s wall on {cores} threads"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cfg = oracle.default_config(seconds=SECONDS)
+    cores = oracle.hardware_threads()
+    # each step is a bounded sample of the workload: 16 voices of one batch
+    voices = list(range(16))
+    for s in range(args.warmup):
+        oracle.render_batch(cfg, s, s, BATCH, threads=cores, voices=voices)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.render_batch(cfg, s, s, BATCH, threads=cores, voices=voices)
+    el = time.perf_counter() - t0
+    samples = args.steps * len(voices) * N_SAMPLES
+    mhz = samples / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": mhz, "unit": "MHz", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (parameters drawn per voice from seed and voice index)",
+            "config": {"workload": "Voice batch 128 x 4 s @ 44.1 kHz, seed = batch index; "
+                                   "reference step = 16 voices of the batch", "global_batch": BATCH,
+                       "seconds": SECONDS, "sample_rate": SR},
+            "cpu_baseline": {"value": mhz, "unit": "MHz", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} steps x 16 voices x 4 s"},
+            "e2e": {"value": mhz, "unit": "MHz", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2104_12922_gb300 as pkg
+    from paper_2104_12922_gb300 import build as b
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or ws == 1:
+        b.build()
+    if ws > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    syn = pkg.Synth(seconds=SECONDS, max_batch=BATCH)
+    K, W = args.steps, max(3, args.warmup)
+    n_buf = 4  # 4 x 90.3 MB rotating outputs: > L2 (129 MB), writes reach HBM
+    outs = [torch.empty((BATCH, N_SAMPLES), dtype=torch.float32, device=dev) for _ in range(n_buf)]
+    pouts = [torch.empty((BATCH, 78), dtype=torch.float32, device=dev) for _ in range(n_buf)]
+    stream = torch.cuda.Stream(device=dev)
+
+    def batch_index(step):
+        return step * ws + rank
+
+    def record(g_steps, plain=False):
+        for s in range(g_steps):
+            bi = batch_index(s)
+            syn.render(bi, bi, BATCH, out=outs[s % n_buf], params_out=pouts[s % n_buf],
+                       stream=stream, plain=plain)
+
+    # warm-up (untimed), then capture K steps in one graph
+    with torch.cuda.stream(stream):
+        record(W)
+    stream.synchronize()
+    syn.sync(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        record(K)
+    graph.replay()  # untimed replay primes the graph
+    stream.synchronize()
+
+    def timed(fn, clocks=False, preload=None):
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        if preload is not None:  # untimed load so the clock samples see a busy GPU
+            preload()
+        start.record(stream)
+        fn()
+        end.record(stream)
+        end.synchronize()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        ms = start.elapsed_time(end)
+        if ws > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.barrier()
+            ms = float(t.item())
+        return ms, (sampler.summary() if sampler else None)
+
+    # untimed replays (about 1 s of load), then exactly K timed steps
+    ms1, _ = timed(lambda: graph.replay())
+    n_pre = max(1, int(1000 / max(ms1, 1e-3)))
+
+    def preload():
+        for _ in range(n_pre):
+            graph.replay()
+
+    ms, clocks = timed(lambda: graph.replay(), clocks=True, preload=preload)
+    syn.sync(stream)
+    steps = K
+    samples_total = steps * BATCH * N_SAMPLES * ws
+    value = samples_total / (ms / 1e3) / 1e6
+    ms_per_step = ms / steps
+
+    # plain unfused form on the same GPU (same workload)
+    plain = None
+    if not args.no_plain:
+        Kp = min(K, 64)
+        with torch.cuda.stream(stream):
+            record(2, plain=True)
+        stream.synchronize()
+        gp = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gp, stream=stream):
+            record(Kp, plain=True)
+        gp.replay()
+        stream.synchronize()
+        msp, _ = timed(lambda: gp.replay())
+        plain = {"value": Kp * BATCH * N_SAMPLES * ws / (msp / 1e3) / 1e6, "unit": "MHz",
+                 "ms_per_step": msp / Kp, "steps": Kp,
+                 "kernels_per_step": 14}
+        del gp
+
+    # end to end through the public API with host buffers: per step the render
+    # and a device->host read of the step's audio and parameters into pinned
+    # memory (the only inputs are the seed and the batch index: 0 H2D bytes)
+    Ke = min(K, 64)
+    host_a = torch.empty((BATCH, N_SAMPLES), dtype=torch.float32, pin_memory=True)
+    host_p = torch.empty((BATCH, 78), dtype=torch.float32, pin_memory=True)
+
+    def e2e_steps():
+        with torch.cuda.stream(stream):
+            for s in range(Ke):
+                bi = batch_index(s)
+                a, p = syn.render(bi, bi, BATCH, out=outs[s % n_buf], params_out=pouts[s % n_buf],
+                                  stream=stream)
+                host_a.copy_(a, non_blocking=True)
+                host_p.copy_(p, non_blocking=True)
+    e2e_steps()
+    stream.synchronize()
+    mse, _ = timed(e2e_steps)
+    e2e = {"value": Ke * BATCH * N_SAMPLES * ws / (mse / 1e3) / 1e6, "unit": "MHz",
+           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": BATCH * N_SAMPLES * 4 + BATCH * 78 * 4}
+
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = measured_peaks()
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # transcendental issue bound: 4 per sample (sine sin; square-saw sin, cos,
+    # tanh) at 16 per clock per SM, at the maximum SM clock
+    alu_peak = num_sms * 16 * sm_max * 1e6 / 4
+    per_gpu_rate = BATCH * N_SAMPLES / (ms_per_step / 1e3)
+    hbm_peak_samples = peaks["hbm_gbs"] * 1e9 / 4
+    roofline = {"bound": "alu", "achieved": per_gpu_rate / 1e9, "peak": alu_peak / 1e9,
+                "unit": "Gsample/s", "frac": per_gpu_rate / alu_peak, "traffic": None,
+                "peak_source": f"{num_sms} SMs x 16 transcendentals/clk x {sm_max:.0f} MHz / 4 per sample",
+                "hbm": {"achieved": per_gpu_rate * 4 / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": per_gpu_rate / hbm_peak_samples, "peak_source": peak_src}}
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_oracle_baseline(args.cpu_seconds)
+    line = {"metric": METRIC, "value": value, "unit": "MHz", "n_gpus": ws, "steps": steps,
+            "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (synth1B1 workload: parameters drawn per voice from seed and voice index)",
+            "config": {"workload": "Voice batch 128 x 4 s @ 44.1 kHz, FP32 out, seed = batch index, "
+                                   f"{K} batches per CUDA graph", "global_batch": BATCH * ws,
+                       "seconds": SECONDS, "sample_rate": SR,
+                       "l2": "4 rotating 90.3 MB output buffers (> 129 MB L2)",
+                       "parallelism": f"replicas x{ws} (disjoint batch indices)"},
+            "x_realtime": value * 1e6 / SR,
+            "paper_context": {"value": PAPER_MHZ, "unit": "MHz", "hardware": "single V100 (Sec. 2.2)"},
+            "plain": plain, "fused_over_plain": (value / plain["value"]) if plain else None,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": steps}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+/*
+ * synth.h -- C ABI of libsynth.so, the GB300 (sm_103a) batched Voice renderer.
+ *
+ * Paper: Turian et al., "One Billion Audio Sounds from GPU-enabled Modular
+ * Synthesis" (DAFx 2021). The problem statement the calls follow (Sec. 2.1,
+ * 2.2): a batch index and a seed in; a replicable batch of 4 s, 44.1 kHz
+ * voices paired with their parameter vectors out; batch 128 by default.
+ *
+ * Conventions for every call below:
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library never frees them and never allocates inside a render call
+ *    (scratch lives in the handle and is sized by synth_config.max_batch).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Calls are stream-ordered and asynchronous unless stated.
+ *  - Layouts are row-major and contiguous: audio[batch][N] float32 with
+ *    N = round(seconds * sample_rate); params[batch][78] float32 holding the
+ *    normalized parameters u in [0,1].
+ *  - Global voice index: voice v of a call has g = batch_index * batch + v,
+ *    and a voice depends only on (seed, g) -- the same g renders the same
+ *    sound in any batch size (Sec. 2.2 replicability).
+ *  - Every call returns a synth_status and never aborts. Argument errors are
+ *    caught before any launch. A device-side error (a bounded wait that gave
+ *    up) is recorded in the handle and returned by synth_sync.
+ *  - One handle renders one batch at a time: calls on one handle must be
+ *    ordered on one stream (they share the handle's scratch).
+ */
+#ifndef SYNTH_H
+#define SYNTH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SYNTH_NUM_PARAMS 78
+
+typedef enum {
+  SYNTH_OK = 0,
+  SYNTH_ERR_ARG = 1,         /* invalid argument; nothing was launched */
+  SYNTH_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  SYNTH_ERR_OOM = 3,         /* device or pinned allocation failed (create only) */
+  SYNTH_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (output invalid) */
+  SYNTH_ERR_STATE = 5,       /* handle not usable (destroyed / earlier failure) */
+  SYNTH_ERR_UNSUPPORTED = 6  /* configuration the kernels do not implement */
+} synth_status;
+
+typedef struct synth_handle_s* synth_handle;
+
+/* Sec. 3.3 range-map hyper-parameters ("nebula"): for each of the 78
+ * parameters the human range [lo, hi], a curve exponent c > 0 and a symmetric
+ * flag. Non-symmetric: y = lo + (hi - lo) u^c. Symmetric: s = 2u - 1,
+ * y = lo + (hi - lo) (1 + sgn(s)|s|^c) / 2. */
+typedef struct {
+  double lo[SYNTH_NUM_PARAMS];
+  double hi[SYNTH_NUM_PARAMS];
+  double curve[SYNTH_NUM_PARAMS];
+  int32_t symmetric[SYNTH_NUM_PARAMS];
+} synth_nebula;
+
+/* Phase-scan carry precision (precision study). */
+#define SYNTH_CARRY_FP64 0  /* default: FP64 carry and per-segment offsets */
+#define SYNTH_CARRY_FP32 1  /* study only: carry and offsets rounded to FP32 */
+
+typedef struct {
+  double sample_rate;   /* Hz; Sec. 3.1 default 44100 */
+  double control_rate;  /* Hz; Sec. 3.1 default 441. sample_rate/control_rate
+                           must be an integer multiple of 4 */
+  double seconds;       /* voice length; Abstract: 4 s */
+  int32_t max_batch;    /* largest batch any call on this handle will use */
+  int32_t carry;        /* SYNTH_CARRY_FP64 (default) or SYNTH_CARRY_FP32 */
+  const synth_nebula* nebula; /* NULL = the library's default nebula n0;
+                                 otherwise copied at create */
+} synth_config;
+
+/* Defaults: 44100 Hz, 441 Hz, 4 s, max_batch 128, FP64 carry, nebula n0. */
+void synth_default_config(synth_config* out);
+
+/* The library's default nebula n0 (its own choice of ranges and curves; the
+ * authors' nebula values are not given in the paper). */
+void synth_default_nebula(synth_nebula* out);
+
+/* Allocates the handle and its device scratch on the current CUDA device.
+ * Errors: SYNTH_ERR_ARG (NULL pointers, non-integer or non-multiple-of-4
+ * sample_rate/control_rate, seconds <= 0, max_batch < 1),
+ * SYNTH_ERR_OOM, SYNTH_ERR_CUDA. */
+synth_status synth_create(const synth_config* cfg, synth_handle* out);
+synth_status synth_destroy(synth_handle h);
+
+int32_t synth_num_params(synth_handle h);   /* 78 (Sec. 1.1.3) */
+int64_t synth_num_samples(synth_handle h);  /* N per voice */
+
+/* Batched Voice render, fused form: one persistent kernel launch.
+ * Sec. 3.1-3.3: per voice, parameters are drawn (Philox4x32-10, key = seed,
+ * counter = (g, block, stream 0)) or taken from params_in_dev, mapped to
+ * their ranges; 6 ADSRs, 2 LFOs and the modulation mixer run at the control
+ * rate; control signals are linearly upsampled; a prefix scan over the
+ * instantaneous frequency gives each VCO's phase; sine, square-saw and noise
+ * (Philox, stream 1) pass through VCAs and the mixer.
+ *  params_in_dev  [batch][78] float or NULL (NULL = draw from seed). Values
+ *                 are clamped to [0,1].
+ *  audio_dev      [batch][N] float, required.
+ *  params_out_dev [batch][78] float or NULL: the normalized parameters used.
+ * Errors: SYNTH_ERR_ARG (batch < 0 or > max_batch, NULL audio_dev),
+ * SYNTH_ERR_CUDA. batch == 0 is a no-op. */
+synth_status synth_render(synth_handle h, uint64_t seed, uint64_t batch_index, int32_t batch,
+                          const float* params_in_dev, float* audio_dev, float* params_out_dev,
+                          void* stream);
+
+/* The same render as a plain, unfused sequence of module kernels (one per
+ * module, every control-rate and audio-rate intermediate in a caller-owned
+ * workspace in device memory), the torchsynth-style design of Sec. 3.1.
+ * Same results as synth_render to within floating-point reordering.
+ * workspace_dev must hold synth_render_plain_workspace_size(h, batch) bytes
+ * (256-byte aligned). Errors as synth_render, plus SYNTH_ERR_ARG when the
+ * workspace is NULL or too small. */
+synth_status synth_render_plain_workspace_size(synth_handle h, int32_t batch, size_t* bytes);
+synth_status synth_render_plain(synth_handle h, uint64_t seed, uint64_t batch_index, int32_t batch,
+                                const float* params_in_dev, float* audio_dev, float* params_out_dev,
+                                void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Waits for the stream, then reports (and clears) a device-side error
+ * recorded by any earlier call on this handle: SYNTH_ERR_TIMEOUT if a bounded
+ * wait gave up, SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. */
+synth_status synth_sync(synth_handle h, void* stream);
+
+/* Host-side range map of normalized parameters (Sec. 3.3): y[count][78]
+ * from u[count][78] under the handle's nebula. Host pointers. */
+synth_status synth_params_to_human(synth_handle h, const float* u_host, double* y_host,
+                                   int32_t count);
+
+/* Sec. 2.2 train/test split: 1 if global voice g is in the test set
+ * (blocks of 1024 voices, every tenth block), else 0. */
+int32_t synth_is_test(uint64_t global_voice_index);
+
+const char* synth_status_string(synth_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,237 @@
+"""GB300 (sm_103a) batched Voice renderer -- Python binding of libsynth.so.
+
+The binding only marshals arguments: every step of a render runs in the CUDA
+kernels of ``libsynth.so`` (C ABI in ``include/synth.h``). PyTorch is used
+for device memory and streams. There is no CPU fallback: if the library is not
+built, importing the binding raises.
+
+Paper: Turian et al., "One Billion Audio Sounds from GPU-enabled Modular
+Synthesis" (DAFx 2021), Sec. 2-3.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+NUM_PARAMS = 78
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsynth.so")
+
+SYNTH_OK, SYNTH_ERR_ARG, SYNTH_ERR_CUDA, SYNTH_ERR_OOM = 0, 1, 2, 3
+SYNTH_ERR_TIMEOUT, SYNTH_ERR_STATE, SYNTH_ERR_UNSUPPORTED = 4, 5, 6
+SYNTH_CARRY_FP64, SYNTH_CARRY_FP32 = 0, 1
+
+
+class SynthError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {synth_status_string(status)} (status {status})")
+        self.status = status
+
+
+class synth_nebula(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * NUM_PARAMS), ("hi", ctypes.c_double * NUM_PARAMS),
+                ("curve", ctypes.c_double * NUM_PARAMS), ("symmetric", ctypes.c_int32 * NUM_PARAMS)]
+
+
+class synth_config(ctypes.Structure):
+    _fields_ = [("sample_rate", ctypes.c_double), ("control_rate", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("max_batch", ctypes.c_int32),
+                ("carry", ctypes.c_int32), ("nebula", ctypes.POINTER(synth_nebula))]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libsynth.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "(the renderer has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u64, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64
+        P = ctypes.POINTER
+        L.synth_default_config.argtypes = [P(synth_config)]
+        L.synth_default_config.restype = None
+        L.synth_default_nebula.argtypes = [P(synth_nebula)]
+        L.synth_default_nebula.restype = None
+        L.synth_create.argtypes = [P(synth_config), P(vp)]
+        L.synth_destroy.argtypes = [vp]
+        L.synth_num_params.argtypes = [vp]
+        L.synth_num_params.restype = i32
+        L.synth_num_samples.argtypes = [vp]
+        L.synth_num_samples.restype = i64
+        L.synth_render.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp]
+        L.synth_render_plain_workspace_size.argtypes = [vp, i32, P(ctypes.c_size_t)]
+        L.synth_render_plain.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.synth_sync.argtypes = [vp, vp]
+        L.synth_params_to_human.argtypes = [vp, vp, vp, i32]
+        L.synth_is_test.argtypes = [u64]
+        L.synth_is_test.restype = i32
+        L.synth_status_string.argtypes = [ctypes.c_int]
+        L.synth_status_string.restype = ctypes.c_char_p
+        for name in ("synth_create", "synth_destroy", "synth_render", "synth_render_plain",
+                     "synth_render_plain_workspace_size", "synth_sync", "synth_params_to_human"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+# ---- thin wrappers with the C names -------------------------------------------
+def synth_status_string(status: int) -> str:
+    return lib().synth_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str) -> None:
+    if status != SYNTH_OK:
+        raise SynthError(status, what)
+
+
+def synth_default_config() -> synth_config:
+    cfg = synth_config()
+    lib().synth_default_config(ctypes.byref(cfg))
+    return cfg
+
+
+def synth_default_nebula() -> synth_nebula:
+    nb = synth_nebula()
+    lib().synth_default_nebula(ctypes.byref(nb))
+    return nb
+
+
+def synth_create(cfg: synth_config) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().synth_create(ctypes.byref(cfg), ctypes.byref(h)), "synth_create")
+    return h.value
+
+
+def synth_destroy(h: int) -> None:
+    _check(lib().synth_destroy(h), "synth_destroy")
+
+
+def synth_render(h, seed, batch_index, batch, params_in_ptr, audio_ptr, params_out_ptr, stream) -> int:
+    return lib().synth_render(h, seed, batch_index, batch, params_in_ptr, audio_ptr, params_out_ptr,
+                              stream)
+
+
+def synth_render_plain(h, seed, batch_index, batch, params_in_ptr, audio_ptr, params_out_ptr,
+                       workspace_ptr, workspace_bytes, stream) -> int:
+    return lib().synth_render_plain(h, seed, batch_index, batch, params_in_ptr, audio_ptr,
+                                    params_out_ptr, workspace_ptr, workspace_bytes, stream)
+
+
+def synth_render_plain_workspace_size(h, batch) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().synth_render_plain_workspace_size(h, batch, ctypes.byref(n)),
+           "synth_render_plain_workspace_size")
+    return n.value
+
+
+def synth_sync(h, stream) -> int:
+    return lib().synth_sync(h, stream)
+
+
+def synth_is_test(g: int) -> bool:
+    return bool(lib().synth_is_test(g))
+
+
+def make_nebula(d: dict) -> synth_nebula:
+    nb = synth_nebula()
+    for p in range(NUM_PARAMS):
+        nb.lo[p] = float(d["lo"][p])
+        nb.hi[p] = float(d["hi"][p])
+        nb.curve[p] = float(d["curve"][p])
+        nb.symmetric[p] = int(d["symmetric"][p])
+    return nb
+
+
+def nebula_dict(nb: synth_nebula) -> dict:
+    import numpy as np
+    return {"lo": np.array(nb.lo[:]), "hi": np.array(nb.hi[:]), "curve": np.array(nb.curve[:]),
+            "symmetric": np.array(nb.symmetric[:], dtype=np.int32)}
+
+
+# ---- torch convenience layer ----------------------------------------------------
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Synth:
+    """One renderer handle on the current CUDA device.
+
+    ``render`` fills caller-visible torch tensors (float32, contiguous, on the
+    handle's device) through the C ABI; nothing is computed in Python.
+    """
+
+    def __init__(self, seconds: float = 4.0, sample_rate: float = 44100.0,
+                 control_rate: float = 441.0, max_batch: int = 128, carry: int = SYNTH_CARRY_FP64,
+                 nebula: dict | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Synth needs a CUDA device (there is no CPU fallback)")
+        cfg = synth_default_config()
+        cfg.sample_rate, cfg.control_rate, cfg.seconds = sample_rate, control_rate, seconds
+        cfg.max_batch, cfg.carry = max_batch, carry
+        self._nebula = make_nebula(nebula) if nebula is not None else None
+        if self._nebula is not None:
+            cfg.nebula = ctypes.pointer(self._nebula)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.handle = synth_create(cfg)
+        self.max_batch = max_batch
+        self.num_samples = int(lib().synth_num_samples(self.handle))
+        self._workspace = None
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            synth_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_tensor(self, t, shape, name):
+        import torch
+        if t is None:
+            return
+        if t.dtype != torch.float32 or not t.is_contiguous() or t.device != self.device:
+            raise ValueError(f"{name} must be a contiguous float32 tensor on {self.device}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+    def render(self, seed: int, batch_index: int, batch: int, params_in=None, out=None,
+               params_out=None, stream=None, plain: bool = False):
+        """Renders voices g = batch_index * batch + v; returns (audio, params)."""
+        import torch
+        if out is None:
+            out = torch.empty((batch, self.num_samples), dtype=torch.float32, device=self.device)
+        if params_out is None:
+            params_out = torch.empty((batch, NUM_PARAMS), dtype=torch.float32, device=self.device)
+        self._check_tensor(out, (batch, self.num_samples), "out")
+        self._check_tensor(params_out, (batch, NUM_PARAMS), "params_out")
+        self._check_tensor(params_in, (batch, NUM_PARAMS), "params_in")
+        st = _stream_ptr(stream)
+        if plain:
+            need = synth_render_plain_workspace_size(self.handle, batch)
+            if self._workspace is None or self._workspace.numel() < need:
+                self._workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+            status = synth_render_plain(self.handle, seed, batch_index, batch, _ptr(params_in),
+                                        _ptr(out), _ptr(params_out), _ptr(self._workspace),
+                                        self._workspace.numel(), st)
+        else:
+            status = synth_render(self.handle, seed, batch_index, batch, _ptr(params_in), _ptr(out),
+                                  _ptr(params_out), st)
+        _check(status, "synth_render_plain" if plain else "synth_render")
+        return out, params_out
+
+    def sync(self, stream=None) -> None:
+        _check(synth_sync(self.handle, _stream_ptr(stream)), "synth_sync")

@@ -1,0 +1,56 @@
+// internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "voice_device.cuh"
+
+namespace synth {
+
+// Device scratch header for the persistent kernels: a work counter, a
+// completion counter, a launch epoch that tags look-back flags (so flags of
+// an earlier launch are never mistaken for this one's), and an error word.
+struct ScratchHeader {
+  unsigned int work;
+  unsigned int done;
+  unsigned int epoch;
+  unsigned int error;   // bit 0: a bounded look-back wait gave up
+  unsigned int pad[60];
+};
+static_assert(sizeof(ScratchHeader) == 256, "header is one 256-byte block");
+
+// Look-back state of one tile (voice, window) for the two scan chains
+// (0: LFO phases, 1: VCO phases), two components each.
+struct TileState {
+  unsigned int flag[2];  // (epoch << 2) | state; state 1 = aggregate, 2 = inclusive
+  unsigned int pad[2];
+  double agg[2][2];
+  double inc[2][2];
+};
+static_assert(sizeof(TileState) == 80, "tile state layout");
+
+constexpr unsigned int kErrLookbackTimeout = 1u;
+
+constexpr int kFusedThreads = 256;
+constexpr int kFusedTileSeg = 128;  // control intervals per tile of the fused kernel
+
+inline int windows_per_voice(int K) { return (K + kFusedTileSeg - 1) / kFusedTileSeg; }
+
+// Launches the fused persistent render. Returns the CUDA error of the launch.
+cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
+                                int batch, const float* params_in, float* audio,
+                                float* params_out, ScratchHeader* hdr, TileState* tiles,
+                                int grid, cudaStream_t stream);
+int fused_max_active_blocks_per_sm();
+
+// Plain (unfused) form.
+size_t plain_workspace_bytes(const VoiceConst& vc, int batch);
+cudaError_t launch_render_plain(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
+                                int batch, const float* params_in, float* audio,
+                                float* params_out, void* workspace, ScratchHeader* hdr,
+                                TileState* tiles, cudaStream_t stream);
+
+}  // namespace synth

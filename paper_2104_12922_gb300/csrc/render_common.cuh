@@ -1,0 +1,276 @@
+// render_common.cuh -- pieces shared by the fused and the plain render kernels:
+// per-interval VCO phase description, its per-sample evaluation, the block
+// scan, the decoupled look-back, and the audio-rate oscillators.
+#pragma once
+
+#include <cuda/atomic>
+
+#include "internal.h"
+#include "voice_device.cuh"
+
+namespace synth {
+
+// How a VCO's phase advances inside one control interval. The pitch in midi
+// is linear in the sample index j (Sec. 3.2 upsampling), so the per-sample
+// increment f(j)/SR is geometric in j -- until the pitch reaches the Nyquist
+// cap, after which it is the constant 1/2. The interval is therefore at most
+// two pieces, A for j < jc and B for j >= jc, each either geometric (first
+// increment c, ratio e^x) or linear (constant increment c).
+struct SegVco {
+  float phase0;  // phase in cycles at the interval's first sample, in [0, 1)
+  float cA;      // first increment of piece A
+  float cB;      // first increment of piece B
+  float LB;      // phase advanced over piece A (cycles) = local phase where B starts
+  float x;       // log of the per-sample increment ratio
+  float E1;      // expm1(x)
+  float invE;    // 1 / expm1(x)
+  int jc_flags;  // jc | (A linear) << 16 | (B linear) << 17
+};
+
+constexpr double kLn2 = 0.69314718055994530942;
+
+// Phase advanced by k samples of a geometric piece starting at increment c:
+// sum_{i<k} c e^{i x} = c expm1(k x) / expm1(x) (c k when x == 0).
+__device__ __forceinline__ double geo_sum(double c, double x, int k) {
+  if (k <= 0) return 0.0;
+  if (x == 0.0) return c * (double)k;
+  return c * expm1((double)k * x) / expm1(x);
+}
+
+// Builds one interval's description from the pitch (midi) at its two control
+// points and returns the phase it advances over its Rk samples (FP64).
+// Sample j of the interval has pitch m_a + (j / R) (m_b - m_a), capped at the
+// Nyquist pitch; its increment is 440 * 2^((m - 69)/12) / SR.
+__device__ inline double vco_interval(double m_a, double m_b, int R, int Rk, const VoiceConst& vc,
+                                      SegVco* out) {
+  const double dm = m_b - m_a;
+  const double inv_sr = 1.0 / vc.sample_rate;
+  const double x = dm * (kLn2 / (12.0 * (double)R));
+  auto m_lin = [&](int j) { return m_a + ((double)j / (double)R) * dm; };
+  auto capped = [&](int j) { return m_lin(j) > vc.m_nyq; };
+  auto inc_at = [&](double m) { return 440.0 * exp2((m - 69.0) / 12.0) * inv_sr; };
+  const bool c_first = capped(0), c_last = capped(Rk - 1);
+  int jc;
+  bool a_lin, b_lin;
+  double cA, cB, LB, total;
+  if (!c_first && !c_last) {  // no cap inside: one geometric piece
+    jc = Rk; a_lin = (x == 0.0); b_lin = true;
+    cA = inc_at(m_a); cB = 0.5; LB = 0.0;
+    total = geo_sum(cA, x, Rk);
+  } else if (c_first && c_last) {  // capped throughout: half a cycle per sample
+    jc = 0; a_lin = true; b_lin = true;
+    cA = 0.5; cB = 0.5; LB = 0.0;
+    total = 0.5 * (double)Rk;
+  } else if (!c_first) {  // rising through the cap at jc
+    double js = (vc.m_nyq - m_a) * (double)R / dm;
+    jc = (int)fmin(fmax(ceil(js), 0.0), (double)(Rk - 1));
+    while (jc > 0 && capped(jc - 1)) --jc;
+    while (jc < Rk && !capped(jc)) ++jc;
+    a_lin = (x == 0.0); b_lin = true;
+    cA = inc_at(m_a); cB = 0.5;
+    LB = geo_sum(cA, x, jc);
+    total = LB + 0.5 * (double)(Rk - jc);
+  } else {  // falling out of the cap at jc
+    double js = (vc.m_nyq - m_a) * (double)R / dm;
+    jc = (int)fmin(fmax(ceil(js), 0.0), (double)(Rk - 1));
+    while (jc > 0 && !capped(jc - 1)) --jc;
+    while (jc < Rk && capped(jc)) ++jc;
+    a_lin = true; b_lin = (x == 0.0);
+    cA = 0.5; cB = inc_at(m_lin(jc));
+    LB = 0.5 * (double)jc;
+    total = LB + geo_sum(cB, x, Rk - jc);
+  }
+  // float description; geometric pieces with |x| below 1e-30 are linear to
+  // well within float rounding (relative error ~ j x / 2)
+  const float xf = (float)x;
+  const bool tiny = fabsf(xf) < 1e-30f;
+  out->cA = (float)cA;
+  out->cB = (float)cB;
+  out->LB = (float)LB;
+  out->x = xf;
+  out->E1 = tiny ? 0.f : expm1f(xf);
+  out->invE = tiny ? 0.f : 1.0f / expm1f(xf);
+  out->jc_flags = jc | ((a_lin || tiny) ? 1 << 16 : 0) | ((b_lin || tiny) ? 1 << 17 : 0);
+  return total;
+}
+
+// Phases (cycles, wrapped to [-1/2, 1/2)) of samples j0..j0+3 of an interval.
+__device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
+  const int jc = s.jc_flags & 0xffff;
+  float loc[4];
+  if (j0 + 3 < jc || j0 >= jc) {
+    const bool in_b = j0 >= jc;
+    const float L = in_b ? s.LB : 0.f;
+    const float c = in_b ? s.cB : s.cA;
+    const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
+    const int d0 = j0 - (in_b ? jc : 0);
+    if (lin) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) loc[i] = fmaf(c, (float)(d0 + i), L);
+    } else {
+      // r^(d0+i) - 1 = E0 + Ei + E0 Ei with E0 = expm1(d0 x), Ei = expm1(i x)
+      const float E0 = expm1f((float)d0 * s.x);
+      const float E1 = s.E1;
+      const float E2 = E1 * (2.f + E1);
+      const float E3 = fmaf(E1, 1.f + E2, E2);
+      const float cE = c * s.invE;
+      loc[0] = fmaf(cE, E0, L);
+      loc[1] = fmaf(cE, E0 + E1 + E0 * E1, L);
+      loc[2] = fmaf(cE, E0 + E2 + E0 * E2, L);
+      loc[3] = fmaf(cE, E0 + E3 + E0 * E3, L);
+    }
+  } else {  // the quad straddles the piece boundary
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = j0 + i;
+      const bool in_b = j >= jc;
+      const float L = in_b ? s.LB : 0.f;
+      const float c = in_b ? s.cB : s.cA;
+      const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
+      const int d = j - (in_b ? jc : 0);
+      loc[i] = lin ? fmaf(c, (float)d, L) : fmaf(c * s.invE, expm1f((float)d * s.x), L);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float p = s.phase0 + loc[i];
+    p -= floorf(p);
+    ph[i] = p >= 0.5f ? p - 1.f : p;
+  }
+}
+
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+// tanh via one exponential: 1 - 2 / (1 + e^{2z}); the argument is bounded to
+// |z| <= 15 where tanh is 1 to within 2e-13.
+__device__ __forceinline__ float tanh_fast(float z) {
+  z = fminf(fmaxf(z, -15.f), 15.f);
+  return 1.f - __fdividef(2.f, 1.f + __expf(2.f * z));
+}
+
+// Square-saw at phase p (cycles in [-1/2, 1/2)): theta = 2 pi p,
+// tanh(kappa sin theta) / tanh(kappa) * (1 + shape cos theta) / (1 + shape).
+__device__ __forceinline__ float square_saw(float p, float kappa, float inv_tanh_kappa, float shape,
+                                            float inv_1p_shape) {
+  float sn, cs;
+  __sincosf(kTwoPiF * p, &sn, &cs);
+  return tanh_fast(kappa * sn) * inv_tanh_kappa * fmaf(shape, cs, 1.f) * inv_1p_shape;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of two values per thread (all threads take part).
+// ---------------------------------------------------------------------------
+template <class T, int NT>
+__device__ __forceinline__ void block_exclusive_scan2(T& a, T& b, T* warp_tot /*[2][NT/32]*/,
+                                                      T& tot_a, T& tot_b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T na = __shfl_up_sync(0xffffffffu, ia, o);
+    T nb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) { ia += na; ib += nb; }
+  }
+  if (lane == 31) { warp_tot[warp] = ia; warp_tot[NT / 32 + warp] = ib; }
+  __syncthreads();
+  if (warp == 0) {
+    T wa = lane < NT / 32 ? warp_tot[lane] : T(0);
+    T wb = lane < NT / 32 ? warp_tot[NT / 32 + lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < NT / 32; o <<= 1) {
+      T na = __shfl_up_sync(0xffffffffu, wa, o);
+      T nb = __shfl_up_sync(0xffffffffu, wb, o);
+      if (lane >= o) { wa += na; wb += nb; }
+    }
+    if (lane < NT / 32) { warp_tot[lane] = wa; warp_tot[NT / 32 + lane] = wb; }
+  }
+  __syncthreads();
+  const T pa = warp > 0 ? warp_tot[warp - 1] : T(0);
+  const T pb = warp > 0 ? warp_tot[NT / 32 + warp - 1] : T(0);
+  tot_a = warp_tot[NT / 32 - 1];
+  tot_b = warp_tot[2 * (NT / 32) - 1];
+  // exclusive prefix within the warp = the previous lane's inclusive prefix
+  T ea = __shfl_up_sync(0xffffffffu, ia, 1);
+  T eb = __shfl_up_sync(0xffffffffu, ib, 1);
+  if (lane == 0) { ea = T(0); eb = T(0); }
+  a = pa + ea;
+  b = pb + eb;
+  __syncthreads();
+}
+
+template <class T> __device__ __forceinline__ T wrap01(T x) { return x - floor(x); }
+template <> __device__ __forceinline__ float wrap01<float>(float x) { return x - floorf(x); }
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back along one voice's windows (Merrill & Garland's
+// single-pass prefix scan): publish this window's aggregate, add the
+// predecessors' aggregates until one with an inclusive prefix is found,
+// publish the inclusive prefix. Called by one thread. Values are phases in
+// cycles, kept wrapped to [0,1). Every wait is bounded: on timeout the error
+// bit is set in the header and the missing term is taken as 0.
+// ---------------------------------------------------------------------------
+constexpr int kLookbackSpinLimit = 1 << 22;
+
+template <class T>
+__device__ inline void lookback(TileState* voice_tiles, int w, int chain, unsigned int epoch,
+                                T own0, T own1, T& ex0, T& ex1, ScratchHeader* hdr) {
+  TileState* me = voice_tiles + w;
+  const unsigned int tag = (epoch & 0x3fffffffu) << 2;
+  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> my_flag(me->flag[chain]);
+  if (w == 0) {
+    __stcg(&me->inc[chain][0], (double)own0);
+    __stcg(&me->inc[chain][1], (double)own1);
+    my_flag.store(tag | 2u, cuda::memory_order_release);
+    ex0 = T(0); ex1 = T(0);
+    return;
+  }
+  __stcg(&me->agg[chain][0], (double)own0);
+  __stcg(&me->agg[chain][1], (double)own1);
+  my_flag.store(tag | 1u, cuda::memory_order_release);
+  T s0 = T(0), s1 = T(0);
+  for (int j = w - 1; j >= 0; --j) {
+    TileState* p = voice_tiles + j;
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> pf(p->flag[chain]);
+    unsigned int f = 0;
+    int spins = 0;
+    for (;;) {
+      f = pf.load(cuda::memory_order_acquire);
+      if ((f & ~3u) == tag && (f & 3u) != 0) break;
+      if (++spins > kLookbackSpinLimit) { f = 0; break; }
+      __nanosleep(64);
+    }
+    if (f == 0) {
+      atomicOr(&hdr->error, kErrLookbackTimeout);
+      break;
+    }
+    if ((f & 3u) == 2u) {
+      s0 += (T)__ldcg(&p->inc[chain][0]);
+      s1 += (T)__ldcg(&p->inc[chain][1]);
+      break;
+    }
+    s0 += (T)__ldcg(&p->agg[chain][0]);
+    s1 += (T)__ldcg(&p->agg[chain][1]);
+  }
+  ex0 = wrap01(s0);
+  ex1 = wrap01(s1);
+  __stcg(&me->inc[chain][0], (double)wrap01(ex0 + own0));
+  __stcg(&me->inc[chain][1], (double)wrap01(ex1 + own1));
+  my_flag.store(tag | 2u, cuda::memory_order_release);
+}
+
+// End-of-launch bookkeeping of the persistent kernels: the last CTA to finish
+// resets the work counters and advances the epoch for the next launch.
+__device__ inline void persistent_finish(ScratchHeader* hdr) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(&hdr->done, 1u);
+    if (prev == gridDim.x - 1) {
+      hdr->work = 0;
+      hdr->done = 0;
+      hdr->epoch = hdr->epoch + 1;
+      __threadfence();
+    }
+  }
+}
+
+}  // namespace synth

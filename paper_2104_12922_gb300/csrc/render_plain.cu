@@ -1,0 +1,348 @@
+// render_plain.cu -- the plain, unfused Voice render: one kernel per module,
+// each reading its inputs from and writing its output to device memory, the
+// way a framework of batched tensor ops renders the Voice (Sec. 3.1: "all
+// modules render audio in batches"; Sec. 3.2 routing). It computes the same
+// quantities as the fused kernel with the same numerics, so the two differ
+// only in how the work is scheduled and how much memory traffic it makes.
+//
+// Workspace (caller-owned, 256-byte aligned sections), B voices, P = K + 1
+// control points, N samples:
+//   y[B][78] f64 | env[B][6][P] f64 | lfo_inc[B][2][P] f64 | lfo_phase[B][2][P] f64
+//   dest[B][5][P] f64 | seg[B][2][K] SegVco | seg_sum[B][2][K] f64 | kappa[B][2][K] f32
+//   amp[B][3][N] f32 | phase[B][2][N] f32 | osc[B][3][N] f32
+
+#include "internal.h"
+#include "render_common.cuh"
+
+namespace synth {
+
+namespace {
+
+constexpr int kPT = 256;
+
+struct PlainLayout {
+  size_t y, env, lfo_inc, lfo_phase, dest, seg, seg_sum, kappa, amp, phase, osc, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+PlainLayout plain_layout(const VoiceConst& vc, int B) {
+  const size_t P = (size_t)vc.K + 1, K = (size_t)vc.K, N = (size_t)vc.n_samples;
+  PlainLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+  L.y = take(sizeof(double) * B * kNumParams);
+  L.env = take(sizeof(double) * B * 6 * P);
+  L.lfo_inc = take(sizeof(double) * B * 2 * P);
+  L.lfo_phase = take(sizeof(double) * B * 2 * P);
+  L.dest = take(sizeof(double) * B * 5 * P);
+  L.seg = take(sizeof(SegVco) * B * 2 * K);
+  L.seg_sum = take(sizeof(double) * B * 2 * K);
+  L.kappa = take(sizeof(float) * B * 2 * K);
+  L.amp = take(sizeof(float) * B * 3 * N);
+  L.phase = take(sizeof(float) * B * 2 * N);
+  L.osc = take(sizeof(float) * B * 3 * N);
+  L.total = o;
+  return L;
+}
+
+// Parameter module: draw (or read) and range-map.
+__global__ void plain_params(const __grid_constant__ VoiceConst vc, uint64_t seed,
+                             uint64_t batch_index, int batch, const float* params_in,
+                             float* params_out, double* y) {
+  const int v = blockIdx.x, p = threadIdx.x;
+  if (p >= kNumParams) return;
+  const uint64_t g = batch_index * (uint64_t)batch + (uint64_t)v;
+  float u;
+  if (params_in) {
+    u = fminf(fmaxf(params_in[(size_t)v * kNumParams + p], 0.f), 1.f);
+  } else {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(p >> 2),
+                                             kStreamParam),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    u = u01f(w[p & 3]);
+  }
+  if (params_out) params_out[(size_t)v * kNumParams + p] = u;
+  y[(size_t)v * kNumParams + p] = range_map((double)u, vc.lo[p], vc.hi[p], vc.curve[p], vc.sym[p]);
+}
+
+// ADSR modules (6 per voice) at the control points.
+__global__ void plain_adsr(const __grid_constant__ VoiceConst vc, int batch, const double* y,
+                           double* env) {
+  const int P = vc.K + 1;
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P) return;
+  const double* yv = y + (size_t)v * kNumParams;
+  const double t = (double)k / vc.control_rate;
+  for (int a = 0; a < 6; ++a) {
+    const double* q = yv + kAdsr + 5 * a;
+    const double lvl = adsr_gate_on(yv[kDuration], q[0], q[1], q[2], q[4]);
+    env[((size_t)v * 6 + a) * P + k] = adsr_eval(t, q, yv[kDuration], lvl);
+  }
+}
+
+// LFO rate: phase increment per control interval.
+__global__ void plain_lfo_rate(const __grid_constant__ VoiceConst vc, const double* y,
+                               const double* env, double* lfo_inc) {
+  const int P = vc.K + 1;
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P) return;
+  const double* yv = y + (size_t)v * kNumParams;
+  for (int l = 0; l < 2; ++l) {
+    const double e = env[((size_t)v * 6 + 2 + 2 * l) * P + k];
+    const double rate = fmin(fmax(yv[kLfo + 8 * l] + yv[kLfo + 8 * l + 1] * e, 0.0), kLfoMaxHz);
+    lfo_inc[((size_t)v * 2 + l) * P + k] = rate / vc.control_rate;
+  }
+}
+
+// Exclusive running sum of per-step phase increments, wrapped to [0,1),
+// starting from an initial phase; one block scans two sequences of a voice.
+__global__ void plain_phase_scan(const double* inc, double* phase, int len, int stride_seq,
+                                 const double* y, int init_slot0, int init_slot1) {
+  __shared__ double warp_tot[2 * (kPT / 32)];
+  const int v = blockIdx.x;
+  const double two_pi = 6.28318530717958647692;
+  const double* yv = y + (size_t)v * kNumParams;
+  double carry0 = wrap01(yv[init_slot0] / two_pi);
+  double carry1 = wrap01(yv[init_slot1] / two_pi);
+  const double* in0 = inc + (size_t)(2 * v) * stride_seq;
+  const double* in1 = inc + (size_t)(2 * v + 1) * stride_seq;
+  double* out0 = phase + (size_t)(2 * v) * stride_seq;
+  double* out1 = phase + (size_t)(2 * v + 1) * stride_seq;
+  for (int base = 0; base < len; base += kPT) {
+    const int i = base + threadIdx.x;
+    double a = i < len ? in0[i] : 0.0, b = i < len ? in1[i] : 0.0;
+    double ta, tb;
+    block_exclusive_scan2<double, kPT>(a, b, warp_tot, ta, tb);
+    if (i < len) {
+      out0[i] = wrap01(carry0 + a);
+      out1[i] = wrap01(carry1 + b);
+    }
+    carry0 = wrap01(carry0 + ta);
+    carry1 = wrap01(carry1 + tb);
+  }
+}
+
+// LFO outputs and modulation mixer at the control points.
+__global__ void plain_modmix(const __grid_constant__ VoiceConst vc, const double* y,
+                             const double* env, const double* lfo_phase, double* dest) {
+  const int P = vc.K + 1;
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P) return;
+  const double* yv = y + (size_t)v * kNumParams;
+  double lfo[2];
+  for (int l = 0; l < 2; ++l) {
+    const double* q = yv + kLfo + 8 * l;
+    const double wsum = q[3] + q[4] + q[5] + q[6] + q[7];
+    const double th = lfo_phase[((size_t)v * 2 + l) * P + k];
+    lfo[l] = env[((size_t)v * 6 + 3 + 2 * l) * P + k] * lfo_mix(th, q + 3, wsum);
+  }
+  const double src[4] = {env[((size_t)v * 6 + 0) * P + k], env[((size_t)v * 6 + 1) * P + k],
+                         lfo[0], lfo[1]};
+  for (int j = 0; j < 5; ++j) {
+    double acc = 0.0, ws = 0.0;
+    for (int i = 0; i < 4; ++i) {
+      acc += yv[kMod + 5 * i + j] * src[i];
+      ws += yv[kMod + 5 * i + j];
+    }
+    dest[((size_t)v * 5 + j) * P + k] = acc / fmax(1.0, ws);
+  }
+}
+
+// VCO interval descriptions and the phase each interval advances.
+__global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const double* y,
+                                    const double* dest, SegVco* seg, double* seg_sum,
+                                    float* kappa) {
+  const int P = vc.K + 1, K = vc.K;
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const double* yv = y + (size_t)v * kNumParams;
+  const int64_t rem = vc.n_samples - (int64_t)k * vc.R;
+  const int Rk = rem < vc.R ? (int)rem : vc.R;
+  for (int o = 0; o < 2; ++o) {
+    const int base = o == 0 ? kSine : kSqr;
+    const double* pd = dest + ((size_t)v * 5 + (o == 0 ? 0 : 2)) * P;
+    const double ma = yv[kMidi] + yv[base] + yv[base + 1] * pd[k];
+    const double mb = yv[kMidi] + yv[base] + yv[base + 1] * pd[k + 1];
+    seg_sum[((size_t)v * 2 + o) * K + k] =
+        vco_interval(ma, mb, vc.R, Rk, vc, &seg[((size_t)v * 2 + o) * K + k]);
+    if (o == 1) {
+      const double fk = 440.0 * exp2((fmin(ma, vc.m_nyq) - 69.0) / 12.0);
+      const double kap = fmin(kBrightnessMax, 1.0 + vc.sample_rate / (8.0 * fk));
+      kappa[((size_t)v * 2 + 0) * K + k] = (float)kap;
+      kappa[((size_t)v * 2 + 1) * K + k] = (float)(1.0 / tanh(kap));
+    }
+  }
+}
+
+// Writes the scanned interval start phases into the interval descriptions.
+__global__ void plain_seg_phase(const __grid_constant__ VoiceConst vc, const double* seg_phase,
+                                SegVco* seg, int batch) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)batch * 2 * vc.K) return;
+  seg[i].phase0 = (float)seg_phase[i];
+}
+
+// Upsampled amplitudes (VCA control inputs) at audio rate.
+__global__ void plain_upsample_amp(const __grid_constant__ VoiceConst vc, int batch,
+                                   const double* dest, float* amp) {
+  const int64_t N = vc.n_samples;
+  const int P = vc.K + 1;
+  const size_t total = (size_t)batch * N;
+  const float invR = 1.0f / (float)vc.R;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int v = (int)(i / N);
+    const int64_t n = (int64_t)(i - (size_t)v * N);
+    const int k = (int)(n / vc.R);
+    const float fj = (float)(n - (int64_t)k * vc.R) * invR;
+    const int dj[3] = {1, 3, 4};
+    for (int c = 0; c < 3; ++c) {
+      const double* d = dest + ((size_t)v * 5 + dj[c]) * P;
+      const float a0 = (float)d[k], a1 = (float)d[k + 1];
+      amp[((size_t)v * 3 + c) * N + n] = fmaf(fj, a1 - a0, a0);
+    }
+  }
+}
+
+// VCO phase at audio rate (one thread per quad of samples).
+__global__ void plain_vco_phase(const __grid_constant__ VoiceConst vc, int batch, const SegVco* seg,
+                                float* phase) {
+  const int64_t N = vc.n_samples;
+  const int64_t nq = (N + 3) / 4;
+  const size_t total = (size_t)batch * 2 * nq;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t vo = i / nq;
+    const int64_t q = (int64_t)(i - vo * nq);
+    const int64_t n0 = 4 * q;
+    const int k = (int)(n0 / vc.R);
+    const int j0 = (int)(n0 - (int64_t)k * vc.R);
+    float ph[4];
+    vco_quad(seg[vo * vc.K + k], j0, ph);
+    for (int t = 0; t < 4; ++t)
+      if (n0 + t < N) phase[vo * N + n0 + t] = ph[t];
+  }
+}
+
+__global__ void plain_sine(const __grid_constant__ VoiceConst vc, int batch, const float* phase,
+                           float* osc) {
+  const int64_t N = vc.n_samples;
+  const size_t total = (size_t)batch * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = i / N;
+    const int64_t n = (int64_t)(i - v * N);
+    osc[(v * 3 + 0) * N + n] = __sinf(kTwoPiF * phase[(v * 2 + 0) * N + n]);
+  }
+}
+
+__global__ void plain_square_saw(const __grid_constant__ VoiceConst vc, int batch, const double* y,
+                                 const float* phase, const float* kappa, float* osc) {
+  const int64_t N = vc.n_samples;
+  const size_t total = (size_t)batch * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = i / N;
+    const int64_t n = (int64_t)(i - v * N);
+    const int k = (int)(n / vc.R);
+    const double sh = y[v * kNumParams + kSqr + 3];
+    osc[(v * 3 + 1) * N + n] =
+        square_saw(phase[(v * 2 + 1) * N + n], kappa[(v * 2 + 0) * vc.K + k],
+                   kappa[(v * 2 + 1) * vc.K + k], (float)sh, (float)(1.0 / (1.0 + sh)));
+  }
+}
+
+__global__ void plain_noise(const __grid_constant__ VoiceConst vc, uint64_t seed,
+                            uint64_t batch_index, int batch, float* osc) {
+  const int64_t N = vc.n_samples;
+  const int64_t nq = (N + 3) / 4;
+  const size_t total = (size_t)batch * nq;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = i / nq;
+    const int64_t q = (int64_t)(i - v * nq);
+    const uint64_t g = batch_index * (uint64_t)batch + v;
+    const uint4 r = philox4x32_10(
+        make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)q, kStreamNoise), key);
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    for (int t = 0; t < 4; ++t)
+      if (4 * q + t < N) osc[(v * 3 + 2) * N + 4 * q + t] = fmaf(2.f, u01f(w[t]), -1.f);
+  }
+}
+
+__global__ void plain_vca_mix(const __grid_constant__ VoiceConst vc, int batch, const double* y,
+                              const float* amp, const float* osc, float* audio) {
+  const int64_t N = vc.n_samples;
+  const size_t total = (size_t)batch * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = i / N;
+    const int64_t n = (int64_t)(i - v * N);
+    const double* yv = y + v * kNumParams;
+    const double norm = fmax(1.0, yv[kMix] + yv[kMix + 1] + yv[kMix + 2]);
+    float acc = 0.f;
+    for (int c = 0; c < 3; ++c)
+      acc += (float)(yv[kMix + c] / norm) * amp[(v * 3 + c) * N + n] * osc[(v * 3 + c) * N + n];
+    audio[v * N + n] = acc;
+  }
+}
+
+int grid_for(size_t total) {
+  size_t b = (total + kPT - 1) / kPT;
+  return (int)(b < 152 * 32 ? b : 152 * 32);
+}
+
+}  // namespace
+
+size_t plain_workspace_bytes(const VoiceConst& vc, int batch) {
+  return plain_layout(vc, batch).total;
+}
+
+cudaError_t launch_render_plain(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
+                                int batch, const float* params_in, float* audio,
+                                float* params_out, void* workspace, ScratchHeader*, TileState*,
+                                cudaStream_t st) {
+  const PlainLayout L = plain_layout(vc, batch);
+  char* ws = static_cast<char*>(workspace);
+  double* y = reinterpret_cast<double*>(ws + L.y);
+  double* env = reinterpret_cast<double*>(ws + L.env);
+  double* lfo_inc = reinterpret_cast<double*>(ws + L.lfo_inc);
+  double* lfo_phase = reinterpret_cast<double*>(ws + L.lfo_phase);
+  double* dest = reinterpret_cast<double*>(ws + L.dest);
+  SegVco* seg = reinterpret_cast<SegVco*>(ws + L.seg);
+  double* seg_sum = reinterpret_cast<double*>(ws + L.seg_sum);
+  float* kappa = reinterpret_cast<float*>(ws + L.kappa);
+  float* amp = reinterpret_cast<float*>(ws + L.amp);
+  float* phase = reinterpret_cast<float*>(ws + L.phase);
+  float* osc = reinterpret_cast<float*>(ws + L.osc);
+  const int P = vc.K + 1, K = vc.K;
+  const size_t NS = (size_t)batch * vc.n_samples;
+  plain_params<<<batch, 128, 0, st>>>(vc, seed, batch_index, batch, params_in, params_out, y);
+  dim3 gp((P + kPT - 1) / kPT, batch), gk((K + kPT - 1) / kPT, batch);
+  plain_adsr<<<gp, kPT, 0, st>>>(vc, batch, y, env);
+  plain_lfo_rate<<<gp, kPT, 0, st>>>(vc, y, env, lfo_inc);
+  plain_phase_scan<<<batch, kPT, 0, st>>>(lfo_inc, lfo_phase, P, P, y, kLfo + 2, kLfo + 8 + 2);
+  plain_modmix<<<gp, kPT, 0, st>>>(vc, y, env, lfo_phase, dest);
+  plain_vco_intervals<<<gk, kPT, 0, st>>>(vc, y, dest, seg, seg_sum, kappa);
+  // scan of interval sums -> interval start phases (into the LFO-increment buffer)
+  double* seg_start = lfo_inc;  // needs B*2*K doubles; lfo_inc holds B*2*P >= that
+  plain_phase_scan<<<batch, kPT, 0, st>>>(seg_sum, seg_start, K, K, y, kSine + 2, kSqr + 2);
+  plain_seg_phase<<<(int)(((size_t)batch * 2 * K + kPT - 1) / kPT), kPT, 0, st>>>(vc, seg_start,
+                                                                                 seg, batch);
+  plain_upsample_amp<<<grid_for(NS), kPT, 0, st>>>(vc, batch, dest, amp);
+  plain_vco_phase<<<grid_for(NS / 2), kPT, 0, st>>>(vc, batch, seg, phase);
+  plain_sine<<<grid_for(NS), kPT, 0, st>>>(vc, batch, phase, osc);
+  plain_square_saw<<<grid_for(NS), kPT, 0, st>>>(vc, batch, y, phase, kappa, osc);
+  plain_noise<<<grid_for(NS / 4), kPT, 0, st>>>(vc, seed, batch_index, batch, osc);
+  plain_vca_mix<<<grid_for(NS), kPT, 0, st>>>(vc, batch, y, amp, osc, audio);
+  return cudaGetLastError();
+}
+
+}  // namespace synth

@@ -1,0 +1,250 @@
+// synth_api.cu -- the C ABI of libsynth.so (declared in include/synth.h):
+// handle lifetime, argument checks, launches, lazy device-error reporting.
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "synth.h"
+
+using namespace synth;
+
+struct synth_handle_s {
+  synth_config cfg;
+  synth_nebula nebula;
+  VoiceConst vc;
+  int device = 0;
+  int num_sms = 0;
+  int fused_grid = 0;
+  int n_windows = 0;
+  void* scratch = nullptr;  // ScratchHeader + TileState[max_batch * n_windows]
+  size_t scratch_bytes = 0;
+  bool plain_ready = false;
+};
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+// The library's default nebula n0 (Sec. 3.3 ranges, curves, symmetric flags).
+void fill_default_nebula(synth_nebula* nb) {
+  auto set = [&](int i, double lo, double hi, double c, int sym) {
+    nb->lo[i] = lo; nb->hi[i] = hi; nb->curve[i] = c; nb->symmetric[i] = sym;
+  };
+  set(kMidi, 0.0, 127.0, 1.0, 0);
+  set(kDuration, 0.0, 4.0, 1.0, 0);
+  for (int a = 0; a < 6; ++a) {
+    const int b = kAdsr + 5 * a;
+    set(b + 0, 0.0, 2.0, 2.0, 0);   // attack s
+    set(b + 1, 0.0, 2.0, 2.0, 0);   // decay s
+    set(b + 2, 0.0, 1.0, 1.0, 0);   // sustain
+    set(b + 3, 0.0, 5.0, 2.0, 0);   // release s
+    set(b + 4, 0.1, 6.0, 2.0, 0);   // alpha
+  }
+  for (int l = 0; l < 2; ++l) {
+    const int b = kLfo + 8 * l;
+    set(b + 0, 0.0, kLfoMaxHz, 2.0, 0);
+    set(b + 1, -20.0, 20.0, 3.0, 1);
+    set(b + 2, -kPi, kPi, 1.0, 1);
+    for (int s = 0; s < 5; ++s) set(b + 3 + s, 0.0, 1.0, 1.0, 0);
+  }
+  for (int i = 0; i < 20; ++i) set(kMod + i, 0.0, 1.0, 2.0, 0);
+  set(kSine + 0, -24.0, 24.0, 1.0, 1);
+  set(kSine + 1, -96.0, 96.0, 3.0, 1);
+  set(kSine + 2, -kPi, kPi, 1.0, 1);
+  set(kSqr + 0, -24.0, 24.0, 1.0, 1);
+  set(kSqr + 1, -96.0, 96.0, 3.0, 1);
+  set(kSqr + 2, -kPi, kPi, 1.0, 1);
+  set(kSqr + 3, 0.0, 1.0, 1.0, 0);
+  for (int i = 0; i < 3; ++i) set(kMix + i, 0.0, 1.0, 1.0, 0);
+}
+
+// Host copy of the Sec. 3.3 map (for synth_params_to_human).
+double host_range_map(double u, double lo, double hi, double c, int sym) {
+  auto cp = [&](double x) {
+    if (c == 1.0) return x;
+    if (c == 2.0) return x * x;
+    if (c == 3.0) return x * x * x;
+    return x <= 0.0 ? 0.0 : std::pow(x, c);
+  };
+  if (!sym) return lo + (hi - lo) * cp(u);
+  const double s = 2.0 * u - 1.0;
+  const double a = cp(std::fabs(s));
+  return lo + (hi - lo) * (1.0 + (s < 0.0 ? -a : a)) * 0.5;
+}
+
+synth_status check_cuda(cudaError_t e) { return e == cudaSuccess ? SYNTH_OK : SYNTH_ERR_CUDA; }
+
+bool valid_handle(synth_handle h) { return h != nullptr && h->scratch != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+void synth_default_nebula(synth_nebula* out) {
+  if (out) fill_default_nebula(out);
+}
+
+void synth_default_config(synth_config* out) {
+  if (!out) return;
+  out->sample_rate = 44100.0;
+  out->control_rate = 441.0;
+  out->seconds = 4.0;
+  out->max_batch = 128;
+  out->carry = SYNTH_CARRY_FP64;
+  out->nebula = nullptr;
+}
+
+synth_status synth_create(const synth_config* cfg, synth_handle* out) {
+  if (!cfg || !out) return SYNTH_ERR_ARG;
+  *out = nullptr;
+  const double sr = cfg->sample_rate, cr = cfg->control_rate;
+  if (!(sr > 0.0) || !(cr > 0.0) || !(cfg->seconds > 0.0) || cfg->max_batch < 1)
+    return SYNTH_ERR_ARG;
+  if (cfg->carry != SYNTH_CARRY_FP64 && cfg->carry != SYNTH_CARRY_FP32) return SYNTH_ERR_ARG;
+  const double r = sr / cr;
+  const long long R = std::llround(r);
+  const double n = cfg->seconds * sr;
+  const long long N = std::llround(n);
+  if (R < 4 || std::fabs(r - (double)R) > 1e-9 || (R & 3) != 0) return SYNTH_ERR_UNSUPPORTED;
+  if (std::fabs(n - (double)N) > 1e-6 || N < 1 || N > (1LL << 31)) return SYNTH_ERR_UNSUPPORTED;
+  synth_handle h = new (std::nothrow) synth_handle_s();
+  if (!h) return SYNTH_ERR_OOM;
+  h->cfg = *cfg;
+  if (cfg->nebula) h->nebula = *cfg->nebula;
+  else fill_default_nebula(&h->nebula);
+  h->cfg.nebula = &h->nebula;
+  for (int p = 0; p < kNumParams; ++p) {
+    if (!(h->nebula.curve[p] > 0.0)) { delete h; return SYNTH_ERR_ARG; }
+    h->vc.lo[p] = h->nebula.lo[p];
+    h->vc.hi[p] = h->nebula.hi[p];
+    h->vc.curve[p] = h->nebula.curve[p];
+    h->vc.sym[p] = h->nebula.symmetric[p] ? 1 : 0;
+  }
+  h->vc.sample_rate = sr;
+  h->vc.control_rate = cr;
+  h->vc.m_nyq = 69.0 + 12.0 * std::log2(0.5 * sr / 440.0);
+  h->vc.n_samples = N;
+  h->vc.R = (int32_t)R;
+  h->vc.K = (int32_t)((N + R - 1) / R);
+  h->vc.carry_fp32 = cfg->carry == SYNTH_CARRY_FP32 ? 1 : 0;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    delete h;
+    return SYNTH_ERR_CUDA;
+  }
+  h->n_windows = windows_per_voice(h->vc.K);
+  const int per_sm = fused_max_active_blocks_per_sm();
+  h->fused_grid = h->num_sms * (per_sm > 0 ? per_sm : 1);
+  h->scratch_bytes = sizeof(ScratchHeader) + sizeof(TileState) * (size_t)cfg->max_batch * h->n_windows;
+  if (cudaMalloc(&h->scratch, h->scratch_bytes) != cudaSuccess) {
+    h->scratch = nullptr;
+    delete h;
+    return SYNTH_ERR_OOM;
+  }
+  if (cudaMemset(h->scratch, 0, h->scratch_bytes) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(h->scratch);
+    delete h;
+    return SYNTH_ERR_CUDA;
+  }
+  *out = h;
+  return SYNTH_OK;
+}
+
+synth_status synth_destroy(synth_handle h) {
+  if (!h) return SYNTH_ERR_ARG;
+  if (h->scratch) cudaFree(h->scratch);
+  h->scratch = nullptr;
+  delete h;
+  return SYNTH_OK;
+}
+
+int32_t synth_num_params(synth_handle h) { return h ? kNumParams : -1; }
+int64_t synth_num_samples(synth_handle h) { return h ? h->vc.n_samples : -1; }
+
+synth_status synth_render(synth_handle h, uint64_t seed, uint64_t batch_index, int32_t batch,
+                          const float* params_in_dev, float* audio_dev, float* params_out_dev,
+                          void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (batch == 0) return SYNTH_OK;
+  if (!audio_dev) return SYNTH_ERR_ARG;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
+  return check_cuda(launch_render_fused(h->vc, seed, batch_index, batch, params_in_dev, audio_dev,
+                                        params_out_dev, hdr, tiles, h->fused_grid,
+                                        static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_render_plain_workspace_size(synth_handle h, int32_t batch, size_t* bytes) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!bytes || batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  *bytes = plain_workspace_bytes(h->vc, batch);
+  return SYNTH_OK;
+}
+
+synth_status synth_render_plain(synth_handle h, uint64_t seed, uint64_t batch_index, int32_t batch,
+                                const float* params_in_dev, float* audio_dev, float* params_out_dev,
+                                void* workspace_dev, size_t workspace_bytes, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (batch == 0) return SYNTH_OK;
+  if (!audio_dev || !workspace_dev) return SYNTH_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return SYNTH_ERR_ARG;
+  if (workspace_bytes < plain_workspace_bytes(h->vc, batch)) return SYNTH_ERR_ARG;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
+  return check_cuda(launch_render_plain(h->vc, seed, batch_index, batch, params_in_dev, audio_dev,
+                                        params_out_dev, workspace_dev, hdr, tiles,
+                                        static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_sync(synth_handle h, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SYNTH_ERR_CUDA;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  unsigned int err = 0;
+  if (cudaMemcpy(&err, &hdr->error, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SYNTH_ERR_CUDA;
+  if (err != 0) {
+    const unsigned int zero = 0;
+    if (cudaMemcpy(&hdr->error, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+      return SYNTH_ERR_CUDA;
+    return SYNTH_ERR_TIMEOUT;
+  }
+  return SYNTH_OK;
+}
+
+synth_status synth_params_to_human(synth_handle h, const float* u_host, double* y_host,
+                                   int32_t count) {
+  if (!h) return SYNTH_ERR_STATE;
+  if (count < 0 || (count > 0 && (!u_host || !y_host))) return SYNTH_ERR_ARG;
+  for (int32_t i = 0; i < count; ++i)
+    for (int p = 0; p < kNumParams; ++p) {
+      double u = (double)u_host[(size_t)i * kNumParams + p];
+      u = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+      y_host[(size_t)i * kNumParams + p] =
+          host_range_map(u, h->vc.lo[p], h->vc.hi[p], h->vc.curve[p], h->vc.sym[p]);
+    }
+  return SYNTH_OK;
+}
+
+int32_t synth_is_test(uint64_t g) { return ((g / 1024u) % 10u) == 9u ? 1 : 0; }
+
+const char* synth_status_string(synth_status s) {
+  switch (s) {
+    case SYNTH_OK: return "ok";
+    case SYNTH_ERR_ARG: return "invalid argument";
+    case SYNTH_ERR_CUDA: return "CUDA error";
+    case SYNTH_ERR_OOM: return "out of memory";
+    case SYNTH_ERR_TIMEOUT: return "device-side wait timed out";
+    case SYNTH_ERR_STATE: return "invalid handle state";
+    case SYNTH_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

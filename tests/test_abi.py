@@ -1,0 +1,90 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/*.h declares, rejects bad arguments before touching a
+device, and its host-side pieces agree with the oracle's definitions."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2104_12922_gb300 import build as b
+    b.build()
+    import paper_2104_12922_gb300 as p
+    return p
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(synth_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_boundary():
+    names = _declared_functions()
+    for required in ("synth_create", "synth_destroy", "synth_render", "synth_render_plain",
+                     "synth_sync", "synth_is_test", "synth_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(pkg):
+    lib = ctypes.CDLL(pkg.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(pkg):
+    for s in range(7):
+        assert pkg.synth_status_string(s)
+    assert pkg.synth_status_string(99) == "unknown status"
+
+
+def test_create_rejects_bad_config_without_device(pkg):
+    L = pkg.lib()
+    cfg = pkg.synth_default_config()
+    h = ctypes.c_void_p()
+    assert L.synth_create(None, ctypes.byref(h)) == pkg.SYNTH_ERR_ARG
+    for field, bad in [("seconds", 0.0), ("sample_rate", -1.0), ("max_batch", 0)]:
+        c = pkg.synth_default_config()
+        setattr(c, field, bad)
+        assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_ARG
+    c = pkg.synth_default_config()
+    c.control_rate = 441.0 * 100 / 98  # R = 98 is not a multiple of 4
+    assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_UNSUPPORTED
+    c = pkg.synth_default_config()
+    c.carry = 7
+    assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_ARG
+
+
+def test_calls_on_null_handle_return_status(pkg):
+    L = pkg.lib()
+    assert L.synth_render(None, 0, 0, 1, None, None, None, None) == pkg.SYNTH_ERR_STATE
+    assert L.synth_sync(None, None) == pkg.SYNTH_ERR_STATE
+    assert L.synth_destroy(None) == pkg.SYNTH_ERR_ARG
+
+
+def test_split_rule(pkg):
+    """Sec. 2.2: 9 blocks of 1024 train, then 1024 test, repeating."""
+    for g in [0, 1023, 9 * 1024 - 1, 10 * 1024 - 1, 19 * 1024 + 5]:
+        assert pkg.synth_is_test(g) == (g >= 9 * 1024 and g < 10 * 1024 or 19 * 1024 <= g < 20 * 1024)
+    flags = np.array([pkg.synth_is_test(g) for g in range(0, 20 * 1024, 256)])
+    assert flags.mean() == pytest.approx(0.1)
+
+
+def test_default_nebula_matches_oracle(pkg, oracle_mod):
+    """The library's n0 table and the oracle's are written independently."""
+    lib_nb = pkg.nebula_dict(pkg.synth_default_nebula())
+    ora_nb = oracle_mod.default_nebula()
+    for k in ("lo", "hi", "curve", "symmetric"):
+        assert np.array_equal(lib_nb[k], ora_nb[k]), k

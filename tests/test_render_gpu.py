@@ -1,0 +1,177 @@
+"""GPU parity of the fused and plain renders against the FP64 oracle.
+
+Bar (the benchmark spec): parameter draws bit-exact; audio max-abs error <= 2e-4 per
+sample over 4 s voices. Inputs are the synth1B1 workload itself: parameters
+drawn from (seed, global voice index), 44.1 kHz, 4 s.
+"""
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_12922_gb300 import build as b
+    b.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def synth4(torch_cuda):
+    import paper_2104_12922_gb300 as pkg
+    s = pkg.Synth(seconds=4.0, max_batch=128)
+    yield s
+    s.close()
+
+
+def _oracle_batch(oracle_mod, seconds, seed, batch_index, batch, u_in=None, voices=None, nebula=None):
+    cfg = oracle_mod.default_config(seconds=seconds, nebula=nebula)
+    return oracle_mod.render_batch(cfg, seed, batch_index, batch, u_in=u_in, voices=voices)
+
+
+def _check(audio, params, ref_audio, ref_params, rows=None, tol=TOL):
+    a = audio.cpu().numpy()
+    p = params.cpu().numpy()
+    if rows is not None:
+        a, p, ref_audio, ref_params = a[rows], p[rows], ref_audio[rows], ref_params[rows]
+    assert np.array_equal(p, ref_params), "parameter draw must be bit-exact"
+    assert np.all(np.isfinite(a))
+    err = float(np.max(np.abs(a - ref_audio)))
+    assert err <= tol, f"max-abs error {err:.3e}"
+    return err
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_batch16_4s_matches_oracle(synth4, oracle_mod, plain):
+    """Plain Voice, batch 16 x 4 s, seed 0, batch index 0."""
+    audio, params = synth4.render(0, 0, 16, plain=plain)
+    synth4.sync()
+    ref_a, ref_p = _oracle_batch(oracle_mod, 4.0, 0, 0, 16)
+    _check(audio, params, ref_a, ref_p)
+
+
+@pytest.mark.parametrize("batch_index", [1, 1023])
+def test_batch128_sampled_voices(synth4, oracle_mod, batch_index):
+    """Full-size batch 128 x 4 s, seed = batch index, as the throughput run
+    launches it; a sample of voices is checked against the oracle."""
+    audio, params = synth4.render(batch_index, batch_index, 128)
+    synth4.sync()
+    rows = si.sample_voices(batch_index, 128, 8)
+    ref_a, ref_p = _oracle_batch(oracle_mod, 4.0, batch_index, batch_index, 128, voices=rows)
+    _check(audio, params, ref_a, ref_p, rows=rows)
+    assert np.all(np.abs(audio.cpu().numpy()) <= 1.0)
+
+
+def test_fused_equals_plain(synth4):
+    a1, p1 = synth4.render(3, 2, 64)
+    a2, p2 = synth4.render(3, 2, 64, plain=True)
+    synth4.sync()
+    assert np.array_equal(p1.cpu().numpy(), p2.cpu().numpy())
+    assert float((a1 - a2).abs().max()) <= 1e-5
+
+
+def test_replay_is_deterministic(synth4, torch_cuda):
+    torch = torch_cuda
+    a1, _ = synth4.render(11, 5, 32)
+    a1 = a1.clone()
+    out = torch.empty_like(a1)
+    pout = torch.empty((32, 78), device=a1.device)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        synth4.render(11, 5, 32, out=out, params_out=pout, stream=s)  # warm
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(3):
+            synth4.render(11, 5, 32, out=out, params_out=pout, stream=s)
+    out.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    synth4.sync()
+    assert torch.equal(out, a1)
+
+
+def test_index_rule_across_batch_sizes(synth4):
+    """Voice g renders identically in a batch of 16 and a batch of 8."""
+    a16, p16 = synth4.render(9, 1, 16)   # g = 16..31
+    a8, p8 = synth4.render(9, 3, 8)      # g = 24..31
+    synth4.sync()
+    assert np.array_equal(p16[8:].cpu().numpy(), p8.cpu().numpy())
+    assert np.array_equal(a16[8:].cpu().numpy(), a8.cpu().numpy())
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_params_in_edge_corners(torch_cuda, oracle_mod, plain):
+    """Degenerate parameter corners (zero-length sections, all-zero weights,
+    extreme pitch) given through params_in."""
+    import paper_2104_12922_gb300 as pkg
+    torch = torch_cuda
+    u = si.edge_params(10)
+    syn = pkg.Synth(seconds=1.0, max_batch=10)
+    pin = torch.tensor(u, dtype=torch.float32, device="cuda")
+    audio, params = syn.render(0, 0, 10, params_in=pin, plain=plain)
+    syn.sync()
+    ref_a, ref_p = _oracle_batch(oracle_mod, 1.0, 0, 0, 10, u_in=u)
+    _check(audio, params, ref_a, ref_p)
+    syn.close()
+
+
+@pytest.mark.parametrize("plain", [False, True])
+@pytest.mark.parametrize("seconds", [44 / 44100, 0.1, 12800 / 44100, 0.29])
+def test_ragged_lengths(torch_cuda, oracle_mod, seconds, plain):
+    """Lengths shorter than one control interval, a ragged last interval,
+    N not a multiple of 4, and exactly one full tile of intervals."""
+    import paper_2104_12922_gb300 as pkg
+    syn = pkg.Synth(seconds=seconds, max_batch=5)
+    audio, params = syn.render(21, 7, 5, plain=plain)
+    syn.sync()
+    ref_a, ref_p = _oracle_batch(oracle_mod, seconds, 21, 7, 5)
+    _check(audio, params, ref_a, ref_p)
+    syn.close()
+
+
+def test_large_voice_index(synth4, oracle_mod):
+    """Global voice index above 2^32 (counter word 1 of Philox in use)."""
+    bi = (1 << 33) + 17
+    audio, params = synth4.render(5, bi, 4)
+    synth4.sync()
+    ref_a, ref_p = _oracle_batch(oracle_mod, 4.0, 5, bi, 4)
+    _check(audio, params, ref_a, ref_p)
+
+
+def test_argument_errors(synth4, torch_cuda):
+    import paper_2104_12922_gb300 as pkg
+    L = pkg.lib()
+    out = torch_cuda.empty((1, synth4.num_samples), device="cuda")
+    assert L.synth_render(synth4.handle, 0, 0, 129, None, out.data_ptr(), None, None) == pkg.SYNTH_ERR_ARG
+    assert L.synth_render(synth4.handle, 0, 0, -1, None, out.data_ptr(), None, None) == pkg.SYNTH_ERR_ARG
+    assert L.synth_render(synth4.handle, 0, 0, 1, None, None, None, None) == pkg.SYNTH_ERR_ARG
+    assert L.synth_render(synth4.handle, 0, 0, 0, None, None, None, None) == pkg.SYNTH_OK
+    assert L.synth_render_plain(synth4.handle, 0, 0, 1, None, out.data_ptr(), None, None, 0,
+                                None) == pkg.SYNTH_ERR_ARG
+    synth4.sync()
+
+
+def test_params_to_human_matches_oracle(synth4, oracle_mod):
+    import ctypes
+    import paper_2104_12922_gb300 as pkg
+    u = si.uniform_params(4, 3).astype(np.float32)
+    y = np.zeros((3, 78))
+    st = pkg.lib().synth_params_to_human(synth4.handle, u.ctypes.data_as(ctypes.c_void_p),
+                                         y.ctypes.data_as(ctypes.c_void_p), 3)
+    assert st == 0
+    nb = oracle_mod.default_nebula()
+    for i in range(3):
+        for p in range(78):
+            want = oracle_mod.range_map(float(u[i, p]), nb["lo"][p], nb["hi"][p], nb["curve"][p],
+                                        nb["symmetric"][p])
+            assert y[i, p] == pytest.approx(want, rel=1e-15, abs=1e-15)
