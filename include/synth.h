@@ -120,6 +120,29 @@ synth_status synth_render_plain(synth_handle h, uint64_t seed, uint64_t batch_in
                                 const float* params_in_dev, float* audio_dev, float* params_out_dev,
                                 void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* Adjoint of synth_render (reverse mode): for every voice,
+ * grad_params[v][p] = sum_n grad_audio[v][n] * d audio[v][n] / d u[v][p],
+ * the derivative with respect to the normalized parameters u. The paper
+ * lists differentiable modules as future work (Sec. 6); where the render
+ * branches (envelope section, clamp, Nyquist cap, square LFO) this is the
+ * derivative of the branch taken, and it is 0 at u = 0 for curve exponents
+ * whose derivative is unbounded there.
+ *  params_dev      [batch][78] float: the normalized parameters the forward
+ *                  used (e.g. its params_out), required.
+ *  seed, batch_index: as in the forward (they key the noise).
+ *  grad_audio_dev  [batch][N] float; grad_params_dev [batch][78] float out.
+ *  workspace_dev   synth_render_backward_workspace_size(h, batch) bytes,
+ *                  256-byte aligned, caller-owned.
+ * The forward control rate is recomputed from the parameters; its
+ * per-interval phase descriptions are the checkpoints from which every
+ * audio sample is rebuilt. Errors as synth_render_plain; SYNTH_ERR_UNSUPPORTED
+ * when sample_rate/control_rate > 128. */
+synth_status synth_render_backward_workspace_size(synth_handle h, int32_t batch, size_t* bytes);
+synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch_index,
+                                   int32_t batch, const float* params_dev,
+                                   const float* grad_audio_dev, float* grad_params_dev,
+                                   void* workspace_dev, size_t workspace_bytes, void* stream);
+
 /* Waits for the stream, then reports (and clears) a device-side error
  * recorded by any earlier call on this handle: SYNTH_ERR_TIMEOUT if a bounded
  * wait gave up, SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. */

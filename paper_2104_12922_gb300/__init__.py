@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
         L.synth_render.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp]
         L.synth_render_plain_workspace_size.argtypes = [vp, i32, P(ctypes.c_size_t)]
         L.synth_render_plain.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.synth_render_backward_workspace_size.argtypes = [vp, i32, P(ctypes.c_size_t)]
+        L.synth_render_backward.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.synth_sync.argtypes = [vp, vp]
         L.synth_params_to_human.argtypes = [vp, vp, vp, i32]
         L.synth_is_test.argtypes = [u64]
@@ -72,7 +74,8 @@ def lib() -> ctypes.CDLL:
         L.synth_status_string.argtypes = [ctypes.c_int]
         L.synth_status_string.restype = ctypes.c_char_p
         for name in ("synth_create", "synth_destroy", "synth_render", "synth_render_plain",
-                     "synth_render_plain_workspace_size", "synth_sync", "synth_params_to_human"):
+                     "synth_render_plain_workspace_size", "synth_sync", "synth_params_to_human",
+                     "synth_render_backward", "synth_render_backward_workspace_size"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -126,6 +129,19 @@ def synth_render_plain_workspace_size(h, batch) -> int:
     _check(lib().synth_render_plain_workspace_size(h, batch, ctypes.byref(n)),
            "synth_render_plain_workspace_size")
     return n.value
+
+
+def synth_render_backward_workspace_size(h, batch) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().synth_render_backward_workspace_size(h, batch, ctypes.byref(n)),
+           "synth_render_backward_workspace_size")
+    return n.value
+
+
+def synth_render_backward(h, seed, batch_index, batch, params_ptr, grad_audio_ptr, grad_params_ptr,
+                          workspace_ptr, workspace_bytes, stream) -> int:
+    return lib().synth_render_backward(h, seed, batch_index, batch, params_ptr, grad_audio_ptr,
+                                       grad_params_ptr, workspace_ptr, workspace_bytes, stream)
 
 
 def synth_sync(h, stream) -> int:
@@ -187,6 +203,7 @@ class Synth:
         self.max_batch = max_batch
         self.num_samples = int(lib().synth_num_samples(self.handle))
         self._workspace = None
+        self._bwd_workspace = None
 
     def close(self) -> None:
         if getattr(self, "handle", None):
@@ -235,3 +252,43 @@ class Synth:
 
     def sync(self, stream=None) -> None:
         _check(synth_sync(self.handle, _stream_ptr(stream)), "synth_sync")
+
+    def backward(self, seed: int, batch_index: int, params, grad_audio, grad_params=None,
+                 stream=None):
+        """grad_params = (d audio / d u)^T grad_audio through the C-ABI adjoint."""
+        import torch
+        batch = params.shape[0]
+        self._check_tensor(params, (batch, NUM_PARAMS), "params")
+        self._check_tensor(grad_audio, (batch, self.num_samples), "grad_audio")
+        if grad_params is None:
+            grad_params = torch.empty((batch, NUM_PARAMS), dtype=torch.float32, device=self.device)
+        self._check_tensor(grad_params, (batch, NUM_PARAMS), "grad_params")
+        need = synth_render_backward_workspace_size(self.handle, batch)
+        if self._bwd_workspace is None or self._bwd_workspace.numel() < need:
+            self._bwd_workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+        _check(synth_render_backward(self.handle, seed, batch_index, batch, _ptr(params),
+                                     _ptr(grad_audio), _ptr(grad_params),
+                                     _ptr(self._bwd_workspace), self._bwd_workspace.numel(),
+                                     _stream_ptr(stream)), "synth_render_backward")
+        return grad_params
+
+
+def render_autograd(synth: "Synth", seed: int, batch_index: int, params):
+    """Differentiable render: audio = Voice(params), with the hand-written
+    adjoint as the backward (a torch.autograd.Function)."""
+    import torch
+
+    class _Render(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u):
+            u = u.detach().contiguous()
+            audio, _ = synth.render(seed, batch_index, u.shape[0], params_in=u)
+            ctx.save_for_backward(u)
+            return audio
+
+        @staticmethod
+        def backward(ctx, grad_audio):
+            (u,) = ctx.saved_tensors
+            return synth.backward(seed, batch_index, u, grad_audio.contiguous())
+
+    return _Render.apply(params)

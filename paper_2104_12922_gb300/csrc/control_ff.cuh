@@ -1,0 +1,201 @@
+// control_ff.cuh -- the Voice's control-rate chain in float-float arithmetic.
+//
+// Everything that feeds a VCO's pitch -- the 6 ADSRs (Sec. 3.1; LFO rate and
+// amplitude envelopes, Sec. 3.2), the LFO shapes, the modulation mixer, the
+// pitch in midi and the phase advanced over each control interval -- is
+// computed in float-float (about 48 bits), because a pitch error that holds
+// over many intervals integrates into phase drift: at 4 s and 10 kHz a
+// relative frequency error of 1e-8 is already 4e-4 cycles. Running sums
+// across intervals (the scan carries) are FP64.
+#pragma once
+
+#include "ff.cuh"
+#include "render_common.cuh"
+#include "voice_device.cuh"
+
+namespace synth {
+
+// Per-voice constants of the control chain, derived once per tile from the
+// FP64 human-range parameters y.
+struct VoiceFF {
+  ff a[6], dc[6], s[6], r[6], alpha[6];
+  ff inv_a[6], inv_dc[6], inv_r[6];
+  ff level_d[6];      // gate-on level at note-off
+  ff dur;             // note-on duration d
+  ff lfo_freq[2], lfo_depth[2];
+  ff lfo_w[2][5];
+  ff lfo_inv_wsum[2]; // 1 / sum of shape weights (0 if the sum is < 1e-12)
+  ff mod_w[4][5];
+  ff inv_norm[5];     // 1 / max(1, column sum of modulation weights)
+  ff pitch_base[2];   // midi f0 + tune, per VCO
+  ff depth[2];        // pitch modulation depth (semitones), per VCO
+};
+
+// Sec. 3.1 ADSR at time t: the section is chosen first, then one x^alpha.
+// Section boundaries are continuous, so a comparison that rounds the other
+// way at an exact tie gives the same value.
+__device__ __forceinline__ ff adsr_ff(ff t, int i, const VoiceFF& V, const FFTables& T) {
+  ff base, scale, x;
+  if (ff_lt(t, V.dur)) {
+    if (ff_lt(t, V.a[i])) {
+      base = ff_make(0.f); scale = ff_make(1.f); x = ff_mul(t, V.inv_a[i]);
+    } else {
+      const ff ta = ff_sub(t, V.a[i]);
+      if (ff_lt(ta, V.dc[i])) {
+        base = ff_make(1.f); scale = ff_sub(V.s[i], ff_make(1.f)); x = ff_mul(ta, V.inv_dc[i]);
+      } else {
+        return V.s[i];
+      }
+    }
+  } else {
+    const ff tau = ff_sub(t, V.dur);
+    if (!ff_lt(tau, V.r[i])) return ff_make(0.f);
+    base = V.level_d[i]; scale = ff_neg(V.level_d[i]); x = ff_mul(tau, V.inv_r[i]);
+  }
+  return ff_add(base, ff_mul(scale, ff_pow01(x, V.alpha[i], T)));
+}
+
+// Gate-on level at note-off d (attack, decay or sustain value at t = d).
+__device__ __forceinline__ ff gate_level_ff(int i, const VoiceFF& V, const FFTables& T) {
+  const ff t = V.dur;
+  if (ff_lt(t, V.a[i])) return ff_pow01(ff_mul(t, V.inv_a[i]), V.alpha[i], T);
+  const ff ta = ff_sub(t, V.a[i]);
+  if (ff_lt(ta, V.dc[i]))
+    return ff_add(ff_make(1.f), ff_mul(ff_sub(V.s[i], ff_make(1.f)),
+                                       ff_pow01(ff_mul(ta, V.inv_dc[i]), V.alpha[i], T)));
+  return V.s[i];
+}
+
+// Fills VoiceFF from y (FP64). `part` selects which slice this thread fills
+// so that the work spreads over several threads; call with part = 0..15.
+__device__ inline void voice_ff_fill(VoiceFF& V, const double* y, int part) {
+  if (part < 6) {
+    const int i = part;
+    const double* q = y + kAdsr + 5 * i;
+    V.a[i] = ff_from_double(q[0]);
+    V.dc[i] = ff_from_double(q[1]);
+    V.s[i] = ff_from_double(q[2]);
+    V.r[i] = ff_from_double(q[3]);
+    V.alpha[i] = ff_from_double(q[4]);
+    V.inv_a[i] = ff_from_double(1.0 / q[0]);
+    V.inv_dc[i] = ff_from_double(1.0 / q[1]);
+    V.inv_r[i] = ff_from_double(1.0 / q[3]);
+  } else if (part < 8) {
+    const int l = part - 6;
+    const double* q = y + kLfo + 8 * l;
+    V.lfo_freq[l] = ff_from_double(q[0]);
+    V.lfo_depth[l] = ff_from_double(q[1]);
+    double ws = 0.0;
+    for (int s = 0; s < 5; ++s) {
+      V.lfo_w[l][s] = ff_from_double(q[3 + s]);
+      ws += q[3 + s];
+    }
+    V.lfo_inv_wsum[l] = ff_from_double(ws < 1e-12 ? 0.0 : 1.0 / ws);
+  } else if (part < 13) {
+    const int j = part - 8;
+    double ws = 0.0;
+    for (int i = 0; i < 4; ++i) {
+      V.mod_w[i][j] = ff_from_double(y[kMod + 5 * i + j]);
+      ws += y[kMod + 5 * i + j];
+    }
+    V.inv_norm[j] = ff_from_double(1.0 / fmax(1.0, ws));
+  } else if (part < 15) {
+    const int o = part - 13;
+    const int base = o == 0 ? kSine : kSqr;
+    V.pitch_base[o] = ff_add(ff_from_double(y[kMidi]), ff_from_double(y[base]));
+    V.depth[o] = ff_from_double(y[base + 1]);
+  } else {
+    V.dur = ff_from_double(y[kDuration]);
+  }
+}
+
+// LFO output at phase p in [0,1): shapes sin 2 pi p, triangle 1 - 4|p - 1/2|,
+// saw 2p - 1, reverse saw 1 - 2p, square sign(1/2 - p) (+1 at p < 1/2),
+// mixed by weight over the weight sum, times the amplitude envelope.
+__device__ __forceinline__ ff lfo_ff(ff p, int l, ff env_amp, const VoiceFF& V, const FFTables& T) {
+  if (V.lfo_inv_wsum[l].hi == 0.f) return ff_make(0.f);
+  const ff sn = ff_sin2pi(p, T);
+  const ff saw = ff_add_f(ff_ldexp(p, 1), -1.f);
+  const ff tri = ff_add_f(ff_ldexp(ff_neg(ff_abs(ff_add_f(p, -0.5f))), 2), 1.f);
+  const float sqr = ff_lt(p, ff_make(0.5f)) ? 1.f : -1.f;
+  ff acc = ff_mul(V.lfo_w[l][0], sn);
+  acc = ff_add(acc, ff_mul(V.lfo_w[l][1], tri));
+  acc = ff_add(acc, ff_mul(ff_sub(V.lfo_w[l][2], V.lfo_w[l][3]), saw));
+  acc = ff_add(acc, ff_mul_f(V.lfo_w[l][4], sqr));
+  return ff_mul(env_amp, ff_mul(acc, V.lfo_inv_wsum[l]));
+}
+
+// Per-VCO phase increment (cycles per sample) at pitch m (midi), uncapped:
+// 440 * 2^((m - 69)/12) / SR = 2^((m - 69)/12 + log2(440/SR)).
+__device__ __forceinline__ ff inc_at_ff(ff m, ff log2_440_over_sr, const FFTables& T) {
+  const ff twelfth = {0.0833333358168602f, -2.483526865641276e-09f};
+  return ff_exp2(ff_add(ff_mul(ff_add_f(m, -69.f), twelfth), log2_440_over_sr), T);
+}
+
+// Sum of k geometric increments starting at c with ratio e^x:
+// c expm1(k x) / expm1(x), or c k when x == 0.
+__device__ __forceinline__ ff geo_sum_ff(ff c, ff x, int k, const FFTables& T) {
+  if (k <= 0) return ff_make(0.f);
+  if (x.hi == 0.f) return ff_mul_f(c, (float)k);
+  return ff_mul(c, ff_div(ff_expm1(ff_mul_f(x, (float)k), T), ff_expm1(x, T)));
+}
+
+// The description (SegVco) of how a VCO's phase advances over one control
+// interval of Rk samples, from the pitch at its two control points; returns
+// the phase advanced (cycles). Sample j of the interval has pitch
+// m_a + (j / R)(m_b - m_a), capped at the Nyquist pitch.
+__device__ inline double vco_interval_ff(ff m_a, ff m_b, int R, int Rk, ff inv_R, ff ln2_12R,
+                                         ff m_nyq, ff log2_440_over_sr, const FFTables& T,
+                                         SegVco* out) {
+  const ff dm = ff_sub(m_b, m_a);
+  const ff x = ff_mul(dm, ln2_12R);
+  auto capped = [&](int j) {
+    return ff_gt(ff_add(m_a, ff_mul(dm, ff_mul_f(inv_R, (float)j))), m_nyq);
+  };
+  const bool c_first = capped(0), c_last = capped(Rk - 1);
+  int jc;
+  bool a_lin, b_lin;
+  ff cA, cB, LB, total;
+  const ff half = ff_make(0.5f);
+  if (!c_first && !c_last) {
+    jc = Rk; a_lin = (x.hi == 0.f); b_lin = true;
+    cA = inc_at_ff(m_a, log2_440_over_sr, T); cB = half; LB = ff_make(0.f);
+    total = geo_sum_ff(cA, x, Rk, T);
+  } else if (c_first && c_last) {
+    jc = 0; a_lin = true; b_lin = true;
+    cA = half; cB = half; LB = ff_make(0.f);
+    total = ff_make(0.5f * (float)Rk);
+  } else {
+    const float js = (m_nyq.hi - m_a.hi) * (float)R / dm.hi;
+    jc = (int)fminf(fmaxf(ceilf(js), 0.f), (float)(Rk - 1));
+    if (!c_first) {  // rising through the cap at jc
+      while (jc > 0 && capped(jc - 1)) --jc;
+      while (jc < Rk && !capped(jc)) ++jc;
+      a_lin = (x.hi == 0.f); b_lin = true;
+      cA = inc_at_ff(m_a, log2_440_over_sr, T); cB = half;
+      LB = geo_sum_ff(cA, x, jc, T);
+      total = ff_add_f(LB, 0.5f * (float)(Rk - jc));
+    } else {  // falling out of the cap at jc
+      while (jc > 0 && !capped(jc - 1)) --jc;
+      while (jc < Rk && capped(jc)) ++jc;
+      a_lin = true; b_lin = (x.hi == 0.f);
+      cA = half;
+      cB = inc_at_ff(ff_add(m_a, ff_mul(dm, ff_mul_f(inv_R, (float)jc))), log2_440_over_sr, T);
+      LB = ff_make(0.5f * (float)jc);
+      total = ff_add(LB, geo_sum_ff(cB, x, Rk - jc, T));
+    }
+  }
+  const float xf = x.hi;
+  const bool tiny = fabsf(xf) < 1e-30f;
+  out->cA = cA.hi + cA.lo;
+  out->cB = cB.hi + cB.lo;
+  out->LB = LB.hi + LB.lo;
+  out->x = xf;
+  out->E1 = tiny ? 0.f : expm1f(xf);
+  out->invE = tiny ? 0.f : 1.0f / expm1f(xf);
+  out->jc_flags = jc | ((a_lin || tiny) ? 1 << 16 : 0) | ((b_lin || tiny) ? 1 << 17 : 0) |
+                  (c_first ? 1 << 18 : 0) | (c_last ? 1 << 19 : 0);
+  return ff_to_double(total);
+}
+
+}  // namespace synth

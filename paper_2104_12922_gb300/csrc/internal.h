@@ -53,4 +53,10 @@ cudaError_t launch_render_plain(const VoiceConst& vc, uint64_t seed, uint64_t ba
                                 float* params_out, void* workspace, ScratchHeader* hdr,
                                 TileState* tiles, cudaStream_t stream);
 
+// Adjoint.
+size_t backward_workspace_bytes(const VoiceConst& vc, int batch);
+cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
+                                   int batch, const float* params, const float* grad_audio,
+                                   float* grad_params, void* workspace, cudaStream_t stream);
+
 }  // namespace synth

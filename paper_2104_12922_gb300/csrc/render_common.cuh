@@ -24,75 +24,26 @@ struct SegVco {
   float x;       // log of the per-sample increment ratio
   float E1;      // expm1(x)
   float invE;    // 1 / expm1(x)
-  int jc_flags;  // jc | (A linear) << 16 | (B linear) << 17
+  int jc_flags;  // jc | (A linear) << 16 | (B linear) << 17 | (A capped) << 18 | (B capped) << 19
 };
 
-constexpr double kLn2 = 0.69314718055994530942;
-
-// Phase advanced by k samples of a geometric piece starting at increment c:
-// sum_{i<k} c e^{i x} = c expm1(k x) / expm1(x) (c k when x == 0).
-__device__ __forceinline__ double geo_sum(double c, double x, int k) {
-  if (k <= 0) return 0.0;
-  if (x == 0.0) return c * (double)k;
-  return c * expm1((double)k * x) / expm1(x);
-}
-
-// Builds one interval's description from the pitch (midi) at its two control
-// points and returns the phase it advances over its Rk samples (FP64).
-// Sample j of the interval has pitch m_a + (j / R) (m_b - m_a), capped at the
-// Nyquist pitch; its increment is 440 * 2^((m - 69)/12) / SR.
-__device__ inline double vco_interval(double m_a, double m_b, int R, int Rk, const VoiceConst& vc,
-                                      SegVco* out) {
-  const double dm = m_b - m_a;
-  const double inv_sr = 1.0 / vc.sample_rate;
-  const double x = dm * (kLn2 / (12.0 * (double)R));
-  auto m_lin = [&](int j) { return m_a + ((double)j / (double)R) * dm; };
-  auto capped = [&](int j) { return m_lin(j) > vc.m_nyq; };
-  auto inc_at = [&](double m) { return 440.0 * exp2((m - 69.0) / 12.0) * inv_sr; };
-  const bool c_first = capped(0), c_last = capped(Rk - 1);
-  int jc;
-  bool a_lin, b_lin;
-  double cA, cB, LB, total;
-  if (!c_first && !c_last) {  // no cap inside: one geometric piece
-    jc = Rk; a_lin = (x == 0.0); b_lin = true;
-    cA = inc_at(m_a); cB = 0.5; LB = 0.0;
-    total = geo_sum(cA, x, Rk);
-  } else if (c_first && c_last) {  // capped throughout: half a cycle per sample
-    jc = 0; a_lin = true; b_lin = true;
-    cA = 0.5; cB = 0.5; LB = 0.0;
-    total = 0.5 * (double)Rk;
-  } else if (!c_first) {  // rising through the cap at jc
-    double js = (vc.m_nyq - m_a) * (double)R / dm;
-    jc = (int)fmin(fmax(ceil(js), 0.0), (double)(Rk - 1));
-    while (jc > 0 && capped(jc - 1)) --jc;
-    while (jc < Rk && !capped(jc)) ++jc;
-    a_lin = (x == 0.0); b_lin = true;
-    cA = inc_at(m_a); cB = 0.5;
-    LB = geo_sum(cA, x, jc);
-    total = LB + 0.5 * (double)(Rk - jc);
-  } else {  // falling out of the cap at jc
-    double js = (vc.m_nyq - m_a) * (double)R / dm;
-    jc = (int)fmin(fmax(ceil(js), 0.0), (double)(Rk - 1));
-    while (jc > 0 && !capped(jc - 1)) --jc;
-    while (jc < Rk && capped(jc)) ++jc;
-    a_lin = true; b_lin = (x == 0.0);
-    cA = 0.5; cB = inc_at(m_lin(jc));
-    LB = 0.5 * (double)jc;
-    total = LB + geo_sum(cB, x, Rk - jc);
+// Per-sample phase increments (cycles/sample) of samples j0..j0+3 and whether
+// each sample's pitch is capped at Nyquist (used by the adjoint).
+__device__ __forceinline__ void vco_inc_quad(const SegVco& s, int j0, float inc[4], bool capped[4]) {
+  const int jc = s.jc_flags & 0xffff;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = j0 + i;
+    const bool in_b = j >= jc;
+    const float c = in_b ? s.cB : s.cA;
+    const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
+    capped[i] = (s.jc_flags >> (in_b ? 19 : 18)) & 1;
+    const int d = j - (in_b ? jc : 0);
+    inc[i] = lin ? c : c * (1.f + expm1f((float)d * s.x));
   }
-  // float description; geometric pieces with |x| below 1e-30 are linear to
-  // well within float rounding (relative error ~ j x / 2)
-  const float xf = (float)x;
-  const bool tiny = fabsf(xf) < 1e-30f;
-  out->cA = (float)cA;
-  out->cB = (float)cB;
-  out->LB = (float)LB;
-  out->x = xf;
-  out->E1 = tiny ? 0.f : expm1f(xf);
-  out->invE = tiny ? 0.f : 1.0f / expm1f(xf);
-  out->jc_flags = jc | ((a_lin || tiny) ? 1 << 16 : 0) | ((b_lin || tiny) ? 1 << 17 : 0);
-  return total;
 }
+
+constexpr double kLn2 = 0.69314718055994530942;
 
 // Phases (cycles, wrapped to [-1/2, 1/2)) of samples j0..j0+3 of an interval.
 __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {

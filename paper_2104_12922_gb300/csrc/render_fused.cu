@@ -8,9 +8,11 @@
 //  2. control rate (Sec. 3.1): 6 ADSRs at the window's control points, the
 //     LFO rates, an exclusive block scan of the LFO phase increments and a
 //     decoupled look-back for the LFO phase carry from earlier windows;
-//     LFO shapes, modulation mixer, VCO pitch, amplitudes -- all in FP64;
+//     LFO shapes, modulation mixer, VCO pitch, amplitudes -- in float-float
+//     (control_ff.cuh), with FP64 running sums;
 //  3. per control interval and VCO, the phase advanced over the interval
-//     (closed-form geometric sum of the upsampled pitch's increments, FP64),
+//     (closed-form geometric sum of the upsampled pitch's increments,
+//     float-float),
 //     an exclusive block scan of those sums and a second look-back for the
 //     VCO phase carry (FP64; FP32 in the precision-study mode);
 //  4. audio rate (Sec. 3.2): each thread renders quads of 4 consecutive
@@ -20,6 +22,7 @@
 // from the 80-byte look-back record per tile.
 
 #include "internal.h"
+#include "control_ff.cuh"
 #include "render_common.cuh"
 
 namespace synth {
@@ -28,12 +31,14 @@ namespace {
 
 constexpr int NT = kFusedThreads;
 constexpr int TS = kFusedTileSeg;
+static_assert(NT == 2 * TS, "one thread per (control interval, VCO) pair");
 
 struct __align__(16) FusedSmem {
   double y[kNumParams];
-  double level_at_d[6];
-  double env[6][TS + 1];
-  double m[2][TS + 1];       // VCO pitch (midi) at the window's control points
+  VoiceFF V;
+  FFTables T;
+  ff env[6][TS + 1];
+  ff m[2][TS + 1];           // VCO pitch (midi) at the window's control points
   float amp[3][TS + 1];      // sine, square-saw, noise amplitudes
   SegVco seg[2][TS];
   float kappa[TS];
@@ -41,10 +46,10 @@ struct __align__(16) FusedSmem {
   double warp_tot[2 * (NT / 32)];
   float warp_tot_f[2 * (NT / 32)];
   double prefix[2];
-  float prefix_f[2];
   float u[80];
   float gain[3];
   float shape, inv_1p_shape;
+  ff inv_cr, inv_R, ln2_12R, m_nyq, log2_440_over_sr;
   int tile;
   unsigned int epoch;
 };
@@ -69,7 +74,15 @@ __global__ void __launch_bounds__(NT) render_fused_kernel(
   const float invR = 1.0f / (float)R;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   const double two_pi = 6.28318530717958647692;
-  if (tid == 0) sm.epoch = *(volatile unsigned int*)&hdr->epoch;
+  if (tid == 0) {
+    sm.epoch = *(volatile unsigned int*)&hdr->epoch;
+    sm.inv_cr = ff_from_double(1.0 / vc.control_rate);
+    sm.inv_R = ff_from_double(1.0 / (double)R);
+    sm.ln2_12R = ff_from_double(kLn2 / (12.0 * (double)R));
+    sm.m_nyq = ff_from_double(vc.m_nyq);
+    sm.log2_440_over_sr = ff_from_double(log2(440.0 / vc.sample_rate));
+  }
+  if (tid < 33) ff_tables_fill_entry(sm.T, tid);
 
   for (;;) {
     if (tid == 0) sm.tile = (int)atomicAdd(&hdr->work, 1u);
@@ -104,9 +117,8 @@ __global__ void __launch_bounds__(NT) render_fused_kernel(
     }
     __syncthreads();
     const double* y = sm.y;
-    if (tid < 6) {
-      const double* q = y + kAdsr + 5 * tid;
-      sm.level_at_d[tid] = adsr_gate_on(y[kDuration], q[0], q[1], q[2], q[4]);
+    if (tid < 16) {
+      voice_ff_fill(sm.V, y, tid);
     } else if (tid == 32) {
       const double l0 = y[kMix], l1 = y[kMix + 1], l2 = y[kMix + 2];
       const double norm = fmax(1.0, l0 + l1 + l2);
@@ -117,21 +129,27 @@ __global__ void __launch_bounds__(NT) render_fused_kernel(
       sm.inv_1p_shape = (float)(1.0 / (1.0 + y[kSqr + 3]));
     }
     __syncthreads();
+    const VoiceFF& V = sm.V;
+    if (tid < 6) sm.V.level_d[tid] = gate_level_ff(tid, V, sm.T);
+    __syncthreads();
 
     // ---- 2. envelopes at control points k0 .. k0 + nseg -------------------
-    for (int i = tid; i <= nseg; i += NT) {
-      const double tk = (double)(k0 + i) / vc.control_rate;
-#pragma unroll
-      for (int a = 0; a < 6; ++a)
-        sm.env[a][i] = adsr_eval(tk, y + kAdsr + 5 * a, y[kDuration], sm.level_at_d[a]);
+    // (one thread per (point, ADSR) pair keeps the threads busy)
+    for (int i = tid; i < 6 * (nseg + 1); i += NT) {
+      const int pt = i / 6, a = i - 6 * pt;
+      const ff tk = ff_mul_f(sm.inv_cr, (float)(k0 + pt));
+      sm.env[a][pt] = adsr_ff(tk, a, V, sm.T);
     }
     __syncthreads();
 
-    // LFO phase increments rate_k / CR at points k0 .. k0 + nseg - 1, scanned.
+    // LFO phase increments rate_k / CR at points k0 .. k0 + nseg - 1, scanned
+    // in FP64.
     double r0 = 0.0, r1 = 0.0;
     if (tid < nseg) {
-      r0 = fmin(fmax(y[kLfo + 0] + y[kLfo + 1] * sm.env[2][tid], 0.0), kLfoMaxHz) / vc.control_rate;
-      r1 = fmin(fmax(y[kLfo + 8] + y[kLfo + 9] * sm.env[4][tid], 0.0), kLfoMaxHz) / vc.control_rate;
+      const ff lim = ff_make((float)kLfoMaxHz);
+      const ff z = ff_make(0.f);
+      r0 = ff_to_double(ff_mul(ff_min(ff_max(ff_add(V.lfo_freq[0], ff_mul(V.lfo_depth[0], sm.env[2][tid])), z), lim), sm.inv_cr));
+      r1 = ff_to_double(ff_mul(ff_min(ff_max(ff_add(V.lfo_freq[1], ff_mul(V.lfo_depth[1], sm.env[4][tid])), z), lim), sm.inv_cr));
     }
     double tot0, tot1;
     block_exclusive_scan2<double, NT>(r0, r1, sm.warp_tot, tot0, tot1);
@@ -145,47 +163,63 @@ __global__ void __launch_bounds__(NT) render_fused_kernel(
 
     // LFOs, modulation mixer, pitch and amplitudes at each control point.
     if (tid <= nseg) {
-      double lfo[2];
+      ff lfo[2];
 #pragma unroll
       for (int l = 0; l < 2; ++l) {
-        const double* q = y + kLfo + 8 * l;
-        const double theta = wrap01(wrap01(q[2] / two_pi) + sm.prefix[l] + (l == 0 ? r0 : r1));
-        const double wsum = q[3] + q[4] + q[5] + q[6] + q[7];
-        lfo[l] = sm.env[3 + 2 * l][tid] * lfo_mix(theta, q + 3, wsum);
+        const double theta = wrap01(wrap01(y[kLfo + 8 * l + 2] / two_pi) + sm.prefix[l] + (l == 0 ? r0 : r1));
+        lfo[l] = lfo_ff(ff_from_double(theta), l, sm.env[3 + 2 * l][tid], V, sm.T);
       }
-      const double src[4] = {sm.env[0][tid], sm.env[1][tid], lfo[0], lfo[1]};
-      double dest[5];
+      const ff src[4] = {sm.env[0][tid], sm.env[1][tid], lfo[0], lfo[1]};
+      ff dest[5];
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        double acc = 0.0, ws = 0.0;
+        ff acc = ff_mul(V.mod_w[0][j], src[0]);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          acc += y[kMod + 5 * i + j] * src[i];
-          ws += y[kMod + 5 * i + j];
-        }
-        dest[j] = acc / fmax(1.0, ws);
+        for (int i = 1; i < 4; ++i) acc = ff_add(acc, ff_mul(V.mod_w[i][j], src[i]));
+        dest[j] = ff_mul(acc, V.inv_norm[j]);
       }
-      sm.m[0][tid] = y[kMidi] + y[kSine] + y[kSine + 1] * dest[0];
-      sm.m[1][tid] = y[kMidi] + y[kSqr] + y[kSqr + 1] * dest[2];
-      sm.amp[0][tid] = (float)dest[1];
-      sm.amp[1][tid] = (float)dest[3];
-      sm.amp[2][tid] = (float)dest[4];
+      sm.m[0][tid] = ff_add(V.pitch_base[0], ff_mul(V.depth[0], dest[0]));
+      sm.m[1][tid] = ff_add(V.pitch_base[1], ff_mul(V.depth[1], dest[2]));
+      sm.amp[0][tid] = dest[1].hi + dest[1].lo;
+      sm.amp[1][tid] = dest[3].hi + dest[3].lo;
+      sm.amp[2][tid] = dest[4].hi + dest[4].lo;
     }
     __syncthreads();
 
     // ---- 3. VCO phase over each control interval, scanned -----------------
+    // (threads 0..nseg-1 take the sine VCO, threads 128.. the square-saw)
+    double s_own = 0.0;
+    {
+      const int o = tid >= TS ? 1 : 0;
+      const int si = tid - o * TS;
+      if (si < nseg) {
+        const int k = k0 + si;
+        const int64_t rem = N - (int64_t)k * R;
+        const int Rk = rem < R ? (int)rem : R;
+        s_own = vco_interval_ff(sm.m[o][si], sm.m[o][si + 1], R, Rk, sm.inv_R, sm.ln2_12R, sm.m_nyq,
+                                sm.log2_440_over_sr, sm.T, &sm.seg[o][si]);
+        if (o == 1) {
+          const ff mk = ff_min(sm.m[1][si], sm.m_nyq);
+          const float fk = (float)vc.sample_rate * ff_to_float(inc_at_ff(mk, sm.log2_440_over_sr, sm.T));
+          const float kap = fminf((float)kBrightnessMax, 1.f + (float)vc.sample_rate / (8.f * fk));
+          sm.kappa[si] = kap;
+          sm.inv_tanh_kappa[si] = 1.f / tanhf(kap);
+        }
+      }
+    }
+    __syncthreads();
+    // gather the two VCOs' sums onto the scan threads 0..nseg-1
     CarryT s0 = CarryT(0), s1 = CarryT(0);
-    if (tid < nseg) {
-      const int k = k0 + tid;
-      const int64_t rem = N - (int64_t)k * R;
-      const int Rk = rem < R ? (int)rem : R;
-      s0 = (CarryT)vco_interval(sm.m[0][tid], sm.m[0][tid + 1], R, Rk, vc, &sm.seg[0][tid]);
-      s1 = (CarryT)vco_interval(sm.m[1][tid], sm.m[1][tid + 1], R, Rk, vc, &sm.seg[1][tid]);
-      const double mk = fmin(sm.m[1][tid], vc.m_nyq);
-      const double fk = 440.0 * exp2((mk - 69.0) / 12.0);
-      const double kap = fmin(kBrightnessMax, 1.0 + vc.sample_rate / (8.0 * fk));
-      sm.kappa[tid] = (float)kap;
-      sm.inv_tanh_kappa[tid] = (float)(1.0 / tanh(kap));
+    {
+      __shared__ double sums[2][TS];
+      const int o = tid >= TS ? 1 : 0;
+      const int si = tid - o * TS;
+      if (si < nseg) sums[o][si] = s_own;
+      __syncthreads();
+      if (tid < nseg) {
+        s0 = (CarryT)sums[0][tid];
+        s1 = (CarryT)sums[1][tid];
+      }
     }
     CarryT t0, t1;
     block_exclusive_scan2<CarryT, NT>(s0, s1, warp_buf<CarryT>(sm), t0, t1);

@@ -7,12 +7,15 @@
 //
 // Workspace (caller-owned, 256-byte aligned sections), B voices, P = K + 1
 // control points, N samples:
-//   y[B][78] f64 | env[B][6][P] f64 | lfo_inc[B][2][P] f64 | lfo_phase[B][2][P] f64
-//   dest[B][5][P] f64 | seg[B][2][K] SegVco | seg_sum[B][2][K] f64 | kappa[B][2][K] f32
-//   amp[B][3][N] f32 | phase[B][2][N] f32 | osc[B][3][N] f32
+//   y[B][78] f64 | vff[B] VoiceFF | env[B][6][P] ff | lfo_inc[B][2][P] f64
+//   lfo_phase[B][2][P] f64 | dest[B][5][P] ff | seg[B][2][K] SegVco
+//   seg_sum[B][2][K] f64 | kappa[B][2][K] f32 | amp[B][3][N] f32
+//   phase[B][2][N] f32 | osc[B][3][N] f32
+// Control-rate values are float-float and running sums FP64, as in the fused
+// kernel (control_ff.cuh).
 
 #include "internal.h"
-#include "render_common.cuh"
+#include "control_pipeline.cuh"
 
 namespace synth {
 
@@ -20,25 +23,17 @@ namespace {
 
 constexpr int kPT = 256;
 
-struct PlainLayout {
-  size_t y, env, lfo_inc, lfo_phase, dest, seg, seg_sum, kappa, amp, phase, osc, total;
-};
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-PlainLayout plain_layout(const VoiceConst& vc, int B) {
-  const size_t P = (size_t)vc.K + 1, K = (size_t)vc.K, N = (size_t)vc.n_samples;
-  PlainLayout L;
-  size_t o = 0;
+struct AudioLayout {
+  size_t amp, phase, osc, total;
+};
+
+AudioLayout audio_layout(const VoiceConst& vc, int B, size_t base) {
+  const size_t N = (size_t)vc.n_samples;
+  AudioLayout L;
+  size_t o = base;
   auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
-  L.y = take(sizeof(double) * B * kNumParams);
-  L.env = take(sizeof(double) * B * 6 * P);
-  L.lfo_inc = take(sizeof(double) * B * 2 * P);
-  L.lfo_phase = take(sizeof(double) * B * 2 * P);
-  L.dest = take(sizeof(double) * B * 5 * P);
-  L.seg = take(sizeof(SegVco) * B * 2 * K);
-  L.seg_sum = take(sizeof(double) * B * 2 * K);
-  L.kappa = take(sizeof(float) * B * 2 * K);
   L.amp = take(sizeof(float) * B * 3 * N);
   L.phase = take(sizeof(float) * B * 2 * N);
   L.osc = take(sizeof(float) * B * 3 * N);
@@ -67,34 +62,47 @@ __global__ void plain_params(const __grid_constant__ VoiceConst vc, uint64_t see
   y[(size_t)v * kNumParams + p] = range_map((double)u, vc.lo[p], vc.hi[p], vc.curve[p], vc.sym[p]);
 }
 
-// ADSR modules (6 per voice) at the control points.
-__global__ void plain_adsr(const __grid_constant__ VoiceConst vc, int batch, const double* y,
-                           double* env) {
-  const int P = vc.K + 1;
-  const int v = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= P) return;
-  const double* yv = y + (size_t)v * kNumParams;
-  const double t = (double)k / vc.control_rate;
-  for (int a = 0; a < 6; ++a) {
-    const double* q = yv + kAdsr + 5 * a;
-    const double lvl = adsr_gate_on(yv[kDuration], q[0], q[1], q[2], q[4]);
-    env[((size_t)v * 6 + a) * P + k] = adsr_eval(t, q, yv[kDuration], lvl);
-  }
+// Per-voice constants of the control modules (float-float).
+__global__ void plain_voice_consts(const double* y, VoiceFF* vff) {
+  __shared__ FFTables T;
+  const int v = blockIdx.x;
+  if (threadIdx.x < 33) ff_tables_fill_entry(T, threadIdx.x);
+  __syncthreads();
+  VoiceFF& V = vff[v];
+  if (threadIdx.x < 16) voice_ff_fill(V, y + (size_t)v * kNumParams, threadIdx.x);
+  __syncthreads();
+  __threadfence_block();
+  if (threadIdx.x < 6) V.level_d[threadIdx.x] = gate_level_ff(threadIdx.x, V, T);
 }
 
-// LFO rate: phase increment per control interval.
-__global__ void plain_lfo_rate(const __grid_constant__ VoiceConst vc, const double* y,
-                               const double* env, double* lfo_inc) {
+// ADSR modules (6 per voice) at the control points.
+__global__ void plain_adsr(const __grid_constant__ VoiceConst vc, const VoiceFF* vff, ff* env) {
+  __shared__ FFTables T;
+  if (threadIdx.x < 33) ff_tables_fill_entry(T, threadIdx.x);
+  __syncthreads();
+  const int P = vc.K + 1;
+  const int v = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * P) return;
+  const int a = i / P, k = i - a * P;
+  const ff tk = ff_mul_f(ff_from_double(1.0 / vc.control_rate), (float)k);
+  env[((size_t)v * 6 + a) * P + k] = adsr_ff(tk, a, vff[v], T);
+}
+
+// LFO rate: phase increment per control interval (rate / CR, FP64 for the scan).
+__global__ void plain_lfo_rate(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
+                               const ff* env, double* lfo_inc) {
   const int P = vc.K + 1;
   const int v = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P) return;
-  const double* yv = y + (size_t)v * kNumParams;
+  const VoiceFF& V = vff[v];
+  const ff inv_cr = ff_from_double(1.0 / vc.control_rate);
   for (int l = 0; l < 2; ++l) {
-    const double e = env[((size_t)v * 6 + 2 + 2 * l) * P + k];
-    const double rate = fmin(fmax(yv[kLfo + 8 * l] + yv[kLfo + 8 * l + 1] * e, 0.0), kLfoMaxHz);
-    lfo_inc[((size_t)v * 2 + l) * P + k] = rate / vc.control_rate;
+    const ff e = env[((size_t)v * 6 + 2 + 2 * l) * P + k];
+    const ff rate = ff_min(ff_max(ff_add(V.lfo_freq[l], ff_mul(V.lfo_depth[l], e)), ff_make(0.f)),
+                           ff_make((float)kLfoMaxHz));
+    lfo_inc[((size_t)v * 2 + l) * P + k] = ff_to_double(ff_mul(rate, inv_cr));
   }
 }
 
@@ -127,55 +135,58 @@ __global__ void plain_phase_scan(const double* inc, double* phase, int len, int 
 }
 
 // LFO outputs and modulation mixer at the control points.
-__global__ void plain_modmix(const __grid_constant__ VoiceConst vc, const double* y,
-                             const double* env, const double* lfo_phase, double* dest) {
+__global__ void plain_modmix(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
+                             const ff* env, const double* lfo_phase, ff* dest) {
+  __shared__ FFTables T;
+  if (threadIdx.x < 33) ff_tables_fill_entry(T, threadIdx.x);
+  __syncthreads();
   const int P = vc.K + 1;
   const int v = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P) return;
-  const double* yv = y + (size_t)v * kNumParams;
-  double lfo[2];
+  const VoiceFF& V = vff[v];
+  ff lfo[2];
   for (int l = 0; l < 2; ++l) {
-    const double* q = yv + kLfo + 8 * l;
-    const double wsum = q[3] + q[4] + q[5] + q[6] + q[7];
     const double th = lfo_phase[((size_t)v * 2 + l) * P + k];
-    lfo[l] = env[((size_t)v * 6 + 3 + 2 * l) * P + k] * lfo_mix(th, q + 3, wsum);
+    lfo[l] = lfo_ff(ff_from_double(th), l, env[((size_t)v * 6 + 3 + 2 * l) * P + k], V, T);
   }
-  const double src[4] = {env[((size_t)v * 6 + 0) * P + k], env[((size_t)v * 6 + 1) * P + k],
-                         lfo[0], lfo[1]};
+  const ff src[4] = {env[((size_t)v * 6 + 0) * P + k], env[((size_t)v * 6 + 1) * P + k], lfo[0],
+                     lfo[1]};
   for (int j = 0; j < 5; ++j) {
-    double acc = 0.0, ws = 0.0;
-    for (int i = 0; i < 4; ++i) {
-      acc += yv[kMod + 5 * i + j] * src[i];
-      ws += yv[kMod + 5 * i + j];
-    }
-    dest[((size_t)v * 5 + j) * P + k] = acc / fmax(1.0, ws);
+    ff acc = ff_mul(V.mod_w[0][j], src[0]);
+    for (int i = 1; i < 4; ++i) acc = ff_add(acc, ff_mul(V.mod_w[i][j], src[i]));
+    dest[((size_t)v * 5 + j) * P + k] = ff_mul(acc, V.inv_norm[j]);
   }
 }
 
 // VCO interval descriptions and the phase each interval advances.
-__global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const double* y,
-                                    const double* dest, SegVco* seg, double* seg_sum,
-                                    float* kappa) {
+__global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
+                                    const ff* dest, SegVco* seg, double* seg_sum, float* kappa) {
+  __shared__ FFTables T;
+  if (threadIdx.x < 33) ff_tables_fill_entry(T, threadIdx.x);
+  __syncthreads();
   const int P = vc.K + 1, K = vc.K;
   const int v = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
-  const double* yv = y + (size_t)v * kNumParams;
+  const VoiceFF& V = vff[v];
   const int64_t rem = vc.n_samples - (int64_t)k * vc.R;
   const int Rk = rem < vc.R ? (int)rem : vc.R;
+  const ff inv_R = ff_from_double(1.0 / (double)vc.R);
+  const ff ln2_12R = ff_from_double(kLn2 / (12.0 * (double)vc.R));
+  const ff m_nyq = ff_from_double(vc.m_nyq);
+  const ff l440 = ff_from_double(log2(440.0 / vc.sample_rate));
   for (int o = 0; o < 2; ++o) {
-    const int base = o == 0 ? kSine : kSqr;
-    const double* pd = dest + ((size_t)v * 5 + (o == 0 ? 0 : 2)) * P;
-    const double ma = yv[kMidi] + yv[base] + yv[base + 1] * pd[k];
-    const double mb = yv[kMidi] + yv[base] + yv[base + 1] * pd[k + 1];
-    seg_sum[((size_t)v * 2 + o) * K + k] =
-        vco_interval(ma, mb, vc.R, Rk, vc, &seg[((size_t)v * 2 + o) * K + k]);
+    const ff* pd = dest + ((size_t)v * 5 + (o == 0 ? 0 : 2)) * P;
+    const ff ma = ff_add(V.pitch_base[o], ff_mul(V.depth[o], pd[k]));
+    const ff mb = ff_add(V.pitch_base[o], ff_mul(V.depth[o], pd[k + 1]));
+    seg_sum[((size_t)v * 2 + o) * K + k] = vco_interval_ff(
+        ma, mb, vc.R, Rk, inv_R, ln2_12R, m_nyq, l440, T, &seg[((size_t)v * 2 + o) * K + k]);
     if (o == 1) {
-      const double fk = 440.0 * exp2((fmin(ma, vc.m_nyq) - 69.0) / 12.0);
-      const double kap = fmin(kBrightnessMax, 1.0 + vc.sample_rate / (8.0 * fk));
-      kappa[((size_t)v * 2 + 0) * K + k] = (float)kap;
-      kappa[((size_t)v * 2 + 1) * K + k] = (float)(1.0 / tanh(kap));
+      const float fk = (float)vc.sample_rate * ff_to_float(inc_at_ff(ff_min(ma, m_nyq), l440, T));
+      const float kap = fminf((float)kBrightnessMax, 1.f + (float)vc.sample_rate / (8.f * fk));
+      kappa[((size_t)v * 2 + 0) * K + k] = kap;
+      kappa[((size_t)v * 2 + 1) * K + k] = 1.f / tanhf(kap);
     }
   }
 }
@@ -190,7 +201,7 @@ __global__ void plain_seg_phase(const __grid_constant__ VoiceConst vc, const dou
 
 // Upsampled amplitudes (VCA control inputs) at audio rate.
 __global__ void plain_upsample_amp(const __grid_constant__ VoiceConst vc, int batch,
-                                   const double* dest, float* amp) {
+                                   const ff* dest, float* amp) {
   const int64_t N = vc.n_samples;
   const int P = vc.K + 1;
   const size_t total = (size_t)batch * N;
@@ -203,8 +214,8 @@ __global__ void plain_upsample_amp(const __grid_constant__ VoiceConst vc, int ba
     const float fj = (float)(n - (int64_t)k * vc.R) * invR;
     const int dj[3] = {1, 3, 4};
     for (int c = 0; c < 3; ++c) {
-      const double* d = dest + ((size_t)v * 5 + dj[c]) * P;
-      const float a0 = (float)d[k], a1 = (float)d[k + 1];
+      const ff* d = dest + ((size_t)v * 5 + dj[c]) * P;
+      const float a0 = ff_to_float(d[k]), a1 = ff_to_float(d[k + 1]);
       amp[((size_t)v * 3 + c) * N + n] = fmaf(fj, a1 - a0, a0);
     }
   }
@@ -301,47 +312,84 @@ int grid_for(size_t total) {
 
 }  // namespace
 
+size_t control_bytes(const VoiceConst& vc, int B) {
+  const size_t P = (size_t)vc.K + 1, K = (size_t)vc.K;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { o = align256(o + bytes); };
+  take(sizeof(double) * B * kNumParams);
+  take(sizeof(VoiceFF) * B);
+  take(sizeof(ff) * B * 6 * P);
+  take(sizeof(double) * B * 2 * P);
+  take(sizeof(double) * B * 2 * P);
+  take(sizeof(ff) * B * 5 * P);
+  take(sizeof(SegVco) * B * 2 * K);
+  take(sizeof(double) * B * 2 * K);
+  take(sizeof(double) * B * 2 * K);
+  take(sizeof(float) * B * 2 * K);
+  return o;
+}
+
+ControlBuffers control_carve(const VoiceConst& vc, int B, void* ws) {
+  const size_t P = (size_t)vc.K + 1, K = (size_t)vc.K;
+  char* base = static_cast<char*>(ws);
+  size_t o = 0;
+  auto take = [&](size_t bytes) { char* at = base + o; o = align256(o + bytes); return at; };
+  ControlBuffers cb;
+  cb.y = reinterpret_cast<double*>(take(sizeof(double) * B * kNumParams));
+  cb.vff = reinterpret_cast<VoiceFF*>(take(sizeof(VoiceFF) * B));
+  cb.env = reinterpret_cast<ff*>(take(sizeof(ff) * B * 6 * P));
+  cb.lfo_inc = reinterpret_cast<double*>(take(sizeof(double) * B * 2 * P));
+  cb.lfo_phase = reinterpret_cast<double*>(take(sizeof(double) * B * 2 * P));
+  cb.dest = reinterpret_cast<ff*>(take(sizeof(ff) * B * 5 * P));
+  cb.seg = reinterpret_cast<SegVco*>(take(sizeof(SegVco) * B * 2 * K));
+  cb.seg_sum = reinterpret_cast<double*>(take(sizeof(double) * B * 2 * K));
+  cb.seg_start = reinterpret_cast<double*>(take(sizeof(double) * B * 2 * K));
+  cb.kappa = reinterpret_cast<float*>(take(sizeof(float) * B * 2 * K));
+  return cb;
+}
+
+void launch_control_pipeline(const VoiceConst& vc, uint64_t seed, uint64_t batch_index, int batch,
+                             const float* params_in, float* params_out, const ControlBuffers& cb,
+                             cudaStream_t st) {
+  const int P = vc.K + 1, K = vc.K;
+  dim3 gp((P + kPT - 1) / kPT, batch), gk((K + kPT - 1) / kPT, batch);
+  dim3 g6((6 * P + kPT - 1) / kPT, batch);
+  plain_params<<<batch, 128, 0, st>>>(vc, seed, batch_index, batch, params_in, params_out, cb.y);
+  plain_voice_consts<<<batch, 64, 0, st>>>(cb.y, cb.vff);
+  plain_adsr<<<g6, kPT, 0, st>>>(vc, cb.vff, cb.env);
+  plain_lfo_rate<<<gp, kPT, 0, st>>>(vc, cb.vff, cb.env, cb.lfo_inc);
+  plain_phase_scan<<<batch, kPT, 0, st>>>(cb.lfo_inc, cb.lfo_phase, P, P, cb.y, kLfo + 2,
+                                          kLfo + 8 + 2);
+  plain_modmix<<<gp, kPT, 0, st>>>(vc, cb.vff, cb.env, cb.lfo_phase, cb.dest);
+  plain_vco_intervals<<<gk, kPT, 0, st>>>(vc, cb.vff, cb.dest, cb.seg, cb.seg_sum, cb.kappa);
+  plain_phase_scan<<<batch, kPT, 0, st>>>(cb.seg_sum, cb.seg_start, K, K, cb.y, kSine + 2,
+                                          kSqr + 2);
+  plain_seg_phase<<<(int)(((size_t)batch * 2 * K + kPT - 1) / kPT), kPT, 0, st>>>(
+      vc, cb.seg_start, cb.seg, batch);
+}
+
 size_t plain_workspace_bytes(const VoiceConst& vc, int batch) {
-  return plain_layout(vc, batch).total;
+  return audio_layout(vc, batch, control_bytes(vc, batch)).total;
 }
 
 cudaError_t launch_render_plain(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, void* workspace, ScratchHeader*, TileState*,
                                 cudaStream_t st) {
-  const PlainLayout L = plain_layout(vc, batch);
+  const ControlBuffers cb = control_carve(vc, batch, workspace);
+  const AudioLayout L = audio_layout(vc, batch, control_bytes(vc, batch));
   char* ws = static_cast<char*>(workspace);
-  double* y = reinterpret_cast<double*>(ws + L.y);
-  double* env = reinterpret_cast<double*>(ws + L.env);
-  double* lfo_inc = reinterpret_cast<double*>(ws + L.lfo_inc);
-  double* lfo_phase = reinterpret_cast<double*>(ws + L.lfo_phase);
-  double* dest = reinterpret_cast<double*>(ws + L.dest);
-  SegVco* seg = reinterpret_cast<SegVco*>(ws + L.seg);
-  double* seg_sum = reinterpret_cast<double*>(ws + L.seg_sum);
-  float* kappa = reinterpret_cast<float*>(ws + L.kappa);
   float* amp = reinterpret_cast<float*>(ws + L.amp);
   float* phase = reinterpret_cast<float*>(ws + L.phase);
   float* osc = reinterpret_cast<float*>(ws + L.osc);
-  const int P = vc.K + 1, K = vc.K;
   const size_t NS = (size_t)batch * vc.n_samples;
-  plain_params<<<batch, 128, 0, st>>>(vc, seed, batch_index, batch, params_in, params_out, y);
-  dim3 gp((P + kPT - 1) / kPT, batch), gk((K + kPT - 1) / kPT, batch);
-  plain_adsr<<<gp, kPT, 0, st>>>(vc, batch, y, env);
-  plain_lfo_rate<<<gp, kPT, 0, st>>>(vc, y, env, lfo_inc);
-  plain_phase_scan<<<batch, kPT, 0, st>>>(lfo_inc, lfo_phase, P, P, y, kLfo + 2, kLfo + 8 + 2);
-  plain_modmix<<<gp, kPT, 0, st>>>(vc, y, env, lfo_phase, dest);
-  plain_vco_intervals<<<gk, kPT, 0, st>>>(vc, y, dest, seg, seg_sum, kappa);
-  // scan of interval sums -> interval start phases (into the LFO-increment buffer)
-  double* seg_start = lfo_inc;  // needs B*2*K doubles; lfo_inc holds B*2*P >= that
-  plain_phase_scan<<<batch, kPT, 0, st>>>(seg_sum, seg_start, K, K, y, kSine + 2, kSqr + 2);
-  plain_seg_phase<<<(int)(((size_t)batch * 2 * K + kPT - 1) / kPT), kPT, 0, st>>>(vc, seg_start,
-                                                                                 seg, batch);
-  plain_upsample_amp<<<grid_for(NS), kPT, 0, st>>>(vc, batch, dest, amp);
-  plain_vco_phase<<<grid_for(NS / 2), kPT, 0, st>>>(vc, batch, seg, phase);
+  launch_control_pipeline(vc, seed, batch_index, batch, params_in, params_out, cb, st);
+  plain_upsample_amp<<<grid_for(NS), kPT, 0, st>>>(vc, batch, cb.dest, amp);
+  plain_vco_phase<<<grid_for(NS / 2), kPT, 0, st>>>(vc, batch, cb.seg, phase);
   plain_sine<<<grid_for(NS), kPT, 0, st>>>(vc, batch, phase, osc);
-  plain_square_saw<<<grid_for(NS), kPT, 0, st>>>(vc, batch, y, phase, kappa, osc);
+  plain_square_saw<<<grid_for(NS), kPT, 0, st>>>(vc, batch, cb.y, phase, cb.kappa, osc);
   plain_noise<<<grid_for(NS / 4), kPT, 0, st>>>(vc, seed, batch_index, batch, osc);
-  plain_vca_mix<<<grid_for(NS), kPT, 0, st>>>(vc, batch, y, amp, osc, audio);
+  plain_vca_mix<<<grid_for(NS), kPT, 0, st>>>(vc, batch, cb.y, amp, osc, audio);
   return cudaGetLastError();
 }
 

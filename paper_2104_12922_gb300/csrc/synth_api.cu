@@ -202,6 +202,29 @@ synth_status synth_render_plain(synth_handle h, uint64_t seed, uint64_t batch_in
                                         static_cast<cudaStream_t>(stream)));
 }
 
+synth_status synth_render_backward_workspace_size(synth_handle h, int32_t batch, size_t* bytes) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!bytes || batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  *bytes = backward_workspace_bytes(h->vc, batch);
+  return SYNTH_OK;
+}
+
+synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch_index,
+                                   int32_t batch, const float* params_dev,
+                                   const float* grad_audio_dev, float* grad_params_dev,
+                                   void* workspace_dev, size_t workspace_bytes, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (batch == 0) return SYNTH_OK;
+  if (!params_dev || !grad_audio_dev || !grad_params_dev || !workspace_dev) return SYNTH_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return SYNTH_ERR_ARG;
+  if (workspace_bytes < backward_workspace_bytes(h->vc, batch)) return SYNTH_ERR_ARG;
+  if (h->vc.R > 128) return SYNTH_ERR_UNSUPPORTED;
+  return check_cuda(launch_render_backward(h->vc, seed, batch_index, batch, params_dev,
+                                           grad_audio_dev, grad_params_dev, workspace_dev,
+                                           static_cast<cudaStream_t>(stream)));
+}
+
 synth_status synth_sync(synth_handle h, void* stream) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SYNTH_ERR_CUDA;

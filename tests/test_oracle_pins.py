@@ -366,3 +366,26 @@ def test_fp32_pitch_chain_error_is_measured(oracle_mod):
         b = oracle_mod.render_voice(cfg, u, 0, g, flags=oracle_mod.ROUND_PITCH_CHAIN_F32)
         worst = max(worst, float(np.max(np.abs(a - b))))
     assert 1e-7 < worst < 1e-2
+
+
+def test_dual_number_gradient_matches_finite_differences(oracle_mod):
+    """The oracle's forward-mode gradient equals FP64 central differences on
+    every parameter where the render is smooth at the step size."""
+    cfg = oracle_mod.default_config(seconds=0.05)
+    u = np.clip(oracle_mod.draw_params(2, 1), 0.02, 0.98)
+    w = si.upstream_grad(9, (oracle_mod.num_samples(cfg),))
+    grad = oracle_mod.render_vjp(cfg, u, 2, 1, w)
+    checked = 0
+    for p in range(78):
+        fd = []
+        for h in (1e-6, 2.5e-7):
+            up, um = u.copy(), u.copy()
+            up[p] += h
+            um[p] -= h
+            fd.append(float(np.dot(w, oracle_mod.render_voice(cfg, up, 2, 1) -
+                                   oracle_mod.render_voice(cfg, um, 2, 1))) / (2 * h))
+        if abs(fd[0] - fd[1]) > 1e-5 * (abs(fd[0]) + 1e-3):
+            continue
+        checked += 1
+        assert grad[p] == pytest.approx(fd[0], rel=1e-5, abs=1e-6), p
+    assert checked >= 60
