@@ -143,6 +143,18 @@ synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch
                                    const float* grad_audio_dev, float* grad_params_dev,
                                    void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* The dense contraction under the STFT-as-GEMM and the proposal MLP, exposed
+ * on its own: C[m][n] = alpha * sum_k A[m][k] B[n][k] with A, B bfloat16
+ * (row-major, K contiguous, row strides lda, ldb in elements: multiples of 8,
+ * >= k; 16-byte aligned bases), FP32 accumulation on the tcgen05 tensor
+ * cores, C float32 row-major with row stride ldc >= n. k must be a multiple
+ * of 8; m, n any positive size. Device pointers, caller-owned.
+ * Errors: SYNTH_ERR_ARG, SYNTH_ERR_CUDA; a bounded wait that gave up is
+ * reported by synth_sync as SYNTH_ERR_TIMEOUT. */
+synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, const void* b_dev,
+                             int32_t ldb, float* c_dev, int32_t ldc, int32_t m, int32_t n,
+                             int32_t k, float alpha, void* stream);
+
 /* Waits for the stream, then reports (and clears) a device-side error
  * recorded by any earlier call on this handle: SYNTH_ERR_TIMEOUT if a bounded
  * wait gave up, SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. */

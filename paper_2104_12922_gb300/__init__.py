@@ -67,6 +67,9 @@ def lib() -> ctypes.CDLL:
         L.synth_render_plain.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.synth_render_backward_workspace_size.argtypes = [vp, i32, P(ctypes.c_size_t)]
         L.synth_render_backward.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.synth_gemm_bf16.argtypes = [vp, vp, i32, vp, i32, vp, i32, i32, i32, i32,
+                                      ctypes.c_float, vp]
+        L.synth_gemm_bf16.restype = ctypes.c_int
         L.synth_sync.argtypes = [vp, vp]
         L.synth_params_to_human.argtypes = [vp, vp, vp, i32]
         L.synth_is_test.argtypes = [u64]

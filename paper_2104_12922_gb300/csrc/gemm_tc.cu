@@ -1,0 +1,329 @@
+// gemm_tc.cu -- BF16 GEMM on Blackwell's 5th-generation tensor cores.
+//
+// C[M][N] = A[M][K] * B[N][K]^T, A and B bf16 and K-contiguous, FP32
+// accumulation in tensor memory (TMEM), a fused epilogue. Used for the
+// STFT-as-GEMM, the mel projection and the proposal MLP.
+//
+// One CTA computes one 128 x BN output tile with 6 warps:
+//   warp 0      TMA producer: cp.async.bulk.tensor loads of 128x64 A and BNx64 B
+//               tiles (128-byte swizzle) into a STAGES-deep shared-memory ring;
+//   warp 1      allocates TMEM; one elected lane issues tcgen05.mma
+//               (kind::f16, M = 128, N = BN, K = 16 per instruction) and
+//               tcgen05.commit frees each stage and finally signals the epilogue;
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator rows (warp w owns TMEM
+//               lanes 32 (w mod 4) ..), the fused epilogue, global stores.
+// Every mbarrier wait is bounded; on timeout the CTA records an error and
+// finishes without touching the tile.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "gemm_tc.h"
+
+namespace synth {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;          // one 128-byte swizzle row of bf16
+constexpr int kStages = 4;
+constexpr int kGemmThreads = 192;
+constexpr long long kWaitLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Waits for the phase with the given parity; false if the bounded wait ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile stored with the
+// 128-byte swizzle (as TMA writes it): start address >> 4 in bits 0-13,
+// leading byte offset (unused for this layout) in 16-29, stride byte offset
+// 1024 B (8 rows of 128 B) in 32-45, descriptor version 1 in 46-47, swizzle
+// mode "128B" (2) in 61-63.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits
+// 4-5 = 1), bf16 A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+struct __align__(1024) GemmSmem {
+  __nv_bfloat16 a[kStages][BM * BK];
+  __nv_bfloat16 b[kStages][BN * BK];
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t accum;
+  uint32_t tmem_base;
+  int failed;
+};
+
+__device__ __forceinline__ float sigmoidf(float x) { return 1.f / (1.f + __expf(-x)); }
+
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
+    const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+    GemmEpilogue epi, int M, int N, int K, unsigned int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  GemmSmem<BN>& sm = *reinterpret_cast<GemmSmem<BN>*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nk = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    mbar_init(&sm.accum, 1);
+    sm.failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sm.tmem_base)),
+                 "r"((uint32_t)BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+      if (!mbar_wait(&sm.empty[s], ph ^ 1u)) { sm.failed = 1; break; }
+      mbar_expect_tx(&sm.full[s], (uint32_t)((BM + BN) * BK * 2));
+      tma_load_2d(sm.a[s], &map_a, &sm.full[s], kb * BK, m0);
+      tma_load_2d(sm.b[s], &map_b, &sm.full[s], kb * BK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+      if (!mbar_wait(&sm.full[s], ph)) { sm.failed = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sm.a[s]), b0 = smem_u32(sm.b[s]);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        umma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
+                  (kb | kk) != 0 ? 1u : 0u);
+      umma_commit(&sm.empty[s]);
+    }
+    umma_commit(&sm.accum);
+  } else if (warp >= 2) {
+    // epilogue
+    const bool ok = mbar_wait(&sm.accum, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = m0 + 32 * q + lane;
+    if (!ok) sm.failed = 1;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+      if (!ok || row >= M) continue;
+      const int col0 = n0 + c;
+      switch (epi.kind) {
+        case kEpiStoreF32: {
+          float* out = epi.out_f32 + (size_t)row * epi.ldc;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (col0 + i < N) out[col0 + i] = v[i] * epi.alpha;
+          break;
+        }
+        case kEpiBiasActBF16: {
+          // y = act(acc + bias) in bf16 (and optionally the transposed copy)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int col = col0 + i;
+            if (col >= N) continue;
+            float z = v[i] + (epi.bias ? epi.bias[col] : 0.f);
+            if (epi.act == kActRelu) z = fmaxf(z, 0.f);
+            else if (epi.act == kActSigmoid) z = sigmoidf(z);
+            const __nv_bfloat16 b = __float2bfloat16(z);
+            if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + col] = b;
+            if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ldc_t + row] = b;
+            if (epi.out_f32) epi.out_f32[(size_t)row * epi.ldc + col] = z;
+          }
+          break;
+        }
+        case kEpiPowerPairs: {
+          // columns (2b, 2b+1) hold (re, im) of bin b: out[row][b] = re^2 + im^2
+          float* out = epi.out_f32 + (size_t)row * epi.ldc;
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            const int bin = (col0 + i) >> 1;
+            if (col0 + i + 1 < N && bin < epi.n_valid) out[bin] = v[i] * v[i] + v[i + 1] * v[i + 1];
+          }
+          break;
+        }
+        case kEpiLogBF16: {
+          // features = log(acc + eps) in bf16
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int col = col0 + i;
+            if (col < N && col < epi.n_valid)
+              epi.out_bf16[(size_t)row * epi.ldc + col] = __float2bfloat16(__logf(v[i] + epi.eps));
+          }
+          break;
+        }
+        default:
+          break;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0 && lane == 0 && sm.failed) atomicOr(err, 1u);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)BN));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D bf16 tensor map: rows x cols (cols contiguous), row stride in elements,
+// box 64 columns x box_rows rows, 128-byte swizzle, zero fill out of bounds.
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) != 0 || ((size_t)ld * 2) % 16 != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEpilogue& epi, int M,
+                      int N, int K, unsigned int* err, cudaStream_t st) {
+  const size_t smem = sizeof(GemmSmem<BN>) + 1024;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(gemm_bf16_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  gemm_bf16_tc<BN><<<grid, kGemmThreads, smem, st>>>(ma, mb, epi, M, N, K, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
+                      int N, int K, const GemmEpilogue& epi, unsigned int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0 || (K % 8) != 0) return cudaErrorInvalidValue;
+  const int bn = N > 128 ? 256 : 128;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, K, lda, BM) || !make_map(&mb, B, N, K, ldb, bn))
+    return cudaErrorInvalidValue;
+  if (bn == 256) return launch_bn<256>(ma, mb, epi, M, N, K, err, st);
+  return launch_bn<128>(ma, mb, epi, M, N, K, err, st);
+}
+
+}  // namespace synth

@@ -1,0 +1,37 @@
+// gemm_tc.h -- host interface of the tcgen05 BF16 GEMM (gemm_tc.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace synth {
+
+enum GemmEpiKind : int {
+  kEpiStoreF32 = 0,     // out_f32[row][col] = alpha * acc
+  kEpiBiasActBF16 = 1,  // z = act(acc + bias[col]) -> out_bf16 / out_bf16_t (transposed) / out_f32
+  kEpiPowerPairs = 2,   // out_f32[row][b] = acc[2b]^2 + acc[2b+1]^2 for b < n_valid
+  kEpiLogBF16 = 3,      // out_bf16[row][col] = log(acc + eps) for col < n_valid
+};
+enum GemmAct : int { kActNone = 0, kActRelu = 1, kActSigmoid = 2 };
+
+struct GemmEpilogue {
+  int kind = kEpiStoreF32;
+  int act = kActNone;
+  float* out_f32 = nullptr;
+  __nv_bfloat16* out_bf16 = nullptr;
+  __nv_bfloat16* out_bf16_t = nullptr;
+  const float* bias = nullptr;
+  int ldc = 0;      // row stride (elements) of out_f32 / out_bf16
+  int ldc_t = 0;    // row stride of the transposed copy
+  int n_valid = 0;  // valid output columns (power pairs: bins; log: columns)
+  float alpha = 1.f;
+  float eps = 0.f;
+};
+
+// C = A[M][K] * B[N][K]^T on the tensor cores; A, B bf16 with row strides lda,
+// ldb (elements, multiples of 8), K a multiple of 8, 16-byte aligned bases.
+// err: device word, bit 0 set if a bounded wait gave up.
+cudaError_t gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
+                      int N, int K, const GemmEpilogue& epi, unsigned int* err, cudaStream_t st);
+
+}  // namespace synth

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 
+#include "gemm_tc.h"
 #include "internal.h"
 #include "synth.h"
 
@@ -223,6 +224,26 @@ synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch
   return check_cuda(launch_render_backward(h->vc, seed, batch_index, batch, params_dev,
                                            grad_audio_dev, grad_params_dev, workspace_dev,
                                            static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, const void* b_dev,
+                             int32_t ldb, float* c_dev, int32_t ldc, int32_t m, int32_t n,
+                             int32_t k, float alpha, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!a_dev || !b_dev || !c_dev || m < 1 || n < 1 || k < 8 || (k % 8) != 0 || lda < k ||
+      ldb < k || ldc < n || (lda % 8) != 0 || (ldb % 8) != 0)
+    return SYNTH_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(a_dev) & 15) || (reinterpret_cast<uintptr_t>(b_dev) & 15))
+    return SYNTH_ERR_ARG;
+  GemmEpilogue epi;
+  epi.kind = kEpiStoreF32;
+  epi.out_f32 = c_dev;
+  epi.ldc = ldc;
+  epi.alpha = alpha;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  return check_cuda(gemm_bf16(static_cast<const __nv_bfloat16*>(a_dev), lda,
+                              static_cast<const __nv_bfloat16*>(b_dev), ldb, m, n, k, epi,
+                              &hdr->error, static_cast<cudaStream_t>(stream)));
 }
 
 synth_status synth_sync(synth_handle h, void* stream) {
