@@ -1,0 +1,129 @@
+"""Pins of the spectral oracle (no GPU): STFT against a brute-force DFT with
+explicit reflect padding and periodic Hann window, Parseval, a pure tone's
+peak bin, the multi-resolution distance's zero/symmetry and gradient, the
+Slaney mel scale's fixed points and the filterbank's band placement, and
+the MLP gradient against finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import spectral as sp
+
+
+def _brute_stft(x, n_fft):
+    hop = n_fft // 4
+    pad = n_fft // 2
+    N = len(x)
+    idx = np.arange(-pad, N + pad)
+    idx = np.where(idx < 0, -idx, idx)
+    idx = np.where(idx >= N, 2 * (N - 1) - idx, idx)
+    xp = x[idx]
+    w = 0.5 - 0.5 * np.cos(2 * math.pi * np.arange(n_fft) / n_fft)
+    n_frames = 1 + N // hop
+    out = np.zeros((n_fft // 2 + 1, n_frames), dtype=complex)
+    for f in range(n_frames):
+        seg = xp[f * hop: f * hop + n_fft] * w
+        for k in range(n_fft // 2 + 1):
+            out[k, f] = sum(seg[t] * complex(math.cos(2 * math.pi * k * t / n_fft),
+                                             -math.sin(2 * math.pi * k * t / n_fft))
+                            for t in range(n_fft))
+    return out
+
+
+def test_stft_matches_brute_force_dft():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(64)
+    got = sp.stft(x[None, :], 16)[0].numpy()
+    want = _brute_stft(x, 16)
+    assert got.shape == want.shape
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+def test_stft_parseval_per_frame():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(256)
+    n = 32
+    X = sp.stft(x[None, :], n)[0].numpy()
+    w = 0.5 - 0.5 * np.cos(2 * math.pi * np.arange(n) / n)
+    xp = np.pad(x, n // 2, mode="reflect")
+    for f in [0, 3, X.shape[1] - 1]:
+        seg = xp[f * n // 4: f * n // 4 + n] * w
+        e = np.abs(X[0, f]) ** 2 + np.abs(X[-1, f]) ** 2 + 2 * np.sum(np.abs(X[1:-1, f]) ** 2)
+        assert e == pytest.approx(n * np.sum(seg ** 2), rel=1e-12)
+
+
+def test_pure_tone_peaks_at_its_bin():
+    n, k0 = 512, 37
+    t = np.arange(44100 // 10)
+    x = np.sin(2 * math.pi * k0 * t / n)
+    mag = sp.stft(x[None, :], n)[0].abs().numpy()
+    assert np.all(np.argmax(mag[:, 4:-4], axis=0) == k0)
+
+
+def test_mrstft_zero_symmetric_and_gradient():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((2, 2048))
+    y = rng.standard_normal((2, 2048))
+    assert float(sp.mrstft_loss(x, x)) == 0.0
+    assert float(sp.mrstft_loss(x, y)) == pytest.approx(float(sp.mrstft_loss(y, x)), rel=1e-14)
+    loss, g = sp.mrstft_loss_and_grad(x, y, n_ffts=(64, 128))
+    for (b, i) in [(0, 5), (1, 1000), (0, 2047)]:
+        h = 1e-6
+        xp, xm = x.copy(), x.copy()
+        xp[b, i] += h
+        xm[b, i] -= h
+        fd = (float(sp.mrstft_loss(xp, y, (64, 128), per_voice=True).sum()) -
+              float(sp.mrstft_loss(xm, y, (64, 128), per_voice=True).sum())) / (2 * h)
+        assert g[b, i] == pytest.approx(fd, rel=1e-5, abs=1e-8)
+
+
+def test_slaney_mel_scale_points():
+    assert float(sp.hz_to_mel(1000.0)) == pytest.approx(15.0)
+    assert float(sp.hz_to_mel(6400.0)) == pytest.approx(42.0)
+    assert float(sp.hz_to_mel(200.0)) == pytest.approx(3.0)
+    f = np.array([0.0, 100.0, 999.0, 1000.0, 5000.0, 22050.0])
+    assert np.allclose(sp.mel_to_hz(sp.hz_to_mel(f)), f, rtol=1e-12, atol=1e-9)
+
+
+def test_mel_filterbank_band_placement():
+    fb = sp.mel_filterbank(2048, 128, 44100.0)
+    assert fb.shape == (128, 1025) and fb.min() >= 0.0
+    assert np.all(fb.sum(axis=1) > 0)
+    edges = sp.mel_to_hz(np.linspace(0.0, float(sp.hz_to_mel(22050.0)), 130))
+    bins = np.arange(1025) * 44100.0 / 2048
+    for i in [5, 40, 100, 127]:
+        # the band's peak sits at the FFT bin nearest its centre edge
+        assert abs(bins[np.argmax(fb[i])] - edges[i + 1]) <= 44100.0 / 2048
+        # unit area in Hz (triangles several bins wide)
+        if edges[i + 2] - edges[i] > 10 * 44100.0 / 2048:
+            assert np.sum(fb[i]) * 44100.0 / 2048 == pytest.approx(1.0, rel=0.02)
+
+
+def test_log_mel_shape_and_tone_band():
+    sr = 44100.0
+    t = np.arange(int(sr)) / sr
+    x = np.sin(2 * math.pi * 3000.0 * t)
+    feats = sp.log_mel(x[None, :]).numpy()[0]
+    assert feats.shape == (1 + 44100 // 512, 128)
+    fb = sp.mel_filterbank()
+    k = int(round(3000.0 * 2048 / sr))
+    assert np.argmax(feats[40]) in np.argsort(fb[:, k])[-2:]
+
+
+def test_mlp_gradients_match_finite_differences():
+    rng = np.random.default_rng(3)
+    dims = [6, 5, 4, 3]
+    ws = [rng.standard_normal((dims[i + 1], dims[i])) * 0.5 for i in range(3)]
+    bs = [rng.standard_normal(dims[i + 1]) * 0.1 for i in range(3)]
+    x = rng.standard_normal((4, 6))
+    tgt = rng.uniform(size=(4, 3))
+    loss, gw, gb = sp.mlp_loss_and_grads(x, tgt, ws, bs)
+    h = 1e-6
+    for l, (i, j) in [(0, (1, 2)), (1, (3, 0)), (2, (2, 3))]:
+        wp = [w.copy() for w in ws]
+        wm = [w.copy() for w in ws]
+        wp[l][i, j] += h
+        wm[l][i, j] -= h
+        fd = (sp.mlp_loss_and_grads(x, tgt, wp, bs)[0] - sp.mlp_loss_and_grads(x, tgt, wm, bs)[0]) / (2 * h)
+        assert gw[l][i, j] == pytest.approx(fd, rel=1e-6, abs=1e-9)
