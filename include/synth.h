@@ -155,6 +155,77 @@ synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, con
                              int32_t ldb, float* c_dev, int32_t ldc, int32_t m, int32_t n,
                              int32_t k, float alpha, void* stream);
 
+/* Multi-resolution log-magnitude STFT distance (the paper's multi-scale
+ * spectrogram distance, Sec. 4.4) between x and y, both [batch][N] float
+ * device arrays of the handle's voice length (N >= 2048):
+ *   L_v = sum over n_fft in {512, 1024, 2048} of the mean over (bins, frames)
+ *         of |log(|X| + 1e-7) - log(|Y| + 1e-7)|,
+ * periodic Hann window, hop n_fft/4, centred frames with reflect padding,
+ * STFT as a bf16 tensor-core GEMM with FP32 accumulation.
+ *  loss_voice_dev [batch] double (device) or NULL: L_v per voice.
+ *  grad_x_dev     [batch][N] float or NULL: d(sum_v L_v)/dx.
+ *  target_ready   nonzero to reuse the target spectra an earlier call with the
+ *                 same y and workspace left there.
+ *  workspace      synth_mrstft_workspace_size(h, batch) bytes, 256-byte aligned.
+ * Errors: SYNTH_ERR_ARG, SYNTH_ERR_UNSUPPORTED (N < 2048), SYNTH_ERR_CUDA. */
+synth_status synth_mrstft_workspace_size(synth_handle h, int32_t batch, size_t* bytes);
+synth_status synth_mrstft(synth_handle h, const float* x_dev, const float* y_dev, int32_t batch,
+                          int32_t target_ready, double* loss_voice_dev, float* grad_x_dev,
+                          void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* One Adam step (Kingma & Ba; beta 0.9 / 0.999, eps 1e-8, step >= 1) on
+ * normalized parameters u[count] with gradient grad[count] and moments m, v
+ * (device, caller-owned, zero before step 1); u is kept inside [0, 1]. Used
+ * for adjoint refinement in parameter space. */
+synth_status synth_param_adam(synth_handle h, float* u_dev, const float* grad_dev, float* m_dev,
+                              float* v_dev, int32_t count, int32_t step, float lr, void* stream);
+
+/* ---- learned parameter proposal (inverse synthesis, Sec. 2) ----------------
+ * A network maps 128-band log-mel features (|STFT|^2, n_fft 2048, hop 512,
+ * Slaney mel, log(x + 1e-6); frames = 1 + N/512) through a 4-layer MLP
+ * (1024-1024-1024 ReLU, 78 sigmoid outputs) to normalized Voice parameters.
+ * bf16 tensor-core GEMMs with FP32 accumulation; FP32 master weights, Adam.
+ * The model owns its device memory (allocated at create) and is tied to the
+ * handle it was created with (voice length, renderer for training). */
+typedef struct synth_model_s* synth_model;
+
+/* max_batch: a multiple of 8 and <= the handle's max_batch. Weights are drawn
+ * from Philox(seed) uniform in +-1/sqrt(fan_in), biases 0. Synchronous.
+ * Errors: SYNTH_ERR_ARG, SYNTH_ERR_UNSUPPORTED (voice shorter than 2048
+ * samples), SYNTH_ERR_OOM, SYNTH_ERR_CUDA. */
+synth_status synth_model_create(synth_handle h, int32_t max_batch, uint64_t seed, synth_model* out);
+synth_status synth_model_destroy(synth_model m);
+/* Feature length per voice: frames * 128. */
+int64_t synth_model_feature_dim(synth_model m);
+/* Log-mel features of audio [batch][N] -> features_dev [batch][feature_dim] bf16. */
+synth_status synth_model_features(synth_model m, const float* audio_dev, int32_t batch,
+                                  void* features_dev, void* stream);
+/* Network forward on features -> params_out [batch][78] float in (0, 1). */
+synth_status synth_model_forward(synth_model m, const void* features_dev, int32_t batch,
+                                 float* params_out_dev, void* stream);
+/* One training step on given features and target parameters [batch][78]:
+ * forward, MSE (mean over batch x 78), backward, Adam(lr). batch: a multiple
+ * of 8. loss_dev (device float) receives the loss before the update, or NULL. */
+synth_status synth_model_train_features(synth_model m, const void* features_dev,
+                                        const float* target_dev, int32_t batch, float lr,
+                                        float* loss_dev, void* stream);
+/* One training step on voices rendered on the fly: synth_render(seed,
+ * batch_index, batch) into the model's buffers, features, train step. */
+synth_status synth_model_train_step(synth_model m, uint64_t seed, uint64_t batch_index,
+                                    int32_t batch, float lr, float* loss_dev, void* stream);
+/* Proposal: parameters_out [batch][78] for audio [batch][N] (features + forward). */
+synth_status synth_propose(synth_handle h, synth_model m, const float* audio_dev, int32_t batch,
+                           float* params_out_dev, void* stream);
+/* Copies an FP32 tensor out of the model: which = 0 weights [out][in],
+ * 1 biases [out], 2 last weight gradients, 3 last bias gradients; layer 0..3;
+ * count must equal the tensor's size. */
+synth_status synth_model_get_tensor(synth_model m, int32_t which, int32_t layer, float* dst_dev,
+                                    size_t count, void* stream);
+/* Checkpoint: every model tensor (weights, Adam moments) and the step count
+ * to / from a host file. Synchronous. */
+synth_status synth_model_save(synth_model m, const char* path);
+synth_status synth_model_load(synth_model m, const char* path);
+
 /* Waits for the stream, then reports (and clears) a device-side error
  * recorded by any earlier call on this handle: SYNTH_ERR_TIMEOUT if a bounded
  * wait gave up, SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. */

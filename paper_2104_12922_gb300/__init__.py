@@ -70,6 +70,27 @@ def lib() -> ctypes.CDLL:
         L.synth_gemm_bf16.argtypes = [vp, vp, i32, vp, i32, vp, i32, i32, i32, i32,
                                       ctypes.c_float, vp]
         L.synth_gemm_bf16.restype = ctypes.c_int
+        L.synth_mrstft_workspace_size.argtypes = [vp, i32, P(ctypes.c_size_t)]
+        L.synth_mrstft.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, ctypes.c_size_t, vp]
+        L.synth_param_adam.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, vp]
+        L.synth_model_create.argtypes = [vp, i32, u64, P(vp)]
+        L.synth_model_destroy.argtypes = [vp]
+        L.synth_model_feature_dim.argtypes = [vp]
+        L.synth_model_feature_dim.restype = i64
+        L.synth_model_features.argtypes = [vp, vp, i32, vp, vp]
+        L.synth_model_forward.argtypes = [vp, vp, i32, vp, vp]
+        L.synth_model_train_features.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp]
+        L.synth_model_train_step.argtypes = [vp, u64, u64, i32, ctypes.c_float, vp, vp]
+        L.synth_propose.argtypes = [vp, vp, vp, i32, vp, vp]
+        L.synth_model_get_tensor.argtypes = [vp, i32, i32, vp, ctypes.c_size_t, vp]
+        L.synth_model_save.argtypes = [vp, ctypes.c_char_p]
+        L.synth_model_load.argtypes = [vp, ctypes.c_char_p]
+        for name in ("synth_mrstft_workspace_size", "synth_mrstft", "synth_param_adam",
+                     "synth_model_create", "synth_model_destroy", "synth_model_features",
+                     "synth_model_forward", "synth_model_train_features", "synth_model_train_step",
+                     "synth_propose", "synth_model_get_tensor", "synth_model_save",
+                     "synth_model_load"):
+            getattr(L, name).restype = ctypes.c_int
         L.synth_sync.argtypes = [vp, vp]
         L.synth_params_to_human.argtypes = [vp, vp, vp, i32]
         L.synth_is_test.argtypes = [u64]
@@ -295,3 +316,99 @@ def render_autograd(synth: "Synth", seed: int, batch_index: int, params):
             return synth.backward(seed, batch_index, u, grad_audio.contiguous())
 
     return _Render.apply(params)
+
+
+# ---- spectral distance, refinement and the learned proposal -------------------
+class MRSTFT:
+    """Multi-resolution log-magnitude STFT distance on the tensor cores
+    (synth_mrstft): per-voice loss and gradient w.r.t. x."""
+
+    def __init__(self, synth: Synth, batch: int):
+        import torch
+        n = ctypes.c_size_t()
+        _check(lib().synth_mrstft_workspace_size(synth.handle, batch, ctypes.byref(n)),
+               "synth_mrstft_workspace_size")
+        self.synth, self.batch = synth, batch
+        self.ws = torch.empty(n.value, dtype=torch.uint8, device=synth.device)
+        self.loss = torch.empty(batch, dtype=torch.float64, device=synth.device)
+
+    def __call__(self, x, y, grad=True, target_ready=False, stream=None):
+        import torch
+        gx = torch.empty_like(x) if grad else None
+        _check(lib().synth_mrstft(self.synth.handle, _ptr(x), _ptr(y), self.batch,
+                                  1 if target_ready else 0, _ptr(self.loss), _ptr(gx),
+                                  _ptr(self.ws), self.ws.numel(), _stream_ptr(stream)),
+               "synth_mrstft")
+        return self.loss, gx
+
+
+def param_adam(synth: Synth, u, grad, m, v, step: int, lr: float, stream=None) -> None:
+    _check(lib().synth_param_adam(synth.handle, _ptr(u), _ptr(grad), _ptr(m), _ptr(v), u.numel(),
+                                  step, lr, _stream_ptr(stream)), "synth_param_adam")
+
+
+class ProposalModel:
+    """Log-mel -> MLP -> sigmoid Voice parameters (synth_model_* calls)."""
+
+    def __init__(self, synth: Synth, max_batch: int = 128, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().synth_model_create(synth.handle, max_batch, seed, ctypes.byref(h)),
+               "synth_model_create")
+        self.synth, self.handle, self.max_batch = synth, h.value, max_batch
+        self.feature_dim = int(lib().synth_model_feature_dim(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().synth_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def features(self, audio, stream=None):
+        import torch
+        f = torch.empty((audio.shape[0], self.feature_dim), dtype=torch.bfloat16, device=audio.device)
+        _check(lib().synth_model_features(self.handle, _ptr(audio), audio.shape[0], _ptr(f),
+                                          _stream_ptr(stream)), "synth_model_features")
+        return f
+
+    def forward(self, feats, stream=None):
+        import torch
+        out = torch.empty((feats.shape[0], NUM_PARAMS), dtype=torch.float32, device=feats.device)
+        _check(lib().synth_model_forward(self.handle, _ptr(feats), feats.shape[0], _ptr(out),
+                                         _stream_ptr(stream)), "synth_model_forward")
+        return out
+
+    def train_features(self, feats, target, lr, loss=None, stream=None):
+        _check(lib().synth_model_train_features(self.handle, _ptr(feats), _ptr(target),
+                                                feats.shape[0], lr, _ptr(loss), _stream_ptr(stream)),
+               "synth_model_train_features")
+
+    def train_step(self, seed, batch_index, batch, lr, loss=None, stream=None):
+        _check(lib().synth_model_train_step(self.handle, seed, batch_index, batch, lr, _ptr(loss),
+                                            _stream_ptr(stream)), "synth_model_train_step")
+
+    def propose(self, audio, stream=None):
+        import torch
+        out = torch.empty((audio.shape[0], NUM_PARAMS), dtype=torch.float32, device=audio.device)
+        _check(lib().synth_propose(self.synth.handle, self.handle, _ptr(audio), audio.shape[0],
+                                   _ptr(out), _stream_ptr(stream)), "synth_propose")
+        return out
+
+    def tensor(self, which: int, layer: int):
+        import torch
+        dims = [self.feature_dim, 1024, 1024, 1024, NUM_PARAMS]
+        shape = (dims[layer + 1], dims[layer]) if which in (0, 2) else (dims[layer + 1],)
+        t = torch.empty(shape, dtype=torch.float32, device=self.synth.device)
+        _check(lib().synth_model_get_tensor(self.handle, which, layer, _ptr(t), t.numel(),
+                                            _stream_ptr(None)), "synth_model_get_tensor")
+        return t
+
+    def save(self, path: str):
+        _check(lib().synth_model_save(self.handle, path.encode()), "synth_model_save")
+
+    def load(self, path: str):
+        _check(lib().synth_model_load(self.handle, path.encode()), "synth_model_load")

@@ -233,11 +233,14 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
         }
         case kEpiPowerPairs: {
           // columns (2b, 2b+1) hold (re, im) of bin b: out[row][b] = re^2 + im^2
-          float* out = epi.out_f32 + (size_t)row * epi.ldc;
 #pragma unroll
           for (int i = 0; i < 16; i += 2) {
             const int bin = (col0 + i) >> 1;
-            if (col0 + i + 1 < N && bin < epi.n_valid) out[bin] = v[i] * v[i] + v[i + 1] * v[i + 1];
+            if (col0 + i + 1 < N && bin < epi.n_valid) {
+              const float pw = v[i] * v[i] + v[i + 1] * v[i + 1];
+              if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + bin] = __float2bfloat16(pw);
+              else epi.out_f32[(size_t)row * epi.ldc + bin] = pw;
+            }
           }
           break;
         }

@@ -1,0 +1,328 @@
+// mlp.cu -- the learned parameter proposal: log-mel features -> 4-layer MLP
+// (ReLU hidden layers of width 1024, sigmoid output of the 78 normalized
+// parameters), trained with MSE against the parameters the synth drew, on
+// voices rendered on the fly (inverse synthesis, Sec. 2 of the paper; the
+// paper trains no network itself).
+//
+// All contractions run on the tcgen05 GEMM (gemm_tc.cu) with bf16 operands
+// and FP32 accumulation; master weights, gradients and Adam moments are FP32.
+// Every operand the GEMM reads is K-contiguous, so the forward epilogues also
+// write the transposed activations the weight gradients need, and the
+// optimizer writes a transposed bf16 copy of the hidden weights for the
+// input gradients.
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "gemm_tc.h"
+#include "mlp.h"
+#include "voice_device.cuh"
+
+namespace synth {
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int grid_of(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 152 * 64 ? b : 152 * 64);
+}
+
+// Uniform(-bound, bound) from Philox (key = seed, counter = (i / 4, tensor id, 0, 2)).
+__global__ void init_uniform(float* w, int64_t n, float bound, uint64_t seed, uint32_t tensor) {
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)(i >> 2), tensor, 0u, 2u), key);
+    const uint32_t words[4] = {r.x, r.y, r.z, r.w};
+    w[i] = bound * fmaf(2.f, u01f(words[i & 3]), -1.f);
+  }
+}
+
+__global__ void to_bf16(const float* __restrict__ w, int rows, int cols, __nv_bfloat16* __restrict__ wb,
+                        __nv_bfloat16* __restrict__ wt, int ld_t) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / cols), c = (int)(i % cols);
+    const __nv_bfloat16 b = __float2bfloat16(w[i]);
+    wb[i] = b;
+    if (wt) wt[(int64_t)c * ld_t + r] = b;
+  }
+}
+
+// out[c][r] = in[r][c] (bf16), for the input features of the first layer.
+__global__ void transpose_bf16(const __nv_bfloat16* __restrict__ in, int rows, int cols,
+                               __nv_bfloat16* __restrict__ out) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int r = r0 + dy, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[dy][threadIdx.x] = in[(int64_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int c = c0 + dy, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(int64_t)c * rows + r] = tile[threadIdx.x][dy];
+  }
+}
+
+// Output layer: MSE against the target (mean over batch x outputs) through
+// the sigmoid: dZ = 2 (y - u) / (B P) * y (1 - y); writes dZ and dZ^T (bf16,
+// zero-padded to P_pad columns / rows) and the loss sum.
+__global__ void mse_sigmoid_grad(const float* __restrict__ y, const float* __restrict__ target,
+                                 int batch, int P, int P_pad, __nv_bfloat16* __restrict__ dz,
+                                 __nv_bfloat16* __restrict__ dzt, float* __restrict__ loss) {
+  __shared__ float red[8];
+  float local = 0.f;
+  const float scale = 2.f / (float)(batch * P);
+  for (int i = threadIdx.x; i < batch * P_pad; i += blockDim.x) {
+    const int b = i / P_pad, p = i % P_pad;
+    float g = 0.f;
+    if (p < P) {
+      const float yy = y[b * P + p], d = yy - target[b * P + p];
+      local += d * d;
+      g = scale * d * yy * (1.f - yy);
+    }
+    dz[i] = __float2bfloat16(g);
+    dzt[(int64_t)p * batch + b] = __float2bfloat16(g);
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0 && loss) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *loss = t / (float)(batch * P);
+  }
+}
+
+// Hidden layer: dZ = dH * relu'(Z) with relu'(Z) = (H > 0); writes dZ, dZ^T.
+__global__ void relu_grad(const float* __restrict__ dh, const __nv_bfloat16* __restrict__ h, int batch,
+                          int width, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt) {
+  const int64_t total = (int64_t)batch * width;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / width), c = (int)(i % width);
+    const float g = __bfloat162float(h[i]) > 0.f ? dh[i] : 0.f;
+    const __nv_bfloat16 gb = __float2bfloat16(g);
+    dz[i] = gb;
+    dzt[(int64_t)c * batch + b] = gb;
+  }
+}
+
+// Bias gradient: db[c] = sum_b dZ[b][c] (one thread per column).
+__global__ void bias_grad(const __nv_bfloat16* __restrict__ dz, int batch, int width, int ld,
+                          float* __restrict__ db) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= width) return;
+  float s = 0.f;
+  for (int b = 0; b < batch; ++b) s += __bfloat162float(dz[(int64_t)b * ld + c]);
+  db[c] = s;
+}
+
+// Adam (Kingma & Ba, 2015) on FP32 master values; also refreshes the bf16
+// copy (and its transpose) the GEMMs read. rows x cols, row-major.
+__global__ void adam_update(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t rows, int cols, float lr, float b1,
+                            float b2, float eps, float c1, float c2, __nv_bfloat16* __restrict__ wb,
+                            __nv_bfloat16* __restrict__ wt, int ld_t) {
+  const int64_t total = rows * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) {
+      const __nv_bfloat16 b = __float2bfloat16(wi);
+      wb[i] = b;
+      if (wt) wt[(int64_t)(i % cols) * ld_t + i / cols] = b;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- layout
+MlpLayout mlp_layout(int in_dim, int hidden, int out_dim, int max_batch) {
+  MlpLayout L;
+  L.dims[0] = in_dim;
+  L.dims[1] = L.dims[2] = L.dims[3] = hidden;
+  L.dims[4] = out_dim;
+  L.out_pad = (out_dim + 7) & ~7;
+  L.max_batch = max_batch;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = al256(o + bytes); return at; };
+  for (int l = 0; l < 4; ++l) {
+    const size_t in = L.dims[l], out = L.dims[l + 1];
+    L.w[l] = take(sizeof(float) * in * out);
+    L.b[l] = take(sizeof(float) * out);
+    L.mw[l] = take(sizeof(float) * in * out);
+    L.vw[l] = take(sizeof(float) * in * out);
+    L.mb[l] = take(sizeof(float) * out);
+    L.vb[l] = take(sizeof(float) * out);
+    L.gw[l] = take(sizeof(float) * in * out);
+    L.gb[l] = take(sizeof(float) * out);
+    L.wb[l] = take(sizeof(__nv_bfloat16) * in * out);
+    // transposed bf16 weights [in][out_pad] for the input gradient (layers 1..3)
+    const size_t outp = l == 3 ? (size_t)L.out_pad : out;
+    L.wt[l] = l == 0 ? 0 : take(sizeof(__nv_bfloat16) * in * outp);
+  }
+  const size_t B = max_batch;
+  L.h0t = take(sizeof(__nv_bfloat16) * in_dim * B);
+  for (int l = 1; l < 4; ++l) {
+    L.h[l] = take(sizeof(__nv_bfloat16) * B * hidden);
+    L.ht[l] = take(sizeof(__nv_bfloat16) * hidden * B);
+  }
+  L.y = take(sizeof(float) * B * out_dim);
+  L.dz = take(sizeof(__nv_bfloat16) * B * (hidden > L.out_pad ? hidden : L.out_pad));
+  L.dzt = take(sizeof(__nv_bfloat16) * B * (hidden > L.out_pad ? hidden : L.out_pad));
+  L.dh = take(sizeof(float) * B * hidden);
+  L.loss = take(sizeof(float) * 4);
+  L.total = o;
+  return L;
+}
+
+cudaError_t mlp_init(const MlpLayout& L, char* base, uint64_t seed, cudaStream_t st) {
+  cudaMemsetAsync(base, 0, L.total, st);
+  for (int l = 0; l < 4; ++l) {
+    const int64_t n = (int64_t)L.dims[l] * L.dims[l + 1];
+    const float bound = 1.0f / sqrtf((float)L.dims[l]);
+    init_uniform<<<grid_of(n), 256, 0, st>>>(reinterpret_cast<float*>(base + L.w[l]), n, bound,
+                                             seed, (uint32_t)l);
+    const int outp = l == 3 ? L.out_pad : L.dims[l + 1];
+    to_bf16<<<grid_of(n), 256, 0, st>>>(reinterpret_cast<float*>(base + L.w[l]), L.dims[l + 1],
+                                        L.dims[l], reinterpret_cast<__nv_bfloat16*>(base + L.wb[l]),
+                                        l == 0 ? nullptr
+                                               : reinterpret_cast<__nv_bfloat16*>(base + L.wt[l]),
+                                        outp);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_forward(const MlpLayout& L, char* base, const __nv_bfloat16* x, int batch,
+                        bool keep_transposes, float* y_out, unsigned int* err, cudaStream_t st) {
+  const __nv_bfloat16* in = x;
+  int in_dim = L.dims[0];
+  cudaError_t e;
+  for (int l = 0; l < 4; ++l) {
+    const int out = L.dims[l + 1];
+    GemmEpilogue ep;
+    ep.kind = kEpiBiasActBF16;
+    ep.bias = reinterpret_cast<const float*>(base + L.b[l]);
+    if (l < 3) {
+      ep.act = kActRelu;
+      ep.out_bf16 = reinterpret_cast<__nv_bfloat16*>(base + L.h[l + 1]);
+      ep.ldc = out;
+      if (keep_transposes) {
+        ep.out_bf16_t = reinterpret_cast<__nv_bfloat16*>(base + L.ht[l + 1]);
+        ep.ldc_t = batch;
+      }
+    } else {
+      ep.act = kActSigmoid;
+      ep.out_f32 = y_out ? y_out : reinterpret_cast<float*>(base + L.y);
+      ep.ldc = out;
+    }
+    e = gemm_bf16(in, in_dim, reinterpret_cast<const __nv_bfloat16*>(base + L.wb[l]), in_dim, batch,
+                  out, in_dim, ep, err, st);
+    if (e != cudaSuccess) return e;
+    in = reinterpret_cast<const __nv_bfloat16*>(base + L.h[l + 1 < 4 ? l + 1 : 3]);
+    in_dim = out;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* x,
+                           const float* target, int batch, float lr, int step, float* loss_out,
+                           unsigned int* err, cudaStream_t st) {
+  if (batch % 8 != 0 || batch > L.max_batch) return cudaErrorInvalidValue;
+  cudaError_t e = mlp_forward(L, base, x, batch, true, nullptr, err, st);
+  if (e != cudaSuccess) return e;
+  __nv_bfloat16* h0t = reinterpret_cast<__nv_bfloat16*>(base + L.h0t);
+  {
+    dim3 g((L.dims[0] + 31) / 32, (batch + 31) / 32), b(32, 8);
+    transpose_bf16<<<g, b, 0, st>>>(x, batch, L.dims[0], h0t);
+  }
+  __nv_bfloat16* dz = reinterpret_cast<__nv_bfloat16*>(base + L.dz);
+  __nv_bfloat16* dzt = reinterpret_cast<__nv_bfloat16*>(base + L.dzt);
+  float* dh = reinterpret_cast<float*>(base + L.dh);
+  float* loss = reinterpret_cast<float*>(base + L.loss);
+  const int P = L.dims[4], Pp = L.out_pad;
+  mse_sigmoid_grad<<<1, 256, 0, st>>>(reinterpret_cast<const float*>(base + L.y), target, batch, P,
+                                      Pp, dz, dzt, loss);
+  if (loss_out) cudaMemcpyAsync(loss_out, loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
+  for (int l = 3; l >= 0; --l) {
+    const int in = L.dims[l], out = L.dims[l + 1];
+    const int ldz = l == 3 ? Pp : out;
+    // bias and weight gradients: dW[out][in] = dZ^T[out][B] * H_{l}^T[in][B]^T
+    bias_grad<<<(out + 255) / 256, 256, 0, st>>>(dz, batch, out, ldz,
+                                                 reinterpret_cast<float*>(base + L.gb[l]));
+    const __nv_bfloat16* hprev_t =
+        l == 0 ? h0t : reinterpret_cast<const __nv_bfloat16*>(base + L.ht[l]);
+    GemmEpilogue ew;
+    ew.kind = kEpiStoreF32;
+    ew.out_f32 = reinterpret_cast<float*>(base + L.gw[l]);
+    ew.ldc = in;
+    if ((e = gemm_bf16(dzt, batch, hprev_t, batch, out, in, batch, ew, err, st)) != cudaSuccess)
+      return e;
+    if (l > 0) {
+      // dH_{l}[B][in] = dZ[B][ldz] * W^T[in][ldz]^T
+      GemmEpilogue eh;
+      eh.kind = kEpiStoreF32;
+      eh.out_f32 = dh;
+      eh.ldc = in;
+      if ((e = gemm_bf16(dz, ldz, reinterpret_cast<const __nv_bfloat16*>(base + L.wt[l]), ldz,
+                         batch, in, ldz, eh, err, st)) != cudaSuccess)
+        return e;
+      relu_grad<<<grid_of((int64_t)batch * in), 256, 0, st>>>(
+          dh, reinterpret_cast<const __nv_bfloat16*>(base + L.h[l]), batch, in, dz, dzt);
+    }
+  }
+  // Adam
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  for (int l = 0; l < 4; ++l) {
+    const int in = L.dims[l], out = L.dims[l + 1];
+    const int outp = l == 3 ? Pp : out;
+    adam_update<<<grid_of((int64_t)in * out), 256, 0, st>>>(
+        reinterpret_cast<float*>(base + L.w[l]), reinterpret_cast<const float*>(base + L.gw[l]),
+        reinterpret_cast<float*>(base + L.mw[l]), reinterpret_cast<float*>(base + L.vw[l]), out, in,
+        lr, b1, b2, eps, c1, c2, reinterpret_cast<__nv_bfloat16*>(base + L.wb[l]),
+        l == 0 ? nullptr : reinterpret_cast<__nv_bfloat16*>(base + L.wt[l]), outp);
+    adam_update<<<grid_of(out), 256, 0, st>>>(
+        reinterpret_cast<float*>(base + L.b[l]), reinterpret_cast<const float*>(base + L.gb[l]),
+        reinterpret_cast<float*>(base + L.mb[l]), reinterpret_cast<float*>(base + L.vb[l]), 1, out,
+        lr, b1, b2, eps, c1, c2, nullptr, nullptr, 0);
+  }
+  return cudaGetLastError();
+}
+
+// Adam on normalized Voice parameters (refinement in parameter space), kept
+// inside [0, 1].
+__global__ void param_adam_kernel(float* u, const float* g, float* m, float* v, int n, float lr,
+                                  float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  u[i] = fminf(fmaxf(u[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f), 0.f), 1.f);
+}
+
+cudaError_t param_adam(float* u, const float* g, float* m, float* v, int n, int step, float lr,
+                       cudaStream_t st) {
+  const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
+  param_adam_kernel<<<(n + 255) / 256, 256, 0, st>>>(u, g, m, v, n, lr, c1, c2);
+  return cudaGetLastError();
+}
+
+}  // namespace synth

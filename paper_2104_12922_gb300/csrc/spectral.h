@@ -1,0 +1,44 @@
+// spectral.h -- STFT-as-GEMM front ends (spectral.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace synth {
+
+constexpr int kMelFFT = 2048;   // log-mel: n_fft 2048, hop 512
+constexpr int kMelBands = 128;
+
+// Centred frames of an N-sample signal at hop n/4.
+int stft_frames(int64_t N, int n_fft);
+
+struct DftTables {
+  int n_fft, nb, rows, ld_bwd;
+  __nv_bfloat16* fwd;  // [rows = 2 nb][n_fft]: (w cos, -w sin) interleaved per bin
+  __nv_bfloat16* bwd;  // [n_fft][ld_bwd]: the same, transposed, zero-padded columns
+};
+size_t dft_bytes(int n_fft);
+DftTables dft_carve(int n_fft, void* mem);
+cudaError_t dft_fill(const DftTables& t, cudaStream_t st);
+
+// Multi-resolution log-magnitude distance between x and y ([batch][N] FP32,
+// device) and its gradient w.r.t. x. loss_voice_out [batch] (device, FP64,
+// may be NULL); grad_x [batch][N] or NULL. With target_ready the tables and
+// the target log-magnitudes left in ws by an earlier call for the same y are
+// reused.
+size_t mrstft_workspace_bytes(int64_t N, int batch, const int* n_ffts, int n_res);
+cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batch,
+                             const int* n_ffts, int n_res, float eps, bool target_ready,
+                             double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
+                             cudaStream_t st);
+
+// Log-mel features [batch][frames][128] (bf16, flattened per voice).
+size_t logmel_workspace_bytes(int64_t N, int batch);
+cudaError_t logmel_init(int64_t N, int batch, double sample_rate, void* ws, cudaStream_t st);
+cudaError_t logmel_features(const float* audio, int64_t N, int batch, void* ws,
+                            __nv_bfloat16* features, unsigned int* err, cudaStream_t st);
+
+}  // namespace synth

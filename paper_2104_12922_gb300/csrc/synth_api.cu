@@ -2,12 +2,16 @@
 // handle lifetime, argument checks, launches, lazy device-error reporting.
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "gemm_tc.h"
 #include "internal.h"
+#include "mlp.h"
+#include "spectral.h"
 #include "synth.h"
 
 using namespace synth;
@@ -244,6 +248,220 @@ synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, con
   return check_cuda(gemm_bf16(static_cast<const __nv_bfloat16*>(a_dev), lda,
                               static_cast<const __nv_bfloat16*>(b_dev), ldb, m, n, k, epi,
                               &hdr->error, static_cast<cudaStream_t>(stream)));
+}
+
+// ---------------------------------------------------------------- MR-STFT
+static const int kMrFFT[3] = {512, 1024, 2048};
+
+synth_status synth_mrstft_workspace_size(synth_handle h, int32_t batch, size_t* bytes) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!bytes || batch < 1) return SYNTH_ERR_ARG;
+  if (h->vc.n_samples < 2048) return SYNTH_ERR_UNSUPPORTED;
+  *bytes = mrstft_workspace_bytes(h->vc.n_samples, batch, kMrFFT, 3);
+  return SYNTH_OK;
+}
+
+synth_status synth_mrstft(synth_handle h, const float* x_dev, const float* y_dev, int32_t batch,
+                          int32_t target_ready, double* loss_voice_dev, float* grad_x_dev,
+                          void* workspace_dev, size_t workspace_bytes, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (batch < 1 || !x_dev || !y_dev || !workspace_dev) return SYNTH_ERR_ARG;
+  if (h->vc.n_samples < 2048) return SYNTH_ERR_UNSUPPORTED;
+  if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return SYNTH_ERR_ARG;
+  if (workspace_bytes < mrstft_workspace_bytes(h->vc.n_samples, batch, kMrFFT, 3))
+    return SYNTH_ERR_ARG;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  return check_cuda(mrstft_loss_grad(x_dev, y_dev, h->vc.n_samples, batch, kMrFFT, 3, 1e-7f,
+                                     target_ready != 0, loss_voice_dev, grad_x_dev, workspace_dev,
+                                     &hdr->error, static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_param_adam(synth_handle h, float* u_dev, const float* grad_dev, float* m_dev,
+                              float* v_dev, int32_t count, int32_t step, float lr, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!u_dev || !grad_dev || !m_dev || !v_dev || count < 1 || step < 1 || !(lr > 0.f))
+    return SYNTH_ERR_ARG;
+  return check_cuda(param_adam(u_dev, grad_dev, m_dev, v_dev, count, step, lr,
+                               static_cast<cudaStream_t>(stream)));
+}
+
+// ------------------------------------------------------------ proposal model
+struct synth_model_s {
+  synth_handle synth = nullptr;
+  MlpLayout L;
+  char* mem = nullptr;        // MlpLayout tensors
+  void* work = nullptr;       // audio, params, features, log-mel workspace
+  float* audio = nullptr;     // [max_batch][N]
+  float* params = nullptr;    // [max_batch][78]
+  __nv_bfloat16* feats = nullptr;  // [max_batch][frames * 128]
+  void* mel_ws = nullptr;
+  int max_batch = 0;
+  int frames = 0;
+  int step = 0;
+};
+
+static const int kHidden = 1024;
+
+synth_status synth_model_create(synth_handle h, int32_t max_batch, uint64_t seed, synth_model* out) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!out || max_batch < 8 || max_batch % 8 != 0 || max_batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (h->vc.n_samples < kMelFFT) return SYNTH_ERR_UNSUPPORTED;
+  *out = nullptr;
+  synth_model m = new (std::nothrow) synth_model_s();
+  if (!m) return SYNTH_ERR_OOM;
+  m->synth = h;
+  m->max_batch = max_batch;
+  m->frames = stft_frames(h->vc.n_samples, kMelFFT);
+  m->L = mlp_layout(m->frames * kMelBands, kHidden, kNumParams, max_batch);
+  const size_t N = (size_t)h->vc.n_samples;
+  const size_t a_bytes = (sizeof(float) * max_batch * N + 255) & ~size_t(255);
+  const size_t p_bytes = (sizeof(float) * max_batch * kNumParams + 255) & ~size_t(255);
+  const size_t f_bytes = (sizeof(__nv_bfloat16) * max_batch * m->frames * kMelBands + 255) & ~size_t(255);
+  const size_t mel_bytes = logmel_workspace_bytes(h->vc.n_samples, max_batch);
+  if (cudaMalloc(reinterpret_cast<void**>(&m->mem), m->L.total) != cudaSuccess) {
+    delete m;
+    return SYNTH_ERR_OOM;
+  }
+  if (cudaMalloc(&m->work, a_bytes + p_bytes + f_bytes + mel_bytes) != cudaSuccess) {
+    cudaFree(m->mem);
+    delete m;
+    return SYNTH_ERR_OOM;
+  }
+  char* w = static_cast<char*>(m->work);
+  m->audio = reinterpret_cast<float*>(w);
+  m->params = reinterpret_cast<float*>(w + a_bytes);
+  m->feats = reinterpret_cast<__nv_bfloat16*>(w + a_bytes + p_bytes);
+  m->mel_ws = w + a_bytes + p_bytes + f_bytes;
+  if (mlp_init(m->L, m->mem, seed, 0) != cudaSuccess ||
+      logmel_init(h->vc.n_samples, max_batch, h->vc.sample_rate, m->mel_ws, 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(m->mem);
+    cudaFree(m->work);
+    delete m;
+    return SYNTH_ERR_CUDA;
+  }
+  *out = m;
+  return SYNTH_OK;
+}
+
+synth_status synth_model_destroy(synth_model m) {
+  if (!m) return SYNTH_ERR_ARG;
+  cudaFree(m->mem);
+  cudaFree(m->work);
+  delete m;
+  return SYNTH_OK;
+}
+
+int64_t synth_model_feature_dim(synth_model m) {
+  return m ? (int64_t)m->frames * kMelBands : -1;
+}
+
+synth_status synth_model_features(synth_model m, const float* audio_dev, int32_t batch,
+                                  void* features_dev, void* stream) {
+  if (!m) return SYNTH_ERR_STATE;
+  if (!audio_dev || !features_dev || batch < 1 || batch > m->max_batch) return SYNTH_ERR_ARG;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(m->synth->scratch);
+  return check_cuda(logmel_features(audio_dev, m->synth->vc.n_samples, batch, m->mel_ws,
+                                    static_cast<__nv_bfloat16*>(features_dev), &hdr->error,
+                                    static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_model_forward(synth_model m, const void* features_dev, int32_t batch,
+                                 float* params_out_dev, void* stream) {
+  if (!m) return SYNTH_ERR_STATE;
+  if (!features_dev || !params_out_dev || batch < 1 || batch > m->max_batch) return SYNTH_ERR_ARG;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(m->synth->scratch);
+  return check_cuda(mlp_forward(m->L, m->mem, static_cast<const __nv_bfloat16*>(features_dev), batch,
+                                false, params_out_dev, &hdr->error,
+                                static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_model_train_features(synth_model m, const void* features_dev,
+                                        const float* target_dev, int32_t batch, float lr,
+                                        float* loss_dev, void* stream) {
+  if (!m) return SYNTH_ERR_STATE;
+  if (!features_dev || !target_dev || batch < 8 || batch % 8 != 0 || batch > m->max_batch ||
+      !(lr > 0.f))
+    return SYNTH_ERR_ARG;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(m->synth->scratch);
+  m->step += 1;
+  return check_cuda(mlp_train_step(m->L, m->mem, static_cast<const __nv_bfloat16*>(features_dev),
+                                   target_dev, batch, lr, m->step, loss_dev, &hdr->error,
+                                   static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_model_train_step(synth_model m, uint64_t seed, uint64_t batch_index,
+                                    int32_t batch, float lr, float* loss_dev, void* stream) {
+  if (!m) return SYNTH_ERR_STATE;
+  if (batch < 8 || batch % 8 != 0 || batch > m->max_batch || !(lr > 0.f)) return SYNTH_ERR_ARG;
+  synth_status s = synth_render(m->synth, seed, batch_index, batch, nullptr, m->audio, m->params,
+                                stream);
+  if (s != SYNTH_OK) return s;
+  s = synth_model_features(m, m->audio, batch, m->feats, stream);
+  if (s != SYNTH_OK) return s;
+  return synth_model_train_features(m, m->feats, m->params, batch, lr, loss_dev, stream);
+}
+
+synth_status synth_propose(synth_handle h, synth_model m, const float* audio_dev, int32_t batch,
+                           float* params_out_dev, void* stream) {
+  if (!valid_handle(h) || !m || m->synth != h) return SYNTH_ERR_STATE;
+  if (!audio_dev || !params_out_dev || batch < 1 || batch > m->max_batch) return SYNTH_ERR_ARG;
+  synth_status s = synth_model_features(m, audio_dev, batch, m->feats, stream);
+  if (s != SYNTH_OK) return s;
+  return synth_model_forward(m, m->feats, batch, params_out_dev, stream);
+}
+
+// which: 0 weights [out][in], 1 biases [out], 2 weight gradients, 3 bias
+// gradients (FP32); layer 0..3.
+static float* model_tensor(synth_model m, int32_t which, int32_t layer, size_t* count) {
+  if (!m || layer < 0 || layer > 3 || which < 0 || which > 3) return nullptr;
+  const size_t in = m->L.dims[layer], out = m->L.dims[layer + 1];
+  const size_t off[4] = {m->L.w[layer], m->L.b[layer], m->L.gw[layer], m->L.gb[layer]};
+  *count = (which == 0 || which == 2) ? in * out : out;
+  return reinterpret_cast<float*>(m->mem + off[which]);
+}
+
+synth_status synth_model_get_tensor(synth_model m, int32_t which, int32_t layer, float* dst_dev,
+                                    size_t count, void* stream) {
+  size_t n = 0;
+  float* src = model_tensor(m, which, layer, &n);
+  if (!src || !dst_dev || count != n) return SYNTH_ERR_ARG;
+  return check_cuda(cudaMemcpyAsync(dst_dev, src, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_model_save(synth_model m, const char* path) {
+  if (!m || !path) return SYNTH_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SYNTH_ERR_CUDA;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return SYNTH_ERR_ARG;
+  std::vector<char> host(m->L.total);
+  bool ok = cudaMemcpy(host.data(), m->mem, m->L.total, cudaMemcpyDeviceToHost) == cudaSuccess;
+  const uint64_t magic = 0x53594e544d4f444cull, total = m->L.total;
+  const int64_t step = m->step;
+  ok = ok && std::fwrite(&magic, 8, 1, f) == 1 && std::fwrite(&total, 8, 1, f) == 1 &&
+       std::fwrite(&step, 8, 1, f) == 1 && std::fwrite(host.data(), 1, host.size(), f) == host.size();
+  std::fclose(f);
+  return ok ? SYNTH_OK : SYNTH_ERR_CUDA;
+}
+
+synth_status synth_model_load(synth_model m, const char* path) {
+  if (!m || !path) return SYNTH_ERR_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return SYNTH_ERR_ARG;
+  uint64_t magic = 0, total = 0;
+  int64_t step = 0;
+  bool ok = std::fread(&magic, 8, 1, f) == 1 && std::fread(&total, 8, 1, f) == 1 &&
+            std::fread(&step, 8, 1, f) == 1 && magic == 0x53594e544d4f444cull &&
+            total == m->L.total;
+  std::vector<char> host(ok ? total : 0);
+  ok = ok && std::fread(host.data(), 1, host.size(), f) == host.size();
+  std::fclose(f);
+  if (!ok) return SYNTH_ERR_ARG;
+  if (cudaMemcpy(m->mem, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
+    return SYNTH_ERR_CUDA;
+  m->step = (int)step;
+  return SYNTH_OK;
 }
 
 synth_status synth_sync(synth_handle h, void* stream) {

@@ -1,0 +1,142 @@
+"""GPU spectral front ends and the learned proposal against the FP64 oracle.
+
+Tolerances follow from the bf16 arithmetic of the tensor-core GEMMs: every
+bf16 operand carries a relative rounding of at most 2^-9, so an energy that
+passes through four bf16 roundings (frames, DFT weights, power, mel
+weights) is within about 1e-2 relative, i.e. 1e-2 in the log domain.
+"""
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2104_12922_gb300 as pkg
+    from paper_2104_12922_gb300 import build as b
+    b.build()
+    return torch, pkg
+
+
+def test_mrstft_loss_and_gradient_match_oracle(env):
+    from oracle import spectral as sp
+    torch, pkg = env
+    syn = pkg.Synth(seconds=0.1, max_batch=2)
+    x, _ = syn.render(1, 0, 2)
+    y, _ = syn.render(2, 0, 2)
+    mr = pkg.MRSTFT(syn, 2)
+    loss, gx = mr(x, y)
+    syn.sync()
+    ref_loss, ref_g = sp.mrstft_loss_and_grad(x.cpu().numpy(), y.cpu().numpy())
+    ref_voice = sp.mrstft_loss(x.cpu().numpy(), y.cpu().numpy(), per_voice=True).numpy()
+    assert np.allclose(loss.cpu().numpy(), ref_voice, rtol=2e-2)
+    g = gx.cpu().numpy().astype(np.float64)
+    cos = float(np.sum(g * ref_g) / np.sqrt(np.sum(g * g) * np.sum(ref_g * ref_g)))
+    assert cos > 0.98
+    assert np.linalg.norm(g - ref_g) <= 0.2 * np.linalg.norm(ref_g)
+    # the target spectra kept in the workspace give the same result
+    loss2, gx2 = mr(x, y, target_ready=True)
+    syn.sync()
+    assert torch.equal(loss, loss2) and torch.equal(gx, gx2)
+    syn.close()
+
+
+def test_logmel_features_match_oracle(env):
+    from oracle import spectral as sp
+    torch, pkg = env
+    syn = pkg.Synth(seconds=1.0, max_batch=8)
+    model = pkg.ProposalModel(syn, max_batch=8, seed=0)
+    audio, _ = syn.render(4, 0, 8)
+    feats = model.features(audio)
+    syn.sync()
+    got = feats.float().cpu().numpy().reshape(8, -1, 128)
+    ref = sp.log_mel(audio.cpu().numpy()).numpy()
+    assert got.shape == ref.shape
+    loud = ref > np.log(1e-3)           # bands well above the log floor
+    err = np.abs(got - ref)
+    assert np.max(err[loud]) < 0.06
+    assert np.median(err) < 0.02
+    model.close()
+    syn.close()
+
+
+def _bf16(t):
+    return t.to(dtype=__import__("torch").bfloat16).float().cpu().numpy().astype(np.float64)
+
+
+def test_mlp_forward_and_gradients_match_oracle(env):
+    from oracle import spectral as sp
+    torch, pkg = env
+    syn = pkg.Synth(seconds=0.25, max_batch=16)
+    model = pkg.ProposalModel(syn, max_batch=16, seed=3)
+    audio, params = syn.render(5, 0, 16)
+    feats = model.features(audio)
+    ws = [model.tensor(0, l) for l in range(4)]
+    bs = [model.tensor(1, l) for l in range(4)]
+    out = model.forward(feats)
+    syn.sync()
+    x = feats.float().cpu().numpy().astype(np.float64)
+    ref = sp.mlp_forward(x, [_bf16(w) for w in ws], [b.cpu().numpy() for b in bs]).numpy()
+    assert np.max(np.abs(out.cpu().numpy() - ref)) < 2e-2
+    # one training step: the gradients it leaves behind against autograd in FP64
+    model.train_features(feats, params, lr=1e-4)
+    syn.sync()
+    _, gw, gb = sp.mlp_loss_and_grads(x, params.cpu().numpy(), [_bf16(w) for w in ws],
+                                      [b.cpu().numpy() for b in bs])
+    for l in range(4):
+        got_w = model.tensor(2, l).cpu().numpy()
+        got_b = model.tensor(3, l).cpu().numpy()
+        for got, want in ((got_w, gw[l]), (got_b, gb[l])):
+            denom = np.linalg.norm(want) + 1e-12
+            assert np.linalg.norm(got - want) / denom < 5e-2, l
+    model.close()
+    syn.close()
+
+
+def test_training_reduces_loss_and_checkpoint_roundtrip(env, tmp_path):
+    torch, pkg = env
+    syn = pkg.Synth(seconds=1.0, max_batch=32)
+    model = pkg.ProposalModel(syn, max_batch=32, seed=1)
+    loss = torch.zeros(1, device="cuda")
+    hist = []
+    for step in range(150):
+        model.train_step(seed=7, batch_index=step, batch=32, lr=3e-4, loss=loss)
+        if step % 10 == 0:
+            syn.sync()
+            hist.append(float(loss.item()))
+    syn.sync()
+    assert np.isfinite(hist).all()
+    assert np.mean(hist[-3:]) < 0.9 * hist[0]
+    audio, _ = syn.render(9, 3, 8)
+    p1 = model.propose(audio)
+    path = str(tmp_path / "model.bin")
+    model.save(path)
+    other = pkg.ProposalModel(syn, max_batch=32, seed=99)
+    other.load(path)
+    p2 = other.propose(audio)
+    syn.sync()
+    assert torch.equal(p1, p2)
+    other.close()
+    model.close()
+    syn.close()
+
+
+def test_param_adam_descends_and_stays_in_range(env):
+    torch, pkg = env
+    syn = pkg.Synth(seconds=0.01, max_batch=1)
+    u = torch.full((78,), 0.5, device="cuda")
+    m = torch.zeros_like(u)
+    v = torch.zeros_like(u)
+    g = torch.linspace(-1, 1, 78, device="cuda")
+    for step in range(1, 200):
+        pkg.param_adam(syn, u, g, m, v, step, 0.01)
+    syn.sync()
+    assert float(u.min()) >= 0.0 and float(u.max()) <= 1.0
+    assert float(u[0]) > 0.99 and float(u[-1]) < 0.01
+    syn.close()
