@@ -25,12 +25,11 @@ static_assert(sizeof(ScratchHeader) == 256, "header is one 256-byte block");
 // Look-back state of one tile (voice, window) for the two scan chains
 // (0: LFO phases, 1: VCO phases), two components each.
 struct TileState {
-  unsigned int flag[2];  // (epoch << 2) | state; state 1 = aggregate, 2 = inclusive
+  unsigned int flag[2];  // (epoch << 2) | 1 once agg[chain] of this launch is published
   unsigned int pad[2];
   double agg[2][2];
-  double inc[2][2];
 };
-static_assert(sizeof(TileState) == 80, "tile state layout");
+static_assert(sizeof(TileState) == 48, "tile state layout");
 
 constexpr unsigned int kErrLookbackTimeout = 1u;
 

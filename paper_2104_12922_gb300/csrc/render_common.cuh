@@ -153,60 +153,57 @@ template <class T> __device__ __forceinline__ T wrap01(T x) { return x - floor(x
 template <> __device__ __forceinline__ float wrap01<float>(float x) { return x - floorf(x); }
 
 // ---------------------------------------------------------------------------
-// Decoupled look-back along one voice's windows (Merrill & Garland's
-// single-pass prefix scan): publish this window's aggregate, add the
-// predecessors' aggregates until one with an inclusive prefix is found,
-// publish the inclusive prefix. Called by one thread. Values are phases in
-// cycles, kept wrapped to [0,1). Every wait is bounded: on timeout the error
-// bit is set in the header and the missing term is taken as 0.
+// Look-back along one voice's windows (after Merrill & Garland's single-pass
+// prefix scan): each window publishes its aggregate as soon as its own block
+// scan is done, then sums the aggregates of all earlier windows of the voice.
+// The sum runs in a fixed order (lane j of warp 0 adds windows j, j+32, ...
+// in turn, then a fixed shuffle tree), so the carry -- and with it the audio
+// -- is bitwise reproducible whatever order the windows finish in; the
+// inclusive-prefix shortcut would make the floating-point association depend
+// on timing. Values are phases in cycles, kept wrapped to [0,1).
+// Every wait is bounded; a timeout sets the error bit in the header, and
+// once the bit is set no wait of any window spins any more (fail fast).
+// Called by all 32 lanes of one warp.
 // ---------------------------------------------------------------------------
-constexpr int kLookbackSpinLimit = 1 << 22;
+constexpr int kLookbackSpinLimit = 1 << 20;
 
 template <class T>
 __device__ inline void lookback(TileState* voice_tiles, int w, int chain, unsigned int epoch,
                                 T own0, T own1, T& ex0, T& ex1, ScratchHeader* hdr) {
+  const int lane = threadIdx.x & 31;
   TileState* me = voice_tiles + w;
   const unsigned int tag = (epoch & 0x3fffffffu) << 2;
-  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> my_flag(me->flag[chain]);
-  if (w == 0) {
-    __stcg(&me->inc[chain][0], (double)own0);
-    __stcg(&me->inc[chain][1], (double)own1);
-    my_flag.store(tag | 2u, cuda::memory_order_release);
-    ex0 = T(0); ex1 = T(0);
-    return;
+  if (lane == 0) {
+    __stcg(&me->agg[chain][0], (double)own0);
+    __stcg(&me->agg[chain][1], (double)own1);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> my_flag(me->flag[chain]);
+    my_flag.store(tag | 1u, cuda::memory_order_release);
   }
-  __stcg(&me->agg[chain][0], (double)own0);
-  __stcg(&me->agg[chain][1], (double)own1);
-  my_flag.store(tag | 1u, cuda::memory_order_release);
   T s0 = T(0), s1 = T(0);
-  for (int j = w - 1; j >= 0; --j) {
+  for (int j = lane; j < w; j += 32) {
     TileState* p = voice_tiles + j;
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> pf(p->flag[chain]);
-    unsigned int f = 0;
-    int spins = 0;
-    for (;;) {
-      f = pf.load(cuda::memory_order_acquire);
-      if ((f & ~3u) == tag && (f & 3u) != 0) break;
-      if (++spins > kLookbackSpinLimit) { f = 0; break; }
+    bool ready = false;
+    for (int spins = 0; spins < kLookbackSpinLimit; ++spins) {
+      const unsigned int f = pf.load(cuda::memory_order_acquire);
+      if (f == (tag | 1u)) { ready = true; break; }
+      if (*(volatile unsigned int*)&hdr->error & kErrLookbackTimeout) break;
       __nanosleep(64);
     }
-    if (f == 0) {
+    if (!ready) {
       atomicOr(&hdr->error, kErrLookbackTimeout);
-      break;
-    }
-    if ((f & 3u) == 2u) {
-      s0 += (T)__ldcg(&p->inc[chain][0]);
-      s1 += (T)__ldcg(&p->inc[chain][1]);
       break;
     }
     s0 += (T)__ldcg(&p->agg[chain][0]);
     s1 += (T)__ldcg(&p->agg[chain][1]);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
   ex0 = wrap01(s0);
   ex1 = wrap01(s1);
-  __stcg(&me->inc[chain][0], (double)wrap01(ex0 + own0));
-  __stcg(&me->inc[chain][1], (double)wrap01(ex1 + own1));
-  my_flag.store(tag | 2u, cuda::memory_order_release);
 }
 
 // End-of-launch bookkeeping of the persistent kernels: the last CTA to finish

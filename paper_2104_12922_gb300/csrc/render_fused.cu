@@ -153,11 +153,13 @@ __global__ void __launch_bounds__(NT) render_fused_kernel(
     }
     double tot0, tot1;
     block_exclusive_scan2<double, NT>(r0, r1, sm.warp_tot, tot0, tot1);
-    if (tid == 0) {
+    if (tid < 32) {
       double e0, e1;
       lookback<double>(vt, w, 0, epoch, wrap01(tot0), wrap01(tot1), e0, e1, hdr);
-      sm.prefix[0] = e0;
-      sm.prefix[1] = e1;
+      if (tid == 0) {
+        sm.prefix[0] = e0;
+        sm.prefix[1] = e1;
+      }
     }
     __syncthreads();
 
@@ -223,11 +225,13 @@ __global__ void __launch_bounds__(NT) render_fused_kernel(
     }
     CarryT t0, t1;
     block_exclusive_scan2<CarryT, NT>(s0, s1, warp_buf<CarryT>(sm), t0, t1);
-    if (tid == 0) {
+    if (tid < 32) {
       CarryT e0, e1;
       lookback<CarryT>(vt, w, 1, epoch, wrap01(t0), wrap01(t1), e0, e1, hdr);
-      sm.prefix[0] = (double)e0;
-      sm.prefix[1] = (double)e1;
+      if (tid == 0) {
+        sm.prefix[0] = (double)e0;
+        sm.prefix[1] = (double)e1;
+      }
     }
     __syncthreads();
     if (tid < nseg) {
