@@ -197,7 +197,10 @@ synth_status synth_model_create(synth_handle h, int32_t max_batch, uint64_t seed
 synth_status synth_model_destroy(synth_model m);
 /* Feature length per voice: frames * 128. */
 int64_t synth_model_feature_dim(synth_model m);
-/* Log-mel features of audio [batch][N] -> features_dev [batch][feature_dim] bf16. */
+/* Network input features of audio [batch][N] -> features_dev
+ * [batch][feature_dim] bf16: (log(mel + 1e-6) + 2.5) / 6 per band and frame
+ * (frames major, bands minor); the fixed affine map keeps the inputs in about
+ * [-2, 2]. */
 synth_status synth_model_features(synth_model m, const float* audio_dev, int32_t batch,
                                   void* features_dev, void* stream);
 /* Network forward on features -> params_out [batch][78] float in (0, 1). */

@@ -20,6 +20,9 @@ LIB_PATH = os.path.join(_HERE, "libsynth.so")
 SYNTH_OK, SYNTH_ERR_ARG, SYNTH_ERR_CUDA, SYNTH_ERR_OOM = 0, 1, 2, 3
 SYNTH_ERR_TIMEOUT, SYNTH_ERR_STATE, SYNTH_ERR_UNSUPPORTED = 4, 5, 6
 SYNTH_CARRY_FP64, SYNTH_CARRY_FP32 = 0, 1
+# Network input features = (log(mel + 1e-6) - FEATURE_SHIFT) / FEATURE_SCALE
+# (the affine map synth_model_features applies; see include/synth.h).
+FEATURE_SHIFT, FEATURE_SCALE = -2.5, 6.0
 
 
 class SynthError(RuntimeError):

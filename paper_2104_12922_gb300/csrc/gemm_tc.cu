@@ -245,12 +245,13 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
           break;
         }
         case kEpiLogBF16: {
-          // features = log(acc + eps) in bf16
+          // features = alpha (log(acc + eps) - shift) in bf16
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int col = col0 + i;
             if (col < N && col < epi.n_valid)
-              epi.out_bf16[(size_t)row * epi.ldc + col] = __float2bfloat16(__logf(v[i] + epi.eps));
+              epi.out_bf16[(size_t)row * epi.ldc + col] =
+                  __float2bfloat16(epi.alpha * (__logf(v[i] + epi.eps) - epi.shift));
           }
           break;
         }

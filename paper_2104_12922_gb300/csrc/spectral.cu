@@ -385,6 +385,8 @@ cudaError_t logmel_features(const float* audio, int64_t N, int batch, void* ws,
   em.ldc = kMelBands;
   em.n_valid = kMelBands;
   em.eps = 1e-6f;
+  em.shift = kFeatureShift;
+  em.alpha = 1.0f / kFeatureScale;
   return gemm_bf16(power, ldp, melfb, ldp, (int)M, kMelBands, ldp, em, err, st);
 }
 

@@ -11,6 +11,11 @@ namespace synth {
 
 constexpr int kMelFFT = 2048;   // log-mel: n_fft 2048, hop 512
 constexpr int kMelBands = 128;
+// Network input = (log(mel + 1e-6) - shift) / scale: a fixed affine map that
+// takes the log floor (-13.8) to about -1.9 and a full-scale tone's bands
+// (about +9) to about +1.9.
+constexpr float kFeatureShift = -2.5f;
+constexpr float kFeatureScale = 6.0f;
 
 // Centred frames of an N-sample signal at hop n/4.
 int stft_frames(int64_t N, int n_fft);

@@ -29,6 +29,7 @@ def test_precision_study_60s(oracle_mod, glide):
     b.build()
     nb = si.precision_patch_nebula(oracle_mod.default_nebula(), SECONDS, MIDI_LO, MIDI_HI, DEPTH)
     u, m01 = si.precision_patch_params(31 if glide else 30, BATCH, MIDI_LO, MIDI_HI, DEPTH, glide)
+    u = u.astype(np.float32).astype(np.float64)  # both sides see the same float32 inputs
     cfg = oracle_mod.default_config(seconds=SECONDS, nebula=nb)
     ref, _ = oracle_mod.render_batch(cfg, 0, 0, BATCH, u_in=u)
     pin = torch.tensor(u, dtype=torch.float32, device="cuda")
