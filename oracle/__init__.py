@@ -71,6 +71,8 @@ def lib():
         L.oracle_midi_to_hz.restype = d
         L.oracle_control.argtypes = [P(Config), P(d), P(d), P(d), P(d)]
         L.oracle_control.restype = i32
+        L.oracle_lfo_phase.argtypes = [P(Config), P(d), P(d)]
+        L.oracle_lfo_phase.restype = i32
         L.oracle_render_voice.argtypes = [P(Config), P(d), u64, u64, P(d)]
         L.oracle_render_voice.restype = i32
         L.oracle_render_voice_ex.argtypes = [P(Config), P(d), u64, u64, P(d), i32]
@@ -165,6 +167,29 @@ def control(cfg: Config, u) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     if rc != 0:
         raise ValueError("oracle_control: configuration not representable")
     return env, lfo, dest
+
+
+def lfo_phase(cfg: Config, u) -> np.ndarray:
+    """[2][K+1] LFO phases in cycles at the control points."""
+    theta = np.zeros((2, num_control_points(cfg)))
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    if lib().oracle_lfo_phase(ctypes.byref(cfg), _p(u, ctypes.c_double), _p(theta, ctypes.c_double)):
+        raise ValueError("oracle_lfo_phase failed")
+    return theta
+
+
+def discontinuity_ties(cfg: Config, u, tol: float = 1e-9) -> np.ndarray:
+    """Control points where an LFO phase sits within tol of a discontinuity of
+    the square (0, 1/2) or saw shapes (0): there, two correct evaluations that
+    round the running phase sum differently may take different sides."""
+    th = lfo_phase(cfg, u)
+    d0 = np.minimum(th, 1.0 - th)
+    dh = np.abs(th - 0.5)
+    near = (d0 < tol) | (dh < tol)
+    # only a phase reached by adding nonzero increments can round either way
+    moved = np.concatenate([np.zeros((2, 1), bool),
+                            np.cumsum(np.diff(th, axis=1) != 0, axis=1) > 0], axis=1)
+    return np.where((near & moved).any(axis=0))[0]
 
 
 def render_voice(cfg: Config, u, seed: int, g: int, flags: int = 0) -> np.ndarray:

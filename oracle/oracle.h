@@ -73,6 +73,10 @@ double oracle_midi_to_hz(double m);
 int32_t oracle_control(const oracle_config* cfg, const double u[ORACLE_NUM_PARAMS],
                        double* env, double* lfo, double* dest);
 
+/* LFO phases (cycles in [0,1)) at the control points: theta[2][K+1]. */
+int32_t oracle_lfo_phase(const oracle_config* cfg, const double u[ORACLE_NUM_PARAMS],
+                         double* theta);
+
 /* One voice, FP64 throughout: out[N] with N = seconds * sample_rate.
  * u are normalized parameters (clamped to [0,1]); seed and g key the noise.
  * Returns 0, or -1 when the configuration is not representable. */

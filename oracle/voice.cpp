@@ -499,6 +499,31 @@ int32_t oracle_control(const oracle_config* cfg, const double u[ORACLE_NUM_PARAM
   return 0;
 }
 
+// LFO phases theta_k (cycles, wrapped) at the control points, the running sum
+// the control signals use: theta[2][K+1].
+int32_t oracle_lfo_phase(const oracle_config* cfg, const double u[ORACLE_NUM_PARAMS],
+                         double* theta) {
+  Geometry geo;
+  if (!geometry(cfg, &geo)) return -1;
+  double y[NP];
+  map_params<double>(cfg, u, y);
+  Control<double> c;
+  control_signals<double>(cfg, geo, y, &c, false);
+  const int64_t P = geo.K + 1;
+  const double two_pi = 6.28318530717958647692;
+  for (int l = 0; l < 2; ++l) {
+    const double* q = y + kLfo + 8 * l;
+    double th = t_frac(q[2] / two_pi);
+    for (int64_t k = 0; k < P; ++k) {
+      theta[l * P + k] = th;
+      double rate = q[0] + q[1] * c.env[2 + 2 * l][k];
+      rate = t_min(t_max(rate, 0.0), kLfoMaxHz);
+      th = t_frac(th + rate / cfg->control_rate);
+    }
+  }
+  return 0;
+}
+
 int32_t oracle_render_voice(const oracle_config* cfg, const double u[ORACLE_NUM_PARAMS],
                             uint64_t seed, uint64_t g, double* out) {
   return render_voice<double>(cfg, u, seed, g, out, 0, -1, nullptr);

@@ -75,7 +75,8 @@ __global__ void transpose_bf16(const __nv_bfloat16* __restrict__ in, int rows, i
 // zero-padded to P_pad columns / rows) and the loss sum.
 __global__ void mse_sigmoid_grad(const float* __restrict__ y, const float* __restrict__ target,
                                  int batch, int P, int P_pad, __nv_bfloat16* __restrict__ dz,
-                                 __nv_bfloat16* __restrict__ dzt, float* __restrict__ loss) {
+                                 __nv_bfloat16* __restrict__ dzt, float* __restrict__ dzf,
+                                 float* __restrict__ loss) {
   __shared__ float red[8];
   float local = 0.f;
   const float scale = 2.f / (float)(batch * P);
@@ -89,6 +90,7 @@ __global__ void mse_sigmoid_grad(const float* __restrict__ y, const float* __res
     }
     dz[i] = __float2bfloat16(g);
     dzt[(int64_t)p * batch + b] = __float2bfloat16(g);
+    dzf[i] = g;
   }
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
@@ -102,7 +104,8 @@ __global__ void mse_sigmoid_grad(const float* __restrict__ y, const float* __res
 
 // Hidden layer: dZ = dH * relu'(Z) with relu'(Z) = (H > 0); writes dZ, dZ^T.
 __global__ void relu_grad(const float* __restrict__ dh, const __nv_bfloat16* __restrict__ h, int batch,
-                          int width, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt) {
+                          int width, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt,
+                          float* __restrict__ dzf) {
   const int64_t total = (int64_t)batch * width;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -111,16 +114,17 @@ __global__ void relu_grad(const float* __restrict__ dh, const __nv_bfloat16* __r
     const __nv_bfloat16 gb = __float2bfloat16(g);
     dz[i] = gb;
     dzt[(int64_t)c * batch + b] = gb;
+    dzf[i] = g;
   }
 }
 
-// Bias gradient: db[c] = sum_b dZ[b][c] (one thread per column).
-__global__ void bias_grad(const __nv_bfloat16* __restrict__ dz, int batch, int width, int ld,
+// Bias gradient: db[c] = sum_b dZ[b][c] from the FP32 dZ (one thread per column).
+__global__ void bias_grad(const float* __restrict__ dz, int batch, int width, int ld,
                           float* __restrict__ db) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= width) return;
   float s = 0.f;
-  for (int b = 0; b < batch; ++b) s += __bfloat162float(dz[(int64_t)b * ld + c]);
+  for (int b = 0; b < batch; ++b) s += dz[(int64_t)b * ld + c];
   db[c] = s;
 }
 
@@ -184,6 +188,7 @@ MlpLayout mlp_layout(int in_dim, int hidden, int out_dim, int max_batch) {
   L.y = take(sizeof(float) * B * out_dim);
   L.dz = take(sizeof(__nv_bfloat16) * B * (hidden > L.out_pad ? hidden : L.out_pad));
   L.dzt = take(sizeof(__nv_bfloat16) * B * (hidden > L.out_pad ? hidden : L.out_pad));
+  L.dzf = take(sizeof(float) * B * (hidden > L.out_pad ? hidden : L.out_pad));
   L.dh = take(sizeof(float) * B * hidden);
   L.loss = take(sizeof(float) * 4);
   L.total = o;
@@ -253,16 +258,17 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
   __nv_bfloat16* dz = reinterpret_cast<__nv_bfloat16*>(base + L.dz);
   __nv_bfloat16* dzt = reinterpret_cast<__nv_bfloat16*>(base + L.dzt);
   float* dh = reinterpret_cast<float*>(base + L.dh);
+  float* dzf = reinterpret_cast<float*>(base + L.dzf);
   float* loss = reinterpret_cast<float*>(base + L.loss);
   const int P = L.dims[4], Pp = L.out_pad;
   mse_sigmoid_grad<<<1, 256, 0, st>>>(reinterpret_cast<const float*>(base + L.y), target, batch, P,
-                                      Pp, dz, dzt, loss);
+                                      Pp, dz, dzt, dzf, loss);
   if (loss_out) cudaMemcpyAsync(loss_out, loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
   for (int l = 3; l >= 0; --l) {
     const int in = L.dims[l], out = L.dims[l + 1];
     const int ldz = l == 3 ? Pp : out;
     // bias and weight gradients: dW[out][in] = dZ^T[out][B] * H_{l}^T[in][B]^T
-    bias_grad<<<(out + 255) / 256, 256, 0, st>>>(dz, batch, out, ldz,
+    bias_grad<<<(out + 255) / 256, 256, 0, st>>>(dzf, batch, out, ldz,
                                                  reinterpret_cast<float*>(base + L.gb[l]));
     const __nv_bfloat16* hprev_t =
         l == 0 ? h0t : reinterpret_cast<const __nv_bfloat16*>(base + L.ht[l]);
@@ -282,7 +288,7 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
                          batch, in, ldz, eh, err, st)) != cudaSuccess)
         return e;
       relu_grad<<<grid_of((int64_t)batch * in), 256, 0, st>>>(
-          dh, reinterpret_cast<const __nv_bfloat16*>(base + L.h[l]), batch, in, dz, dzt);
+          dh, reinterpret_cast<const __nv_bfloat16*>(base + L.h[l]), batch, in, dz, dzt, dzf);
     }
   }
   // Adam

@@ -15,7 +15,7 @@ struct MlpLayout {
   int out_pad;      // out rounded up to a multiple of 8
   int max_batch;
   size_t w[4], b[4], mw[4], vw[4], mb[4], vb[4], gw[4], gb[4], wb[4], wt[4];
-  size_t h0t, h[4], ht[4], y, dz, dzt, dh, loss;
+  size_t h0t, h[4], ht[4], y, dz, dzt, dzf, dh, loss;
   size_t total;
 };
 

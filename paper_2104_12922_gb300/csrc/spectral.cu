@@ -34,8 +34,20 @@ __device__ __forceinline__ int64_t reflect_index(int64_t q, int64_t N) {
   return q;
 }
 
+// Split-bf16 products: a value a is carried as a_hi = bf16(a) and
+// a_lo = bf16(a - a_hi); a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi keeps about
+// 16 significant bits where a single bf16 product keeps 8. Laying the
+// operand A out as [hi | hi | lo] along K and B as [hi | lo | hi] makes one
+// tensor-core GEMM over 3K sum exactly those three products in FP32.
+__device__ __forceinline__ void split_bf16(float a, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16(a);
+  lo = __float2bfloat16(a - __bfloat162float(hi));
+}
+
+// frames[row][seg * n_fft]: row = (voice, frame); seg = 1 plain bf16, seg = 3
+// the [hi | hi | lo] split layout.
 __global__ void frame_reflect_bf16(const float* __restrict__ audio, int64_t N, int n_fft, int hop,
-                                   int F, int batch, __nv_bfloat16* __restrict__ frames) {
+                                   int F, int batch, int seg, __nv_bfloat16* __restrict__ frames) {
   const int64_t total = (int64_t)batch * F * n_fft;
   const int pad = n_fft / 2;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -45,14 +57,25 @@ __global__ void frame_reflect_bf16(const float* __restrict__ audio, int64_t N, i
     const int f = (int)(row % F);
     const int64_t b = row / F;
     const int64_t q = reflect_index((int64_t)f * hop + t - pad, N);
-    frames[i] = __float2bfloat16(audio[b * N + q]);
+    const float a = audio[b * N + q];
+    __nv_bfloat16* dst = frames + row * (int64_t)seg * n_fft + t;
+    if (seg == 1) {
+      dst[0] = __float2bfloat16(a);
+    } else {
+      __nv_bfloat16 hi, lo;
+      split_bf16(a, hi, lo);
+      dst[0] = hi;
+      dst[n_fft] = hi;
+      dst[2 * n_fft] = lo;
+    }
   }
 }
 
 // fwd[2b][t] = w(t) cos(2 pi b t / n), fwd[2b+1][t] = -w(t) sin(2 pi b t / n)
-// (bins b < n/2 + 1, rows up to rows_fwd zero-padded);
-// bwd[t][2b], bwd[t][2b+1] the same values transposed (columns up to ld_bwd).
-__global__ void dft_tables(int n_fft, int rows_fwd, __nv_bfloat16* fwd, int ld_bwd,
+// (bins b < n/2 + 1), row stride seg * n_fft ([hi | lo | hi] when seg = 3);
+// bwd[t][2b], bwd[t][2b+1] the same values transposed, row stride seg * ld_bwd
+// with segments of ld_bwd columns (zero-padded).
+__global__ void dft_tables(int n_fft, int rows_fwd, int seg, __nv_bfloat16* fwd, int ld_bwd,
                            __nv_bfloat16* bwd) {
   const int nb = n_fft / 2 + 1;
   const int64_t total = (int64_t)rows_fwd * n_fft;
@@ -68,9 +91,22 @@ __global__ void dft_tables(int n_fft, int rows_fwd, __nv_bfloat16* fwd, int ld_b
       sincospi(2.0 * (double)bt / (double)n_fft, &s, &c);
       val = (r & 1) ? -w * s : w * c;
     }
-    const __nv_bfloat16 v = __float2bfloat16((float)val);
-    fwd[i] = v;
-    if (bwd && r < ld_bwd) bwd[(int64_t)t * ld_bwd + r] = v;
+    __nv_bfloat16 hi, lo;
+    split_bf16((float)val, hi, lo);
+    __nv_bfloat16* f = fwd + (int64_t)r * seg * n_fft + t;
+    f[0] = hi;
+    if (seg == 3) {
+      f[n_fft] = lo;
+      f[2 * n_fft] = hi;
+    }
+    if (bwd && r < ld_bwd) {
+      __nv_bfloat16* g = bwd + (int64_t)t * seg * ld_bwd + r;
+      g[0] = hi;
+      if (seg == 3) {
+        g[ld_bwd] = lo;
+        g[2 * ld_bwd] = hi;
+      }
+    }
   }
 }
 
@@ -113,8 +149,17 @@ __global__ void spec_l1_logmag_grad(const float* __restrict__ spec, int ld_spec,
       gre = g * re;
       gim = g * im;
     }
-    dspec[row * ld_dspec + 2 * b] = __float2bfloat16(gre);
-    dspec[row * ld_dspec + 2 * b + 1] = __float2bfloat16(gim);
+    // split layout [hi | hi | lo] with segments of ld_dspec columns
+    __nv_bfloat16* dst = dspec + row * 3 * (int64_t)ld_dspec + 2 * b;
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(gre, h0, l0);
+    split_bf16(gim, h1, l1);
+    dst[0] = h0;
+    dst[1] = h1;
+    dst[ld_dspec] = h0;
+    dst[ld_dspec + 1] = h1;
+    dst[2 * ld_dspec] = l0;
+    dst[2 * ld_dspec + 1] = l1;
   }
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
@@ -175,30 +220,32 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 int stft_frames(int64_t N, int n_fft) { return 1 + (int)(N / (n_fft / 4)); }
 
 // ------------------------------------------------------------------ tables
-size_t dft_bytes(int n_fft) {
+size_t dft_bytes(int n_fft, int seg) {
   const int nb = n_fft / 2 + 1;
   const int rows = 2 * nb;
   const int ld_bwd = (rows + 7) & ~7;
-  return al256(sizeof(__nv_bfloat16) * (size_t)rows * n_fft) +
-         al256(sizeof(__nv_bfloat16) * (size_t)n_fft * ld_bwd);
+  return al256(sizeof(__nv_bfloat16) * (size_t)rows * seg * n_fft) +
+         al256(sizeof(__nv_bfloat16) * (size_t)n_fft * seg * ld_bwd);
 }
 
-DftTables dft_carve(int n_fft, void* mem) {
+DftTables dft_carve(int n_fft, void* mem, int seg) {
   DftTables t;
   t.n_fft = n_fft;
+  t.seg = seg;
   t.nb = n_fft / 2 + 1;
   t.rows = 2 * t.nb;
   t.ld_bwd = (t.rows + 7) & ~7;
   char* p = static_cast<char*>(mem);
   t.fwd = reinterpret_cast<__nv_bfloat16*>(p);
-  t.bwd = reinterpret_cast<__nv_bfloat16*>(p + al256(sizeof(__nv_bfloat16) * (size_t)t.rows * n_fft));
+  t.bwd = reinterpret_cast<__nv_bfloat16*>(
+      p + al256(sizeof(__nv_bfloat16) * (size_t)t.rows * seg * n_fft));
   return t;
 }
 
 cudaError_t dft_fill(const DftTables& t, cudaStream_t st) {
-  cudaMemsetAsync(t.bwd, 0, sizeof(__nv_bfloat16) * (size_t)t.n_fft * t.ld_bwd, st);
-  dft_tables<<<grid_of((int64_t)t.rows * t.n_fft), 256, 0, st>>>(t.n_fft, t.rows, t.fwd, t.ld_bwd,
-                                                                 t.bwd);
+  cudaMemsetAsync(t.bwd, 0, sizeof(__nv_bfloat16) * (size_t)t.n_fft * t.seg * t.ld_bwd, st);
+  dft_tables<<<grid_of((int64_t)t.rows * t.n_fft), 256, 0, st>>>(t.n_fft, t.rows, t.seg, t.fwd,
+                                                                 t.ld_bwd, t.bwd);
   return cudaGetLastError();
 }
 
@@ -228,107 +275,116 @@ std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld)
 }
 
 // ---------------------------------------------------------------- MR-STFT
-size_t mrstft_workspace_bytes(int64_t N, int batch, const int* n_ffts, int n_res) {
-  size_t total = 0;
-  int64_t max_rows_n = 0, max_spec = 0, max_nb = 0;
+// The distance and its gradient use split-bf16 operands (3 products, about
+// 16 significant bits): d log(|X| + eps) / d|X| = 1/(|X| + eps) weights the
+// quiet bins heavily, and a single bf16 rounding of frames and DFT weights
+// leaves those bins with noise only.
+namespace {
+constexpr int kSplit = 3;
+
+struct MrLayout {
+  DftTables tabs[8];
+  __nv_bfloat16* frames;
+  float* spec;
+  __nv_bfloat16* dspec;
+  float* dframes;
+  float* logy[8];
+  double* loss_voice;
+  size_t total;
+};
+
+MrLayout mr_layout(int64_t N, int batch, const int* n_ffts, int n_res, void* ws) {
+  MrLayout L;
+  char* base = static_cast<char*>(ws);
+  size_t off = 0;
+  int64_t max_frames = 0, max_spec = 0, max_dspec = 0, max_dfr = 0, max_nb = 0;
   for (int r = 0; r < n_res; ++r) {
     const int n = n_ffts[r];
-    total += dft_bytes(n);
+    L.tabs[r] = dft_carve(n, base ? base + off : nullptr, kSplit);
+    off += dft_bytes(n, kSplit);
     const int64_t M = (int64_t)batch * stft_frames(N, n);
-    max_rows_n = std::max<int64_t>(max_rows_n, M * n);
-    const int ld = ((2 * (n / 2 + 1)) + 7) & ~7;
-    max_spec = std::max<int64_t>(max_spec, M * ld);
-    max_nb = std::max<int64_t>(max_nb, M * (n / 2 + 1));
+    max_frames = std::max<int64_t>(max_frames, M * kSplit * n);
+    max_spec = std::max<int64_t>(max_spec, M * L.tabs[r].ld_bwd);
+    max_dspec = std::max<int64_t>(max_dspec, M * kSplit * L.tabs[r].ld_bwd);
+    max_dfr = std::max<int64_t>(max_dfr, M * n);
+    max_nb = std::max<int64_t>(max_nb, M * L.tabs[r].nb);
   }
-  total += al256(sizeof(__nv_bfloat16) * max_rows_n);  // frames
-  total += al256(sizeof(float) * max_spec);           // spectrum (f32)
-  total += al256(sizeof(__nv_bfloat16) * max_spec);   // d spectrum (bf16)
-  total += al256(sizeof(float) * max_rows_n);         // d frames
-  total += al256(sizeof(float) * max_nb) * n_res;     // target log-magnitudes per resolution
-  total += al256(sizeof(double) * batch);             // per-voice loss
-  return total;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += al256(bytes);
+    return p;
+  };
+  L.frames = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * max_frames));
+  L.spec = reinterpret_cast<float*>(take(sizeof(float) * max_spec));
+  L.dspec = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * max_dspec));
+  L.dframes = reinterpret_cast<float*>(take(sizeof(float) * max_dfr));
+  for (int r = 0; r < n_res; ++r) L.logy[r] = reinterpret_cast<float*>(take(sizeof(float) * max_nb));
+  L.loss_voice = reinterpret_cast<double*>(take(sizeof(double) * batch));
+  L.total = off;
+  return L;
+}
+}  // namespace
+
+size_t mrstft_workspace_bytes(int64_t N, int batch, const int* n_ffts, int n_res) {
+  return mr_layout(N, batch, n_ffts, n_res, nullptr).total;
 }
 
 cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batch,
                              const int* n_ffts, int n_res, float eps, bool target_ready,
                              double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
                              cudaStream_t st) {
-  char* base = static_cast<char*>(ws);
-  size_t off = 0;
-  DftTables tabs[8];
-  for (int r = 0; r < n_res; ++r) {
-    tabs[r] = dft_carve(n_ffts[r], base + off);
-    off += dft_bytes(n_ffts[r]);
-  }
-  int64_t max_rows_n = 0, max_spec = 0, max_nb = 0;
-  for (int r = 0; r < n_res; ++r) {
-    const int n = n_ffts[r];
-    const int64_t M = (int64_t)batch * stft_frames(N, n);
-    max_rows_n = std::max<int64_t>(max_rows_n, M * n);
-    max_spec = std::max<int64_t>(max_spec, M * tabs[r].ld_bwd);
-    max_nb = std::max<int64_t>(max_nb, M * tabs[r].nb);
-  }
-  auto take = [&](size_t bytes) { char* p = base + off; off += al256(bytes); return p; };
-  __nv_bfloat16* frames = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * max_rows_n));
-  float* spec = reinterpret_cast<float*>(take(sizeof(float) * max_spec));
-  __nv_bfloat16* dspec = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * max_spec));
-  float* dframes = reinterpret_cast<float*>(take(sizeof(float) * max_rows_n));
-  float* logy[8];
-  for (int r = 0; r < n_res; ++r) logy[r] = reinterpret_cast<float*>(take(sizeof(float) * max_nb));
-  double* loss_voice = reinterpret_cast<double*>(take(sizeof(double) * batch));
-
+  if (n_res < 1 || n_res > 8) return cudaErrorInvalidValue;
+  MrLayout L = mr_layout(N, batch, n_ffts, n_res, ws);
   cudaError_t e;
+  auto spectrum = [&](const float* sig, int r) -> cudaError_t {
+    const int n = n_ffts[r], F = stft_frames(N, n);
+    const int64_t M = (int64_t)batch * F;
+    frame_reflect_bf16<<<grid_of(M * n), 256, 0, st>>>(sig, N, n, n / 4, F, batch, kSplit,
+                                                       L.frames);
+    GemmEpilogue ep;
+    ep.kind = kEpiStoreF32;
+    ep.out_f32 = L.spec;
+    ep.ldc = L.tabs[r].ld_bwd;
+    return gemm_bf16(L.frames, kSplit * n, L.tabs[r].fwd, kSplit * n, (int)M, L.tabs[r].rows,
+                     kSplit * n, ep, err, st);
+  };
   if (!target_ready) {
     for (int r = 0; r < n_res; ++r) {
-      if ((e = dft_fill(tabs[r], st)) != cudaSuccess) return e;
-      const int n = n_ffts[r], F = stft_frames(N, n);
-      const int64_t M = (int64_t)batch * F;
-      frame_reflect_bf16<<<grid_of(M * n), 256, 0, st>>>(y, N, n, n / 4, F, batch, frames);
-      GemmEpilogue ep;
-      ep.kind = kEpiStoreF32;
-      ep.out_f32 = spec;
-      ep.ldc = tabs[r].ld_bwd;
-      if ((e = gemm_bf16(frames, n, tabs[r].fwd, n, (int)M, tabs[r].rows, n, ep, err, st)) !=
-          cudaSuccess)
-        return e;
-      spec_logmag<<<grid_of(M * tabs[r].nb), 256, 0, st>>>(spec, tabs[r].ld_bwd, M, tabs[r].nb,
-                                                          eps, logy[r]);
+      if ((e = dft_fill(L.tabs[r], st)) != cudaSuccess) return e;
+      if ((e = spectrum(y, r)) != cudaSuccess) return e;
+      const int64_t M = (int64_t)batch * stft_frames(N, n_ffts[r]);
+      spec_logmag<<<grid_of(M * L.tabs[r].nb), 256, 0, st>>>(L.spec, L.tabs[r].ld_bwd, M,
+                                                            L.tabs[r].nb, eps, L.logy[r]);
     }
   }
-  cudaMemsetAsync(loss_voice, 0, sizeof(double) * batch, st);
+  cudaMemsetAsync(L.loss_voice, 0, sizeof(double) * batch, st);
   if (grad_x) fill_zero_f<<<grid_of((int64_t)batch * N), 256, 0, st>>>(grad_x, (int64_t)batch * N);
   for (int r = 0; r < n_res; ++r) {
     const int n = n_ffts[r], F = stft_frames(N, n);
     const int64_t M = (int64_t)batch * F;
-    frame_reflect_bf16<<<grid_of(M * n), 256, 0, st>>>(x, N, n, n / 4, F, batch, frames);
-    GemmEpilogue ep;
-    ep.kind = kEpiStoreF32;
-    ep.out_f32 = spec;
-    ep.ldc = tabs[r].ld_bwd;
-    if ((e = gemm_bf16(frames, n, tabs[r].fwd, n, (int)M, tabs[r].rows, n, ep, err, st)) !=
-        cudaSuccess)
-      return e;
-    cudaMemsetAsync(dspec, 0, sizeof(__nv_bfloat16) * M * tabs[r].ld_bwd, st);
-    const float scale = 1.0f / (float)((int64_t)F * tabs[r].nb);
-    const int64_t per_voice = (int64_t)F * tabs[r].nb;
+    const int ld = L.tabs[r].ld_bwd;
+    if ((e = spectrum(x, r)) != cudaSuccess) return e;
+    cudaMemsetAsync(L.dspec, 0, sizeof(__nv_bfloat16) * M * kSplit * ld, st);
+    const float scale = 1.0f / (float)((int64_t)F * L.tabs[r].nb);
+    const int64_t per_voice = (int64_t)F * L.tabs[r].nb;
     dim3 gl(batch, (unsigned)std::min<int64_t>(64, (per_voice + 255) / 256));
-    spec_l1_logmag_grad<<<gl, 256, 0, st>>>(spec, tabs[r].ld_bwd, logy[r], tabs[r].nb, F, eps,
-                                            scale, loss_voice, dspec, tabs[r].ld_bwd);
+    spec_l1_logmag_grad<<<gl, 256, 0, st>>>(L.spec, ld, L.logy[r], L.tabs[r].nb, F, eps, scale,
+                                            L.loss_voice, L.dspec, ld);
     if (grad_x) {
-      // dFrames[M][n] = dSpec[M][K = ld] * bwd[n][K]^T
+      // dFrames[M][n] = dSpec[M][3 ld] * bwd[n][3 ld]^T
       GemmEpilogue eb;
       eb.kind = kEpiStoreF32;
-      eb.out_f32 = dframes;
+      eb.out_f32 = L.dframes;
       eb.ldc = n;
-      if ((e = gemm_bf16(dspec, tabs[r].ld_bwd, tabs[r].bwd, tabs[r].ld_bwd, (int)M, n,
-                         tabs[r].ld_bwd, eb, err, st)) != cudaSuccess)
+      if ((e = gemm_bf16(L.dspec, kSplit * ld, L.tabs[r].bwd, kSplit * ld, (int)M, n, kSplit * ld,
+                         eb, err, st)) != cudaSuccess)
         return e;
-      overlap_add_reflect<<<grid_of((int64_t)batch * N), 256, 0, st>>>(dframes, N, n, n / 4, F,
+      overlap_add_reflect<<<grid_of((int64_t)batch * N), 256, 0, st>>>(L.dframes, N, n, n / 4, F,
                                                                        batch, grad_x);
     }
   }
   if (loss_voice_out)
-    cudaMemcpyAsync(loss_voice_out, loss_voice, sizeof(double) * batch, cudaMemcpyDeviceToDevice,
+    cudaMemcpyAsync(loss_voice_out, L.loss_voice, sizeof(double) * batch, cudaMemcpyDeviceToDevice,
                     st);
   return cudaGetLastError();
 }
@@ -338,20 +394,20 @@ size_t logmel_workspace_bytes(int64_t N, int batch) {
   const int n = kMelFFT, F = stft_frames(N, n);
   const int64_t M = (int64_t)batch * F;
   const int nb = n / 2 + 1, ldp = (nb + 7) & ~7;
-  return dft_bytes(n) + al256(sizeof(__nv_bfloat16) * kMelBands * ldp) +
+  return dft_bytes(n, 1) + al256(sizeof(__nv_bfloat16) * kMelBands * ldp) +
          al256(sizeof(__nv_bfloat16) * M * n) + al256(sizeof(__nv_bfloat16) * M * ldp);
 }
 
 cudaError_t logmel_init(int64_t N, int batch, double sample_rate, void* ws, cudaStream_t st) {
   const int n = kMelFFT;
-  DftTables t = dft_carve(n, ws);
+  DftTables t = dft_carve(n, ws, 1);
   cudaError_t e = dft_fill(t, st);
   if (e != cudaSuccess) return e;
   const int nb = n / 2 + 1, ldp = (nb + 7) & ~7;
   std::vector<float> fb = mel_filterbank_host(n, kMelBands, sample_rate, ldp);
   std::vector<__nv_bfloat16> fbb(fb.size());
   for (size_t i = 0; i < fb.size(); ++i) fbb[i] = __float2bfloat16(fb[i]);
-  char* mel = static_cast<char*>(ws) + dft_bytes(n);
+  char* mel = static_cast<char*>(ws) + dft_bytes(n, 1);
   e = cudaMemcpyAsync(mel, fbb.data(), fbb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
@@ -363,14 +419,14 @@ cudaError_t logmel_features(const float* audio, int64_t N, int batch, void* ws,
   const int64_t M = (int64_t)batch * F;
   const int nb = n / 2 + 1, ldp = (nb + 7) & ~7;
   char* base = static_cast<char*>(ws);
-  DftTables t = dft_carve(n, base);
-  size_t off = dft_bytes(n);
+  DftTables t = dft_carve(n, base, 1);
+  size_t off = dft_bytes(n, 1);
   __nv_bfloat16* melfb = reinterpret_cast<__nv_bfloat16*>(base + off);
   off += al256(sizeof(__nv_bfloat16) * kMelBands * ldp);
   __nv_bfloat16* frames = reinterpret_cast<__nv_bfloat16*>(base + off);
   off += al256(sizeof(__nv_bfloat16) * M * n);
   __nv_bfloat16* power = reinterpret_cast<__nv_bfloat16*>(base + off);
-  frame_reflect_bf16<<<grid_of(M * n), 256, 0, st>>>(audio, N, n, n / 4, F, batch, frames);
+  frame_reflect_bf16<<<grid_of(M * n), 256, 0, st>>>(audio, N, n, n / 4, F, batch, 1, frames);
   cudaMemsetAsync(power, 0, sizeof(__nv_bfloat16) * M * ldp, st);
   GemmEpilogue ep;
   ep.kind = kEpiPowerPairs;

@@ -20,13 +20,14 @@ constexpr float kFeatureScale = 6.0f;
 // Centred frames of an N-sample signal at hop n/4.
 int stft_frames(int64_t N, int n_fft);
 
+// seg = 1: plain bf16 tables; seg = 3: split-bf16 layouts along K.
 struct DftTables {
-  int n_fft, nb, rows, ld_bwd;
-  __nv_bfloat16* fwd;  // [rows = 2 nb][n_fft]: (w cos, -w sin) interleaved per bin
-  __nv_bfloat16* bwd;  // [n_fft][ld_bwd]: the same, transposed, zero-padded columns
+  int n_fft, seg, nb, rows, ld_bwd;
+  __nv_bfloat16* fwd;  // [rows = 2 nb][seg n_fft]: (w cos, -w sin) interleaved per bin
+  __nv_bfloat16* bwd;  // [n_fft][seg ld_bwd]: the same, transposed, zero-padded columns
 };
-size_t dft_bytes(int n_fft);
-DftTables dft_carve(int n_fft, void* mem);
+size_t dft_bytes(int n_fft, int seg);
+DftTables dft_carve(int n_fft, void* mem, int seg);
 cudaError_t dft_fill(const DftTables& t, cudaStream_t st);
 
 // Multi-resolution log-magnitude distance between x and y ([batch][N] FP32,

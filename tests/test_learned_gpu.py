@@ -77,13 +77,13 @@ def test_logmel_features_match_oracle(env):
     got = feats.float().cpu().numpy().reshape(8, -1, 128) * pkg.FEATURE_SCALE + pkg.FEATURE_SHIFT
     ref = sp.log_mel(audio.cpu().numpy()).numpy()
     assert got.shape == ref.shape
-    # bf16 frames carry rounding noise about 2^-9 below each sample, so bands
-    # more than ~40 dB under the frame's loudest band are noise-limited;
-    # compare the bands within 40 dB of it
-    loud = ref > (ref.max(axis=2, keepdims=True) - np.log(1e4))
+    # bf16 frames and DFT weights carry a relative rounding of 2^-9, which
+    # leaves a noise floor in every bin about 50 dB under the frame energy;
+    # bands within 30 dB of the voice's loudest band sit well above it
+    loud = ref > (ref.max(axis=(1, 2), keepdims=True) - np.log(1e3))
     err = np.abs(got - ref)
     assert np.max(err[loud]) < 0.06
-    assert np.median(err[loud]) < 0.02
+    assert np.median(err[loud]) < 0.01
     model.close()
     syn.close()
 
@@ -114,32 +114,41 @@ def test_mlp_forward_and_gradients_match_oracle(env):
     for l in range(4):
         got_w = model.tensor(2, l).cpu().numpy()
         got_b = model.tensor(3, l).cpu().numpy()
-        for got, want in ((got_w, gw[l]), (got_b, gb[l])):
+        # bf16 GEMM operands (activations, dZ) round at 2^-9 relative; the
+        # weight gradients sum 16 such products, the bias gradients use FP32 dZ
+        for got, want, tol in ((got_w, gw[l], 0.1), (got_b, gb[l], 0.05)):
             denom = np.linalg.norm(want) + 1e-12
-            assert np.linalg.norm(got - want) / denom < 5e-2, l
+            assert np.linalg.norm(got - want) / denom < tol, l
     model.close()
     syn.close()
 
 
-def test_training_reduces_loss_and_checkpoint_roundtrip(env, tmp_path):
+def test_training_learns_pitch_and_checkpoint_roundtrip(env, tmp_path):
+    """On-the-fly training (1 s voices, batch 64, training split) makes the
+    proposal's midi-f0 estimate on held-out test voices clearly better than
+    the best constant guess (MSE 1/12 for a uniform parameter); a saved and
+    reloaded model proposes identical parameters."""
     torch, pkg = env
-    syn = pkg.Synth(seconds=1.0, max_batch=32)
-    model = pkg.ProposalModel(syn, max_batch=32, seed=1)
-    loss = torch.zeros(1, device="cuda")
-    hist = []
-    for step in range(150):
-        model.train_step(seed=7, batch_index=step, batch=32, lr=3e-4, loss=loss)
-        if step % 10 == 0:
-            syn.sync()
-            hist.append(float(loss.item()))
+    from paper_2104_12922_gb300 import proposal as pr
+    syn = pkg.Synth(seconds=1.0, max_batch=64)
+    model = pkg.ProposalModel(syn, max_batch=64, seed=1)
+    pr.train(model, 1500, batch=64, lr=1e-3, log_every=500)
+    it = pr.test_batches(64)
+    errs = []
+    for _ in range(4):
+        b = next(it)
+        audio, u = syn.render(0, b, 64)
+        prop = model.propose(audio)
+        errs.append(((prop - u) ** 2).mean(dim=0).cpu().numpy())
     syn.sync()
-    assert np.isfinite(hist).all()
-    assert np.mean(hist[-3:]) < 0.9 * hist[0]
+    mse = np.mean(errs, axis=0)
+    assert np.all(np.isfinite(mse))
+    assert mse[si.MIDI] < 0.5 / 12.0, mse[si.MIDI]
     audio, _ = syn.render(9, 3, 8)
     p1 = model.propose(audio)
     path = str(tmp_path / "model.bin")
     model.save(path)
-    other = pkg.ProposalModel(syn, max_batch=32, seed=99)
+    other = pkg.ProposalModel(syn, max_batch=64, seed=99)
     other.load(path)
     p2 = other.propose(audio)
     syn.sync()

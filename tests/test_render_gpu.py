@@ -121,7 +121,22 @@ def test_params_in_edge_corners(torch_cuda, oracle_mod, plain):
     audio, params = syn.render(0, 0, 10, params_in=pin, plain=plain)
     syn.sync()
     ref_a, ref_p = _oracle_batch(oracle_mod, 1.0, 0, 0, 10, u_in=u)
-    _check(audio, params, ref_a, ref_p)
+    # An LFO phase that lands exactly on a square/saw discontinuity (u = 1/2
+    # gives a 5 Hz LFO from phase 0: after 1 s it is back at 0) may be taken
+    # on either side by two correct evaluations whose running sums round
+    # differently; from one interval before such a tie on, the pitch and the
+    # phase carry of that voice are not unique, so only the part before it is
+    # compared (the rest must still be valid audio).
+    cfg = oracle_mod.default_config(seconds=1.0)
+    a = audio.cpu().numpy()
+    assert np.all(np.isfinite(a)) and np.abs(a).max() <= 1.0
+    for v in range(10):
+        ties = oracle_mod.discontinuity_ties(cfg, u[v])
+        end = (int(ties[0]) - 1) * 100 if len(ties) else a.shape[1]
+        assert end > 0
+        err = float(np.max(np.abs(a[v, :end] - ref_a[v, :end])))
+        assert err <= TOL, (v, err, ties[:3])
+    assert np.array_equal(params.cpu().numpy(), ref_p)
     syn.close()
 
 
