@@ -33,7 +33,7 @@ static_assert(sizeof(TileState) == 48, "tile state layout");
 
 constexpr unsigned int kErrLookbackTimeout = 1u;
 
-constexpr int kFusedThreads = 256;
+constexpr int kFusedThreads = 384;  // 4 control warps + 8 audio warps
 constexpr int kFusedTileSeg = 128;  // control intervals per tile of the fused kernel
 
 inline int windows_per_voice(int K) { return (K + kFusedTileSeg - 1) / kFusedTileSeg; }

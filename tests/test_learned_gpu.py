@@ -114,9 +114,10 @@ def test_mlp_forward_and_gradients_match_oracle(env):
     for l in range(4):
         got_w = model.tensor(2, l).cpu().numpy()
         got_b = model.tensor(3, l).cpu().numpy()
-        # bf16 GEMM operands (activations, dZ) round at 2^-9 relative; the
-        # weight gradients sum 16 such products, the bias gradients use FP32 dZ
-        for got, want, tol in ((got_w, gw[l], 0.1), (got_b, gb[l], 0.05)):
+        # bf16 GEMM operands (activations, dZ, W) round at 2^-9 relative and
+        # the batch sums cancel: weight gradients sum 16 bf16 products, hidden
+        # bias gradients sum dH, which itself comes out of a bf16 GEMM
+        for got, want, tol in ((got_w, gw[l], 0.1), (got_b, gb[l], 0.1)):
             denom = np.linalg.norm(want) + 1e-12
             assert np.linalg.norm(got - want) / denom < tol, l
     model.close()
