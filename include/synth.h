@@ -229,6 +229,30 @@ synth_status synth_model_get_tensor(synth_model m, int32_t which, int32_t layer,
 synth_status synth_model_save(synth_model m, const char* path);
 synth_status synth_model_load(synth_model m, const char* path);
 
+/* The fused render without a handle and without any device allocation, for
+ * callers that cannot call cudaMalloc (a plugin whose host application owns
+ * all device memory, a process that reserved the whole GPU up front, or a
+ * path where an allocation would synchronize the device). The paper has no
+ * counterpart to this entry point.
+ *  cfg: as for synth_create (max_batch is ignored); seed, batch_index,
+ *  params_in_dev, audio_dev, params_out_dev, stream: as for synth_render,
+ *  with the same results.
+ * Scratch: a fixed 256 KiB device array inside the library, which every GPU
+ * that loads the library holds until the process exits. It needs
+ * 256 + 48 * batch * ceil(ceil(seconds * sample_rate / R) / 128) bytes
+ * (R = sample_rate / control_rate); for 4 s at 44.1 kHz that allows batch
+ * <= 389. Larger requests return SYNTH_ERR_ARG before any launch.
+ * The first call on a device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the one array and each clears the part it uses: calls
+ * whose kernels overlap on the GPU (other streams, other threads) race and
+ * must be serialized by the caller. A device-side wait that gives up is not
+ * reported by this entry point (it has no handle to record it in).
+ * Errors: SYNTH_ERR_ARG, SYNTH_ERR_UNSUPPORTED, SYNTH_ERR_CUDA. */
+synth_status synth_render_noalloc(const synth_config* cfg, uint64_t seed, uint64_t batch_index,
+                                  int32_t batch, const float* params_in_dev, float* audio_dev,
+                                  float* params_out_dev, void* stream);
+
 /* Waits for the stream, then reports (and clears) a device-side error
  * recorded by any earlier call on this handle: SYNTH_ERR_TIMEOUT if a bounded
  * wait gave up, SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. */
