@@ -59,9 +59,11 @@ typedef struct {
   int32_t symmetric[SYNTH_NUM_PARAMS];
 } synth_nebula;
 
-/* Phase-scan carry precision (precision study). */
-#define SYNTH_CARRY_FP64 0  /* default: FP64 carry and per-segment offsets */
-#define SYNTH_CARRY_FP32 1  /* study only: carry and offsets rounded to FP32 */
+/* Precision of the VCO phase running sums (precision study). */
+#define SYNTH_CARRY_FIXED64 0 /* default: 64-bit fixed-point phases (2^-64 cycle
+                                 resolution, exact sums mod 1, finer than FP64) */
+#define SYNTH_CARRY_FP32 1    /* study only: interval phases summed and carried
+                                 in FP32 */
 
 typedef struct {
   double sample_rate;   /* Hz; Sec. 3.1 default 44100 */
@@ -69,12 +71,12 @@ typedef struct {
                            must be an integer multiple of 4 */
   double seconds;       /* voice length; Abstract: 4 s */
   int32_t max_batch;    /* largest batch any call on this handle will use */
-  int32_t carry;        /* SYNTH_CARRY_FP64 (default) or SYNTH_CARRY_FP32 */
+  int32_t carry;        /* SYNTH_CARRY_FIXED64 (default) or SYNTH_CARRY_FP32 */
   const synth_nebula* nebula; /* NULL = the library's default nebula n0;
                                  otherwise copied at create */
 } synth_config;
 
-/* Defaults: 44100 Hz, 441 Hz, 4 s, max_batch 128, FP64 carry, nebula n0. */
+/* Defaults: 44100 Hz, 441 Hz, 4 s, max_batch 128, fixed-point carry, nebula n0. */
 void synth_default_config(synth_config* out);
 
 /* The library's default nebula n0 (its own choice of ranges and curves; the
@@ -239,9 +241,9 @@ synth_status synth_model_load(synth_model m, const char* path);
  *  with the same results.
  * Scratch: a fixed 256 KiB device array inside the library, which every GPU
  * that loads the library holds until the process exits. It needs
- * 256 + 48 * batch * ceil(ceil(seconds * sample_rate / R) / 128) bytes
+ * 256 + 48 * batch * ceil(ceil(seconds * sample_rate / R) / 255) bytes
  * (R = sample_rate / control_rate); for 4 s at 44.1 kHz that allows batch
- * <= 389. Larger requests return SYNTH_ERR_ARG before any launch.
+ * <= 779. Larger requests return SYNTH_ERR_ARG before any launch.
  * The first call on a device (with that device current) looks up the
  * array's device address; make that first call before any stream capture.
  * All calls share the one array and each clears the part it uses: calls

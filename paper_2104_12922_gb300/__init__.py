@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libsynth.so")
 
 SYNTH_OK, SYNTH_ERR_ARG, SYNTH_ERR_CUDA, SYNTH_ERR_OOM = 0, 1, 2, 3
 SYNTH_ERR_TIMEOUT, SYNTH_ERR_STATE, SYNTH_ERR_UNSUPPORTED = 4, 5, 6
-SYNTH_CARRY_FP64, SYNTH_CARRY_FP32 = 0, 1
+SYNTH_CARRY_FIXED64, SYNTH_CARRY_FP32 = 0, 1
 # Network input features = (log(mel + 1e-6) - FEATURE_SHIFT) / FEATURE_SCALE
 # (the affine map synth_model_features applies; see include/synth.h).
 FEATURE_SHIFT, FEATURE_SCALE = -2.5, 6.0
@@ -214,7 +214,7 @@ class Synth:
     """
 
     def __init__(self, seconds: float = 4.0, sample_rate: float = 44100.0,
-                 control_rate: float = 441.0, max_batch: int = 128, carry: int = SYNTH_CARRY_FP64,
+                 control_rate: float = 441.0, max_batch: int = 128, carry: int = SYNTH_CARRY_FIXED64,
                  nebula: dict | None = None):
         import torch
         if not torch.cuda.is_available():

@@ -5,8 +5,8 @@
 // pitch in midi and the phase advanced over each control interval -- is
 // computed in float-float (about 48 bits), because a pitch error that holds
 // over many intervals integrates into phase drift: at 4 s and 10 kHz a
-// relative frequency error of 1e-8 is already 4e-4 cycles. Running sums
-// across intervals (the scan carries) are FP64.
+// relative frequency error of 1e-8 is already 4e-4 cycles. Running sums of
+// phases across intervals are 64-bit fixed point (ff.cuh).
 #pragma once
 
 #include "ff.cuh"
@@ -16,20 +16,33 @@
 namespace synth {
 
 // Per-voice constants of the control chain, derived once per tile from the
-// FP64 human-range parameters y.
+// human-range parameters y (float-float).
 struct VoiceFF {
   ff a[6], dc[6], s[6], r[6], alpha[6];
   ff inv_a[6], inv_dc[6], inv_r[6];
   ff level_d[6];      // gate-on level at note-off
   ff dur;             // note-on duration d
   ff lfo_freq[2], lfo_depth[2];
-  ff lfo_w[2][5];
-  ff lfo_inv_wsum[2]; // 1 / sum of shape weights (0 if the sum is < 1e-12)
-  ff mod_w[4][5];
+  ff lfo_w[2][4];     // sine, triangle, saw (saw minus reverse saw), square weights over their sum
+  int lfo_on[2];      // the shape weights sum to at least 1e-12
+  ff mod_w[4][5];     // modulation weight [source][destination]
   ff inv_norm[5];     // 1 / max(1, column sum of modulation weights)
   ff pitch_base[2];   // midi f0 + tune, per VCO
   ff depth[2];        // pitch modulation depth (semitones), per VCO
+  ff pitch_w[2][4];   // depth_o w[s][d_o] / norm[d_o]: VCO o pitch = base + sum_s pitch_w src_s
+  float amp_w[3][4];  // w[s][d] / norm[d] for the sine, square-saw and noise amplitudes
 };
+
+// Copies the argument-reduction tables (a kernel parameter) into shared
+// memory; every thread of the block takes part, the caller synchronizes.
+__device__ __forceinline__ void load_tables(FFTables& dst, const FFTables& src) {
+  static_assert(sizeof(FFTables) % 16 == 0, "tables copy as 16-byte vectors");
+  const float4* a = reinterpret_cast<const float4*>(&src);
+  float4* b = reinterpret_cast<float4*>(&dst);
+  const int n = (int)(sizeof(FFTables) / 16);
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  for (int i = threadIdx.x; i < n; i += nt) b[i] = a[i];
+}
 
 // Sec. 3.1 ADSR at time t: the section is chosen first, then one x^alpha.
 // Section boundaries are continuous, so a comparison that rounds the other
@@ -66,46 +79,59 @@ __device__ __forceinline__ ff gate_level_ff(int i, const VoiceFF& V, const FFTab
   return V.s[i];
 }
 
-// Fills VoiceFF from y (FP64). `part` selects which slice this thread fills
-// so that the work spreads over several threads; call with part = 0..15.
-__device__ inline void voice_ff_fill(VoiceFF& V, const double* y, int part) {
+// Fills VoiceFF from y (float-float). `part` selects which slice this thread
+// fills so that the work spreads over several threads; call with part = 0..15.
+__device__ inline void voice_ff_fill(VoiceFF& V, const ff* y, int part) {
   if (part < 6) {
     const int i = part;
-    const double* q = y + kAdsr + 5 * i;
-    V.a[i] = ff_from_double(q[0]);
-    V.dc[i] = ff_from_double(q[1]);
-    V.s[i] = ff_from_double(q[2]);
-    V.r[i] = ff_from_double(q[3]);
-    V.alpha[i] = ff_from_double(q[4]);
-    V.inv_a[i] = ff_from_double(1.0 / q[0]);
-    V.inv_dc[i] = ff_from_double(1.0 / q[1]);
-    V.inv_r[i] = ff_from_double(1.0 / q[3]);
+    const ff* q = y + kAdsr + 5 * i;
+    V.a[i] = q[0];
+    V.dc[i] = q[1];
+    V.s[i] = q[2];
+    V.r[i] = q[3];
+    V.alpha[i] = q[4];
+    V.inv_a[i] = ff_rcp(q[0]);
+    V.inv_dc[i] = ff_rcp(q[1]);
+    V.inv_r[i] = ff_rcp(q[3]);
   } else if (part < 8) {
     const int l = part - 6;
-    const double* q = y + kLfo + 8 * l;
-    V.lfo_freq[l] = ff_from_double(q[0]);
-    V.lfo_depth[l] = ff_from_double(q[1]);
-    double ws = 0.0;
-    for (int s = 0; s < 5; ++s) {
-      V.lfo_w[l][s] = ff_from_double(q[3 + s]);
-      ws += q[3 + s];
-    }
-    V.lfo_inv_wsum[l] = ff_from_double(ws < 1e-12 ? 0.0 : 1.0 / ws);
+    const ff* q = y + kLfo + 8 * l;
+    V.lfo_freq[l] = q[0];
+    V.lfo_depth[l] = q[1];
+    ff ws = q[3];
+    for (int s = 1; s < 5; ++s) ws = ff_add(ws, q[3 + s]);
+    V.lfo_on[l] = ws.hi >= 1e-12f;
+    const ff inv = V.lfo_on[l] ? ff_rcp(ws) : ff_make(0.f);
+    V.lfo_w[l][0] = ff_mul(q[3], inv);
+    V.lfo_w[l][1] = ff_mul(q[4], inv);
+    V.lfo_w[l][2] = ff_mul(ff_sub(q[5], q[6]), inv);
+    V.lfo_w[l][3] = ff_mul(q[7], inv);
   } else if (part < 13) {
     const int j = part - 8;
-    double ws = 0.0;
-    for (int i = 0; i < 4; ++i) {
-      V.mod_w[i][j] = ff_from_double(y[kMod + 5 * i + j]);
-      ws += y[kMod + 5 * i + j];
+    ff ws = y[kMod + j];
+    V.mod_w[0][j] = ws;
+    for (int i = 1; i < 4; ++i) {
+      V.mod_w[i][j] = y[kMod + 5 * i + j];
+      ws = ff_add(ws, y[kMod + 5 * i + j]);
     }
-    V.inv_norm[j] = ff_from_double(1.0 / fmax(1.0, ws));
+    V.inv_norm[j] = ff_lt(ws, ff_make(1.f)) ? ff_make(1.f) : ff_rcp(ws);
+    if (j == 1 || j == 3 || j == 4) {
+      const int k = j == 1 ? 0 : (j == 3 ? 1 : 2);
+      for (int i = 0; i < 4; ++i)
+        V.amp_w[k][i] = ff_to_float(ff_mul(y[kMod + 5 * i + j], V.inv_norm[j]));
+    }
   } else if (part < 15) {
     const int o = part - 13;
     const int base = o == 0 ? kSine : kSqr;
-    V.pitch_base[o] = ff_add(ff_from_double(y[kMidi]), ff_from_double(y[base]));
-    V.depth[o] = ff_from_double(y[base + 1]);
+    const int d = o == 0 ? 0 : 2;
+    V.pitch_base[o] = ff_add(y[kMidi], y[base]);
+    V.depth[o] = y[base + 1];
+    ff ws = y[kMod + d];
+    for (int i = 1; i < 4; ++i) ws = ff_add(ws, y[kMod + 5 * i + d]);
+    const ff scale = ff_lt(ws, ff_make(1.f)) ? y[base + 1] : ff_mul(y[base + 1], ff_rcp(ws));
+    for (int i = 0; i < 4; ++i) V.pitch_w[o][i] = ff_mul(y[kMod + 5 * i + d], scale);
   } else {
-    V.dur = ff_from_double(y[kDuration]);
+    V.dur = y[kDuration];
   }
 }
 
@@ -113,16 +139,16 @@ __device__ inline void voice_ff_fill(VoiceFF& V, const double* y, int part) {
 // saw 2p - 1, reverse saw 1 - 2p, square sign(1/2 - p) (+1 at p < 1/2),
 // mixed by weight over the weight sum, times the amplitude envelope.
 __device__ __forceinline__ ff lfo_ff(ff p, int l, ff env_amp, const VoiceFF& V, const FFTables& T) {
-  if (V.lfo_inv_wsum[l].hi == 0.f) return ff_make(0.f);
+  if (!V.lfo_on[l]) return ff_make(0.f);
   const ff sn = ff_sin2pi(p, T);
   const ff saw = ff_add_f(ff_ldexp(p, 1), -1.f);
   const ff tri = ff_add_f(ff_ldexp(ff_neg(ff_abs(ff_add_f(p, -0.5f))), 2), 1.f);
   const float sqr = ff_lt(p, ff_make(0.5f)) ? 1.f : -1.f;
   ff acc = ff_mul(V.lfo_w[l][0], sn);
   acc = ff_add(acc, ff_mul(V.lfo_w[l][1], tri));
-  acc = ff_add(acc, ff_mul(ff_sub(V.lfo_w[l][2], V.lfo_w[l][3]), saw));
-  acc = ff_add(acc, ff_mul_f(V.lfo_w[l][4], sqr));
-  return ff_mul(env_amp, ff_mul(acc, V.lfo_inv_wsum[l]));
+  acc = ff_add(acc, ff_mul(V.lfo_w[l][2], saw));
+  acc = ff_add(acc, ff_mul_f(V.lfo_w[l][3], sqr));
+  return ff_mul(env_amp, acc);
 }
 
 // Per-VCO phase increment (cycles per sample) at pitch m (midi), uncapped:
@@ -137,22 +163,33 @@ __device__ __forceinline__ ff inc_at_ff(ff m, ff log2_440_over_sr, const FFTable
 __device__ __forceinline__ ff geo_sum_ff(ff c, ff x, int k, const FFTables& T) {
   if (k <= 0) return ff_make(0.f);
   if (x.hi == 0.f) return ff_mul_f(c, (float)k);
-  return ff_mul(c, ff_div(ff_expm1(ff_mul_f(x, (float)k), T), ff_expm1(x, T)));
+  return ff_mul(c, ff_mul(ff_expm1(ff_mul_f(x, (float)k), T), ff_rcp(ff_expm1(x, T))));
 }
 
 // The description (SegVco) of how a VCO's phase advances over one control
 // interval of Rk samples, from the pitch at its two control points; returns
-// the phase advanced (cycles). Sample j of the interval has pitch
-// m_a + (j / R)(m_b - m_a), capped at the Nyquist pitch.
-__device__ inline double vco_interval_ff(ff m_a, ff m_b, int R, int Rk, ff inv_R, ff ln2_12R,
-                                         ff m_nyq, ff log2_440_over_sr, const FFTables& T,
-                                         SegVco* out) {
+// the phase advanced (cycles) and, in *inc_first, the increment of the
+// interval's first sample (cycles per sample, capped at 1/2). Sample j of the
+// interval has pitch m_a + (j / R)(m_b - m_a), capped at the Nyquist pitch.
+__device__ inline ff vco_interval_ff(ff m_a, ff m_b, int R, int Rk, ff inv_R, ff ln2_12R,
+                                     ff m_nyq, ff log2_440_over_sr, const FFTables& T,
+                                     SegVco* out, float* inc_first) {
   const ff dm = ff_sub(m_b, m_a);
   const ff x = ff_mul(dm, ln2_12R);
   auto capped = [&](int j) {
     return ff_gt(ff_add(m_a, ff_mul(dm, ff_mul_f(inv_R, (float)j))), m_nyq);
   };
-  const bool c_first = capped(0), c_last = capped(Rk - 1);
+  // The pitch is linear between the two points: when both lie clearly on one
+  // side of the cap, so does every sample of the interval.
+  bool c_first, c_last;
+  const float top = fmaxf(m_a.hi, m_b.hi), bot = fminf(m_a.hi, m_b.hi);
+  if (top < m_nyq.hi - 1e-3f) {
+    c_first = false; c_last = false;
+  } else if (bot > m_nyq.hi + 1e-3f) {
+    c_first = true; c_last = true;
+  } else {
+    c_first = capped(0); c_last = capped(Rk - 1);
+  }
   int jc;
   bool a_lin, b_lin;
   ff cA, cB, LB, total;
@@ -187,15 +224,39 @@ __device__ inline double vco_interval_ff(ff m_a, ff m_b, int R, int Rk, ff inv_R
   }
   const float xf = x.hi;
   const bool tiny = fabsf(xf) < 1e-30f;
+  const float e1 = tiny ? 0.f : expm1f(xf);
   out->cA = cA.hi + cA.lo;
   out->cB = cB.hi + cB.lo;
   out->LB = LB.hi + LB.lo;
   out->x = xf;
-  out->E1 = tiny ? 0.f : expm1f(xf);
-  out->invE = tiny ? 0.f : 1.0f / expm1f(xf);
+  out->E1 = e1;
+  out->invE = tiny ? 0.f : 1.0f / e1;
   out->jc_flags = jc | ((a_lin || tiny) ? 1 << 16 : 0) | ((b_lin || tiny) ? 1 << 17 : 0) |
                   (c_first ? 1 << 18 : 0) | (c_last ? 1 << 19 : 0);
-  return ff_to_double(total);
+  *inc_first = out->cA;
+  return total;
+}
+
+// Sec. 3.3 range map in float-float from a normalized parameter u in [0, 1]:
+// y = base + scale a^c, with a = u (scale = hi - lo, base = lo) or, for a
+// symmetric parameter, a = |2u - 1| signed by 2u - 1 (scale = (hi - lo)/2,
+// base = lo + scale). Curves 1, 2, 3 use exact products.
+__device__ inline ff range_map_ff(float u, ff base, ff scale, ff curve, int code, int sym,
+                                  const FFTables& T) {
+  ff a = ff_make(u);
+  bool neg = false;
+  if (sym) {
+    a = two_sum(2.f * u, -1.f);  // exact
+    neg = a.hi < 0.f;
+    if (neg) a = ff_neg(a);
+  }
+  ff pw;
+  if (code == 1) pw = a;
+  else if (code == 2) pw = ff_mul(a, a);
+  else if (code == 3) pw = ff_mul(ff_mul(a, a), a);
+  else pw = ff_pow01(a, curve, T);
+  if (neg) pw = ff_neg(pw);
+  return ff_add(base, ff_mul(scale, pw));
 }
 
 }  // namespace synth

@@ -23,18 +23,20 @@ struct ScratchHeader {
 static_assert(sizeof(ScratchHeader) == 256, "header is one 256-byte block");
 
 // Look-back state of one tile (voice, window) for the two scan chains
-// (0: LFO phases, 1: VCO phases), two components each.
+// (0: LFO phases, 1: VCO phases), two components each. An aggregate is a
+// 64-bit fixed-point phase, or the bits of a float in the FP32-carry mode.
 struct TileState {
   unsigned int flag[2];  // (epoch << 2) | 1 once agg[chain] of this launch is published
   unsigned int pad[2];
-  double agg[2][2];
+  unsigned long long agg[2][2];
 };
 static_assert(sizeof(TileState) == 48, "tile state layout");
 
 constexpr unsigned int kErrLookbackTimeout = 1u;
 
-constexpr int kFusedThreads = 384;  // 4 control warps + 8 audio warps
-constexpr int kFusedTileSeg = 128;  // control intervals per tile of the fused kernel
+constexpr int kFusedThreads = 256;     // one thread per control point of a tile
+constexpr int kFusedTilePoints = 256;  // control points per tile of the fused kernel
+constexpr int kFusedTileSeg = kFusedTilePoints - 1;  // control intervals per tile
 
 inline int windows_per_voice(int K) { return (K + kFusedTileSeg - 1) / kFusedTileSeg; }
 

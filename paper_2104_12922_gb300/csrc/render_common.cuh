@@ -152,15 +152,28 @@ __device__ __forceinline__ void block_exclusive_scan2(T& a, T& b, T* warp_tot /*
 template <class T> __device__ __forceinline__ T wrap01(T x) { return x - floor(x); }
 template <> __device__ __forceinline__ float wrap01<float>(float x) { return x - floorf(x); }
 
+// Carry values of the look-back: 64-bit fixed-point phases (exact, mod 1 by
+// integer wrap-around) or floats (the FP32-carry mode, wrapped to [0, 1)).
+__device__ __forceinline__ unsigned long long carry_bits(unsigned long long v) { return v; }
+__device__ __forceinline__ unsigned long long carry_bits(float v) { return __float_as_uint(v); }
+template <class T> __device__ __forceinline__ T carry_from_bits(unsigned long long b);
+template <> __device__ __forceinline__ unsigned long long carry_from_bits(unsigned long long b) {
+  return b;
+}
+template <> __device__ __forceinline__ float carry_from_bits(unsigned long long b) {
+  return __uint_as_float((unsigned int)b);
+}
+__device__ __forceinline__ unsigned long long carry_wrap(unsigned long long v) { return v; }
+__device__ __forceinline__ float carry_wrap(float v) { return v - floorf(v); }
+
 // ---------------------------------------------------------------------------
 // Look-back along one voice's windows (after Merrill & Garland's single-pass
 // prefix scan): each window publishes its aggregate as soon as its own block
 // scan is done, then sums the aggregates of all earlier windows of the voice.
 // The sum runs in a fixed order (lane j of warp 0 adds windows j, j+32, ...
 // in turn, then a fixed shuffle tree), so the carry -- and with it the audio
-// -- is bitwise reproducible whatever order the windows finish in; the
-// inclusive-prefix shortcut would make the floating-point association depend
-// on timing. Values are phases in cycles, kept wrapped to [0,1).
+// -- is bitwise reproducible whatever order the windows finish in (fixed-point
+// carries are exact in any order; float carries need the fixed order).
 // Every wait is bounded; a timeout sets the error bit in the header, and
 // once the bit is set no wait of any window spins any more (fail fast).
 // Called by all 32 lanes of one warp.
@@ -174,8 +187,8 @@ __device__ inline void lookback(TileState* voice_tiles, int w, int chain, unsign
   TileState* me = voice_tiles + w;
   const unsigned int tag = (epoch & 0x3fffffffu) << 2;
   if (lane == 0) {
-    __stcg(&me->agg[chain][0], (double)own0);
-    __stcg(&me->agg[chain][1], (double)own1);
+    __stcg(&me->agg[chain][0], carry_bits(own0));
+    __stcg(&me->agg[chain][1], carry_bits(own1));
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> my_flag(me->flag[chain]);
     my_flag.store(tag | 1u, cuda::memory_order_release);
   }
@@ -194,16 +207,16 @@ __device__ inline void lookback(TileState* voice_tiles, int w, int chain, unsign
       atomicOr(&hdr->error, kErrLookbackTimeout);
       break;
     }
-    s0 += (T)__ldcg(&p->agg[chain][0]);
-    s1 += (T)__ldcg(&p->agg[chain][1]);
+    s0 += carry_from_bits<T>(__ldcg(&p->agg[chain][0]));
+    s1 += carry_from_bits<T>(__ldcg(&p->agg[chain][1]));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     s0 += __shfl_xor_sync(0xffffffffu, s0, o);
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
   }
-  ex0 = wrap01(s0);
-  ex1 = wrap01(s1);
+  ex0 = carry_wrap(s0);
+  ex1 = carry_wrap(s1);
 }
 
 // End-of-launch bookkeeping of the persistent kernels: the last CTA to finish

@@ -1,31 +1,31 @@
 // render_fused.cu -- the fused persistent Voice render (one launch per batch).
 //
-// Work unit: a tile = (voice v, window w of kFusedTileSeg control intervals).
+// Work unit: a tile = (voice v, window w) of kFusedTilePoints = 256 control
+// points, i.e. the 255 control intervals between them; window w starts at
+// control point 255 w, so consecutive windows share their boundary point.
 // Tiles are claimed from an atomic counter in window-major order (tile t ->
 // v = t % batch, w = t / batch), so a tile's predecessors along its voice
 // were claimed earlier by running CTAs.
 //
-// Each persistent CTA is warp-specialized:
-//  * control warps (4 warps, one thread per control interval) claim the next
-//    tile and compute everything that runs at the control rate (Sec. 3.1):
-//    parameter draw (Philox, Sec. 2.1) and range map (Sec. 3.3); the 6 ADSRs,
-//    the LFO rates, their phase scan with a look-back carry from earlier
-//    windows, LFO shapes, modulation mixer, pitch and amplitudes (float-float,
-//    control_ff.cuh); per control interval and VCO the phase advanced over the
-//    interval (closed-form geometric sum of the upsampled pitch's increments)
-//    and its scan with a second look-back carry (FP64; FP32 in the
-//    precision-study mode). The result -- one SegVco per interval and VCO, the
-//    amplitudes at the control points, the mixer gains -- goes into one of two
-//    shared-memory hand-off buffers;
-//  * audio warps (8 warps) take filled buffers in order and render the tile
-//    (Sec. 3.2): each thread takes quads of 4 consecutive samples -- VCO
-//    phases from the interval description, sine, square-saw, Philox noise,
-//    VCAs, mixer -- and writes them with one 16-byte streaming store.
-// The two groups hand buffers over through shared-memory mbarriers, so the
-// audio warps never wait on the control group's internal barriers and the
-// control work of tile i+1 overlaps the audio of tile i. Nothing but the
-// audio, the parameters and a 48-byte look-back record per tile is written
-// to device memory.
+// One CTA of 256 threads takes a tile through these steps, one thread per
+// control point (Sec. 3.1 control rate) and then all threads on the audio:
+//  1. parameters: Philox draw (Sec. 2.1) or the caller's values, Sec. 3.3
+//     range map (float-float), the per-voice constants;
+//  2. the 6 ADSRs at the thread's control point, the two LFO rates and their
+//     phase increments over the interval that starts there;
+//  3. a block scan of those increments plus a look-back over the voice's
+//     earlier windows gives each point's LFO phases; LFO shapes, modulation
+//     mixer, pitch of both VCOs and the three amplitudes at the point;
+//  4. per interval and VCO the closed-form description of the phase (SegVco)
+//     and the phase advanced over it; a second scan + look-back gives each
+//     interval's starting phase;
+//  5. the audio (Sec. 3.2): each thread takes quads of 4 consecutive samples
+//     -- VCO phases from the interval description, sine, square-saw, Philox
+//     noise, VCAs, mixer -- written with one 16-byte streaming store.
+// The control chain is float-float (control_ff.cuh); running phase sums are
+// 64-bit fixed point, exact and order-independent (FP32 in the precision-study
+// mode). Nothing but the audio, the parameters and a 48-byte look-back record
+// per tile is written to device memory, and no FP64 instruction runs.
 
 #include "control_ff.cuh"
 #include "internal.h"
@@ -35,387 +35,323 @@ namespace synth {
 
 namespace {
 
-constexpr int TS = kFusedTileSeg;       // control intervals per tile
-constexpr int kCtrl = TS;               // control threads: one per interval
-constexpr int kAudio = 256;             // audio threads
-constexpr int NT = kCtrl + kAudio;
-static_assert(NT == kFusedThreads, "thread count shared with the launcher");
-constexpr int kCtrlWarps = kCtrl / 32;
-constexpr int kAudioWarps = kAudio / 32;
-constexpr long long kHandoffSpinLimit = 1ll << 26;
+constexpr int NT = kFusedThreads;
+constexpr int P = kFusedTilePoints;
+constexpr int TI = kFusedTileSeg;
+constexpr int kWarps = NT / 32;
+static_assert(NT == P, "one thread per control point");
 
-// Control -> audio hand-off of one tile.
-struct __align__(16) TileOut {
-  SegVco seg[2][TS];
-  float kappa[TS];
-  float inv_tanh_kappa[TS];
-  float amp[3][TS + 1];      // sine, square-saw, noise amplitudes at the control points
+using u64 = unsigned long long;
+
+struct __align__(16) Smem {
+  FFTables T;
+  SegVco seg[2][TI];
+  float kappa[TI];
+  float inv_tanh_kappa[TI];
+  float amp[3][P];           // sine, square-saw, noise amplitudes at the control points
+  ff m[2][P];                // VCO pitch (midi) at the control points
+  ff y[kNumParams];          // human-range parameters
+  VoiceFF V;
+  float u[80];
+  u64 warp_tot[2][2][kWarps];  // [scan][chain][warp]
+  float warp_tot_f[2][kWarps];
+  u64 prefix[2][2];            // [scan][chain]: phase carried in from earlier windows
+  float prefix_f[2];
+  u64 lfo_p0[2], vco_p0[2];    // initial phases
   float gain[3];
   float shape, inv_1p_shape;
-  unsigned long long g;      // global voice index
-  int v, k0, nseg, valid;
-};
-
-struct __align__(16) CtrlSmem {
-  double y[kNumParams];
-  VoiceFF V;
-  FFTables T;
-  ff env[6][TS + 1];
-  ff m[2][TS + 1];           // VCO pitch (midi) at the window's control points
-  double lfo_ex[2][TS + 1];  // exclusive LFO phase sums within the window
-  double sums[2][TS];
-  double warp_tot[2 * kCtrlWarps];
-  float warp_tot_f[2 * kCtrlWarps];
-  double prefix[2];
-  double lfo_p0[2], vco_p0[2];  // initial phases in cycles, wrapped
-  float u[80];
-  ff inv_cr, inv_R, ln2_12R, m_nyq, log2_440_over_sr;
   int tile;
   unsigned int epoch;
 };
 
-struct __align__(16) FusedSmem {
-  CtrlSmem c;
-  TileOut out[2];
-  unsigned long long full[2];   // mbarrier: control -> audio (1 arrival)
-  unsigned long long empty[2];  // mbarrier: audio -> control (one arrival per audio warp)
-};
-
-__device__ __forceinline__ void ctrl_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kCtrl) : "memory"); }
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
-}
-// Bounded wait for the phase of the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity) {
-  const uint32_t a = smem_addr(b);
-  for (long long i = 0; i < kHandoffSpinLimit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-// Exclusive scan of two values over the control group's threads.
-template <class T>
-__device__ __forceinline__ void ctrl_exclusive_scan2(T& a, T& b, T* warp_tot, T& tot_a, T& tot_b) {
+// Exclusive block scan of two fixed-point values (exact, any order). After
+// the barrier inside, warp 0 receives the block totals in tot0/tot1 (all
+// lanes) for its look-back; the caller then writes s.prefix and syncs.
+__device__ __forceinline__ void block_scan2_fix(u64& a, u64& b, u64 (*buf)[kWarps], u64& tot0,
+                                                u64& tot1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T ia = a, ib = b;
+  u64 ia = a, ib = b;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const T na = __shfl_up_sync(0xffffffffu, ia, o);
-    const T nb = __shfl_up_sync(0xffffffffu, ib, o);
+    const u64 na = __shfl_up_sync(0xffffffffu, ia, o);
+    const u64 nb = __shfl_up_sync(0xffffffffu, ib, o);
     if (lane >= o) { ia += na; ib += nb; }
   }
-  if (lane == 31) { warp_tot[warp] = ia; warp_tot[kCtrlWarps + warp] = ib; }
-  ctrl_sync();
-  T pa = T(0), pb = T(0), ta = T(0), tb = T(0);
+  if (lane == 31) { buf[0][warp] = ia; buf[1][warp] = ib; }
+  __syncthreads();
+  u64 pa = 0, pb = 0, ta = 0, tb = 0;
 #pragma unroll
-  for (int w = 0; w < kCtrlWarps; ++w) {  // fixed order: deterministic
-    if (w < warp) { pa += warp_tot[w]; pb += warp_tot[kCtrlWarps + w]; }
-    ta += warp_tot[w];
-    tb += warp_tot[kCtrlWarps + w];
+  for (int w = 0; w < kWarps; ++w) {
+    const u64 wa = buf[0][w], wb = buf[1][w];
+    if (w < warp) { pa += wa; pb += wb; }
+    ta += wa;
+    tb += wb;
   }
-  T ea = __shfl_up_sync(0xffffffffu, ia, 1);
-  T eb = __shfl_up_sync(0xffffffffu, ib, 1);
-  if (lane == 0) { ea = T(0); eb = T(0); }
-  a = pa + ea;
-  b = pb + eb;
-  tot_a = ta;
-  tot_b = tb;
-  ctrl_sync();
+  a = pa + ia - a;
+  b = pb + ib - b;
+  tot0 = ta;
+  tot1 = tb;
 }
 
-template <class CarryT>
-__device__ __forceinline__ CarryT* warp_buf(CtrlSmem& c);
-template <> __device__ __forceinline__ double* warp_buf<double>(CtrlSmem& c) { return c.warp_tot; }
-template <> __device__ __forceinline__ float* warp_buf<float>(CtrlSmem& c) { return c.warp_tot_f; }
+// The same for two float values (FP32-carry mode): the warp-level inclusive
+// sums, then the earlier warps' totals added in a fixed order.
+__device__ __forceinline__ void block_scan2_f32(float& a, float& b, float (*buf)[kWarps],
+                                                float& tot0, float& tot1) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float na = __shfl_up_sync(0xffffffffu, ia, o);
+    const float nb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) { ia += na; ib += nb; }
+  }
+  if (lane == 31) { buf[0][warp] = ia; buf[1][warp] = ib; }
+  __syncthreads();
+  float pa = 0.f, pb = 0.f, ta = 0.f, tb = 0.f;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    if (w < warp) { pa += buf[0][w]; pb += buf[1][w]; }
+    ta += buf[0][w];
+    tb += buf[1][w];
+  }
+  float ea = __shfl_up_sync(0xffffffffu, ia, 1);
+  float eb = __shfl_up_sync(0xffffffffu, ib, 1);
+  if (lane == 0) { ea = 0.f; eb = 0.f; }
+  a = pa + ea;
+  b = pb + eb;
+  tot0 = ta;
+  tot1 = tb;
+}
 
-// ----------------------------------------------------------- control group
-template <class CarryT>
-__device__ void control_loop(FusedSmem& sm, const VoiceConst& vc, uint64_t seed,
-                             uint64_t batch_index, int batch, const float* __restrict__ params_in,
-                             float* __restrict__ params_out, ScratchHeader* hdr, TileState* tiles,
-                             int n_windows) {
-  CtrlSmem& c = sm.c;
-  const int tid = threadIdx.x;  // 0 .. kCtrl-1
+template <bool kCarryF32>
+__global__ void __launch_bounds__(NT, 3) render_fused_kernel(
+    const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t batch_index, int batch,
+    const float* __restrict__ params_in, float* __restrict__ audio, float* __restrict__ params_out,
+    ScratchHeader* hdr, TileState* tiles, int n_windows) {
+  __shared__ Smem s;
+  const int tid = threadIdx.x;
   const int total_tiles = batch * n_windows;
-  const int R = vc.R;
+  const int R = vc.R, K = vc.K;
   const int64_t N = vc.n_samples;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  const double two_pi = 6.28318530717958647692;
-  const unsigned int epoch = c.epoch;
-  for (int it = 0;; ++it) {
-    const int b = it & 1;
-    TileOut& o = sm.out[b];
-    if (tid == 0) {
-      // buffer b is free once the audio warps released its previous tile
-      if (!mbar_wait(&sm.empty[b], (((uint32_t)it >> 1) & 1u) ^ 1u))
-        atomicOr(&hdr->error, kErrLookbackTimeout);
-      c.tile = (int)atomicAdd(&hdr->work, 1u);
-    }
-    ctrl_sync();
-    const int t = c.tile;
-    if (t >= total_tiles) {
-      if (tid == 0) {
-        o.valid = 0;
-        mbar_arrive(&sm.full[b]);
-      }
-      break;
-    }
+  const int qps = R >> 2;             // quads per control interval
+  const int dq_s = NT / qps;          // a thread's quad stride NT as (intervals, quads)
+  const int dq_j = NT - dq_s * qps;
+  const bool vec_ok = (N & 3) == 0;
+  const float invR = 1.0f / (float)R;
+  load_tables(s.T, vc.T);
+  if (tid == 0) s.epoch = *(volatile unsigned int*)&hdr->epoch;
+
+  for (;;) {
+    if (tid == 0) s.tile = (int)atomicAdd(&hdr->work, 1u);
+    __syncthreads();  // also: the previous tile's audio is done with the shared buffers
+    const int t = s.tile;
+    if (t >= total_tiles) break;
     const int v = t % batch, w = t / batch;
     const uint64_t g = batch_index * (uint64_t)batch + (uint64_t)v;
-    const int k0 = w * TS;
-    const int nseg = min(TS, vc.K - k0);
+    const int k0 = w * TI;
+    const int nseg = min(TI, K - k0);
     TileState* vt = tiles + (size_t)v * n_windows;
+    const unsigned int epoch = s.epoch;
 
-    // ---- parameters (Sec. 2.1 draw, Sec. 3.3 range map) ----------------
+    // ---- 1. parameters (Sec. 2.1 draw, Sec. 3.3 range map) ---------------
     if (params_in == nullptr) {
       if (tid < 20) {
         const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)tid,
                                                  kStreamParam), key);
-        c.u[4 * tid + 0] = u01f(r.x);
-        c.u[4 * tid + 1] = u01f(r.y);
-        c.u[4 * tid + 2] = u01f(r.z);
-        c.u[4 * tid + 3] = u01f(r.w);
+        s.u[4 * tid + 0] = u01f(r.x);
+        s.u[4 * tid + 1] = u01f(r.y);
+        s.u[4 * tid + 2] = u01f(r.z);
+        s.u[4 * tid + 3] = u01f(r.w);
       }
     } else if (tid < kNumParams) {
-      c.u[tid] = fminf(fmaxf(params_in[(size_t)v * kNumParams + tid], 0.f), 1.f);
+      s.u[tid] = fminf(fmaxf(params_in[(size_t)v * kNumParams + tid], 0.f), 1.f);
     }
-    ctrl_sync();
+    __syncthreads();
     if (tid < kNumParams) {
-      const float u = c.u[tid];
+      const float u = s.u[tid];
       if (w == 0 && params_out) params_out[(size_t)v * kNumParams + tid] = u;
-      c.y[tid] = range_map((double)u, vc.lo[tid], vc.hi[tid], vc.curve[tid], vc.sym[tid]);
+      s.y[tid] = range_map_ff(u, vc.map_base[tid], vc.map_scale[tid], vc.map_curve[tid],
+                              vc.map_code[tid], vc.sym[tid], s.T);
     }
-    ctrl_sync();
-    const double* y = c.y;
+    __syncthreads();
     if (tid < 16) {
-      voice_ff_fill(c.V, y, tid);
+      voice_ff_fill(s.V, s.y, tid);
     } else if (tid == 32) {
-      const double l0 = y[kMix], l1 = y[kMix + 1], l2 = y[kMix + 2];
-      const double norm = fmax(1.0, l0 + l1 + l2);
-      o.gain[0] = (float)(l0 / norm);
-      o.gain[1] = (float)(l1 / norm);
-      o.gain[2] = (float)(l2 / norm);
-      o.shape = (float)y[kSqr + 3];
-      o.inv_1p_shape = (float)(1.0 / (1.0 + y[kSqr + 3]));
-      o.g = g;
-      o.v = v;
-      o.k0 = k0;
-      o.nseg = nseg;
+      const float l0 = ff_to_float(s.y[kMix]), l1 = ff_to_float(s.y[kMix + 1]),
+                  l2 = ff_to_float(s.y[kMix + 2]);
+      const float inv = 1.f / fmaxf(1.f, l0 + l1 + l2);
+      s.gain[0] = l0 * inv;
+      s.gain[1] = l1 * inv;
+      s.gain[2] = l2 * inv;
+      const float sh = ff_to_float(s.y[kSqr + 3]);
+      s.shape = sh;
+      s.inv_1p_shape = 1.f / (1.f + sh);
     } else if (tid == 64) {
-      c.lfo_p0[0] = wrap01(y[kLfo + 2] / two_pi);
-      c.lfo_p0[1] = wrap01(y[kLfo + 8 + 2] / two_pi);
-      c.vco_p0[0] = wrap01(y[kSine + 2] / two_pi);
-      c.vco_p0[1] = wrap01(y[kSqr + 2] / two_pi);
+      s.lfo_p0[0] = ff_to_fix64(ff_mul(s.y[kLfo + 2], vc.inv_2pi));
+      s.lfo_p0[1] = ff_to_fix64(ff_mul(s.y[kLfo + 8 + 2], vc.inv_2pi));
+      s.vco_p0[0] = ff_to_fix64(ff_mul(s.y[kSine + 2], vc.inv_2pi));
+      s.vco_p0[1] = ff_to_fix64(ff_mul(s.y[kSqr + 2], vc.inv_2pi));
     }
-    ctrl_sync();
-    const VoiceFF& V = c.V;
-    if (tid < 6) c.V.level_d[tid] = gate_level_ff(tid, V, c.T);
-    ctrl_sync();
+    __syncthreads();
+    const VoiceFF& V = s.V;
+    if (tid < 6) s.V.level_d[tid] = gate_level_ff(tid, V, s.T);
+    __syncthreads();
 
-    // ---- envelopes at control points k0 .. k0 + nseg (one (point, ADSR) per item)
-    for (int i = tid; i < 6 * (nseg + 1); i += kCtrl) {
-      const int pt = i / 6, a = i - 6 * pt;
-      c.env[a][pt] = adsr_ff(ff_mul_f(c.inv_cr, (float)(k0 + pt)), a, V, c.T);
+    // ---- 2. envelopes at point k0 + tid; LFO increments over interval tid --
+    const bool has_pt = tid <= nseg;
+    ff env[6];
+    if (has_pt) {
+      const ff tk = ff_mul_f(vc.inv_cr, (float)(k0 + tid));
+#pragma unroll
+      for (int a = 0; a < 6; ++a) env[a] = adsr_ff(tk, a, V, s.T);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 6; ++a) env[a] = ff_make(0.f);
     }
-    ctrl_sync();
-
-    // ---- LFO phase increments rate_k / CR at points k0 .. k0 + nseg - 1, scanned (FP64)
-    double r0 = 0.0, r1 = 0.0;
+    u64 r0 = 0, r1 = 0;
     if (tid < nseg) {
       const ff lim = ff_make((float)kLfoMaxHz), z = ff_make(0.f);
-      r0 = ff_to_double(ff_mul(ff_min(ff_max(ff_add(V.lfo_freq[0], ff_mul(V.lfo_depth[0], c.env[2][tid])), z), lim), c.inv_cr));
-      r1 = ff_to_double(ff_mul(ff_min(ff_max(ff_add(V.lfo_freq[1], ff_mul(V.lfo_depth[1], c.env[4][tid])), z), lim), c.inv_cr));
+      r0 = ff_to_fix64(ff_mul(
+          ff_min(ff_max(ff_add(V.lfo_freq[0], ff_mul(V.lfo_depth[0], env[2])), z), lim), vc.inv_cr));
+      r1 = ff_to_fix64(ff_mul(
+          ff_min(ff_max(ff_add(V.lfo_freq[1], ff_mul(V.lfo_depth[1], env[4])), z), lim), vc.inv_cr));
     }
-    double tot0, tot1;
-    ctrl_exclusive_scan2<double>(r0, r1, c.warp_tot, tot0, tot1);
-    if (tid < nseg) {
-      c.lfo_ex[0][tid] = r0;
-      c.lfo_ex[1][tid] = r1;
-    }
-    if (tid == 0) {
-      c.lfo_ex[0][nseg] = tot0;
-      c.lfo_ex[1][nseg] = tot1;
-    }
-    if (tid < 32) {
-      double e0, e1;
-      lookback<double>(vt, w, 0, epoch, wrap01(tot0), wrap01(tot1), e0, e1, hdr);
-      if (tid == 0) {
-        c.prefix[0] = e0;
-        c.prefix[1] = e1;
-      }
-    }
-    ctrl_sync();
 
-    // ---- LFOs, modulation mixer, pitch and amplitudes at each control point
-    for (int i = tid; i <= nseg; i += kCtrl) {
-      ff lfo[2];
-#pragma unroll
-      for (int l = 0; l < 2; ++l) {
-        const double theta = wrap01(c.lfo_p0[l] + c.prefix[l] + c.lfo_ex[l][i]);
-        lfo[l] = lfo_ff(ff_from_double(theta), l, c.env[3 + 2 * l][i], V, c.T);
+    // ---- 3. LFO phases: scan + look-back; LFOs, mixer, pitch, amplitudes --
+    {
+      u64 t0, t1;
+      block_scan2_fix(r0, r1, s.warp_tot[0], t0, t1);
+      if (tid < 32) {
+        u64 e0, e1;
+        lookback<u64>(vt, w, 0, epoch, t0, t1, e0, e1, hdr);
+        if (tid == 0) { s.prefix[0][0] = e0; s.prefix[0][1] = e1; }
       }
-      const ff src[4] = {c.env[0][i], c.env[1][i], lfo[0], lfo[1]};
-      ff dest[5];
-#pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        ff acc = ff_mul(V.mod_w[0][j], src[0]);
-#pragma unroll
-        for (int s = 1; s < 4; ++s) acc = ff_add(acc, ff_mul(V.mod_w[s][j], src[s]));
-        dest[j] = ff_mul(acc, V.inv_norm[j]);
-      }
-      c.m[0][i] = ff_add(V.pitch_base[0], ff_mul(V.depth[0], dest[0]));
-      c.m[1][i] = ff_add(V.pitch_base[1], ff_mul(V.depth[1], dest[2]));
-      o.amp[0][i] = ff_to_float(dest[1]);
-      o.amp[1][i] = ff_to_float(dest[3]);
-      o.amp[2][i] = ff_to_float(dest[4]);
+      __syncthreads();
     }
-    ctrl_sync();
+    if (has_pt) {
+      const ff th0 = fix64_to_ff(s.lfo_p0[0] + s.prefix[0][0] + r0);
+      const ff th1 = fix64_to_ff(s.lfo_p0[1] + s.prefix[0][1] + r1);
+      const ff src[4] = {env[0], env[1], lfo_ff(th0, 0, env[3], V, s.T),
+                         lfo_ff(th1, 1, env[5], V, s.T)};
+#pragma unroll
+      for (int o = 0; o < 2; ++o) {
+        ff acc = V.pitch_base[o];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc = ff_add(acc, ff_mul(V.pitch_w[o][q], src[q]));
+        s.m[o][tid] = acc;
+      }
+      float srcf[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) srcf[q] = ff_to_float(src[q]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float acc = V.amp_w[k][0] * srcf[0];
+#pragma unroll
+        for (int q = 1; q < 4; ++q) acc = fmaf(V.amp_w[k][q], srcf[q], acc);
+        s.amp[k][tid] = acc;
+      }
+    }
+    __syncthreads();
 
-    // ---- VCO phase over each control interval, scanned ---------------------
-    CarryT s0 = CarryT(0), s1 = CarryT(0);
+    // ---- 4. VCO phase over each control interval, scanned -----------------
+    ff tot[2] = {ff_make(0.f), ff_make(0.f)};
     if (tid < nseg) {
-      const int k = k0 + tid;
-      const int64_t rem = N - (int64_t)k * R;
+      const int64_t rem = N - (int64_t)(k0 + tid) * R;
       const int Rk = rem < R ? (int)rem : R;
-      s0 = (CarryT)vco_interval_ff(c.m[0][tid], c.m[0][tid + 1], R, Rk, c.inv_R, c.ln2_12R, c.m_nyq,
-                                   c.log2_440_over_sr, c.T, &o.seg[0][tid]);
-      s1 = (CarryT)vco_interval_ff(c.m[1][tid], c.m[1][tid + 1], R, Rk, c.inv_R, c.ln2_12R, c.m_nyq,
-                                   c.log2_440_over_sr, c.T, &o.seg[1][tid]);
-      const ff mk = ff_min(c.m[1][tid], c.m_nyq);
-      const float fk = (float)vc.sample_rate * ff_to_float(inc_at_ff(mk, c.log2_440_over_sr, c.T));
-      const float kap = fminf((float)kBrightnessMax, 1.f + (float)vc.sample_rate / (8.f * fk));
-      o.kappa[tid] = kap;
-      o.inv_tanh_kappa[tid] = 1.f / tanhf(kap);
+      float inc0, inc1;
+      tot[0] = vco_interval_ff(s.m[0][tid], s.m[0][tid + 1], R, Rk, vc.inv_R, vc.ln2_12R,
+                               vc.m_nyq_ff, vc.log2_440_over_sr, s.T, &s.seg[0][tid], &inc0);
+      tot[1] = vco_interval_ff(s.m[1][tid], s.m[1][tid + 1], R, Rk, vc.inv_R, vc.ln2_12R,
+                               vc.m_nyq_ff, vc.log2_440_over_sr, s.T, &s.seg[1][tid], &inc1);
+      // square-saw drive from the (capped) frequency at the interval start:
+      // 1 + SR / (8 f) = 1 + 1 / (8 inc)
+      const float kap = fminf((float)kBrightnessMax, 1.f + 0.125f / inc1);
+      s.kappa[tid] = kap;
+      s.inv_tanh_kappa[tid] = 1.f / tanhf(kap);
     }
-    CarryT t0, t1;
-    ctrl_exclusive_scan2<CarryT>(s0, s1, warp_buf<CarryT>(c), t0, t1);
-    if (tid < 32) {
-      CarryT e0, e1;
-      lookback<CarryT>(vt, w, 1, epoch, wrap01(t0), wrap01(t1), e0, e1, hdr);
-      if (tid == 0) {
-        c.prefix[0] = (double)e0;
-        c.prefix[1] = (double)e1;
+    if constexpr (!kCarryF32) {
+      u64 c0 = tid < nseg ? ff_to_fix64(tot[0]) : 0ull;
+      u64 c1 = tid < nseg ? ff_to_fix64(tot[1]) : 0ull;
+      u64 t0, t1;
+      block_scan2_fix(c0, c1, s.warp_tot[1], t0, t1);
+      if (tid < 32) {
+        u64 e0, e1;
+        lookback<u64>(vt, w, 1, epoch, t0, t1, e0, e1, hdr);
+        if (tid == 0) { s.prefix[1][0] = e0; s.prefix[1][1] = e1; }
+      }
+      __syncthreads();
+      if (tid < nseg) {
+        s.seg[0][tid].phase0 = fix64_to_float(s.vco_p0[0] + s.prefix[1][0] + c0);
+        s.seg[1][tid].phase0 = fix64_to_float(s.vco_p0[1] + s.prefix[1][1] + c1);
+      }
+    } else {
+      // FP32 carries (precision study): the interval phases are summed in
+      // float within the window and carried across windows in float.
+      float c0 = tid < nseg ? ff_to_float(tot[0]) : 0.f;
+      float c1 = tid < nseg ? ff_to_float(tot[1]) : 0.f;
+      float t0, t1;
+      block_scan2_f32(c0, c1, s.warp_tot_f, t0, t1);
+      if (tid < 32) {
+        float e0, e1;
+        lookback<float>(vt, w, 1, epoch, carry_wrap(t0), carry_wrap(t1), e0, e1, hdr);
+        if (tid == 0) { s.prefix_f[0] = e0; s.prefix_f[1] = e1; }
+      }
+      __syncthreads();
+      if (tid < nseg) {
+        s.seg[0][tid].phase0 = carry_wrap(fix64_to_float(s.vco_p0[0]) + s.prefix_f[0] + c0);
+        s.seg[1][tid].phase0 = carry_wrap(fix64_to_float(s.vco_p0[1]) + s.prefix_f[1] + c1);
       }
     }
-    ctrl_sync();
-    if (tid < nseg) {
-      o.seg[0][tid].phase0 = (float)wrap01((CarryT)c.vco_p0[0] + (CarryT)c.prefix[0] + s0);
-      o.seg[1][tid].phase0 = (float)wrap01((CarryT)c.vco_p0[1] + (CarryT)c.prefix[1] + s1);
-    }
-    ctrl_sync();
-    if (tid == 0) {
-      o.valid = 1;
-      mbar_arrive(&sm.full[b]);  // release: the tile's description is complete
-    }
-  }
-}
+    __syncthreads();
 
-// ------------------------------------------------------------- audio group
-__device__ void audio_loop(FusedSmem& sm, const VoiceConst& vc, uint64_t seed,
-                           float* __restrict__ audio, ScratchHeader* hdr) {
-  const int atid = threadIdx.x - kCtrl;  // 0 .. kAudio-1
-  const int lane = threadIdx.x & 31;
-  const int R = vc.R;
-  const int qps = R >> 2;  // quads per control interval
-  const int64_t N = vc.n_samples;
-  const bool vec_ok = (N & 3) == 0;
-  const float invR = 1.0f / (float)R;
-  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  for (int it = 0;; ++it) {
-    const int b = it & 1;
-    if (!mbar_wait(&sm.full[b], ((uint32_t)it >> 1) & 1u)) {
-      if (atid == 0) atomicOr(&hdr->error, kErrLookbackTimeout);
-      break;
-    }
-    const TileOut& o = sm.out[b];
-    if (!o.valid) break;
-    const float g0 = o.gain[0], g1 = o.gain[1], g2 = o.gain[2];
-    const float shape = o.shape, inv_1p_shape = o.inv_1p_shape;
-    const uint64_t g = o.g;
-    const int k0 = o.k0;
-    float* out_v = audio + (size_t)o.v * (size_t)N;
-    const int nq = o.nseg * qps;
-    for (int q = atid; q < nq; q += kAudio) {
-      const int s = q / qps;
-      const int j0 = (q - s * qps) << 2;
-      const int64_t n0 = (int64_t)(k0 + s) * R + j0;
-      if (n0 >= N) continue;
-      float ps[4], pq[4];
-      vco_quad(o.seg[0][s], j0, ps);
-      vco_quad(o.seg[1][s], j0, pq);
-      const float kap = o.kappa[s], itk = o.inv_tanh_kappa[s];
-      const uint4 nz = philox4x32_10(
-          make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(n0 >> 2), kStreamNoise), key);
-      const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
-      const float a00 = o.amp[0][s], a10 = o.amp[1][s], a20 = o.amp[2][s];
-      const float d0 = o.amp[0][s + 1] - a00, d1 = o.amp[1][s + 1] - a10,
-                  d2 = o.amp[2][s + 1] - a20;
-      float out4[4];
+    // ---- 5. audio ----------------------------------------------------------
+    {
+      const float g0 = s.gain[0], g1 = s.gain[1], g2 = s.gain[2];
+      const float shape = s.shape, inv_1p_shape = s.inv_1p_shape;
+      float* out_v = audio + (size_t)v * (size_t)N;
+      const int nq = nseg * qps;
+      int si = tid / qps;
+      int jq = tid - si * qps;
+      for (int q = tid; q < nq; q += NT) {
+        const int j0 = jq << 2;
+        const int64_t n0 = (int64_t)(k0 + si) * R + j0;
+        if (n0 < N) {
+          float ps[4], pq[4];
+          vco_quad(s.seg[0][si], j0, ps);
+          vco_quad(s.seg[1][si], j0, pq);
+          const float kap = s.kappa[si], itk = s.inv_tanh_kappa[si];
+          const uint4 nz = philox4x32_10(
+              make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(n0 >> 2), kStreamNoise), key);
+          const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
+          const float a00 = s.amp[0][si], a10 = s.amp[1][si], a20 = s.amp[2][si];
+          const float d0 = s.amp[0][si + 1] - a00, d1 = s.amp[1][si + 1] - a10,
+                      d2 = s.amp[2][si + 1] - a20;
+          float out4[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float fj = (float)(j0 + i) * invR;
-        const float x_sin = __sinf(kTwoPiF * ps[i]);
-        const float x_sq = square_saw(pq[i], kap, itk, shape, inv_1p_shape);
-        const float x_nz = fmaf(2.f, u01f(nw[i]), -1.f);
-        out4[i] = g0 * fmaf(fj, d0, a00) * x_sin + g1 * fmaf(fj, d1, a10) * x_sq +
-                  g2 * fmaf(fj, d2, a20) * x_nz;
-      }
-      if (vec_ok && n0 + 3 < N) {
-        __stcs(reinterpret_cast<float4*>(out_v + n0), make_float4(out4[0], out4[1], out4[2], out4[3]));
-      } else {
+          for (int i = 0; i < 4; ++i) {
+            const float fj = (float)(j0 + i) * invR;
+            const float x_sin = __sinf(kTwoPiF * ps[i]);
+            const float x_sq = square_saw(pq[i], kap, itk, shape, inv_1p_shape);
+            const float x_nz = fmaf(2.f, u01f(nw[i]), -1.f);
+            out4[i] = g0 * fmaf(fj, d0, a00) * x_sin + g1 * fmaf(fj, d1, a10) * x_sq +
+                      g2 * fmaf(fj, d2, a20) * x_nz;
+          }
+          if (vec_ok && n0 + 3 < N) {
+            __stcs(reinterpret_cast<float4*>(out_v + n0),
+                   make_float4(out4[0], out4[1], out4[2], out4[3]));
+          } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (n0 + i < N) out_v[n0 + i] = out4[i];
+            for (int i = 0; i < 4; ++i)
+              if (n0 + i < N) out_v[n0 + i] = out4[i];
+          }
+        }
+        si += dq_s;
+        jq += dq_j;
+        if (jq >= qps) { jq -= qps; ++si; }
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&sm.empty[b]);
   }
-}
-
-template <class CarryT>
-__global__ void __launch_bounds__(NT, 2) render_fused_kernel(
-    const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t batch_index, int batch,
-    const float* __restrict__ params_in, float* __restrict__ audio, float* __restrict__ params_out,
-    ScratchHeader* hdr, TileState* tiles, int n_windows) {
-  __shared__ FusedSmem sm;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    sm.c.epoch = *(volatile unsigned int*)&hdr->epoch;
-    sm.c.inv_cr = ff_from_double(1.0 / vc.control_rate);
-    sm.c.inv_R = ff_from_double(1.0 / (double)vc.R);
-    sm.c.ln2_12R = ff_from_double(kLn2 / (12.0 * (double)vc.R));
-    sm.c.m_nyq = ff_from_double(vc.m_nyq);
-    sm.c.log2_440_over_sr = ff_from_double(log2(440.0 / vc.sample_rate));
-    mbar_init(&sm.full[0], 1);
-    mbar_init(&sm.full[1], 1);
-    mbar_init(&sm.empty[0], kAudioWarps);
-    mbar_init(&sm.empty[1], kAudioWarps);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (tid < 33) ff_tables_fill_entry(sm.c.T, tid);
-  __syncthreads();
-  if (tid < kCtrl)
-    control_loop<CarryT>(sm, vc, seed, batch_index, batch, params_in, params_out, hdr, tiles,
-                         n_windows);
-  else
-    audio_loop(sm, vc, seed, audio, hdr);
-  __syncthreads();
   persistent_finish(hdr);
 }
 
@@ -423,7 +359,7 @@ __global__ void __launch_bounds__(NT, 2) render_fused_kernel(
 
 int fused_max_active_blocks_per_sm() {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<double>, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false>, NT, 0);
   return n;
 }
 
@@ -435,11 +371,11 @@ cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t ba
   const int total = batch * n_windows;
   grid = grid < total ? grid : total;
   if (vc.carry_fp32)
-    render_fused_kernel<float><<<grid, NT, 0, stream>>>(vc, seed, batch_index, batch, params_in,
-                                                        audio, params_out, hdr, tiles, n_windows);
+    render_fused_kernel<true><<<grid, NT, 0, stream>>>(vc, seed, batch_index, batch, params_in,
+                                                       audio, params_out, hdr, tiles, n_windows);
   else
-    render_fused_kernel<double><<<grid, NT, 0, stream>>>(vc, seed, batch_index, batch, params_in,
-                                                         audio, params_out, hdr, tiles, n_windows);
+    render_fused_kernel<false><<<grid, NT, 0, stream>>>(vc, seed, batch_index, batch, params_in,
+                                                        audio, params_out, hdr, tiles, n_windows);
   return cudaGetLastError();
 }
 

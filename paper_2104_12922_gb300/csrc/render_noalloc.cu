@@ -59,7 +59,7 @@ synth_status setup_current_device(int* device_out, void** addr_out, int* grid_ou
 synth_status voice_const_from_config(const synth_config* cfg, VoiceConst* vc) {
   const double sr = cfg->sample_rate, cr = cfg->control_rate;
   if (!(sr > 0.0) || !(cr > 0.0) || !(cfg->seconds > 0.0)) return SYNTH_ERR_ARG;
-  if (cfg->carry != SYNTH_CARRY_FP64 && cfg->carry != SYNTH_CARRY_FP32) return SYNTH_ERR_ARG;
+  if (cfg->carry != SYNTH_CARRY_FIXED64 && cfg->carry != SYNTH_CARRY_FP32) return SYNTH_ERR_ARG;
   const double r = sr / cr;
   const long long R = std::llround(r);
   const double n = cfg->seconds * sr;
@@ -83,6 +83,7 @@ synth_status voice_const_from_config(const synth_config* cfg, VoiceConst* vc) {
   vc->R = (int32_t)R;
   vc->K = (int32_t)((N + R - 1) / R);
   vc->carry_fp32 = cfg->carry == SYNTH_CARRY_FP32 ? 1 : 0;
+  voice_const_derive(*vc);
   return SYNTH_OK;
 }
 

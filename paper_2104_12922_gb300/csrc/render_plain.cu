@@ -2,8 +2,9 @@
 // each reading its inputs from and writing its output to device memory, the
 // way a framework of batched tensor ops renders the Voice (Sec. 3.1: "all
 // modules render audio in batches"; Sec. 3.2 routing). It computes the same
-// quantities as the fused kernel with the same numerics, so the two differ
-// only in how the work is scheduled and how much memory traffic it makes.
+// quantities as the fused kernel with the same control-rate arithmetic, so
+// the two differ in how the work is scheduled and how much memory traffic it
+// makes, and in the last bits of the parameters and running sums.
 //
 // Workspace (caller-owned, 256-byte aligned sections), B voices, P = K + 1
 // control points, N samples:
@@ -11,8 +12,8 @@
 //   lfo_phase[B][2][P] f64 | dest[B][5][P] ff | seg[B][2][K] SegVco
 //   seg_sum[B][2][K] f64 | kappa[B][2][K] f32 | amp[B][3][N] f32
 //   phase[B][2][N] f32 | osc[B][3][N] f32
-// Control-rate values are float-float and running sums FP64, as in the fused
-// kernel (control_ff.cuh).
+// Control-rate values are float-float (control_ff.cuh), as in the fused
+// kernel; the parameters and the running phase sums are FP64 here.
 
 #include "internal.h"
 #include "control_pipeline.cuh"
@@ -63,13 +64,17 @@ __global__ void plain_params(const __grid_constant__ VoiceConst vc, uint64_t see
 }
 
 // Per-voice constants of the control modules (float-float).
-__global__ void plain_voice_consts(const double* y, VoiceFF* vff) {
+__global__ void plain_voice_consts(const __grid_constant__ VoiceConst vc, const double* y,
+                                   VoiceFF* vff) {
   __shared__ FFTables T;
+  __shared__ ff yff[kNumParams];
   const int v = blockIdx.x;
-  if (threadIdx.x < 33) ff_tables_fill_entry(T, threadIdx.x);
+  load_tables(T, vc.T);
+  for (int p = threadIdx.x; p < kNumParams; p += blockDim.x)
+    yff[p] = ff_from_double(y[(size_t)v * kNumParams + p]);
   __syncthreads();
   VoiceFF& V = vff[v];
-  if (threadIdx.x < 16) voice_ff_fill(V, y + (size_t)v * kNumParams, threadIdx.x);
+  if (threadIdx.x < 16) voice_ff_fill(V, yff, threadIdx.x);
   __syncthreads();
   __threadfence_block();
   if (threadIdx.x < 6) V.level_d[threadIdx.x] = gate_level_ff(threadIdx.x, V, T);
@@ -78,7 +83,7 @@ __global__ void plain_voice_consts(const double* y, VoiceFF* vff) {
 // ADSR modules (6 per voice) at the control points.
 __global__ void plain_adsr(const __grid_constant__ VoiceConst vc, const VoiceFF* vff, ff* env) {
   __shared__ FFTables T;
-  if (threadIdx.x < 33) ff_tables_fill_entry(T, threadIdx.x);
+  load_tables(T, vc.T);
   __syncthreads();
   const int P = vc.K + 1;
   const int v = blockIdx.y;
@@ -138,7 +143,7 @@ __global__ void plain_phase_scan(const double* inc, double* phase, int len, int 
 __global__ void plain_modmix(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
                              const ff* env, const double* lfo_phase, ff* dest) {
   __shared__ FFTables T;
-  if (threadIdx.x < 33) ff_tables_fill_entry(T, threadIdx.x);
+  load_tables(T, vc.T);
   __syncthreads();
   const int P = vc.K + 1;
   const int v = blockIdx.y;
@@ -163,7 +168,7 @@ __global__ void plain_modmix(const __grid_constant__ VoiceConst vc, const VoiceF
 __global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
                                     const ff* dest, SegVco* seg, double* seg_sum, float* kappa) {
   __shared__ FFTables T;
-  if (threadIdx.x < 33) ff_tables_fill_entry(T, threadIdx.x);
+  load_tables(T, vc.T);
   __syncthreads();
   const int P = vc.K + 1, K = vc.K;
   const int v = blockIdx.y;
@@ -172,19 +177,16 @@ __global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const
   const VoiceFF& V = vff[v];
   const int64_t rem = vc.n_samples - (int64_t)k * vc.R;
   const int Rk = rem < vc.R ? (int)rem : vc.R;
-  const ff inv_R = ff_from_double(1.0 / (double)vc.R);
-  const ff ln2_12R = ff_from_double(kLn2 / (12.0 * (double)vc.R));
-  const ff m_nyq = ff_from_double(vc.m_nyq);
-  const ff l440 = ff_from_double(log2(440.0 / vc.sample_rate));
   for (int o = 0; o < 2; ++o) {
     const ff* pd = dest + ((size_t)v * 5 + (o == 0 ? 0 : 2)) * P;
     const ff ma = ff_add(V.pitch_base[o], ff_mul(V.depth[o], pd[k]));
     const ff mb = ff_add(V.pitch_base[o], ff_mul(V.depth[o], pd[k + 1]));
-    seg_sum[((size_t)v * 2 + o) * K + k] = vco_interval_ff(
-        ma, mb, vc.R, Rk, inv_R, ln2_12R, m_nyq, l440, T, &seg[((size_t)v * 2 + o) * K + k]);
-    if (o == 1) {
-      const float fk = (float)vc.sample_rate * ff_to_float(inc_at_ff(ff_min(ma, m_nyq), l440, T));
-      const float kap = fminf((float)kBrightnessMax, 1.f + (float)vc.sample_rate / (8.f * fk));
+    float inc_first;
+    seg_sum[((size_t)v * 2 + o) * K + k] = ff_to_double(
+        vco_interval_ff(ma, mb, vc.R, Rk, vc.inv_R, vc.ln2_12R, vc.m_nyq_ff, vc.log2_440_over_sr, T,
+                        &seg[((size_t)v * 2 + o) * K + k], &inc_first));
+    if (o == 1) {  // drive 1 + SR / (8 f) at the (capped) frequency of the interval start
+      const float kap = fminf((float)kBrightnessMax, 1.f + 0.125f / inc_first);
       kappa[((size_t)v * 2 + 0) * K + k] = kap;
       kappa[((size_t)v * 2 + 1) * K + k] = 1.f / tanhf(kap);
     }
@@ -355,7 +357,7 @@ void launch_control_pipeline(const VoiceConst& vc, uint64_t seed, uint64_t batch
   dim3 gp((P + kPT - 1) / kPT, batch), gk((K + kPT - 1) / kPT, batch);
   dim3 g6((6 * P + kPT - 1) / kPT, batch);
   plain_params<<<batch, 128, 0, st>>>(vc, seed, batch_index, batch, params_in, params_out, cb.y);
-  plain_voice_consts<<<batch, 64, 0, st>>>(cb.y, cb.vff);
+  plain_voice_consts<<<batch, 96, 0, st>>>(vc, cb.y, cb.vff);
   plain_adsr<<<g6, kPT, 0, st>>>(vc, cb.vff, cb.env);
   plain_lfo_rate<<<gp, kPT, 0, st>>>(vc, cb.vff, cb.env, cb.lfo_inc);
   plain_phase_scan<<<batch, kPT, 0, st>>>(cb.lfo_inc, cb.lfo_phase, P, P, cb.y, kLfo + 2,

@@ -98,7 +98,7 @@ void synth_default_config(synth_config* out) {
   out->control_rate = 441.0;
   out->seconds = 4.0;
   out->max_batch = 128;
-  out->carry = SYNTH_CARRY_FP64;
+  out->carry = SYNTH_CARRY_FIXED64;
   out->nebula = nullptr;
 }
 
@@ -108,7 +108,7 @@ synth_status synth_create(const synth_config* cfg, synth_handle* out) {
   const double sr = cfg->sample_rate, cr = cfg->control_rate;
   if (!(sr > 0.0) || !(cr > 0.0) || !(cfg->seconds > 0.0) || cfg->max_batch < 1)
     return SYNTH_ERR_ARG;
-  if (cfg->carry != SYNTH_CARRY_FP64 && cfg->carry != SYNTH_CARRY_FP32) return SYNTH_ERR_ARG;
+  if (cfg->carry != SYNTH_CARRY_FIXED64 && cfg->carry != SYNTH_CARRY_FP32) return SYNTH_ERR_ARG;
   const double r = sr / cr;
   const long long R = std::llround(r);
   const double n = cfg->seconds * sr;
@@ -135,6 +135,7 @@ synth_status synth_create(const synth_config* cfg, synth_handle* out) {
   h->vc.R = (int32_t)R;
   h->vc.K = (int32_t)((N + R - 1) / R);
   h->vc.carry_fp32 = cfg->carry == SYNTH_CARRY_FP32 ? 1 : 0;
+  voice_const_derive(h->vc);
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     delete h;

@@ -13,6 +13,8 @@
 
 #include <cstdint>
 
+#include "ff.cuh"
+
 namespace synth {
 
 constexpr int kNumParams = 78;
@@ -37,7 +39,9 @@ constexpr uint32_t kStreamParam = 0;
 constexpr uint32_t kStreamNoise = 1;
 
 // Everything a render kernel needs about the configuration (passed by value
-// as a __grid_constant__ kernel parameter).
+// as a __grid_constant__ kernel parameter). The float-float fields and the
+// tables are derived on the host (voice_const_derive), so that the kernels
+// need no FP64 arithmetic for them.
 struct VoiceConst {
   double lo[kNumParams], hi[kNumParams], curve[kNumParams];
   int32_t sym[kNumParams];
@@ -47,7 +51,37 @@ struct VoiceConst {
   int32_t R;         // samples per control interval (multiple of 4)
   int32_t K;         // control intervals, ceil(N / R)
   int32_t carry_fp32;
+  // Sec. 3.3 map as y = map_base + map_scale a^curve (range_map_ff)
+  ff map_base[kNumParams], map_scale[kNumParams], map_curve[kNumParams];
+  int32_t map_code[kNumParams];  // 1, 2, 3 for those integer curves, else 0
+  ff inv_cr;            // 1 / control rate
+  ff inv_R;             // 1 / R
+  ff ln2_12R;           // ln 2 / (12 R)
+  ff m_nyq_ff;          // m_nyq
+  ff log2_440_over_sr;  // log2(440 / SR)
+  ff inv_2pi;           // 1 / (2 pi)
+  alignas(16) FFTables T;
 };
+
+// Fills the derived fields of vc from its FP64 fields (host).
+inline void voice_const_derive(VoiceConst& vc) {
+  for (int p = 0; p < kNumParams; ++p) {
+    const double span = vc.hi[p] - vc.lo[p];
+    const double scale = vc.sym[p] ? 0.5 * span : span;
+    vc.map_base[p] = ff_from_double(vc.sym[p] ? vc.lo[p] + scale : vc.lo[p]);
+    vc.map_scale[p] = ff_from_double(scale);
+    vc.map_curve[p] = ff_from_double(vc.curve[p]);
+    const double c = vc.curve[p];
+    vc.map_code[p] = c == 1.0 ? 1 : (c == 2.0 ? 2 : (c == 3.0 ? 3 : 0));
+  }
+  vc.inv_cr = ff_from_double(1.0 / vc.control_rate);
+  vc.inv_R = ff_from_double(1.0 / (double)vc.R);
+  vc.ln2_12R = ff_from_double(0.69314718055994530942 / (12.0 * (double)vc.R));
+  vc.m_nyq_ff = ff_from_double(vc.m_nyq);
+  vc.log2_440_over_sr = ff_from_double(log2(440.0 / vc.sample_rate));
+  vc.inv_2pi = ff_from_double(0.15915494309189533577);
+  ff_tables_fill(vc.T);
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two

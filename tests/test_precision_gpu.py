@@ -1,7 +1,7 @@
 """Precision study: batch 32 x 60 s sine-only voices, constant pitch and a
 linear midi glide with endpoints uniform in midi over 20 Hz .. 8 kHz; the
-phase-scan carry in FP64 (the library's mode) and in FP32 (study mode),
-each against the FP64 oracle. Max-abs error and the phase drift it implies
+VCO phase running sums in 64-bit fixed point (the library's mode, finer than
+FP64) and in FP32 (study mode), each against the FP64 oracle. Max-abs error and the phase drift it implies
 (|error| / 2 pi cycles, over the last second) are printed as a JSON line."""
 import json
 import math
@@ -35,7 +35,7 @@ def test_precision_study_60s(oracle_mod, glide):
     pin = torch.tensor(u, dtype=torch.float32, device="cuda")
     report = {"glide": glide, "batch": BATCH, "seconds": SECONDS}
     last = int(SECONDS * 44100) - 44100
-    for name, carry in (("fp64_carry", pkg.SYNTH_CARRY_FP64), ("fp32_carry", pkg.SYNTH_CARRY_FP32)):
+    for name, carry in (("fixed64_carry", pkg.SYNTH_CARRY_FIXED64), ("fp32_carry", pkg.SYNTH_CARRY_FP32)):
         syn = pkg.Synth(seconds=SECONDS, max_batch=BATCH, carry=carry, nebula=nb)
         audio, params = syn.render(0, 0, BATCH, params_in=pin)
         syn.sync()
@@ -46,5 +46,5 @@ def test_precision_study_60s(oracle_mod, glide):
                         "drift_cycles_last_1s": float(err[:, last:].max() / (2 * math.pi))}
         syn.close()
     print("PRECISION " + json.dumps(report))
-    assert report["fp64_carry"]["max_abs"] <= 2e-4
-    assert report["fp32_carry"]["max_abs"] > report["fp64_carry"]["max_abs"]
+    assert report["fixed64_carry"]["max_abs"] <= 2e-4
+    assert report["fp32_carry"]["max_abs"] > report["fixed64_carry"]["max_abs"]

@@ -71,11 +71,17 @@ def test_batch128_sampled_voices(synth4, oracle_mod, batch_index):
 
 
 def test_fused_equals_plain(synth4):
+    """The two forms share the control-rate arithmetic but not the parameter
+    map (float-float vs FP64) nor the running phase sums (fixed point vs
+    FP64), so an interval's starting phase may differ in its last float bit;
+    phase0 + local phase (|local| < 64 cycles) then rounds to a neighbouring
+    float, 2^-18 cycles apart: 2 pi 2^-18 = 2.4e-5 per oscillator at unit
+    gain. The bar is twice that."""
     a1, p1 = synth4.render(3, 2, 64)
     a2, p2 = synth4.render(3, 2, 64, plain=True)
     synth4.sync()
     assert np.array_equal(p1.cpu().numpy(), p2.cpu().numpy())
-    assert float((a1 - a2).abs().max()) <= 1e-5
+    assert float((a1 - a2).abs().max()) <= 5e-5
 
 
 def test_replay_is_deterministic(synth4, torch_cuda):
@@ -141,10 +147,11 @@ def test_params_in_edge_corners(torch_cuda, oracle_mod, plain):
 
 
 @pytest.mark.parametrize("plain", [False, True])
-@pytest.mark.parametrize("seconds", [44 / 44100, 0.1, 12800 / 44100, 0.29])
+@pytest.mark.parametrize("seconds", [44 / 44100, 0.1, 25500 / 44100, 25600 / 44100, 0.29])
 def test_ragged_lengths(torch_cuda, oracle_mod, seconds, plain):
     """Lengths shorter than one control interval, a ragged last interval,
-    N not a multiple of 4, and exactly one full tile of intervals."""
+    N not a multiple of 4, exactly one full tile of 255 intervals, and one
+    full tile plus a tile of a single interval."""
     import paper_2104_12922_gb300 as pkg
     syn = pkg.Synth(seconds=seconds, max_batch=5)
     audio, params = syn.render(21, 7, 5, plain=plain)

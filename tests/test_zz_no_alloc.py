@@ -65,8 +65,8 @@ def test_noalloc_rejects_batches_beyond_its_scratch(env):
     torch, pkg, L = env
     cfg = pkg.synth_default_config()
     out = torch.empty(1, device="cuda")
-    # 4 s voices: 256 + 48 * 14 * batch bytes must fit in 256 KiB (batch <= 389)
-    st = L.synth_render_noalloc(ctypes.byref(cfg), 0, 0, 390, None, out.data_ptr(), None, None)
+    # 4 s voices: 256 + 48 * 7 * batch bytes must fit in 256 KiB (batch <= 779)
+    st = L.synth_render_noalloc(ctypes.byref(cfg), 0, 0, 780, None, out.data_ptr(), None, None)
     assert st == pkg.SYNTH_ERR_ARG
     assert L.synth_render_noalloc(None, 0, 0, 1, None, out.data_ptr(), None, None) == pkg.SYNTH_ERR_ARG
     assert L.synth_render_noalloc(ctypes.byref(cfg), 0, 0, 0, None, None, None, None) == pkg.SYNTH_OK
