@@ -190,38 +190,45 @@ __device__ inline ff vco_interval_ff(ff m_a, ff m_b, int R, int Rk, ff inv_R, ff
   } else {
     c_first = capped(0); c_last = capped(Rk - 1);
   }
-  int jc;
-  bool a_lin, b_lin;
-  ff cA, cB, LB, total;
-  const ff half = ff_make(0.5f);
-  if (!c_first && !c_last) {
-    jc = Rk; a_lin = (x.hi == 0.f); b_lin = true;
-    cA = inc_at_ff(m_a, log2_440_over_sr, T); cB = half; LB = ff_make(0.f);
-    total = geo_sum_ff(cA, x, Rk, T);
-  } else if (c_first && c_last) {
-    jc = 0; a_lin = true; b_lin = true;
-    cA = half; cB = half; LB = ff_make(0.f);
-    total = ff_make(0.5f * (float)Rk);
-  } else {
+  // Cases: no cap (one geometric piece A over Rk samples), all capped (one
+  // linear piece at 1/2), rising through the cap at jc (geometric A, then
+  // 1/2), falling out of it at jc (1/2, then geometric B). Each has at most
+  // one geometric piece: its first pitch m_g and length k_g.
+  int jc = Rk;
+  if (c_first != c_last) {
     const float js = (m_nyq.hi - m_a.hi) * (float)R / dm.hi;
     jc = (int)fminf(fmaxf(ceilf(js), 0.f), (float)(Rk - 1));
-    if (!c_first) {  // rising through the cap at jc
+    if (!c_first) {  // rising: first capped sample
       while (jc > 0 && capped(jc - 1)) --jc;
       while (jc < Rk && !capped(jc)) ++jc;
-      a_lin = (x.hi == 0.f); b_lin = true;
-      cA = inc_at_ff(m_a, log2_440_over_sr, T); cB = half;
-      LB = geo_sum_ff(cA, x, jc, T);
-      total = ff_add_f(LB, 0.5f * (float)(Rk - jc));
-    } else {  // falling out of the cap at jc
+    } else {  // falling: first uncapped sample
       while (jc > 0 && !capped(jc - 1)) --jc;
       while (jc < Rk && capped(jc)) ++jc;
-      a_lin = true; b_lin = (x.hi == 0.f);
-      cA = half;
-      cB = inc_at_ff(ff_add(m_a, ff_mul(dm, ff_mul_f(inv_R, (float)jc))), log2_440_over_sr, T);
-      LB = ff_make(0.5f * (float)jc);
-      total = ff_add(LB, geo_sum_ff(cB, x, Rk - jc, T));
     }
+  } else if (c_first) {
+    jc = 0;
   }
+  const ff half = ff_make(0.5f);
+  const bool geo = !(c_first && c_last);
+  const int k_g = c_first ? Rk - jc : jc;  // samples of the geometric piece
+  ff c_g = half, s_g = ff_make(0.5f * (float)k_g);  // all capped: k_g samples at 1/2
+  if (geo) {
+    const ff m_g = c_first ? ff_add(m_a, ff_mul(dm, ff_mul_f(inv_R, (float)jc))) : m_a;
+    c_g = inc_at_ff(m_g, log2_440_over_sr, T);
+    s_g = geo_sum_ff(c_g, x, k_g, T);
+  }
+  const bool xz = x.hi == 0.f;
+  ff cA, cB, LB, total;
+  bool a_lin, b_lin;
+  if (!c_first) {  // A geometric (jc = Rk when never capped), B at 1/2
+    cA = c_g; cB = half; LB = s_g; a_lin = xz; b_lin = true;
+    total = ff_add_f(s_g, 0.5f * (float)(Rk - jc));
+  } else {         // A at 1/2 (jc samples), B geometric (none when all capped)
+    cA = half; cB = geo ? c_g : half; LB = ff_make(0.5f * (float)jc); a_lin = true;
+    b_lin = geo ? xz : true;
+    total = ff_add(LB, s_g);
+  }
+  if (!c_first && !c_last) LB = ff_make(0.f);
   const float xf = x.hi;
   const bool tiny = fabsf(xf) < 1e-30f;
   const float e1 = tiny ? 0.f : expm1f(xf);

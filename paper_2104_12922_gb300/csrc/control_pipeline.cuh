@@ -20,6 +20,7 @@ struct ControlBuffers {
   double* seg_sum;    // [B][2][K] phase advanced over each interval
   double* seg_start;  // [B][2][K] phase at each interval start (wrapped)
   float* kappa;       // [B][2][K] square-saw drive and 1/tanh(drive)
+  float* mixc;        // [B][5] mixer gains (3), square-saw shape, 1 / (1 + shape)
 };
 
 // Bytes of the control buffers for `batch` voices (256-byte aligned sections).

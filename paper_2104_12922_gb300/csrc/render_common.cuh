@@ -45,7 +45,7 @@ __device__ __forceinline__ void vco_inc_quad(const SegVco& s, int j0, float inc[
 
 constexpr double kLn2 = 0.69314718055994530942;
 
-// Phases (cycles, wrapped to [-1/2, 1/2)) of samples j0..j0+3 of an interval.
+// Phases (cycles, wrapped to [-1/2, 1/2]) of samples j0..j0+3 of an interval.
 __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
   const int jc = s.jc_flags & 0xffff;
   float loc[4];
@@ -84,28 +84,48 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float p = s.phase0 + loc[i];
-    p -= floorf(p);
-    ph[i] = p >= 0.5f ? p - 1.f : p;
+    const float p = s.phase0 + loc[i];
+    ph[i] = p - rintf(p);  // exact
   }
 }
 
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
-// tanh via one exponential: 1 - 2 / (1 + e^{2z}); the argument is bounded to
-// |z| <= 15 where tanh is 1 to within 2e-13.
-__device__ __forceinline__ float tanh_fast(float z) {
-  z = fminf(fmaxf(z, -15.f), 15.f);
-  return 1.f - __fdividef(2.f, 1.f + __expf(2.f * z));
+// The SFU's approximate 2^x and 1/x (PTX ex2.approx / rcp.approx; ftz).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// Square-saw at phase p (cycles in [-1/2, 1/2)): theta = 2 pi p,
+// tanh z = 1 - 2 / (1 + e^{2z}), given y = 2 z log2(e): e^{2z} = 2^y. No
+// clamp is needed: 2^y overflows to +inf (tanh = 1) or flushes to 0
+// (tanh = -1), and the reciprocal of +inf is 0.
+__device__ __forceinline__ float tanh_from_y(float y) {
+  return fmaf(-2.f, rcp_approx(1.f + ex2_approx(y)), 1.f);
+}
+constexpr float kTwoLog2e = 2.88539008177792681f;  // 2 log2(e)
+
+// Square-saw from sin and cos of the phase angle and per-interval constants
+// k2 = 2 kappa log2(e), c1 = g / (tanh(kappa) (1 + shape)), c2 = c1 shape:
+// g tanh(kappa sin) / tanh(kappa) * (1 + shape cos) / (1 + shape).
+__device__ __forceinline__ float square_saw_sc(float sn, float cs, float k2, float c1, float c2) {
+  return tanh_from_y(k2 * sn) * fmaf(c2, cs, c1);
+}
+
+// Square-saw at phase p (cycles in [-1/2, 1/2]): theta = 2 pi p,
 // tanh(kappa sin theta) / tanh(kappa) * (1 + shape cos theta) / (1 + shape).
 __device__ __forceinline__ float square_saw(float p, float kappa, float inv_tanh_kappa, float shape,
                                             float inv_1p_shape) {
   float sn, cs;
   __sincosf(kTwoPiF * p, &sn, &cs);
-  return tanh_fast(kappa * sn) * inv_tanh_kappa * fmaf(shape, cs, 1.f) * inv_1p_shape;
+  const float c1 = inv_tanh_kappa * inv_1p_shape;
+  return square_saw_sc(sn, cs, kTwoLog2e * kappa, c1, c1 * shape);
 }
 
 // ---------------------------------------------------------------------------

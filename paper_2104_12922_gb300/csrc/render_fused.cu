@@ -45,10 +45,13 @@ using u64 = unsigned long long;
 
 struct __align__(16) Smem {
   FFTables T;
-  SegVco seg[2][TI];
-  float kappa[TI];
-  float inv_tanh_kappa[TI];
-  float amp[3][P];           // sine, square-saw, noise amplitudes at the control points
+  union {
+    ff env[6][P];            // the 6 ADSRs at the control points (steps 2-3)
+    SegVco seg[2][TI];       // VCO interval descriptions (steps 4-5)
+  };
+  float4 sq[TI];             // square-saw constants per interval: k2, c1, c2 (square_saw_sc)
+  float4 ampv[P];            // gain x amplitude at the control points: sine, square-saw (gain
+                             // folded into sq), noise
   ff m[2][P];                // VCO pitch (midi) at the control points
   ff y[kNumParams];          // human-range parameters
   VoiceFF V;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(NT, 3) render_fused_kernel(
   const int qps = R >> 2;             // quads per control interval
   const int dq_s = NT / qps;          // a thread's quad stride NT as (intervals, quads)
   const int dq_j = NT - dq_s * qps;
-  const bool vec_ok = (N & 3) == 0;
+  const bool vec_ok = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(audio) & 15) == 0;
   const float invR = 1.0f / (float)R;
   load_tables(s.T, vc.T);
   if (tid == 0) s.epoch = *(volatile unsigned int*)&hdr->epoch;
@@ -200,22 +203,21 @@ __global__ void __launch_bounds__(NT, 3) render_fused_kernel(
 
     // ---- 2. envelopes at point k0 + tid; LFO increments over interval tid --
     const bool has_pt = tid <= nseg;
-    ff env[6];
     if (has_pt) {
       const ff tk = ff_mul_f(vc.inv_cr, (float)(k0 + tid));
-#pragma unroll
-      for (int a = 0; a < 6; ++a) env[a] = adsr_ff(tk, a, V, s.T);
-    } else {
-#pragma unroll
-      for (int a = 0; a < 6; ++a) env[a] = ff_make(0.f);
+#pragma unroll 1
+      for (int a = 0; a < 6; ++a) s.env[a][tid] = adsr_ff(tk, a, V, s.T);
     }
     u64 r0 = 0, r1 = 0;
     if (tid < nseg) {
       const ff lim = ff_make((float)kLfoMaxHz), z = ff_make(0.f);
-      r0 = ff_to_fix64(ff_mul(
-          ff_min(ff_max(ff_add(V.lfo_freq[0], ff_mul(V.lfo_depth[0], env[2])), z), lim), vc.inv_cr));
-      r1 = ff_to_fix64(ff_mul(
-          ff_min(ff_max(ff_add(V.lfo_freq[1], ff_mul(V.lfo_depth[1], env[4])), z), lim), vc.inv_cr));
+#pragma unroll 1
+      for (int l = 0; l < 2; ++l) {
+        const ff rate = ff_min(
+            ff_max(ff_add(V.lfo_freq[l], ff_mul(V.lfo_depth[l], s.env[2 + 2 * l][tid])), z), lim);
+        const u64 r = ff_to_fix64(ff_mul(rate, vc.inv_cr));
+        if (l == 0) r0 = r; else r1 = r;
+      }
     }
 
     // ---- 3. LFO phases: scan + look-back; LFOs, mixer, pitch, amplitudes --
@@ -230,10 +232,14 @@ __global__ void __launch_bounds__(NT, 3) render_fused_kernel(
       __syncthreads();
     }
     if (has_pt) {
-      const ff th0 = fix64_to_ff(s.lfo_p0[0] + s.prefix[0][0] + r0);
-      const ff th1 = fix64_to_ff(s.lfo_p0[1] + s.prefix[0][1] + r1);
-      const ff src[4] = {env[0], env[1], lfo_ff(th0, 0, env[3], V, s.T),
-                         lfo_ff(th1, 1, env[5], V, s.T)};
+      ff lfo0, lfo1;
+#pragma unroll 1
+      for (int l = 0; l < 2; ++l) {
+        const ff th = fix64_to_ff(s.lfo_p0[l] + s.prefix[0][l] + (l == 0 ? r0 : r1));
+        const ff val = lfo_ff(th, l, s.env[3 + 2 * l][tid], V, s.T);
+        if (l == 0) lfo0 = val; else lfo1 = val;
+      }
+      const ff src[4] = {s.env[0][tid], s.env[1][tid], lfo0, lfo1};
 #pragma unroll
       for (int o = 0; o < 2; ++o) {
         ff acc = V.pitch_base[o];
@@ -244,13 +250,15 @@ __global__ void __launch_bounds__(NT, 3) render_fused_kernel(
       float srcf[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) srcf[q] = ff_to_float(src[q]);
+      float amp[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         float acc = V.amp_w[k][0] * srcf[0];
 #pragma unroll
         for (int q = 1; q < 4; ++q) acc = fmaf(V.amp_w[k][q], srcf[q], acc);
-        s.amp[k][tid] = acc;
+        amp[k] = acc;
       }
+      s.ampv[tid] = make_float4(s.gain[0] * amp[0], amp[1], s.gain[2] * amp[2], 0.f);
     }
     __syncthreads();
 
@@ -259,16 +267,19 @@ __global__ void __launch_bounds__(NT, 3) render_fused_kernel(
     if (tid < nseg) {
       const int64_t rem = N - (int64_t)(k0 + tid) * R;
       const int Rk = rem < R ? (int)rem : R;
-      float inc0, inc1;
-      tot[0] = vco_interval_ff(s.m[0][tid], s.m[0][tid + 1], R, Rk, vc.inv_R, vc.ln2_12R,
-                               vc.m_nyq_ff, vc.log2_440_over_sr, s.T, &s.seg[0][tid], &inc0);
-      tot[1] = vco_interval_ff(s.m[1][tid], s.m[1][tid + 1], R, Rk, vc.inv_R, vc.ln2_12R,
-                               vc.m_nyq_ff, vc.log2_440_over_sr, s.T, &s.seg[1][tid], &inc1);
+      float inc1 = 0.5f;
+#pragma unroll 1
+      for (int o = 0; o < 2; ++o) {
+        float inc;
+        const ff t_o = vco_interval_ff(s.m[o][tid], s.m[o][tid + 1], R, Rk, vc.inv_R, vc.ln2_12R,
+                                       vc.m_nyq_ff, vc.log2_440_over_sr, s.T, &s.seg[o][tid], &inc);
+        if (o == 0) tot[0] = t_o; else { tot[1] = t_o; inc1 = inc; }
+      }
       // square-saw drive from the (capped) frequency at the interval start:
-      // 1 + SR / (8 f) = 1 + 1 / (8 inc)
+      // kappa = 1 + SR / (8 f) = 1 + 1 / (8 inc), at most 50
       const float kap = fminf((float)kBrightnessMax, 1.f + 0.125f / inc1);
-      s.kappa[tid] = kap;
-      s.inv_tanh_kappa[tid] = 1.f / tanhf(kap);
+      const float c1 = s.gain[1] * s.inv_1p_shape / tanhf(kap);
+      s.sq[tid] = make_float4(kTwoLog2e * kap, c1, c1 * s.shape, 0.f);
     }
     if constexpr (!kCarryF32) {
       u64 c0 = tid < nseg ? ff_to_fix64(tot[0]) : 0ull;
@@ -307,43 +318,47 @@ __global__ void __launch_bounds__(NT, 3) render_fused_kernel(
 
     // ---- 5. audio ----------------------------------------------------------
     {
-      const float g0 = s.gain[0], g1 = s.gain[1], g2 = s.gain[2];
-      const float shape = s.shape, inv_1p_shape = s.inv_1p_shape;
-      float* out_v = audio + (size_t)v * (size_t)N;
+      const int64_t t0 = (int64_t)k0 * R;                     // first sample of the tile
+      float* out_t = audio + (size_t)v * (size_t)N + (size_t)t0;
+      const int n_t = (int)min((int64_t)nseg * R, N - t0);   // samples in the tile
+      const uint32_t q_t = (uint32_t)(t0 >> 2);               // its first quad (R % 4 == 0)
       const int nq = nseg * qps;
       int si = tid / qps;
       int jq = tid - si * qps;
       for (int q = tid; q < nq; q += NT) {
         const int j0 = jq << 2;
-        const int64_t n0 = (int64_t)(k0 + si) * R + j0;
-        if (n0 < N) {
+        const int off = si * R + j0;
+        if (off < n_t) {
           float ps[4], pq[4];
           vco_quad(s.seg[0][si], j0, ps);
           vco_quad(s.seg[1][si], j0, pq);
-          const float kap = s.kappa[si], itk = s.inv_tanh_kappa[si];
+          const float4 sq = s.sq[si];
+          const float4 A = s.ampv[si], B = s.ampv[si + 1];
           const uint4 nz = philox4x32_10(
-              make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(n0 >> 2), kStreamNoise), key);
+              make_uint4((uint32_t)g, (uint32_t)(g >> 32), q_t + (uint32_t)(off >> 2), kStreamNoise),
+              key);
           const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
-          const float a00 = s.amp[0][si], a10 = s.amp[1][si], a20 = s.amp[2][si];
-          const float d0 = s.amp[0][si + 1] - a00, d1 = s.amp[1][si + 1] - a10,
-                      d2 = s.amp[2][si + 1] - a20;
+          const float d0 = B.x - A.x, d1 = B.y - A.y, d2 = B.z - A.z;
+          const float fj0 = (float)j0 * invR;
           float out4[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const float fj = (float)(j0 + i) * invR;
+            const float fj = fmaf((float)i, invR, fj0);
             const float x_sin = __sinf(kTwoPiF * ps[i]);
-            const float x_sq = square_saw(pq[i], kap, itk, shape, inv_1p_shape);
-            const float x_nz = fmaf(2.f, u01f(nw[i]), -1.f);
-            out4[i] = g0 * fmaf(fj, d0, a00) * x_sin + g1 * fmaf(fj, d1, a10) * x_sq +
-                      g2 * fmaf(fj, d2, a20) * x_nz;
+            float sn, cs;
+            __sincosf(kTwoPiF * pq[i], &sn, &cs);
+            const float x_sq = square_saw_sc(sn, cs, sq.x, sq.y, sq.z);
+            const float x_nz = fmaf((float)(nw[i] >> 8), 0x1p-23f, -1.f);  // 2u - 1, exact
+            out4[i] = fmaf(fmaf(fj, d0, A.x), x_sin,
+                           fmaf(fmaf(fj, d1, A.y), x_sq, fmaf(fj, d2, A.z) * x_nz));
           }
-          if (vec_ok && n0 + 3 < N) {
-            __stcs(reinterpret_cast<float4*>(out_v + n0),
+          if (vec_ok && off + 3 < n_t) {
+            __stcs(reinterpret_cast<float4*>(out_t + off),
                    make_float4(out4[0], out4[1], out4[2], out4[3]));
           } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              if (n0 + i < N) out_v[n0 + i] = out4[i];
+              if (off + i < n_t) out_t[off + i] = out4[i];
           }
         }
         si += dq_s;

@@ -65,7 +65,7 @@ __global__ void plain_params(const __grid_constant__ VoiceConst vc, uint64_t see
 
 // Per-voice constants of the control modules (float-float).
 __global__ void plain_voice_consts(const __grid_constant__ VoiceConst vc, const double* y,
-                                   VoiceFF* vff) {
+                                   VoiceFF* vff, float* mixc) {
   __shared__ FFTables T;
   __shared__ ff yff[kNumParams];
   const int v = blockIdx.x;
@@ -74,7 +74,15 @@ __global__ void plain_voice_consts(const __grid_constant__ VoiceConst vc, const 
     yff[p] = ff_from_double(y[(size_t)v * kNumParams + p]);
   __syncthreads();
   VoiceFF& V = vff[v];
-  if (threadIdx.x < 16) voice_ff_fill(V, yff, threadIdx.x);
+  if (threadIdx.x < 16) {
+    voice_ff_fill(V, yff, threadIdx.x);
+  } else if (threadIdx.x == 32) {  // audio mixer gains and square-saw shape
+    const double* yv = y + (size_t)v * kNumParams;
+    const double norm = fmax(1.0, yv[kMix] + yv[kMix + 1] + yv[kMix + 2]);
+    for (int c = 0; c < 3; ++c) mixc[(size_t)v * 5 + c] = (float)(yv[kMix + c] / norm);
+    mixc[(size_t)v * 5 + 3] = (float)yv[kSqr + 3];
+    mixc[(size_t)v * 5 + 4] = (float)(1.0 / (1.0 + yv[kSqr + 3]));
+  }
   __syncthreads();
   __threadfence_block();
   if (threadIdx.x < 6) V.level_d[threadIdx.x] = gate_level_ff(threadIdx.x, V, T);
@@ -255,7 +263,7 @@ __global__ void plain_sine(const __grid_constant__ VoiceConst vc, int batch, con
   }
 }
 
-__global__ void plain_square_saw(const __grid_constant__ VoiceConst vc, int batch, const double* y,
+__global__ void plain_square_saw(const __grid_constant__ VoiceConst vc, int batch, const float* mixc,
                                  const float* phase, const float* kappa, float* osc) {
   const int64_t N = vc.n_samples;
   const size_t total = (size_t)batch * N;
@@ -264,10 +272,9 @@ __global__ void plain_square_saw(const __grid_constant__ VoiceConst vc, int batc
     const size_t v = i / N;
     const int64_t n = (int64_t)(i - v * N);
     const int k = (int)(n / vc.R);
-    const double sh = y[v * kNumParams + kSqr + 3];
     osc[(v * 3 + 1) * N + n] =
         square_saw(phase[(v * 2 + 1) * N + n], kappa[(v * 2 + 0) * vc.K + k],
-                   kappa[(v * 2 + 1) * vc.K + k], (float)sh, (float)(1.0 / (1.0 + sh)));
+                   kappa[(v * 2 + 1) * vc.K + k], mixc[v * 5 + 3], mixc[v * 5 + 4]);
   }
 }
 
@@ -290,7 +297,7 @@ __global__ void plain_noise(const __grid_constant__ VoiceConst vc, uint64_t seed
   }
 }
 
-__global__ void plain_vca_mix(const __grid_constant__ VoiceConst vc, int batch, const double* y,
+__global__ void plain_vca_mix(const __grid_constant__ VoiceConst vc, int batch, const float* mixc,
                               const float* amp, const float* osc, float* audio) {
   const int64_t N = vc.n_samples;
   const size_t total = (size_t)batch * N;
@@ -298,11 +305,9 @@ __global__ void plain_vca_mix(const __grid_constant__ VoiceConst vc, int batch, 
        i += (size_t)gridDim.x * blockDim.x) {
     const size_t v = i / N;
     const int64_t n = (int64_t)(i - v * N);
-    const double* yv = y + v * kNumParams;
-    const double norm = fmax(1.0, yv[kMix] + yv[kMix + 1] + yv[kMix + 2]);
     float acc = 0.f;
     for (int c = 0; c < 3; ++c)
-      acc += (float)(yv[kMix + c] / norm) * amp[(v * 3 + c) * N + n] * osc[(v * 3 + c) * N + n];
+      acc += mixc[v * 5 + c] * amp[(v * 3 + c) * N + n] * osc[(v * 3 + c) * N + n];
     audio[v * N + n] = acc;
   }
 }
@@ -328,6 +333,7 @@ size_t control_bytes(const VoiceConst& vc, int B) {
   take(sizeof(double) * B * 2 * K);
   take(sizeof(double) * B * 2 * K);
   take(sizeof(float) * B * 2 * K);
+  take(sizeof(float) * B * 5);
   return o;
 }
 
@@ -347,6 +353,7 @@ ControlBuffers control_carve(const VoiceConst& vc, int B, void* ws) {
   cb.seg_sum = reinterpret_cast<double*>(take(sizeof(double) * B * 2 * K));
   cb.seg_start = reinterpret_cast<double*>(take(sizeof(double) * B * 2 * K));
   cb.kappa = reinterpret_cast<float*>(take(sizeof(float) * B * 2 * K));
+  cb.mixc = reinterpret_cast<float*>(take(sizeof(float) * B * 5));
   return cb;
 }
 
@@ -357,7 +364,7 @@ void launch_control_pipeline(const VoiceConst& vc, uint64_t seed, uint64_t batch
   dim3 gp((P + kPT - 1) / kPT, batch), gk((K + kPT - 1) / kPT, batch);
   dim3 g6((6 * P + kPT - 1) / kPT, batch);
   plain_params<<<batch, 128, 0, st>>>(vc, seed, batch_index, batch, params_in, params_out, cb.y);
-  plain_voice_consts<<<batch, 96, 0, st>>>(vc, cb.y, cb.vff);
+  plain_voice_consts<<<batch, 96, 0, st>>>(vc, cb.y, cb.vff, cb.mixc);
   plain_adsr<<<g6, kPT, 0, st>>>(vc, cb.vff, cb.env);
   plain_lfo_rate<<<gp, kPT, 0, st>>>(vc, cb.vff, cb.env, cb.lfo_inc);
   plain_phase_scan<<<batch, kPT, 0, st>>>(cb.lfo_inc, cb.lfo_phase, P, P, cb.y, kLfo + 2,
@@ -389,9 +396,9 @@ cudaError_t launch_render_plain(const VoiceConst& vc, uint64_t seed, uint64_t ba
   plain_upsample_amp<<<grid_for(NS), kPT, 0, st>>>(vc, batch, cb.dest, amp);
   plain_vco_phase<<<grid_for(NS / 2), kPT, 0, st>>>(vc, batch, cb.seg, phase);
   plain_sine<<<grid_for(NS), kPT, 0, st>>>(vc, batch, phase, osc);
-  plain_square_saw<<<grid_for(NS), kPT, 0, st>>>(vc, batch, cb.y, phase, cb.kappa, osc);
+  plain_square_saw<<<grid_for(NS), kPT, 0, st>>>(vc, batch, cb.mixc, phase, cb.kappa, osc);
   plain_noise<<<grid_for(NS / 4), kPT, 0, st>>>(vc, seed, batch_index, batch, osc);
-  plain_vca_mix<<<grid_for(NS), kPT, 0, st>>>(vc, batch, cb.y, amp, osc, audio);
+  plain_vca_mix<<<grid_for(NS), kPT, 0, st>>>(vc, batch, cb.mixc, amp, osc, audio);
   return cudaGetLastError();
 }
 
