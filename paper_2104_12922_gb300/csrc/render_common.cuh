@@ -46,30 +46,39 @@ __device__ __forceinline__ void vco_inc_quad(const SegVco& s, int j0, float inc[
 constexpr double kLn2 = 0.69314718055994530942;
 
 // Phases (cycles, wrapped to [-1/2, 1/2]) of samples j0..j0+3 of an interval.
+// Inside one piece the phase of sample j0 + i is base + g e_i: linear pieces
+// have g = c and e_i = i; geometric pieces phase0 + L + (c/E)(r^(d0+i) - 1)
+// = [phase0 + L + (c/E) E0] + (c/E)(1 + E0) expm1(i x), E0 = expm1(d0 x).
+// The base is wrapped once (exactly), so each sample adds a term below
+// 2 cycles to a number below 1/2 and wraps again.
 __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
   const int jc = s.jc_flags & 0xffff;
-  float loc[4];
   if (j0 + 3 < jc || j0 >= jc) {
     const bool in_b = j0 >= jc;
     const float L = in_b ? s.LB : 0.f;
     const float c = in_b ? s.cB : s.cA;
     const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
     const int d0 = j0 - (in_b ? jc : 0);
+    float base, g, e1, e2, e3;
     if (lin) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) loc[i] = fmaf(c, (float)(d0 + i), L);
+      base = s.phase0 + fmaf(c, (float)d0, L);
+      g = c;
+      e1 = 1.f; e2 = 2.f; e3 = 3.f;
     } else {
-      // r^(d0+i) - 1 = E0 + Ei + E0 Ei with E0 = expm1(d0 x), Ei = expm1(i x)
       const float E0 = expm1f((float)d0 * s.x);
-      const float E1 = s.E1;
-      const float E2 = E1 * (2.f + E1);
-      const float E3 = fmaf(E1, 1.f + E2, E2);
       const float cE = c * s.invE;
-      loc[0] = fmaf(cE, E0, L);
-      loc[1] = fmaf(cE, E0 + E1 + E0 * E1, L);
-      loc[2] = fmaf(cE, E0 + E2 + E0 * E2, L);
-      loc[3] = fmaf(cE, E0 + E3 + E0 * E3, L);
+      base = s.phase0 + fmaf(cE, E0, L);
+      g = fmaf(cE, E0, cE);
+      e1 = s.E1;
+      e2 = e1 * (2.f + e1);
+      e3 = fmaf(e1, 1.f + e2, e2);
     }
+    base -= rintf(base);
+    ph[0] = base;
+    const float p1 = fmaf(g, e1, base), p2 = fmaf(g, e2, base), p3 = fmaf(g, e3, base);
+    ph[1] = p1 - rintf(p1);
+    ph[2] = p2 - rintf(p2);
+    ph[3] = p3 - rintf(p3);
   } else {  // the quad straddles the piece boundary
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -79,13 +88,10 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
       const float c = in_b ? s.cB : s.cA;
       const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
       const int d = j - (in_b ? jc : 0);
-      loc[i] = lin ? fmaf(c, (float)d, L) : fmaf(c * s.invE, expm1f((float)d * s.x), L);
+      const float loc = lin ? fmaf(c, (float)d, L) : fmaf(c * s.invE, expm1f((float)d * s.x), L);
+      const float p = s.phase0 + loc;
+      ph[i] = p - rintf(p);
     }
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float p = s.phase0 + loc[i];
-    ph[i] = p - rintf(p);  // exact
   }
 }
 
@@ -200,18 +206,25 @@ __device__ __forceinline__ float carry_wrap(float v) { return v - floorf(v); }
 // ---------------------------------------------------------------------------
 constexpr int kLookbackSpinLimit = 1 << 20;
 
+// Publishes this window's aggregate of one chain (one lane writes).
 template <class T>
-__device__ inline void lookback(TileState* voice_tiles, int w, int chain, unsigned int epoch,
-                                T own0, T own1, T& ex0, T& ex1, ScratchHeader* hdr) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void lookback_publish(TileState* voice_tiles, int w, int chain,
+                                                 unsigned int epoch, T own0, T own1) {
   TileState* me = voice_tiles + w;
   const unsigned int tag = (epoch & 0x3fffffffu) << 2;
-  if (lane == 0) {
-    __stcg(&me->agg[chain][0], carry_bits(own0));
-    __stcg(&me->agg[chain][1], carry_bits(own1));
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> my_flag(me->flag[chain]);
-    my_flag.store(tag | 1u, cuda::memory_order_release);
-  }
+  __stcg(&me->agg[chain][0], carry_bits(own0));
+  __stcg(&me->agg[chain][1], carry_bits(own1));
+  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> my_flag(me->flag[chain]);
+  my_flag.store(tag | 1u, cuda::memory_order_release);
+}
+
+// Sums the published aggregates of windows 0 .. w-1 (all 32 lanes of a warp;
+// every lane receives the wrapped sum).
+template <class T>
+__device__ inline void lookback_consume(TileState* voice_tiles, int w, int chain,
+                                        unsigned int epoch, T& ex0, T& ex1, ScratchHeader* hdr) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int tag = (epoch & 0x3fffffffu) << 2;
   T s0 = T(0), s1 = T(0);
   for (int j = lane; j < w; j += 32) {
     TileState* p = voice_tiles + j;
@@ -237,6 +250,14 @@ __device__ inline void lookback(TileState* voice_tiles, int w, int chain, unsign
   }
   ex0 = carry_wrap(s0);
   ex1 = carry_wrap(s1);
+}
+
+// Publish, then consume (all 32 lanes of one warp).
+template <class T>
+__device__ inline void lookback(TileState* voice_tiles, int w, int chain, unsigned int epoch,
+                                T own0, T own1, T& ex0, T& ex1, ScratchHeader* hdr) {
+  if ((threadIdx.x & 31) == 0) lookback_publish<T>(voice_tiles, w, chain, epoch, own0, own1);
+  lookback_consume<T>(voice_tiles, w, chain, epoch, ex0, ex1, hdr);
 }
 
 // End-of-launch bookkeeping of the persistent kernels: the last CTA to finish

@@ -127,7 +127,7 @@ __device__ __forceinline__ void block_scan2_f32(float& a, float& b, float (*buf)
 }
 
 template <bool kCarryF32>
-__global__ void __launch_bounds__(NT, 3) render_fused_kernel(
+__global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t batch_index, int batch,
     const float* __restrict__ params_in, float* __restrict__ audio, float* __restrict__ params_out,
     ScratchHeader* hdr, TileState* tiles, int n_windows) {
@@ -201,12 +201,12 @@ __global__ void __launch_bounds__(NT, 3) render_fused_kernel(
     if (tid < 6) s.V.level_d[tid] = gate_level_ff(tid, V, s.T);
     __syncthreads();
 
-    // ---- 2. envelopes at point k0 + tid; LFO increments over interval tid --
+    // ---- 2. rate envelopes at point k0 + tid; LFO increments over interval tid
     const bool has_pt = tid <= nseg;
+    const ff tk = ff_mul_f(vc.inv_cr, (float)(k0 + tid));
     if (has_pt) {
-      const ff tk = ff_mul_f(vc.inv_cr, (float)(k0 + tid));
 #pragma unroll 1
-      for (int a = 0; a < 6; ++a) s.env[a][tid] = adsr_ff(tk, a, V, s.T);
+      for (int a = 2; a <= 4; a += 2) s.env[a][tid] = adsr_ff(tk, a, V, s.T);
     }
     u64 r0 = 0, r1 = 0;
     if (tid < nseg) {
@@ -220,13 +220,23 @@ __global__ void __launch_bounds__(NT, 3) render_fused_kernel(
       }
     }
 
-    // ---- 3. LFO phases: scan + look-back; LFOs, mixer, pitch, amplitudes --
+    // ---- 3. LFO phases: scan, publish this window's aggregate, the other
+    // four envelopes, then the look-back (the predecessors have had the time
+    // of four envelopes to publish theirs); LFOs, mixer, pitch, amplitudes --
     {
       u64 t0, t1;
       block_scan2_fix(r0, r1, s.warp_tot[0], t0, t1);
+      if (tid == 0) lookback_publish<u64>(vt, w, 0, epoch, t0, t1);
+      if (has_pt) {
+#pragma unroll 1
+        for (int i = 0; i < 4; ++i) {  // envelopes 0, 1, 3, 5
+          const int a = i < 2 ? i : 2 * i - 1;
+          s.env[a][tid] = adsr_ff(tk, a, V, s.T);
+        }
+      }
       if (tid < 32) {
         u64 e0, e1;
-        lookback<u64>(vt, w, 0, epoch, t0, t1, e0, e1, hdr);
+        lookback_consume<u64>(vt, w, 0, epoch, e0, e1, hdr);
         if (tid == 0) { s.prefix[0][0] = e0; s.prefix[0][1] = e1; }
       }
       __syncthreads();
