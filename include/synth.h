@@ -68,7 +68,7 @@ typedef struct {
 typedef struct {
   double sample_rate;   /* Hz; Sec. 3.1 default 44100 */
   double control_rate;  /* Hz; Sec. 3.1 default 441. sample_rate/control_rate
-                           must be an integer multiple of 4 */
+                           must be an integer multiple of 4, at most 65532 */
   double seconds;       /* voice length; Abstract: 4 s */
   int32_t max_batch;    /* largest batch any call on this handle will use */
   int32_t carry;        /* SYNTH_CARRY_FIXED64 (default) or SYNTH_CARRY_FP32 */

@@ -113,7 +113,9 @@ synth_status synth_create(const synth_config* cfg, synth_handle* out) {
   const long long R = std::llround(r);
   const double n = cfg->seconds * sr;
   const long long N = std::llround(n);
-  if (R < 4 || std::fabs(r - (double)R) > 1e-9 || (R & 3) != 0) return SYNTH_ERR_UNSUPPORTED;
+  // R < 2^16: an interval description keeps its in-interval sample index in 16 bits
+  if (R < 4 || R > 65532 || std::fabs(r - (double)R) > 1e-9 || (R & 3) != 0)
+    return SYNTH_ERR_UNSUPPORTED;
   if (std::fabs(n - (double)N) > 1e-6 || N < 1 || N > (1LL << 31)) return SYNTH_ERR_UNSUPPORTED;
   synth_handle h = new (std::nothrow) synth_handle_s();
   if (!h) return SYNTH_ERR_OOM;

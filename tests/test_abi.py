@@ -63,6 +63,9 @@ def test_create_rejects_bad_config_without_device(pkg):
     c.control_rate = 441.0 * 100 / 98  # R = 98 is not a multiple of 4
     assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_UNSUPPORTED
     c = pkg.synth_default_config()
+    c.control_rate = 44100.0 / 65536  # R = 2^16: above the 16-bit in-interval index
+    assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_UNSUPPORTED
+    c = pkg.synth_default_config()
     c.carry = 7
     assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_ARG
 
