@@ -51,6 +51,10 @@ constexpr double kLn2 = 0.69314718055994530942;
 // = [phase0 + L + (c/E) E0] + (c/E)(1 + E0) expm1(i x), E0 = expm1(d0 x).
 // The base is wrapped once (exactly), so each sample adds a term below
 // 2 cycles to a number below 1/2 and wraps again.
+// With kWrap = false the phases are left in (-1/2, 2) (the wrapped base plus
+// at most three increments of at most 1/2), which the sine unit takes as
+// they are after scaling by 2 pi.
+template <bool kWrap = true>
 __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
   const int jc = s.jc_flags & 0xffff;
   if (j0 + 3 < jc || j0 >= jc) {
@@ -76,9 +80,9 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
     base -= rintf(base);
     ph[0] = base;
     const float p1 = fmaf(g, e1, base), p2 = fmaf(g, e2, base), p3 = fmaf(g, e3, base);
-    ph[1] = p1 - rintf(p1);
-    ph[2] = p2 - rintf(p2);
-    ph[3] = p3 - rintf(p3);
+    ph[1] = kWrap ? p1 - rintf(p1) : p1;
+    ph[2] = kWrap ? p2 - rintf(p2) : p2;
+    ph[3] = kWrap ? p3 - rintf(p3) : p3;
   } else {  // the quad straddles the piece boundary
 #pragma unroll
     for (int i = 0; i < 4; ++i) {

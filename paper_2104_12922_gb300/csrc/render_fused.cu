@@ -340,8 +340,8 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
         const int off = si * R + j0;
         if (off < n_t) {
           float ps[4], pq[4];
-          vco_quad(s.seg[0][si], j0, ps);
-          vco_quad(s.seg[1][si], j0, pq);
+          vco_quad<false>(s.seg[0][si], j0, ps);
+          vco_quad<false>(s.seg[1][si], j0, pq);
           const float4 sq = s.sq[si];
           const float4 A = s.ampv[si], B = s.ampv[si + 1];
           const uint4 nz = philox4x32_10(
