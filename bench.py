@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -168,9 +169,55 @@ def cpu_oracle_baseline(budget_s: float):
             break
     el = time.perf_counter() - t0
     mhz = done * BATCH * N_SAMPLES / el / 1e6
+    # one thread on the small configuration: 16 voices x 4 s, seed 0, batch index 0
+    t1 = time.perf_counter()
+    oracle.render_batch(cfg, 0, 0, 16, threads=1)
+    el1 = time.perf_counter() - t1
     return {"value": mhz, "unit": "MHz", "cores": cores, "kind": "oracle",
             "sample": f"{done} batch(es) of {BATCH} voices x {SECONDS:g} s (seed = batch index), "
-                      f"{el:.1f} s wall on {cores} threads"}
+                      f"{el:.1f} s wall on {cores} threads",
+            "single_thread": {"value": 16 * N_SAMPLES / el1 / 1e6, "unit": "MHz", "cores": 1,
+                              "sample": f"16 voices x {SECONDS:g} s, seed 0, {el1:.2f} s wall"}}
+
+
+def adjoint_leg(pkg, torch, dev, steps: int = 20):
+    """Inverse-synthesis step of batch 64 x 1 s voices: render from the current
+    parameters, multi-resolution STFT distance to target voices of another
+    seed and its gradient, the adjoint render, one Adam step. Device time per
+    step (CUDA events over `steps` steps after 3 untimed ones)."""
+    B, seconds = 64, 1.0
+    syn = pkg.Synth(seconds=seconds, max_batch=B)
+    n = syn.num_samples
+    target, _ = syn.render(1_000_000, 0, B)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    u = torch.rand((B, 78), device=dev, generator=gen)
+    m, v = torch.zeros_like(u), torch.zeros_like(u)
+    audio = torch.empty((B, n), device=dev)
+    pout = torch.empty_like(u)
+    mr = pkg.MRSTFT(syn, B)
+
+    def step(s):
+        syn.render(0, 0, B, params_in=u, out=audio, params_out=pout)
+        _, g_audio = mr(audio, target, grad=True, target_ready=s > 0)
+        g_u = syn.backward(0, 0, u, g_audio)
+        pkg.param_adam(syn, u, g_u, m, v, s + 1, 0.01)
+
+    for s in range(3):
+        step(s)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for s in range(3, 3 + steps):
+        step(s)
+    end.record()
+    end.synchronize()
+    ms = start.elapsed_time(end) / steps
+    syn.sync()
+    syn.close()
+    return {"ms_per_step": ms, "value": B * n / (ms / 1e3) / 1e6, "unit": "MHz",
+            "config": "batch 64 x 1 s; per step: render, MR-STFT distance (n_fft 512/1024/2048, "
+                      "hop n_fft/4) and its gradient, adjoint render, Adam on the 78 parameters",
+            "steps": steps}
 
 
 def run_reference(args):
@@ -366,6 +413,7 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu:
         cpu = cpu_oracle_baseline(args.cpu_seconds)
+    adjoint = None if args.no_adjoint else adjoint_leg(pkg, torch, dev)
     line = {"metric": METRIC, "value": value, "unit": "MHz", "n_gpus": ws, "steps": steps,
             "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
@@ -379,6 +427,7 @@ def run_ours(args):
             "paper_context": {"value": PAPER_MHZ, "unit": "MHz", "hardware": "single V100 (Sec. 2.2)"},
             "plain": plain, "fused_over_plain": (value / plain["value"]) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "adjoint": adjoint,
             "gpu_launches": steps}
     print(json.dumps(line), flush=True)
     if ws > 1:
