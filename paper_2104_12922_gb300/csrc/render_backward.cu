@@ -47,8 +47,8 @@ BwdLayout bwd_layout(const VoiceConst& vc, int B, size_t base) {
   L.stat = take(sizeof(float) * B * K * kStat);
   L.gpt = take(sizeof(double) * B * P * 5);
   L.vacc = take(sizeof(double) * B * 8);
-  L.dtheta = take(sizeof(double) * B * 2 * P);
-  L.denv = take(sizeof(double) * B * 6 * P);
+  L.dtheta = take(sizeof(float) * B * 2 * P);
+  L.denv = take(sizeof(float) * B * 6 * P);
   L.total = o;
   return L;
 }
@@ -277,65 +277,69 @@ __global__ void __launch_bounds__(kBT) bwd_interval_scan(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------
-// 4. control-rate reverse sweep (FP64), one block per voice.
+// 4. control-rate reverse sweep, one block per voice, in FP32: a gradient
+// needs a relative accuracy of about 1e-3, not the forward's float-float (the
+// forward values it differentiates at are recomputed in float-float and FP64
+// and rounded to float here).
 // ---------------------------------------------------------------------------
 constexpr int kGY = 80;  // slots of the per-voice human-range gradient d/dy (78 used)
 
 // x^a for x >= 0 and its partials (0 at x <= 0, as the forward's convention).
-__device__ __forceinline__ void pow_d(double x, double a, double& p, double& dpx, double& dpa) {
-  if (x <= 0.0) { p = 0.0; dpx = 0.0; dpa = 0.0; return; }
-  p = pow(x, a);
-  dpx = a * pow(x, a - 1.0);
-  dpa = p * log(x);
+__device__ __forceinline__ void pow_d(float x, float a, float& p, float& dpx, float& dpa) {
+  if (x <= 0.f) { p = 0.f; dpx = 0.f; dpa = 0.f; return; }
+  const float lx = logf(x);
+  p = expf(a * lx);
+  dpx = a * p / x;
+  dpa = p * lx;
 }
 
 // Gate-on level g(t) and its partials wrt (t, a, dc, s, alpha).
-__device__ void gate_on_d(double t, const double* q, double& val, double d[5]) {
-  const double a = q[0], dc = q[1], s = q[2], al = q[4];
-  for (int i = 0; i < 5; ++i) d[i] = 0.0;
+__device__ void gate_on_d(float t, const float* q, float& val, float d[5]) {
+  const float a = q[0], dc = q[1], s = q[2], al = q[4];
+  for (int i = 0; i < 5; ++i) d[i] = 0.f;
   if (t < a) {
-    double p, px, pa;
+    float p, px, pa;
     pow_d(t / a, al, p, px, pa);
     val = p;
     d[0] = px / a;             // d/dt
     d[1] = -px * t / (a * a);  // d/da
     d[4] = pa;                 // d/dalpha
   } else if (t < a + dc) {
-    double p, px, pa;
-    const double x = (t - a) / dc;
+    float p, px, pa;
+    const float x = (t - a) / dc;
     pow_d(x, al, p, px, pa);
-    val = 1.0 - (1.0 - s) * p;
-    const double dx = -(1.0 - s) * px;
+    val = 1.f - (1.f - s) * p;
+    const float dx = -(1.f - s) * px;
     d[0] = dx / dc;
     d[1] = -dx / dc;
     d[2] = -dx * x / dc;
     d[3] = p;
-    d[4] = -(1.0 - s) * pa;
+    d[4] = -(1.f - s) * pa;
   } else {
     val = s;
-    d[3] = 1.0;
+    d[3] = 1.f;
   }
 }
 
 // Envelope (Sec. 3.1 reading) partials wrt (a, dc, s, r, alpha, d) at time t.
-__device__ void adsr_d(double t, const double* q, double dur, double out[6]) {
-  for (int i = 0; i < 6; ++i) out[i] = 0.0;
-  double gd[5], val;
+__device__ void adsr_d(float t, const float* q, float dur, float out[6]) {
+  for (int i = 0; i < 6; ++i) out[i] = 0.f;
+  float gd[5], val;
   if (t < dur) {
     gate_on_d(t, q, val, gd);
     out[0] = gd[1]; out[1] = gd[2]; out[2] = gd[3]; out[4] = gd[4];
     return;
   }
-  const double r = q[3], al = q[4];
-  const double tau = t - dur;
+  const float r = q[3], al = q[4];
+  const float tau = t - dur;
   if (!(tau < r)) return;
   gate_on_d(dur, q, val, gd);  // L = g(d)
-  const double L = val;
-  double p, px, pa;
-  const double x = tau / r;
+  const float L = val;
+  float p, px, pa;
+  const float x = tau / r;
   pow_d(x, al, p, px, pa);
-  const double dL = 1.0 - p;          // d env / d L
-  const double dx = -L * px;          // d env / d x
+  const float dL = 1.f - p;           // d env / d L
+  const float dx = -L * px;           // d env / d x
   out[0] = dL * gd[1];
   out[1] = dL * gd[2];
   out[2] = dL * gd[3];
@@ -345,19 +349,20 @@ __device__ void adsr_d(double t, const double* q, double dur, double out[6]) {
 }
 
 // Forward LFO shape mix and its derivative wrt the phase.
-__device__ __forceinline__ void lfo_shapes(double p, double sh[5], double dsh[5]) {
-  double sn, cs;
-  sincospi(2.0 * p, &sn, &cs);
-  sh[0] = sn; dsh[0] = 6.28318530717958647692 * cs;
-  sh[1] = 1.0 - 4.0 * fabs(p - 0.5); dsh[1] = (p - 0.5) < 0.0 ? 4.0 : -4.0;
-  sh[2] = 2.0 * p - 1.0; dsh[2] = 2.0;
-  sh[3] = 1.0 - 2.0 * p; dsh[3] = -2.0;
-  sh[4] = p < 0.5 ? 1.0 : -1.0; dsh[4] = 0.0;
+__device__ __forceinline__ void lfo_shapes(float p, float sh[5], float dsh[5]) {
+  float sn, cs;
+  sincospif(2.f * p, &sn, &cs);
+  sh[0] = sn; dsh[0] = 6.28318530717958647692f * cs;
+  sh[1] = 1.f - 4.f * fabsf(p - 0.5f); dsh[1] = (p - 0.5f) < 0.f ? 4.f : -4.f;
+  sh[2] = 2.f * p - 1.f; dsh[2] = 2.f;
+  sh[3] = 1.f - 2.f * p; dsh[3] = -2.f;
+  sh[4] = p < 0.5f ? 1.f : -1.f; dsh[4] = 0.f;
 }
 
-__device__ __forceinline__ void acc_y(double* gy, int slot, double val) {
-  const double w = warp_sum_d(val);
-  if ((threadIdx.x & 31) == 0 && w != 0.0) atomicAdd(&gy[slot], w);
+// Adds a warp's values into one slot of the per-voice gradient.
+__device__ __forceinline__ void acc_y(float* gy, int slot, float val) {
+  const float w = warp_sum(val);
+  if ((threadIdx.x & 31) == 0 && w != 0.f) atomicAdd(&gy[slot], w);
 }
 
 __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ VoiceConst vc,
@@ -367,83 +372,86 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
                                                    const ff* __restrict__ dest,
                                                    const double* __restrict__ gpt,
                                                    const double* __restrict__ vacc,
-                                                   double* __restrict__ dtheta,
-                                                   double* __restrict__ denv,
+                                                   float* __restrict__ dtheta,
+                                                   float* __restrict__ denv,
                                                    float* __restrict__ grad_params) {
-  __shared__ double gy[kGY];
-  __shared__ double warp_tot[2 * (kBT / 32)];
+  __shared__ float gy[kGY];
+  __shared__ float yv[kNumParams];
+  __shared__ float warp_tot[2 * (kBT / 32)];
   const int v = blockIdx.x;
   const int P = vc.K + 1;
-  const double* yv = y + (size_t)v * kNumParams;
-  const double two_pi = 6.28318530717958647692;
-  for (int i = threadIdx.x; i < kGY; i += kBT) gy[i] = 0.0;
+  const float inv_cr = (float)(1.0 / vc.control_rate);
+  const float inv_2pi = 0.15915494309189533577f;
+  for (int i = threadIdx.x; i < kGY; i += kBT) gy[i] = 0.f;
+  for (int i = threadIdx.x; i < kNumParams; i += kBT) yv[i] = (float)y[(size_t)v * kNumParams + i];
   __syncthreads();
-  double inv_norm[5], wsum_col[5];
+  float inv_norm[5], wsum_col[5];
   for (int j = 0; j < 5; ++j) {
-    double ws = 0.0;
+    float ws = 0.f;
     for (int i = 0; i < 4; ++i) ws += yv[kMod + 5 * i + j];
     wsum_col[j] = ws;
-    inv_norm[j] = 1.0 / fmax(1.0, ws);
+    inv_norm[j] = 1.f / fmaxf(1.f, ws);
   }
-  double lfo_wsum[2];
+  float lfo_wsum[2];
   for (int l = 0; l < 2; ++l) {
-    double ws = 0.0;
+    float ws = 0.f;
     for (int s = 0; s < 5; ++s) ws += yv[kLfo + 8 * l + 3 + s];
     lfo_wsum[l] = ws;
   }
   const double* gv = gpt + (size_t)v * P * 5;
-  double* dth = dtheta + (size_t)v * 2 * P;
-  double* de = denv + (size_t)v * 6 * P;
+  float* dth = dtheta + (size_t)v * 2 * P;
+  float* de = denv + (size_t)v * 6 * P;
 
   // pass A: modulation mixer, LFO outputs, pitch
   for (int base = 0; base < P; base += kBT) {
     const int k = base + threadIdx.x;
     const bool ok = k < P;
     const int kk = ok ? k : 0;
-    double e[6];
-    for (int a = 0; a < 6; ++a) e[a] = ff_to_double(env[((size_t)v * 6 + a) * P + kk]);
-    double mix[2], sh[2][5], dsh[2][5], lfo[2];
+    float e[6];
+    for (int a = 0; a < 6; ++a) e[a] = ff_to_float(env[((size_t)v * 6 + a) * P + kk]);
+    float mix[2], sh[2][5], dsh[2][5], lfo[2];
     for (int l = 0; l < 2; ++l) {
-      const double th = lfo_phase[((size_t)v * 2 + l) * P + kk];
+      const float th = (float)lfo_phase[((size_t)v * 2 + l) * P + kk];
       lfo_shapes(th, sh[l], dsh[l]);
-      double accm = 0.0;
+      float accm = 0.f;
       for (int s = 0; s < 5; ++s) accm += yv[kLfo + 8 * l + 3 + s] * sh[l][s];
-      mix[l] = lfo_wsum[l] < 1e-12 ? 0.0 : accm / lfo_wsum[l];
+      mix[l] = lfo_wsum[l] < 1e-12f ? 0.f : accm / lfo_wsum[l];
       lfo[l] = e[3 + 2 * l] * mix[l];
     }
-    const double src[4] = {e[0], e[1], lfo[0], lfo[1]};
-    double dd[5] = {0, 0, 0, 0, 0}, dst[5];
+    const float src[4] = {e[0], e[1], lfo[0], lfo[1]};
+    float dd[5] = {0, 0, 0, 0, 0}, dst[5];
     if (ok) {
-      dd[0] = yv[kSine + 1] * gv[(size_t)k * 5 + 0];
-      dd[2] = yv[kSqr + 1] * gv[(size_t)k * 5 + 1];
-      dd[1] = gv[(size_t)k * 5 + 2];
-      dd[3] = gv[(size_t)k * 5 + 3];
-      dd[4] = gv[(size_t)k * 5 + 4];
+      dd[0] = yv[kSine + 1] * (float)gv[(size_t)k * 5 + 0];
+      dd[2] = yv[kSqr + 1] * (float)gv[(size_t)k * 5 + 1];
+      dd[1] = (float)gv[(size_t)k * 5 + 2];
+      dd[3] = (float)gv[(size_t)k * 5 + 3];
+      dd[4] = (float)gv[(size_t)k * 5 + 4];
     }
-    for (int j = 0; j < 5; ++j) dst[j] = ff_to_double(dest[((size_t)v * 5 + j) * P + kk]);
+    for (int j = 0; j < 5; ++j) dst[j] = ff_to_float(dest[((size_t)v * 5 + j) * P + kk]);
     // pitch: m = midi + tune + depth * dest
-    const double dm0 = ok ? gv[(size_t)k * 5 + 0] : 0.0, dm1 = ok ? gv[(size_t)k * 5 + 1] : 0.0;
+    const float dm0 = ok ? (float)gv[(size_t)k * 5 + 0] : 0.f;
+    const float dm1 = ok ? (float)gv[(size_t)k * 5 + 1] : 0.f;
     acc_y(gy, kMidi, dm0 + dm1);
     acc_y(gy, kSine, dm0);
     acc_y(gy, kSqr, dm1);
     acc_y(gy, kSine + 1, dm0 * dst[0]);
     acc_y(gy, kSqr + 1, dm1 * dst[2]);
     // dest_j = (sum_i W_ij src_i) / max(1, sum_i W_ij)
-    double dsrc[4] = {0, 0, 0, 0};
+    float dsrc[4] = {0, 0, 0, 0};
     for (int j = 0; j < 5; ++j) {
-      const double over = wsum_col[j] > 1.0 ? 1.0 : 0.0;
+      const float over = wsum_col[j] > 1.f ? 1.f : 0.f;
       for (int i = 0; i < 4; ++i) {
         dsrc[i] += dd[j] * yv[kMod + 5 * i + j] * inv_norm[j];
         acc_y(gy, kMod + 5 * i + j, dd[j] * (src[i] * inv_norm[j] - over * dst[j] * inv_norm[j]));
       }
     }
-    double dea[6] = {dsrc[0], dsrc[1], 0.0, 0.0, 0.0, 0.0};
+    float dea[6] = {dsrc[0], dsrc[1], 0.f, 0.f, 0.f, 0.f};
     for (int l = 0; l < 2; ++l) {
-      const double dl = dsrc[2 + l];
+      const float dl = dsrc[2 + l];
       dea[3 + 2 * l] = dl * mix[l];
-      const double dmix = dl * e[3 + 2 * l];
-      double dthv = 0.0;
-      if (lfo_wsum[l] >= 1e-12) {
+      const float dmix = dl * e[3 + 2 * l];
+      float dthv = 0.f;
+      if (lfo_wsum[l] >= 1e-12f) {
         for (int s = 0; s < 5; ++s) {
           acc_y(gy, kLfo + 8 * l + 3 + s, dmix * (sh[l][s] - mix[l]) / lfo_wsum[l]);
           dthv += yv[kLfo + 8 * l + 3 + s] * dsh[l][s];
@@ -459,21 +467,21 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
 
   // pass B: reverse scan of the LFO phase adjoint -> d/d(phase increment);
   // increments rate_k / CR with rate = clamp(freq + depth * env_rate, 0, 20)
-  double carry0 = 0.0, carry1 = 0.0;
+  float carry0 = 0.f, carry1 = 0.f;
   for (int base = 0; base < P; base += kBT) {
     const int idx = P - 1 - (base + (int)threadIdx.x);
     const bool ok = idx >= 0;
-    double a0 = ok ? dth[idx] : 0.0, a1 = ok ? dth[(size_t)P + idx] : 0.0, t0, t1;
-    block_exclusive_scan2<double, kBT>(a0, a1, warp_tot, t0, t1);
+    float a0 = ok ? dth[idx] : 0.f, a1 = ok ? dth[(size_t)P + idx] : 0.f, t0, t1;
+    block_exclusive_scan2<float, kBT>(a0, a1, warp_tot, t0, t1);
     for (int l = 0; l < 2; ++l) {
-      double dinc = 0.0, er = 0.0, rate_raw = 0.0;
+      float dinc = 0.f, er = 0.f, rate_raw = 0.f;
       if (ok) {
         dinc = (l == 0 ? carry0 + a0 : carry1 + a1);  // sum of dtheta over points after idx
-        er = ff_to_double(env[((size_t)v * 6 + 2 + 2 * l) * P + idx]);
+        er = ff_to_float(env[((size_t)v * 6 + 2 + 2 * l) * P + idx]);
         rate_raw = yv[kLfo + 8 * l] + yv[kLfo + 8 * l + 1] * er;
       }
-      const bool inside = ok && rate_raw >= 0.0 && rate_raw <= kLfoMaxHz;
-      const double dr = inside ? dinc / vc.control_rate : 0.0;
+      const bool inside = ok && rate_raw >= 0.f && rate_raw <= (float)kLfoMaxHz;
+      const float dr = inside ? dinc * inv_cr : 0.f;
       acc_y(gy, kLfo + 8 * l, dr);
       acc_y(gy, kLfo + 8 * l + 1, dr * er);
       if (ok) de[(size_t)(2 + 2 * l) * P + idx] = dr * yv[kLfo + 8 * l + 1];
@@ -482,46 +490,47 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
     carry1 += t1;
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&gy[kLfo + 2], carry0 / two_pi);       // theta_0 = frac(phase0 / 2 pi)
-    atomicAdd(&gy[kLfo + 8 + 2], carry1 / two_pi);
+    atomicAdd(&gy[kLfo + 2], carry0 * inv_2pi);       // theta_0 = frac(phase0 / 2 pi)
+    atomicAdd(&gy[kLfo + 8 + 2], carry1 * inv_2pi);
   }
   __syncthreads();
 
-  // pass C: ADSRs
-  for (int base = 0; base < 6 * P; base += kBT) {
-    const int i = base + threadIdx.x;
-    const bool ok = i < 6 * P;
-    const int a = ok ? i / P : 0, k = ok ? i - a * P : 0;
-    double out[6] = {0, 0, 0, 0, 0, 0};
-    double g = 0.0;
-    if (ok) {
-      g = de[(size_t)a * P + k];
-      if (g != 0.0) adsr_d((double)k / vc.control_rate, yv + kAdsr + 5 * a, yv[kDuration], out);
+  // pass C: ADSRs, one at a time: each thread sums its points' partials,
+  // then one block-wide sum per partial
+  float dur_acc = 0.f;
+  for (int a = 0; a < 6; ++a) {
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = threadIdx.x; k < P; k += kBT) {
+      const float g = de[(size_t)a * P + k];
+      if (g != 0.f) {
+        float out[6];
+        adsr_d((float)((double)k / vc.control_rate), yv + kAdsr + 5 * a, yv[kDuration], out);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[q] += g * out[q];
+        dur_acc += g * out[5];
+      }
     }
-    // lanes of a warp may hold different ADSRs: accumulate per ADSR
-    for (int aa = 0; aa < 6; ++aa) {
-      const double m = (ok && a == aa) ? g : 0.0;
-      for (int q = 0; q < 5; ++q) acc_y(gy, kAdsr + 5 * aa + q, m * out[q]);
-    }
-    acc_y(gy, kDuration, g * out[5]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc_y(gy, kAdsr + 5 * a + q, acc[q]);
   }
+  acc_y(gy, kDuration, dur_acc);
   __syncthreads();
 
   if (threadIdx.x == 0) {
     const double* va = vacc + (size_t)v * 8;
-    gy[kSine + 2] += va[0] / two_pi;
-    gy[kSqr + 2] += va[1] / two_pi;
-    gy[kSqr + 3] += va[5];
+    gy[kSine + 2] += (float)va[0] * inv_2pi;
+    gy[kSqr + 2] += (float)va[1] * inv_2pi;
+    gy[kSqr + 3] += (float)va[5];
     // mixer gains g_i = l_i / max(1, sum l)
-    const double l0 = yv[kMix], l1 = yv[kMix + 1], l2 = yv[kMix + 2];
-    const double sum = l0 + l1 + l2, norm = fmax(1.0, sum);
-    const double dotg = va[2] * l0 + va[3] * l1 + va[4] * l2;
+    const float l0 = yv[kMix], l1 = yv[kMix + 1], l2 = yv[kMix + 2];
+    const float sum = l0 + l1 + l2, norm = fmaxf(1.f, sum);
+    const float dotg = (float)va[2] * l0 + (float)va[3] * l1 + (float)va[4] * l2;
     for (int c = 0; c < 3; ++c)
-      gy[kMix + c] += va[2 + c] / norm - (sum > 1.0 ? dotg / (norm * norm) : 0.0);
+      gy[kMix + c] += (float)va[2 + c] / norm - (sum > 1.f ? dotg / (norm * norm) : 0.f);
   }
   __syncthreads();
   // range map: dy/du
-  if (threadIdx.x < kNumParams) grad_params[(size_t)v * kNumParams + threadIdx.x] = (float)gy[threadIdx.x];
+  if (threadIdx.x < kNumParams) grad_params[(size_t)v * kNumParams + threadIdx.x] = gy[threadIdx.x];
 }
 
 // d y / d u of the range map, applied in place to grad (which holds d/dy).
@@ -558,8 +567,8 @@ cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t
   float* stat = reinterpret_cast<float*>(ws + L.stat);
   double* gpt = reinterpret_cast<double*>(ws + L.gpt);
   double* vacc = reinterpret_cast<double*>(ws + L.vacc);
-  double* dtheta = reinterpret_cast<double*>(ws + L.dtheta);
-  double* denv = reinterpret_cast<double*>(ws + L.denv);
+  float* dtheta = reinterpret_cast<float*>(ws + L.dtheta);
+  float* denv = reinterpret_cast<float*>(ws + L.denv);
   const int K = vc.K, P = K + 1;
   launch_control_pipeline(vc, seed, batch_index, batch, params, nullptr, cb, st);
   cudaMemsetAsync(gpt, 0, sizeof(double) * (size_t)batch * P * 5, st);
