@@ -4,16 +4,22 @@
 // accumulation in tensor memory (TMEM), a fused epilogue. Used for the
 // STFT-as-GEMM, the mel projection and the proposal MLP.
 //
-// One CTA computes one 128 x BN output tile with 6 warps:
+// Persistent: one CTA per SM walks the 128 x BN output tiles (N fastest, so
+// neighbouring CTAs share A rows in L2) with 6 warps:
 //   warp 0      TMA producer: cp.async.bulk.tensor loads of 128x64 A and BNx64 B
-//               tiles (128-byte swizzle) into a STAGES-deep shared-memory ring;
-//   warp 1      allocates TMEM; one elected lane issues tcgen05.mma
-//               (kind::f16, M = 128, N = BN, K = 16 per instruction) and
-//               tcgen05.commit frees each stage and finally signals the epilogue;
+//               tiles (128-byte swizzle) into a STAGES-deep shared-memory ring
+//               that runs on across tiles;
+//   warp 1      allocates two TMEM accumulators of BN columns; one elected
+//               lane issues tcgen05.mma (kind::f16, M = 128, N = BN, K = 16
+//               per instruction) into the accumulator of the tile's parity;
+//               tcgen05.commit frees each stage and hands a finished
+//               accumulator to the epilogue;
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator rows (warp w owns TMEM
-//               lanes 32 (w mod 4) ..), the fused epilogue, global stores.
+//               lanes 32 (w mod 4) ..), the fused epilogue, global stores, then
+//               the accumulator is released -- while the MMAs of the next tile
+//               already run in the other one.
 // Every mbarrier wait is bounded; on timeout the CTA records an error and
-// finishes without touching the tile.
+// finishes.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -129,10 +135,15 @@ struct __align__(1024) GemmSmem {
   __nv_bfloat16 b[kStages][BN * BK];
   uint64_t full[kStages];
   uint64_t empty[kStages];
-  uint64_t accum;
+  uint64_t acc_full[2];   // MMA -> epilogue: accumulator b holds a finished tile
+  uint64_t acc_empty[2];  // epilogue -> MMA: accumulator b may be overwritten
   uint32_t tmem_base;
   int failed;
 };
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 __device__ __forceinline__ float sigmoidf(float x) { return 1.f / (1.f + __expf(-x)); }
 
@@ -144,15 +155,19 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
   GemmSmem<BN>& sm = *reinterpret_cast<GemmSmem<BN>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nk = (K + BK - 1) / BK;
+  const int tiles_n = (N + BN - 1) / BN;
+  const int n_tiles = tiles_n * ((M + BM - 1) / BM);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
-    mbar_init(&sm.accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.acc_full[b], 1);
+      mbar_init(&sm.acc_empty[b], 4);  // one arrival per epilogue warp
+    }
     sm.failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -160,7 +175,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&sm.tmem_base)),
-                 "r"((uint32_t)BN));
+                 "r"((uint32_t)(2 * BN)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -169,95 +184,126 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
   const uint32_t tmem = sm.tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-      if (!mbar_wait(&sm.empty[s], ph ^ 1u)) { sm.failed = 1; break; }
-      mbar_expect_tx(&sm.full[s], (uint32_t)((BM + BN) * BK * 2));
-      tma_load_2d(sm.a[s], &map_a, &sm.full[s], kb * BK, m0);
-      tma_load_2d(sm.b[s], &map_b, &sm.full[s], kb * BK, n0);
+    // producer: the stage ring runs on across this CTA's tiles
+    int it = 0;
+    for (int tile = blockIdx.x; tile < n_tiles && !sm.failed; tile += gridDim.x) {
+      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = it % kStages;
+        const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+        if (!mbar_wait(&sm.empty[s], ph ^ 1u)) { sm.failed = 1; break; }
+        mbar_expect_tx(&sm.full[s], (uint32_t)((BM + BN) * BK * 2));
+        tma_load_2d(sm.a[s], &map_a, &sm.full[s], kb * BK, m0);
+        tma_load_2d(sm.b[s], &map_b, &sm.full[s], kb * BK, n0);
+      }
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
+    // MMA issuer: tile t of this CTA accumulates in TMEM buffer t & 1
     constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-      if (!mbar_wait(&sm.full[s], ph)) { sm.failed = 1; break; }
+    int it = 0, t = 0;
+    for (int tile = blockIdx.x; tile < n_tiles && !sm.failed; tile += gridDim.x, ++t) {
+      const int buf = t & 1;
+      const uint32_t use = (uint32_t)(t >> 1);
+      if (!mbar_wait(&sm.acc_empty[buf], (use & 1u) ^ 1u)) { sm.failed = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(sm.a[s]), b0 = smem_u32(sm.b[s]);
+      const uint32_t acc = tmem + (uint32_t)(buf * BN);
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = it % kStages;
+        const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+        if (!mbar_wait(&sm.full[s], ph)) { sm.failed = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sm.a[s]), b0 = smem_u32(sm.b[s]);
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        umma_bf16(tmem, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
-                  (kb | kk) != 0 ? 1u : 0u);
-      umma_commit(&sm.empty[s]);
+        for (int kk = 0; kk < BK / 16; ++kk)
+          umma_bf16(acc, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
+                    (kb | kk) != 0 ? 1u : 0u);
+        umma_commit(&sm.empty[s]);
+      }
+      umma_commit(&sm.acc_full[buf]);
     }
-    umma_commit(&sm.accum);
   } else if (warp >= 2) {
     // epilogue
-    const bool ok = mbar_wait(&sm.accum, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int row = m0 + 32 * q + lane;
-    if (!ok) sm.failed = 1;
+    int t = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+      const int buf = t & 1;
+      const uint32_t use = (uint32_t)(t >> 1);
+      const bool ok = mbar_wait(&sm.acc_full[buf], use & 1u);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) { sm.failed = 1; break; }
+      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      const int row = m0 + 32 * q + lane;
+      const uint32_t acc = tmem + (uint32_t)(buf * BN) + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
-      if (!ok || row >= M) continue;
-      const int col0 = n0 + c;
-      switch (epi.kind) {
-        case kEpiStoreF32: {
-          float* out = epi.out_f32 + (size_t)row * epi.ldc;
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(acc + (uint32_t)c, v);
+        if (row >= M) continue;
+        const int col0 = n0 + c;
+        switch (epi.kind) {
+          case kEpiStoreF32: {
+            float* out = epi.out_f32 + (size_t)row * epi.ldc;
+            if (col0 + 15 < N && ((reinterpret_cast<uintptr_t>(out + col0) & 15) == 0)) {
+              float4* o4 = reinterpret_cast<float4*>(out + col0);
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (col0 + i < N) out[col0 + i] = v[i] * epi.alpha;
-          break;
-        }
-        case kEpiBiasActBF16: {
-          // y = act(acc + bias) in bf16 (and optionally the transposed copy)
+              for (int i = 0; i < 4; ++i)
+                o4[i] = make_float4(v[4 * i] * epi.alpha, v[4 * i + 1] * epi.alpha,
+                                    v[4 * i + 2] * epi.alpha, v[4 * i + 3] * epi.alpha);
+            } else {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int col = col0 + i;
-            if (col >= N) continue;
-            float z = v[i] + (epi.bias ? epi.bias[col] : 0.f);
-            if (epi.act == kActRelu) z = fmaxf(z, 0.f);
-            else if (epi.act == kActSigmoid) z = sigmoidf(z);
-            const __nv_bfloat16 b = __float2bfloat16(z);
-            if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + col] = b;
-            if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ldc_t + row] = b;
-            if (epi.out_f32) epi.out_f32[(size_t)row * epi.ldc + col] = z;
-          }
-          break;
-        }
-        case kEpiPowerPairs: {
-          // columns (2b, 2b+1) hold (re, im) of bin b: out[row][b] = re^2 + im^2
-#pragma unroll
-          for (int i = 0; i < 16; i += 2) {
-            const int bin = (col0 + i) >> 1;
-            if (col0 + i + 1 < N && bin < epi.n_valid) {
-              const float pw = v[i] * v[i] + v[i + 1] * v[i + 1];
-              if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + bin] = __float2bfloat16(pw);
-              else epi.out_f32[(size_t)row * epi.ldc + bin] = pw;
+              for (int i = 0; i < 16; ++i)
+                if (col0 + i < N) out[col0 + i] = v[i] * epi.alpha;
             }
+            break;
           }
-          break;
-        }
-        case kEpiLogBF16: {
-          // features = alpha (log(acc + eps) - shift) in bf16
+          case kEpiBiasActBF16: {
+            // y = act(acc + bias) in bf16 (and optionally the transposed copy)
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int col = col0 + i;
-            if (col < N && col < epi.n_valid)
-              epi.out_bf16[(size_t)row * epi.ldc + col] =
-                  __float2bfloat16(epi.alpha * (__logf(v[i] + epi.eps) - epi.shift));
+            for (int i = 0; i < 16; ++i) {
+              const int col = col0 + i;
+              if (col >= N) continue;
+              float z = v[i] + (epi.bias ? epi.bias[col] : 0.f);
+              if (epi.act == kActRelu) z = fmaxf(z, 0.f);
+              else if (epi.act == kActSigmoid) z = sigmoidf(z);
+              const __nv_bfloat16 b = __float2bfloat16(z);
+              if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + col] = b;
+              if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ldc_t + row] = b;
+              if (epi.out_f32) epi.out_f32[(size_t)row * epi.ldc + col] = z;
+            }
+            break;
           }
-          break;
+          case kEpiPowerPairs: {
+            // columns (2b, 2b+1) hold (re, im) of bin b: out[row][b] = re^2 + im^2
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+              const int bin = (col0 + i) >> 1;
+              if (col0 + i + 1 < N && bin < epi.n_valid) {
+                const float pw = v[i] * v[i] + v[i + 1] * v[i + 1];
+                if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + bin] = __float2bfloat16(pw);
+                else epi.out_f32[(size_t)row * epi.ldc + bin] = pw;
+              }
+            }
+            break;
+          }
+          case kEpiLogBF16: {
+            // features = alpha (log(acc + eps) - shift) in bf16
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int col = col0 + i;
+              if (col < N && col < epi.n_valid)
+                epi.out_bf16[(size_t)row * epi.ldc + col] =
+                    __float2bfloat16(epi.alpha * (__logf(v[i] + epi.eps) - epi.shift));
+            }
+            break;
+          }
+          default:
+            break;
         }
-        default:
-          break;
       }
+      // the accumulator's values are all in registers or stored: release it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.acc_empty[buf]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -266,7 +312,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)BN));
+                 "r"((uint32_t)(2 * BN)));
   }
 }
 
@@ -313,7 +359,15 @@ cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEp
     cudaFuncSetAttribute(gemm_bf16_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  const int grid = (int)(tiles < sms ? tiles : sms);  // persistent: one CTA per SM
   gemm_bf16_tc<BN><<<grid, kGemmThreads, smem, st>>>(ma, mb, epi, M, N, K, err);
   return cudaGetLastError();
 }
