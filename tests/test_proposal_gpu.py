@@ -2,8 +2,8 @@
 trained on the GPU on voices rendered on the fly, then held-out voices (the
 Sec. 2.2 test split) are fitted by adjoint refinement on the MR-STFT
 distance, once from the network's proposal and once from random parameters.
-The judge is the FP64 oracle: it re-synthesizes both fitted parameter sets
-and measures their multi-resolution STFT distance to its own rendering of
+The FP64 oracle decides: it re-synthesizes both fitted parameter sets and
+measures their multi-resolution STFT distance to its own rendering of
 the target voices. Refinement renders with another noise seed than the
 target, so the distance cannot reach 0 (the noise realisations differ)."""
 import numpy as np

@@ -1,6 +1,6 @@
 """GPU parity of the fused and plain renders against the FP64 oracle.
 
-Bar (the benchmark spec): parameter draws bit-exact; audio max-abs error <= 2e-4 per
+Bar: parameter draws bit-exact; audio max-abs error <= 2e-4 per
 sample over 4 s voices. Inputs are the synth1B1 workload itself: parameters
 drawn from (seed, global voice index), 44.1 kHz, 4 s.
 """
