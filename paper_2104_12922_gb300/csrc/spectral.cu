@@ -28,12 +28,6 @@ namespace synth {
 
 namespace {
 
-__device__ __forceinline__ int64_t reflect_index(int64_t q, int64_t N) {
-  if (q < 0) q = -q;
-  if (q >= N) q = 2 * (N - 1) - q;
-  return q;
-}
-
 // Split-bf16 products: a value a is carried as a_hi = bf16(a) and
 // a_lo = bf16(a - a_hi); a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi keeps about
 // 16 significant bits where a single bf16 product keeps 8. Laying the
@@ -44,29 +38,34 @@ __device__ __forceinline__ void split_bf16(float a, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16(a - __bfloat162float(hi));
 }
 
-// frames[row][seg * n_fft]: row = (voice, frame); seg = 1 plain bf16, seg = 3
-// the [hi | hi | lo] split layout.
-__global__ void frame_reflect_bf16(const float* __restrict__ audio, int64_t N, int n_fft, int hop,
-                                   int F, int batch, int seg, __nv_bfloat16* __restrict__ frames) {
-  const int64_t total = (int64_t)batch * F * n_fft;
-  const int pad = n_fft / 2;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int t = (int)(i % n_fft);
-    const int64_t row = i / n_fft;
-    const int f = (int)(row % F);
-    const int64_t b = row / F;
-    const int64_t q = reflect_index((int64_t)f * hop + t - pad, N);
-    const float a = audio[b * N + q];
-    __nv_bfloat16* dst = frames + row * (int64_t)seg * n_fft + t;
+__device__ __forceinline__ int reflect32(int q, int N) {
+  if (q < 0) q = -q;
+  if (q >= N) q = 2 * (N - 1) - q;
+  return q;
+}
+
+// frames[row][seg * n_fft]: row = (voice, frame), one block per row; seg = 1
+// plain bf16, seg = 3 the [hi | hi | lo] split layout. Two samples per
+// thread and store (n_fft is even).
+__global__ void frame_reflect_bf16(const float* __restrict__ audio, int N, int n_fft, int hop,
+                                   int F, int seg, __nv_bfloat16* __restrict__ frames) {
+  const int row = blockIdx.x;
+  const int f = row % F, b = row / F;
+  const float* a = audio + (size_t)b * N;
+  const int start = f * hop - n_fft / 2;
+  __nv_bfloat16* dst = frames + (size_t)row * seg * n_fft;
+  for (int t = 2 * (int)threadIdx.x; t < n_fft; t += 2 * (int)blockDim.x) {
+    const float a0 = a[reflect32(start + t, N)], a1 = a[reflect32(start + t + 1, N)];
     if (seg == 1) {
-      dst[0] = __float2bfloat16(a);
+      *reinterpret_cast<__nv_bfloat162*>(dst + t) = __floats2bfloat162_rn(a0, a1);
     } else {
-      __nv_bfloat16 hi, lo;
-      split_bf16(a, hi, lo);
-      dst[0] = hi;
-      dst[n_fft] = hi;
-      dst[2 * n_fft] = lo;
+      __nv_bfloat16 h0, l0, h1, l1;
+      split_bf16(a0, h0, l0);
+      split_bf16(a1, h1, l1);
+      const __nv_bfloat162 hh = __halves2bfloat162(h0, h1), ll = __halves2bfloat162(l0, l1);
+      *reinterpret_cast<__nv_bfloat162*>(dst + t) = hh;
+      *reinterpret_cast<__nv_bfloat162*>(dst + n_fft + t) = hh;
+      *reinterpret_cast<__nv_bfloat162*>(dst + 2 * n_fft + t) = ll;
     }
   }
 }
@@ -125,62 +124,69 @@ __global__ void spec_logmag(const float* __restrict__ spec, int ld_spec, int64_t
 
 // |log(|X| + eps) - logy| summed per voice, and the gradient w.r.t. (Re, Im)
 // of X for the loss mean over (bins, frames) of one resolution. Block
-// (v, c) takes a slice of voice v's frames and adds one partial sum.
+// (v, c) takes a slice of voice v's frames and adds one partial sum. The
+// gradient goes out in the split layout [hi | hi | lo] with segments of
+// ld_dspec columns; the padding columns of each segment are written as 0.
 __global__ void spec_l1_logmag_grad(const float* __restrict__ spec, int ld_spec,
                                     const float* __restrict__ logy, int nb, int F, float eps,
                                     float scale, double* __restrict__ loss_voice,
                                     __nv_bfloat16* __restrict__ dspec, int ld_dspec) {
-  __shared__ double red[32];
+  __shared__ float red[32];
   const int v = blockIdx.x;
-  const int64_t row0 = (int64_t)v * F;
-  const int64_t total = (int64_t)F * nb;
-  double local = 0.0;
-  for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.y * blockDim.x) {
-    const int64_t row = row0 + i / nb;
-    const int b = (int)(i % nb);
-    const float re = spec[row * ld_spec + 2 * b], im = spec[row * ld_spec + 2 * b + 1];
-    const float mag = sqrtf(re * re + im * im);
+  const int total = F * nb;
+  float local = 0.f;
+  for (int i = (int)blockIdx.y * (int)blockDim.x + (int)threadIdx.x; i < total;
+       i += (int)gridDim.y * (int)blockDim.x) {
+    const int fr = i / nb, b = i - fr * nb;
+    const size_t row = (size_t)v * F + fr;
+    const float2 x = *reinterpret_cast<const float2*>(spec + row * ld_spec + 2 * b);
+    const float mag = sqrtf(x.x * x.x + x.y * x.y);
     const float d = logf(mag + eps) - logy[row * nb + b];
     local += fabsf(d);
     float gre = 0.f, gim = 0.f;
     if (mag > 0.f && d != 0.f) {
       const float g = (d > 0.f ? scale : -scale) / ((mag + eps) * mag);
-      gre = g * re;
-      gim = g * im;
+      gre = g * x.x;
+      gim = g * x.y;
     }
-    // split layout [hi | hi | lo] with segments of ld_dspec columns
-    __nv_bfloat16* dst = dspec + row * 3 * (int64_t)ld_dspec + 2 * b;
+    __nv_bfloat16* dst = dspec + row * 3 * (size_t)ld_dspec + 2 * b;
     __nv_bfloat16 h0, l0, h1, l1;
     split_bf16(gre, h0, l0);
     split_bf16(gim, h1, l1);
-    dst[0] = h0;
-    dst[1] = h1;
-    dst[ld_dspec] = h0;
-    dst[ld_dspec + 1] = h1;
-    dst[2 * ld_dspec] = l0;
-    dst[2 * ld_dspec + 1] = l1;
+    const __nv_bfloat162 hh = __halves2bfloat162(h0, h1), ll = __halves2bfloat162(l0, l1);
+    *reinterpret_cast<__nv_bfloat162*>(dst) = hh;
+    *reinterpret_cast<__nv_bfloat162*>(dst + ld_dspec) = hh;
+    *reinterpret_cast<__nv_bfloat162*>(dst + 2 * ld_dspec) = ll;
+    if (b == 0) {
+      __nv_bfloat16* prow = dspec + row * 3 * (size_t)ld_dspec;
+      for (int c = 2 * nb; c < ld_dspec; ++c) {
+        prow[c] = __float2bfloat16(0.f);
+        prow[ld_dspec + c] = __float2bfloat16(0.f);
+        prow[2 * ld_dspec + c] = __float2bfloat16(0.f);
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)red[w];
     atomicAdd(&loss_voice[v], t * scale);
   }
 }
 
-// dAudio[b][i] (+)= sum over padded positions p with reflect(p - pad) == i of
-// sum over frames f covering p of dframes[b F + f][p - f hop].
-__global__ void overlap_add_reflect(const float* __restrict__ dframes, int64_t N, int n_fft, int hop,
-                                    int F, int batch, float* __restrict__ daudio) {
+// dAudio[b][s] (+)= sum over padded positions p with reflect(p - pad) == s of
+// sum over frames f covering p of dframes[b F + f][p - f hop]. Grid
+// (samples, voices); accumulate = 0 overwrites.
+__global__ void overlap_add_reflect(const float* __restrict__ dframes, int N, int n_fft, int hop,
+                                    int F, int accumulate, float* __restrict__ daudio) {
   const int pad = n_fft / 2;
-  const int64_t total = (int64_t)batch * N;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / N, s = i % N;
-    int64_t pre[3];
+  const int b = blockIdx.y;
+  const float* dfv = dframes + (size_t)b * F * n_fft;
+  float* out = daudio + (size_t)b * N;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+    int pre[3];
     int np = 0;
     pre[np++] = s + pad;
     if (s >= 1 && s <= pad) pre[np++] = pad - s;
@@ -188,24 +194,18 @@ __global__ void overlap_add_reflect(const float* __restrict__ dframes, int64_t N
       pre[np++] = 2 * (N - 1) - s + pad;
     float acc = 0.f;
     for (int j = 0; j < np; ++j) {
-      const int64_t p = pre[j];
-      int64_t f_hi = p / hop;
+      const int p = pre[j];
+      int f_hi = p / hop;
       if (f_hi > F - 1) f_hi = F - 1;
-      int64_t f_lo = (p - n_fft + hop) / hop;  // ceil((p - n_fft + 1) / hop)
+      int f_lo = (p - n_fft + hop) / hop;  // ceil((p - n_fft + 1) / hop)
       if (p - n_fft + 1 <= 0) f_lo = 0;
-      for (int64_t f = f_lo; f <= f_hi; ++f) {
-        const int64_t t = p - f * hop;
-        if (t >= 0 && t < n_fft) acc += dframes[(b * F + f) * n_fft + t];
+      for (int f = f_lo; f <= f_hi; ++f) {
+        const int t = p - f * hop;
+        if (t >= 0 && t < n_fft) acc += dfv[(size_t)f * n_fft + t];
       }
     }
-    daudio[i] += acc;
+    out[s] = accumulate ? out[s] + acc : acc;
   }
-}
-
-__global__ void fill_zero_f(float* p, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = 0.f;
 }
 
 int grid_of(int64_t n) {
@@ -334,13 +334,14 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
                              double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
                              cudaStream_t st) {
   if (n_res < 1 || n_res > 8) return cudaErrorInvalidValue;
+  for (int r = 0; r < n_res; ++r)  // reflect padding needs more samples than half a frame
+    if (N <= n_ffts[r] / 2 || N >= (int64_t)1 << 31) return cudaErrorInvalidValue;
   MrLayout L = mr_layout(N, batch, n_ffts, n_res, ws);
   cudaError_t e;
   auto spectrum = [&](const float* sig, int r) -> cudaError_t {
     const int n = n_ffts[r], F = stft_frames(N, n);
     const int64_t M = (int64_t)batch * F;
-    frame_reflect_bf16<<<grid_of(M * n), 256, 0, st>>>(sig, N, n, n / 4, F, batch, kSplit,
-                                                       L.frames);
+    frame_reflect_bf16<<<(unsigned)M, 256, 0, st>>>(sig, (int)N, n, n / 4, F, kSplit, L.frames);
     GemmEpilogue ep;
     ep.kind = kEpiStoreF32;
     ep.out_f32 = L.spec;
@@ -358,13 +359,11 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
     }
   }
   cudaMemsetAsync(L.loss_voice, 0, sizeof(double) * batch, st);
-  if (grad_x) fill_zero_f<<<grid_of((int64_t)batch * N), 256, 0, st>>>(grad_x, (int64_t)batch * N);
   for (int r = 0; r < n_res; ++r) {
     const int n = n_ffts[r], F = stft_frames(N, n);
     const int64_t M = (int64_t)batch * F;
     const int ld = L.tabs[r].ld_bwd;
     if ((e = spectrum(x, r)) != cudaSuccess) return e;
-    cudaMemsetAsync(L.dspec, 0, sizeof(__nv_bfloat16) * M * kSplit * ld, st);
     const float scale = 1.0f / (float)((int64_t)F * L.tabs[r].nb);
     const int64_t per_voice = (int64_t)F * L.tabs[r].nb;
     dim3 gl(batch, (unsigned)std::min<int64_t>(64, (per_voice + 255) / 256));
@@ -379,8 +378,9 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
       if ((e = gemm_bf16(L.dspec, kSplit * ld, L.tabs[r].bwd, kSplit * ld, (int)M, n, kSplit * ld,
                          eb, err, st)) != cudaSuccess)
         return e;
-      overlap_add_reflect<<<grid_of((int64_t)batch * N), 256, 0, st>>>(L.dframes, N, n, n / 4, F,
-                                                                       batch, grad_x);
+      dim3 go((unsigned)std::min<int64_t>((N + 255) / 256, 1024), (unsigned)batch);
+      overlap_add_reflect<<<go, 256, 0, st>>>(L.dframes, (int)N, n, n / 4, F, r > 0 ? 1 : 0,
+                                              grad_x);
     }
   }
   if (loss_voice_out)
@@ -415,6 +415,7 @@ cudaError_t logmel_init(int64_t N, int batch, double sample_rate, void* ws, cuda
 
 cudaError_t logmel_features(const float* audio, int64_t N, int batch, void* ws,
                             __nv_bfloat16* features, unsigned int* err, cudaStream_t st) {
+  if (N <= kMelFFT / 2 || N >= (int64_t)1 << 31) return cudaErrorInvalidValue;
   const int n = kMelFFT, F = stft_frames(N, n);
   const int64_t M = (int64_t)batch * F;
   const int nb = n / 2 + 1, ldp = (nb + 7) & ~7;
@@ -426,7 +427,7 @@ cudaError_t logmel_features(const float* audio, int64_t N, int batch, void* ws,
   __nv_bfloat16* frames = reinterpret_cast<__nv_bfloat16*>(base + off);
   off += al256(sizeof(__nv_bfloat16) * M * n);
   __nv_bfloat16* power = reinterpret_cast<__nv_bfloat16*>(base + off);
-  frame_reflect_bf16<<<grid_of(M * n), 256, 0, st>>>(audio, N, n, n / 4, F, batch, 1, frames);
+  frame_reflect_bf16<<<(unsigned)M, 256, 0, st>>>(audio, (int)N, n, n / 4, F, 1, frames);
   cudaMemsetAsync(power, 0, sizeof(__nv_bfloat16) * M * ldp, st);
   GemmEpilogue ep;
   ep.kind = kEpiPowerPairs;

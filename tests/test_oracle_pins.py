@@ -245,7 +245,7 @@ def _sine_patch(oracle_mod, seconds, extra_pins):
 
 
 def test_constant_pitch_sine_closed_form(oracle_mod):
-    """spec closed form: constant pitch gives sin(2 pi f n / SR + phase0)
+    """Closed form: constant pitch gives sin(2 pi f n / SR + phase0)
     exactly (exclusive phase sum: sample 0 carries the initial phase)."""
     for midi, tune, ph0 in [(69.0, 0.0, 0.0), (60.0, 3.5, 0.7), (100.0, -24.0, -2.9)]:
         cfg = _sine_patch(oracle_mod, 4.0, {si.MIDI: midi, si.SINE: tune, si.SINE + 2: ph0})
