@@ -110,6 +110,28 @@ synth_status synth_render(synth_handle h, uint64_t seed, uint64_t batch_index, i
                           const float* params_in_dev, float* audio_dev, float* params_out_dev,
                           void* stream);
 
+/* Render with per-voice peak normalisation and silence rejection. Sec. 2
+ * names nearly silent renders among the undesirable products of sampling
+ * parameters uniformly; this is the library's reading of a remedy, not a
+ * step the paper specifies. The voices are rendered as by synth_render (same
+ * seed, batch_index, params_in and params_out semantics) while the kernel
+ * records each voice's peak p = max_n |x[n]|; then a voice with p >= threshold
+ * and p > 0 is scaled by 1/p (its peak becomes 1; the factor is the correctly
+ * rounded float reciprocal) and any other voice is left as rendered and
+ * flagged silent. One kernel launch: the scaling runs as extra work items of
+ * the render, so it overlaps the render's tail.
+ *  threshold      float >= 0, in full-scale units (e.g. 1e-3 for -60 dBFS).
+ *  peak_out_dev   [batch] float or NULL: p before scaling.
+ *  silent_out_dev [batch] int32 or NULL: 1 if the voice was left as rendered.
+ * Errors: as synth_render, plus SYNTH_ERR_ARG for a negative or NaN threshold.
+ * A wait between work items that exceeds its spin limit leaves the affected
+ * voices unscaled and flagged silent and makes the next synth_sync return
+ * SYNTH_ERR_TIMEOUT. */
+synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t batch_index,
+                                    int32_t batch, const float* params_in_dev, float* audio_dev,
+                                    float* params_out_dev, float threshold, float* peak_out_dev,
+                                    int32_t* silent_out_dev, void* stream);
+
 /* The same render as a plain, unfused sequence of module kernels (one per
  * module, every control-rate and audio-rate intermediate in a caller-owned
  * workspace in device memory), the torchsynth-style design of Sec. 3.1.

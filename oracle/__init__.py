@@ -247,5 +247,18 @@ def render_vjp(cfg: Config, u, seed: int, g: int, w, threads: int = 0) -> np.nda
     return grad
 
 
+def peak_normalize(audio, threshold: float):
+    """Per-voice peak normalisation with silence rejection, in FP64 -- the
+    library's reading of a remedy for the nearly silent renders that Sec. 2
+    expects from uniform parameter sampling: p = max_n |x[n]| per voice;
+    a voice with p >= threshold (and p > 0) is divided by p, any other is
+    left as it is and flagged silent. Returns (audio, peak, silent)."""
+    a = np.array(audio, dtype=np.float64)
+    peak = np.max(np.abs(a), axis=1) if a.shape[1] else np.zeros(a.shape[0])
+    loud = (peak >= threshold) & (peak > 0.0)
+    a[loud] = a[loud] / peak[loud, None]
+    return a, peak, ~loud
+
+
 def hardware_threads() -> int:
     return int(lib().oracle_hardware_threads())

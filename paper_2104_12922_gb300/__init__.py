@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
         L.synth_num_samples.argtypes = [vp]
         L.synth_num_samples.restype = i64
         L.synth_render.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp]
+        L.synth_render_normalized.argtypes = [vp, u64, u64, i32, vp, vp, vp, ctypes.c_float, vp,
+                                              vp, vp]
         L.synth_render_plain_workspace_size.argtypes = [vp, i32, P(ctypes.c_size_t)]
         L.synth_render_plain.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.synth_render_backward_workspace_size.argtypes = [vp, i32, P(ctypes.c_size_t)]
@@ -100,7 +102,8 @@ def lib() -> ctypes.CDLL:
         L.synth_is_test.restype = i32
         L.synth_status_string.argtypes = [ctypes.c_int]
         L.synth_status_string.restype = ctypes.c_char_p
-        for name in ("synth_create", "synth_destroy", "synth_render", "synth_render_plain",
+        for name in ("synth_create", "synth_destroy", "synth_render", "synth_render_normalized",
+                     "synth_render_plain",
                      "synth_render_plain_workspace_size", "synth_sync", "synth_params_to_human",
                      "synth_render_backward", "synth_render_backward_workspace_size"):
             getattr(L, name).restype = ctypes.c_int
@@ -276,6 +279,33 @@ class Synth:
                                   _ptr(params_out), st)
         _check(status, "synth_render_plain" if plain else "synth_render")
         return out, params_out
+
+    def render_normalized(self, seed: int, batch_index: int, batch: int, threshold: float = 1e-3,
+                          params_in=None, out=None, params_out=None, peak=None, silent=None,
+                          stream=None):
+        """Render with per-voice peak normalisation and silence rejection
+        (synth_render_normalized); returns (audio, params, peak, silent)."""
+        import torch
+        if out is None:
+            out = torch.empty((batch, self.num_samples), dtype=torch.float32, device=self.device)
+        if params_out is None:
+            params_out = torch.empty((batch, NUM_PARAMS), dtype=torch.float32, device=self.device)
+        self._check_tensor(out, (batch, self.num_samples), "out")
+        self._check_tensor(params_out, (batch, NUM_PARAMS), "params_out")
+        self._check_tensor(params_in, (batch, NUM_PARAMS), "params_in")
+        if peak is None:
+            peak = torch.empty(batch, dtype=torch.float32, device=self.device)
+        if silent is None:
+            silent = torch.empty(batch, dtype=torch.int32, device=self.device)
+        self._check_tensor(peak, (batch,), "peak")
+        if silent.dtype != torch.int32 or not silent.is_contiguous() or tuple(silent.shape) != (batch,):
+            raise ValueError(f"silent must be a contiguous int32 tensor of shape ({batch},)")
+        status = lib().synth_render_normalized(self.handle, seed, batch_index, batch,
+                                               _ptr(params_in), _ptr(out), _ptr(params_out),
+                                               float(threshold), _ptr(peak), _ptr(silent),
+                                               _stream_ptr(stream))
+        _check(status, "synth_render_normalized")
+        return out, params_out, peak, silent
 
     def sync(self, stream=None) -> None:
         _check(synth_sync(self.handle, _stream_ptr(stream)), "synth_sync")

@@ -27,12 +27,14 @@ static_assert(sizeof(ScratchHeader) == 256, "header is one 256-byte block");
 // 64-bit fixed-point phase, or the bits of a float in the FP32-carry mode.
 struct TileState {
   unsigned int flag[2];  // (epoch << 2) | 1 once agg[chain] of this launch is published
-  unsigned int pad[2];
+  unsigned int done;      // (epoch << 2) | 3 once the tile's audio is written (peak variant)
+  unsigned int peak;      // the bits of the tile's largest |sample| (peak variant)
   unsigned long long agg[2][2];
 };
 static_assert(sizeof(TileState) == 48, "tile state layout");
 
 constexpr unsigned int kErrLookbackTimeout = 1u;
+constexpr unsigned int kErrTileWaitTimeout = 2u;
 
 constexpr int kFusedThreads = 256;     // one thread per control point of a tile
 constexpr int kFusedTilePoints = 256;  // control points per tile of the fused kernel
@@ -40,11 +42,23 @@ constexpr int kFusedTileSeg = kFusedTilePoints - 1;  // control intervals per ti
 
 inline int windows_per_voice(int K) { return (K + kFusedTileSeg - 1) / kFusedTileSeg; }
 
-// Launches the fused persistent render. Returns the CUDA error of the launch.
+// Per-voice peak normalisation inside the fused render: after its last
+// render tile the kernel claims normalisation chunks from the same work
+// counter, so the scaling pass overlaps the tail of the render.
+struct PeakNormArgs {
+  float threshold;     // voices with peak >= threshold (and > 0) are scaled to peak 1
+  float* peak_out;     // [batch] peak |sample| of each voice as rendered, nullable
+  int32_t* silent_out; // [batch] 1 where the voice was left as rendered, nullable
+};
+constexpr int kNormChunkSamples = 8192;  // samples per normalisation work item
+
+// Launches the fused persistent render (with `norm`, also the peak
+// normalisation). Returns the CUDA error of the launch.
 cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
-                                int grid, cudaStream_t stream);
+                                int grid, cudaStream_t stream,
+                                const PeakNormArgs* norm = nullptr);
 int fused_max_active_blocks_per_sm();
 
 // Plain (unfused) form.

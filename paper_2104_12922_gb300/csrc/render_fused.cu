@@ -58,6 +58,7 @@ struct __align__(16) Smem {
   float u[80];
   u64 warp_tot[2][2][kWarps];  // [scan][chain][warp]
   float warp_tot_f[2][kWarps];
+  float warp_max[kWarps];      // peak variant: per-warp largest |sample|
   u64 prefix[2][2];            // [scan][chain]: phase carried in from earlier windows
   float prefix_f[2];
   u64 lfo_p0[2], vco_p0[2];    // initial phases
@@ -126,11 +127,79 @@ __device__ __forceinline__ void block_scan2_f32(float& a, float& b, float (*buf)
   tot1 = tb;
 }
 
-template <bool kCarryF32>
+// One normalisation work item: chunk c (kNormChunkSamples samples) of voice
+// v. Waits, with a spin limit, for the done flags of the voice's render
+// tiles, takes the largest of their peaks, and scales the chunk by 1 / peak
+// when the peak reaches the threshold; chunk 0 also writes the voice's peak
+// and silence flag. Every tile it waits for was claimed earlier from the
+// same counter by a running CTA, and render tiles never wait for these
+// items, so the wait ends.
+__device__ __noinline__ void normalize_chunk(Smem& s, float* __restrict__ audio, int64_t N,
+                                             TileState* vt, int n_windows, int v, int c,
+                                             bool vec_ok, const PeakNormArgs& norm,
+                                             ScratchHeader* hdr, unsigned int epoch) {
+  const int tid = threadIdx.x;
+  const unsigned int tag = ((epoch & 0x3fffffffu) << 2) | 3u;
+  float m = 0.f;
+  for (int w = tid; w < n_windows; w += NT) {
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(vt[w].done);
+    bool ready = false;
+    for (int spins = 0; spins < kLookbackSpinLimit; ++spins) {
+      if (f.load(cuda::memory_order_acquire) == tag) { ready = true; break; }
+      if (*(volatile unsigned int*)&hdr->error) break;
+      __nanosleep(128);
+    }
+    if (!ready) {
+      atomicOr(&hdr->error, kErrTileWaitTimeout);
+      break;
+    }
+    m = fmaxf(m, __uint_as_float(__ldcg(&vt[w].peak)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) s.warp_max[tid >> 5] = m;
+  __syncthreads();
+  float peak = s.warp_max[0];
+#pragma unroll
+  for (int i = 1; i < kWarps; ++i) peak = fmaxf(peak, s.warp_max[i]);
+  const bool failed = *(volatile unsigned int*)&hdr->error & kErrTileWaitTimeout;
+  const bool loud = peak >= norm.threshold && peak > 0.f && !failed;
+  if (c == 0 && tid == 0) {
+    if (norm.peak_out) norm.peak_out[v] = peak;
+    if (norm.silent_out) norm.silent_out[v] = loud ? 0 : 1;
+  }
+  if (!loud) return;
+  const float g = 1.0f / peak;
+  const int64_t a0 = (int64_t)c * kNormChunkSamples;
+  const int n = (int)min((int64_t)kNormChunkSamples, N - a0);
+  float* x = audio + (size_t)v * N + a0;
+  if (vec_ok) {  // N % 4 == 0 and a 16-byte aligned buffer: whole quads
+    float4* x4 = reinterpret_cast<float4*>(x);
+    constexpr int kPer = 4;  // quads in flight per thread
+#pragma unroll 1
+    for (int q0 = tid; 4 * q0 < n; q0 += kPer * NT) {
+      float4 r[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int q = q0 + i * NT;
+        if (4 * q < n) r[i] = __ldcg(x4 + q);
+      }
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int q = q0 + i * NT;
+        if (4 * q < n) __stcs(x4 + q, make_float4(r[i].x * g, r[i].y * g, r[i].z * g, r[i].w * g));
+      }
+    }
+  } else {
+    for (int i = tid; i < n; i += NT) x[i] = __ldcg(x + i) * g;
+  }
+}
+
+template <bool kCarryF32, bool kPeak>
 __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t batch_index, int batch,
     const float* __restrict__ params_in, float* __restrict__ audio, float* __restrict__ params_out,
-    ScratchHeader* hdr, TileState* tiles, int n_windows) {
+    ScratchHeader* hdr, TileState* tiles, int n_windows, const PeakNormArgs norm) {
   __shared__ Smem s;
   const int tid = threadIdx.x;
   const int total_tiles = batch * n_windows;
@@ -149,7 +218,17 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     if (tid == 0) s.tile = (int)atomicAdd(&hdr->work, 1u);
     __syncthreads();  // also: the previous tile's audio is done with the shared buffers
     const int t = s.tile;
-    if (t >= total_tiles) break;
+    if (t >= total_tiles) {
+      // peak variant: the scaling chunks follow the render tiles, voice by
+      // voice (window-major tiles finish their voices in that order)
+      if (!kPeak) break;
+      const int chunks = (int)((N + kNormChunkSamples - 1) / kNormChunkSamples);
+      const int j = t - total_tiles;
+      if (j >= chunks * batch) break;
+      normalize_chunk(s, audio, N, tiles + (size_t)(j / chunks) * n_windows, n_windows,
+                      j / chunks, j % chunks, vec_ok, norm, hdr, s.epoch);
+      continue;
+    }
     const int v = t % batch, w = t / batch;
     const uint64_t g = batch_index * (uint64_t)batch + (uint64_t)v;
     const int k0 = w * TI;
@@ -333,6 +412,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       const int n_t = (int)min((int64_t)nseg * R, N - t0);   // samples in the tile
       const uint32_t q_t = (uint32_t)(t0 >> 2);               // its first quad (R % 4 == 0)
       const int nq = nseg * qps;
+      float vmax = 0.f;  // largest |sample| this thread wrote (kPeak)
       int si = tid / qps;
       int jq = tid - si * qps;
       for (int q = tid; q < nq; q += NT) {
@@ -363,17 +443,46 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
                            fmaf(fmaf(fj, d1, A.y), x_sq, fmaf(fj, d2, A.z) * x_nz));
           }
           if (vec_ok && off + 3 < n_t) {
-            __stcs(reinterpret_cast<float4*>(out_t + off),
-                   make_float4(out4[0], out4[1], out4[2], out4[3]));
+            // streaming stores, except when the scaling pass reads the audio
+            // back: then it stays in L2 for that pass
+            if (kPeak)
+              *reinterpret_cast<float4*>(out_t + off) = make_float4(out4[0], out4[1], out4[2], out4[3]);
+            else
+              __stcs(reinterpret_cast<float4*>(out_t + off),
+                     make_float4(out4[0], out4[1], out4[2], out4[3]));
+            if (kPeak)
+              vmax = fmaxf(fmaxf(vmax, fmaxf(fabsf(out4[0]), fabsf(out4[1]))),
+                           fmaxf(fabsf(out4[2]), fabsf(out4[3])));
           } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              if (off + i < n_t) out_t[off + i] = out4[i];
+              if (off + i < n_t) {
+                out_t[off + i] = out4[i];
+                if (kPeak) vmax = fmaxf(vmax, fabsf(out4[i]));
+              }
           }
         }
         si += dq_s;
         jq += dq_j;
         if (jq >= qps) { jq -= qps; ++si; }
+      }
+      if (kPeak) {
+        // the tile's peak (a block maximum), published with a flag once
+        // every thread's stores are visible at device scope
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if ((tid & 31) == 0) s.warp_max[tid >> 5] = vmax;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+          float m = s.warp_max[0];
+#pragma unroll
+          for (int i = 1; i < kWarps; ++i) m = fmaxf(m, s.warp_max[i]);
+          TileState* me = vt + w;
+          me->peak = __float_as_uint(m);
+          cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(me->done);
+          f.store(((epoch & 0x3fffffffu) << 2) | 3u, cuda::memory_order_release);
+        }
       }
     }
   }
@@ -384,23 +493,28 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
 
 int fused_max_active_blocks_per_sm() {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false>, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false, false>, NT, 0);
   return n;
 }
 
 cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
-                                int grid, cudaStream_t stream) {
+                                int grid, cudaStream_t stream, const PeakNormArgs* norm) {
   const int n_windows = windows_per_voice(vc.K);
   const int total = batch * n_windows;
   grid = grid < total ? grid : total;
-  if (vc.carry_fp32)
-    render_fused_kernel<true><<<grid, NT, 0, stream>>>(vc, seed, batch_index, batch, params_in,
-                                                       audio, params_out, hdr, tiles, n_windows);
-  else
-    render_fused_kernel<false><<<grid, NT, 0, stream>>>(vc, seed, batch_index, batch, params_in,
-                                                        audio, params_out, hdr, tiles, n_windows);
+  const PeakNormArgs nz = norm ? *norm : PeakNormArgs{0.f, nullptr, nullptr};
+#define SYNTH_FUSED_ARGS vc, seed, batch_index, batch, params_in, audio, params_out, hdr, tiles, \
+                         n_windows, nz
+  if (vc.carry_fp32) {
+    if (norm) render_fused_kernel<true, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    else render_fused_kernel<true, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+  } else {
+    if (norm) render_fused_kernel<false, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    else render_fused_kernel<false, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+  }
+#undef SYNTH_FUSED_ARGS
   return cudaGetLastError();
 }
 

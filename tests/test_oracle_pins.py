@@ -389,3 +389,26 @@ def test_dual_number_gradient_matches_finite_differences(oracle_mod):
         checked += 1
         assert grad[p] == pytest.approx(fd[0], rel=1e-5, abs=1e-6), p
     assert checked >= 60
+
+
+def test_peak_normalize_pins(oracle_mod):
+    """Peak normalisation: known peaks, a silent voice, the threshold tie."""
+    n = 1000
+    t = np.arange(n)
+    x = np.stack([0.5 * np.sin(2 * np.pi * t / 40.0),    # peak 0.5 (t = 10)
+                  -0.25 * np.ones(n),                      # peak 0.25, negative
+                  np.zeros(n),                             # silent
+                  1e-3 * np.cos(2 * np.pi * t / 40.0)])    # peak exactly 1e-3 (t = 0)
+    out, peak, silent = oracle_mod.peak_normalize(x.astype(np.float32), 1e-3)
+    assert peak[0] == pytest.approx(0.5, abs=1e-7)
+    assert peak[1] == pytest.approx(0.25, abs=1e-7) and peak[2] == 0.0
+    assert list(silent) == [False, False, True, False]  # p == threshold is kept
+    assert np.max(np.abs(out[0])) == pytest.approx(1.0, abs=1e-12)
+    assert np.allclose(out[1], -1.0)
+    assert np.array_equal(out[2], np.zeros(n))
+    # scale invariance: normalising 3 x gives the same voice
+    out3, peak3, _ = oracle_mod.peak_normalize(3.0 * x[:2], 1e-3)
+    assert np.allclose(out3, out[:2]) and np.allclose(peak3, 3.0 * peak[:2])
+    # a voice below the threshold is returned unchanged
+    out_q, _, sil_q = oracle_mod.peak_normalize(x[3:] * 0.5, 1e-3)
+    assert sil_q[0] and np.array_equal(out_q[0], (x[3] * 0.5).astype(np.float64))
