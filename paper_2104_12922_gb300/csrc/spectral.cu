@@ -389,62 +389,4 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- log-mel
-size_t logmel_workspace_bytes(int64_t N, int batch) {
-  const int n = kMelFFT, F = stft_frames(N, n);
-  const int64_t M = (int64_t)batch * F;
-  const int nb = n / 2 + 1, ldp = (nb + 7) & ~7;
-  return dft_bytes(n, 1) + al256(sizeof(__nv_bfloat16) * kMelBands * ldp) +
-         al256(sizeof(__nv_bfloat16) * M * n) + al256(sizeof(__nv_bfloat16) * M * ldp);
-}
-
-cudaError_t logmel_init(int64_t N, int batch, double sample_rate, void* ws, cudaStream_t st) {
-  const int n = kMelFFT;
-  DftTables t = dft_carve(n, ws, 1);
-  cudaError_t e = dft_fill(t, st);
-  if (e != cudaSuccess) return e;
-  const int nb = n / 2 + 1, ldp = (nb + 7) & ~7;
-  std::vector<float> fb = mel_filterbank_host(n, kMelBands, sample_rate, ldp);
-  std::vector<__nv_bfloat16> fbb(fb.size());
-  for (size_t i = 0; i < fb.size(); ++i) fbb[i] = __float2bfloat16(fb[i]);
-  char* mel = static_cast<char*>(ws) + dft_bytes(n, 1);
-  e = cudaMemcpyAsync(mel, fbb.data(), fbb.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(st);
-}
-
-cudaError_t logmel_features(const float* audio, int64_t N, int batch, void* ws,
-                            __nv_bfloat16* features, unsigned int* err, cudaStream_t st) {
-  if (N <= kMelFFT / 2 || N >= (int64_t)1 << 31) return cudaErrorInvalidValue;
-  const int n = kMelFFT, F = stft_frames(N, n);
-  const int64_t M = (int64_t)batch * F;
-  const int nb = n / 2 + 1, ldp = (nb + 7) & ~7;
-  char* base = static_cast<char*>(ws);
-  DftTables t = dft_carve(n, base, 1);
-  size_t off = dft_bytes(n, 1);
-  __nv_bfloat16* melfb = reinterpret_cast<__nv_bfloat16*>(base + off);
-  off += al256(sizeof(__nv_bfloat16) * kMelBands * ldp);
-  __nv_bfloat16* frames = reinterpret_cast<__nv_bfloat16*>(base + off);
-  off += al256(sizeof(__nv_bfloat16) * M * n);
-  __nv_bfloat16* power = reinterpret_cast<__nv_bfloat16*>(base + off);
-  frame_reflect_bf16<<<(unsigned)M, 256, 0, st>>>(audio, (int)N, n, n / 4, F, 1, frames);
-  cudaMemsetAsync(power, 0, sizeof(__nv_bfloat16) * M * ldp, st);
-  GemmEpilogue ep;
-  ep.kind = kEpiPowerPairs;
-  ep.out_bf16 = power;
-  ep.ldc = ldp;
-  ep.n_valid = nb;
-  cudaError_t e = gemm_bf16(frames, n, t.fwd, n, (int)M, t.rows, n, ep, err, st);
-  if (e != cudaSuccess) return e;
-  GemmEpilogue em;
-  em.kind = kEpiLogBF16;
-  em.out_bf16 = features;
-  em.ldc = kMelBands;
-  em.n_valid = kMelBands;
-  em.eps = 1e-6f;
-  em.shift = kFeatureShift;
-  em.alpha = 1.0f / kFeatureScale;
-  return gemm_bf16(power, ldp, melfb, ldp, (int)M, kMelBands, ldp, em, err, st);
-}
-
 }  // namespace synth

@@ -1,4 +1,5 @@
-// spectral.h -- STFT-as-GEMM front ends (spectral.cu).
+// spectral.h -- spectral front ends: the STFT-as-GEMM MR-STFT distance
+// (spectral.cu) and the FFT log-mel features (logmel_fft.cu).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -6,6 +7,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 namespace synth {
 
@@ -41,10 +43,15 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
                              double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
                              cudaStream_t st);
 
-// Log-mel features [batch][frames][128] (bf16, flattened per voice).
-size_t logmel_workspace_bytes(int64_t N, int batch);
-cudaError_t logmel_init(int64_t N, int batch, double sample_rate, void* ws, cudaStream_t st);
-cudaError_t logmel_features(const float* audio, int64_t N, int batch, void* ws,
-                            __nv_bfloat16* features, unsigned int* err, cudaStream_t st);
+// Slaney mel filterbank [n_mels][ld] (unit-area triangles over 0 .. sr/2).
+std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld);
+
+// Log-mel features [batch][frames][128] (bf16, flattened per voice) through a
+// shared-memory FFT (logmel_fft.cu): tables (logmel_fft_table_bytes, filled
+// once by logmel_fft_init) and one kernel.
+size_t logmel_fft_table_bytes();
+cudaError_t logmel_fft_init(double sample_rate, void* tables, cudaStream_t st);
+cudaError_t logmel_features_fft(const float* audio, int64_t N, int batch, const void* tables,
+                                __nv_bfloat16* features, cudaStream_t st);
 
 }  // namespace synth

@@ -337,7 +337,7 @@ synth_status synth_model_create(synth_handle h, int32_t max_batch, uint64_t seed
   const size_t a_bytes = (sizeof(float) * max_batch * N + 255) & ~size_t(255);
   const size_t p_bytes = (sizeof(float) * max_batch * kNumParams + 255) & ~size_t(255);
   const size_t f_bytes = (sizeof(__nv_bfloat16) * max_batch * m->frames * kMelBands + 255) & ~size_t(255);
-  const size_t mel_bytes = logmel_workspace_bytes(h->vc.n_samples, max_batch);
+  const size_t mel_bytes = logmel_fft_table_bytes();
   if (cudaMalloc(reinterpret_cast<void**>(&m->mem), m->L.total) != cudaSuccess) {
     delete m;
     return SYNTH_ERR_OOM;
@@ -353,7 +353,7 @@ synth_status synth_model_create(synth_handle h, int32_t max_batch, uint64_t seed
   m->feats = reinterpret_cast<__nv_bfloat16*>(w + a_bytes + p_bytes);
   m->mel_ws = w + a_bytes + p_bytes + f_bytes;
   if (mlp_init(m->L, m->mem, seed, 0) != cudaSuccess ||
-      logmel_init(h->vc.n_samples, max_batch, h->vc.sample_rate, m->mel_ws, 0) != cudaSuccess ||
+      logmel_fft_init(h->vc.sample_rate, m->mel_ws, 0) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaFree(m->mem);
     cudaFree(m->work);
@@ -380,10 +380,9 @@ synth_status synth_model_features(synth_model m, const float* audio_dev, int32_t
                                   void* features_dev, void* stream) {
   if (!m) return SYNTH_ERR_STATE;
   if (!audio_dev || !features_dev || batch < 1 || batch > m->max_batch) return SYNTH_ERR_ARG;
-  ScratchHeader* hdr = static_cast<ScratchHeader*>(m->synth->scratch);
-  return check_cuda(logmel_features(audio_dev, m->synth->vc.n_samples, batch, m->mel_ws,
-                                    static_cast<__nv_bfloat16*>(features_dev), &hdr->error,
-                                    static_cast<cudaStream_t>(stream)));
+  return check_cuda(logmel_features_fft(audio_dev, m->synth->vc.n_samples, batch, m->mel_ws,
+                                        static_cast<__nv_bfloat16*>(features_dev),
+                                        static_cast<cudaStream_t>(stream)));
 }
 
 synth_status synth_model_forward(synth_model m, const void* features_dev, int32_t batch,

@@ -1,9 +1,10 @@
 """GPU spectral front ends and the learned proposal against the FP64 oracle.
 
-Tolerances follow from the bf16 arithmetic of the tensor-core GEMMs: every
-bf16 operand carries a relative rounding of at most 2^-9, so an energy that
-passes through four bf16 roundings (frames, DFT weights, power, mel
-weights) is within about 1e-2 relative, i.e. 1e-2 in the log domain.
+Tolerances follow from the arithmetic of each path: the MR-STFT distance
+runs on split-bf16 tensor-core GEMMs (about 16 significant bits), the
+log-mel features on an FP32 FFT with a bf16 output, and the MLP on bf16
+operands with FP32 accumulation (a relative rounding of at most 2^-9 per
+operand).
 """
 import numpy as np
 import pytest
@@ -66,24 +67,33 @@ def test_mrstft_gradient_matches_oracle(env):
     syn.close()
 
 
-def test_logmel_features_match_oracle(env):
+@pytest.mark.parametrize("seconds,batch", [(1.0, 8), (0.05, 3), (4.0, 2)])
+def test_logmel_features_fft_bar(env, seconds, batch):
+    """The FFT front end computes the spectrum in FP32, so the bf16 rounding
+    of the output feature f = (logmel + 2.5) / 6 dominates: |f| < 2 gives a
+    half-ulp of at most 2^-8 in f, 6 x 2^-8 = 0.0234 in log units. Bands
+    within 60 dB of the voice's loudest band (FP32 spectrum error far below
+    their energy) meet that bar plus 2e-3; every band, including those at
+    the 1e-6 floor, stays within 0.1. Sizes: 87 frames (a ragged group of 7),
+    5 frames (one group; reflect padding on both sides of every frame),
+    345 frames; 0.05 s and 4 s voices have N % 512 != 0."""
     from oracle import spectral as sp
     torch, pkg = env
-    syn = pkg.Synth(seconds=1.0, max_batch=8)
+    syn = pkg.Synth(seconds=seconds, max_batch=8)
     model = pkg.ProposalModel(syn, max_batch=8, seed=0)
-    audio, _ = syn.render(4, 0, 8)
+    audio, _ = syn.render(6, 1, batch)
     feats = model.features(audio)
     syn.sync()
-    got = feats.float().cpu().numpy().reshape(8, -1, 128) * pkg.FEATURE_SCALE + pkg.FEATURE_SHIFT
+    got = feats.float().cpu().numpy().reshape(batch, -1, 128)
     ref = sp.log_mel(audio.cpu().numpy()).numpy()
+    ref_f = (ref - pkg.FEATURE_SHIFT) / pkg.FEATURE_SCALE
     assert got.shape == ref.shape
-    # bf16 frames and DFT weights carry a relative rounding of 2^-9, which
-    # leaves a noise floor in every bin about 50 dB under the frame energy;
-    # bands within 30 dB of the voice's loudest band sit well above it
-    loud = ref > (ref.max(axis=(1, 2), keepdims=True) - np.log(1e3))
-    err = np.abs(got - ref)
-    assert np.max(err[loud]) < 0.06
-    assert np.median(err[loud]) < 0.01
+    err = np.abs(got - ref_f) * pkg.FEATURE_SCALE
+    near = ref > (ref.max(axis=(1, 2), keepdims=True) - np.log(1e6))
+    print(f"FFT log-mel: max err {err.max():.4f}, within 60 dB {err[near].max():.4f}, "
+          f"median {np.median(err):.5f}")
+    assert np.max(err[near]) <= 6 * 2.0 ** -8 + 2e-3
+    assert np.max(err) <= 0.1
     model.close()
     syn.close()
 
