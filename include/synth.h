@@ -240,6 +240,23 @@ synth_status synth_model_train_features(synth_model m, const void* features_dev,
  * batch_index, batch) into the model's buffers, features, train step. */
 synth_status synth_model_train_step(synth_model m, uint64_t seed, uint64_t batch_index,
                                     int32_t batch, float lr, float* loss_dev, void* stream);
+/* Streaming synth1B1 generator (Sec. 2.2): network input features and
+ * normalized parameters of the voices g = synth_split_voice(split, first + i),
+ * i < count, rendered (parameters drawn from seed) and transformed chunk by
+ * chunk; a chunk's audio lives only in the model's own buffer, so no audio
+ * of the range is materialised.
+ *  split        0: every voice (g = first + i); 1: the train set; 2: the test set.
+ *  chunk        voices per render + features step, 1..model max_batch;
+ *               0 = the model's max_batch.
+ *  features_dev [count][feature_dim] bf16, as synth_model_features.
+ *  params_dev   [count][78] float or NULL.
+ * Stream-ordered; the model's audio buffer is reused by every chunk, so calls
+ * on one model must not overlap. Errors: SYNTH_ERR_ARG (split outside 0..2,
+ * count < 0, chunk outside 0..max_batch, NULL features_dev with count > 0),
+ * SYNTH_ERR_CUDA. count == 0 is a no-op. */
+synth_status synth_stream_features(synth_model m, uint64_t seed, int32_t split, uint64_t first,
+                                   int64_t count, int32_t chunk, void* features_dev,
+                                   float* params_dev, void* stream);
 /* Proposal: parameters_out [batch][78] for audio [batch][N] (features + forward). */
 synth_status synth_propose(synth_handle h, synth_model m, const float* audio_dev, int32_t batch,
                            float* params_out_dev, void* stream);
@@ -290,6 +307,10 @@ synth_status synth_params_to_human(synth_handle h, const float* u_host, double* 
 /* Sec. 2.2 train/test split: 1 if global voice g is in the test set
  * (blocks of 1024 voices, every tenth block), else 0. */
 int32_t synth_is_test(uint64_t global_voice_index);
+/* The global voice index g of the i-th voice of a split (0: every voice,
+ * g = i; 1: train; 2: test): blocks of 1024 voices, nine train blocks then
+ * one test block, repeating. */
+uint64_t synth_split_voice(int32_t split, uint64_t i);
 
 const char* synth_status_string(synth_status s);
 

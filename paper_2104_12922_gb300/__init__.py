@@ -94,12 +94,15 @@ def lib() -> ctypes.CDLL:
                      "synth_model_create", "synth_model_destroy", "synth_model_features",
                      "synth_model_forward", "synth_model_train_features", "synth_model_train_step",
                      "synth_propose", "synth_model_get_tensor", "synth_model_save",
-                     "synth_model_load"):
+                     "synth_model_load", "synth_stream_features"):
             getattr(L, name).restype = ctypes.c_int
         L.synth_sync.argtypes = [vp, vp]
         L.synth_params_to_human.argtypes = [vp, vp, vp, i32]
         L.synth_is_test.argtypes = [u64]
         L.synth_is_test.restype = i32
+        L.synth_split_voice.argtypes = [i32, u64]
+        L.synth_split_voice.restype = u64
+        L.synth_stream_features.argtypes = [vp, u64, i32, u64, ctypes.c_int64, i32, vp, vp, vp]
         L.synth_status_string.argtypes = [ctypes.c_int]
         L.synth_status_string.restype = ctypes.c_char_p
         for name in ("synth_create", "synth_destroy", "synth_render", "synth_render_normalized",
@@ -180,6 +183,14 @@ def synth_sync(h, stream) -> int:
 
 def synth_is_test(g: int) -> bool:
     return bool(lib().synth_is_test(g))
+
+
+SPLIT_ALL, SPLIT_TRAIN, SPLIT_TEST = 0, 1, 2
+
+
+def synth_split_voice(split: int, i: int) -> int:
+    """Global voice index g of the i-th voice of a split (0 all, 1 train, 2 test)."""
+    return int(lib().synth_split_voice(split, i))
 
 
 def make_nebula(d: dict) -> synth_nebula:
@@ -407,6 +418,27 @@ class ProposalModel:
         _check(lib().synth_model_features(self.handle, _ptr(audio), audio.shape[0], _ptr(f),
                                           _stream_ptr(stream)), "synth_model_features")
         return f
+
+    def stream_features(self, seed: int, split: int, first: int, count: int, chunk: int = 0,
+                        features=None, params=None, stream=None):
+        """Features and parameters of voices g = synth_split_voice(split, first + i),
+        i < count, rendered and transformed chunk by chunk
+        (synth_stream_features); returns (features, params)."""
+        import torch
+        dev = self.synth.device
+        if features is None:
+            features = torch.empty((count, self.feature_dim), dtype=torch.bfloat16, device=dev)
+        if params is None:
+            params = torch.empty((count, NUM_PARAMS), dtype=torch.float32, device=dev)
+        if features.dtype != torch.bfloat16 or not features.is_contiguous() or \
+                tuple(features.shape) != (count, self.feature_dim):
+            raise ValueError(f"features must be a contiguous bf16 tensor of shape "
+                             f"({count}, {self.feature_dim})")
+        self.synth._check_tensor(params, (count, NUM_PARAMS), "params")
+        _check(lib().synth_stream_features(self.handle, seed, split, first, count, chunk,
+                                           _ptr(features), _ptr(params), _stream_ptr(stream)),
+               "synth_stream_features")
+        return features, params
 
     def forward(self, feats, stream=None):
         import torch

@@ -42,6 +42,19 @@ constexpr int kFusedTileSeg = kFusedTilePoints - 1;  // control intervals per ti
 
 inline int windows_per_voice(int K) { return (K + kFusedTileSeg - 1) / kFusedTileSeg; }
 
+// Sec. 2.2 train/test split of the synth1B1 voice indices: blocks of 1024
+// consecutive voices, nine train blocks then one test block, repeating.
+// split_voice(split, i) is the global index g of the i-th voice of a split
+// (0: every voice, g = i; 1: train; 2: test).
+constexpr uint64_t kSplitBlock = 1024;
+constexpr uint64_t kSplitPeriod = 10 * kSplitBlock;
+constexpr uint64_t kSplitTrain = 9 * kSplitBlock;
+__host__ __device__ inline uint64_t split_voice(int split, uint64_t i) {
+  if (split == 1) return (i / kSplitTrain) * kSplitPeriod + i % kSplitTrain;
+  if (split == 2) return (i / kSplitBlock) * kSplitPeriod + kSplitTrain + i % kSplitBlock;
+  return i;
+}
+
 // Per-voice peak normalisation inside the fused render: after its last
 // render tile the kernel claims normalisation chunks from the same work
 // counter, so the scaling pass overlaps the tail of the render.
@@ -52,9 +65,10 @@ struct PeakNormArgs {
 };
 constexpr int kNormChunkSamples = 8192;  // samples per normalisation work item
 
-// Launches the fused persistent render (with `norm`, also the peak
-// normalisation). Returns the CUDA error of the launch.
-cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
+// Launches the fused persistent render of voices g = split_voice(split,
+// first + v), v < batch (with `norm`, also the peak normalisation). Returns
+// the CUDA error of the launch.
+cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t first, int split,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
                                 int grid, cudaStream_t stream,

@@ -197,7 +197,7 @@ __device__ __noinline__ void normalize_chunk(Smem& s, float* __restrict__ audio,
 
 template <bool kCarryF32, bool kPeak>
 __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
-    const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t batch_index, int batch,
+    const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t first, int split, int batch,
     const float* __restrict__ params_in, float* __restrict__ audio, float* __restrict__ params_out,
     ScratchHeader* hdr, TileState* tiles, int n_windows, const PeakNormArgs norm) {
   __shared__ Smem s;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       continue;
     }
     const int v = t % batch, w = t / batch;
-    const uint64_t g = batch_index * (uint64_t)batch + (uint64_t)v;
+    const uint64_t g = split_voice(split, first + (uint64_t)v);
     const int k0 = w * TI;
     const int nseg = min(TI, K - k0);
     TileState* vt = tiles + (size_t)v * n_windows;
@@ -497,7 +497,7 @@ int fused_max_active_blocks_per_sm() {
   return n;
 }
 
-cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
+cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t first, int split,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
                                 int grid, cudaStream_t stream, const PeakNormArgs* norm) {
@@ -505,7 +505,7 @@ cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t ba
   const int total = batch * n_windows;
   grid = grid < total ? grid : total;
   const PeakNormArgs nz = norm ? *norm : PeakNormArgs{0.f, nullptr, nullptr};
-#define SYNTH_FUSED_ARGS vc, seed, batch_index, batch, params_in, audio, params_out, hdr, tiles, \
+#define SYNTH_FUSED_ARGS vc, seed, first, split, batch, params_in, audio, params_out, hdr, tiles, \
                          n_windows, nz
   if (vc.carry_fp32) {
     if (norm) render_fused_kernel<true, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);

@@ -116,7 +116,7 @@ extern "C" synth_status synth_render_noalloc(const synth_config* cfg, uint64_t s
   if (cudaMemsetAsync(scratch, 0, need, st) != cudaSuccess) return SYNTH_ERR_CUDA;
   ScratchHeader* hdr = static_cast<ScratchHeader*>(scratch);
   TileState* ts = reinterpret_cast<TileState*>(hdr + 1);
-  return launch_render_fused(vc, seed, batch_index, batch, params_in_dev, audio_dev,
+  return launch_render_fused(vc, seed, batch_index * (uint64_t)batch, 0, batch, params_in_dev, audio_dev,
                              params_out_dev, hdr, ts, grid, st) == cudaSuccess
              ? SYNTH_OK
              : SYNTH_ERR_CUDA;

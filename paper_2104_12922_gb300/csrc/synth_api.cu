@@ -1,6 +1,7 @@
 // synth_api.cu -- the C ABI of libsynth.so (declared in include/synth.h):
 // handle lifetime, argument checks, launches, lazy device-error reporting.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -182,9 +183,9 @@ synth_status synth_render(synth_handle h, uint64_t seed, uint64_t batch_index, i
   if (!audio_dev) return SYNTH_ERR_ARG;
   ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
   TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
-  return check_cuda(launch_render_fused(h->vc, seed, batch_index, batch, params_in_dev, audio_dev,
-                                        params_out_dev, hdr, tiles, h->fused_grid,
-                                        static_cast<cudaStream_t>(stream)));
+  return check_cuda(launch_render_fused(h->vc, seed, batch_index * (uint64_t)batch, 0, batch,
+                                        params_in_dev, audio_dev, params_out_dev, hdr, tiles,
+                                        h->fused_grid, static_cast<cudaStream_t>(stream)));
 }
 
 synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t batch_index,
@@ -199,9 +200,9 @@ synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t bat
   ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
   TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
   const PeakNormArgs norm{threshold, peak_out_dev, silent_out_dev};
-  return check_cuda(launch_render_fused(h->vc, seed, batch_index, batch, params_in_dev, audio_dev,
-                                        params_out_dev, hdr, tiles, h->fused_grid,
-                                        static_cast<cudaStream_t>(stream), &norm));
+  return check_cuda(launch_render_fused(h->vc, seed, batch_index * (uint64_t)batch, 0, batch,
+                                        params_in_dev, audio_dev, params_out_dev, hdr, tiles,
+                                        h->fused_grid, static_cast<cudaStream_t>(stream), &norm));
 }
 
 synth_status synth_render_plain_workspace_size(synth_handle h, int32_t batch, size_t* bytes) {
@@ -385,6 +386,32 @@ synth_status synth_model_features(synth_model m, const float* audio_dev, int32_t
                                         static_cast<cudaStream_t>(stream)));
 }
 
+synth_status synth_stream_features(synth_model m, uint64_t seed, int32_t split, uint64_t first,
+                                   int64_t count, int32_t chunk, void* features_dev,
+                                   float* params_dev, void* stream) {
+  if (!m) return SYNTH_ERR_STATE;
+  if (split < 0 || split > 2 || count < 0 || chunk < 0 || chunk > m->max_batch) return SYNTH_ERR_ARG;
+  if (count == 0) return SYNTH_OK;
+  if (!features_dev) return SYNTH_ERR_ARG;
+  synth_handle h = m->synth;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
+  const int64_t fdim = (int64_t)m->frames * kMelBands;
+  const int c_max = chunk > 0 ? chunk : m->max_batch;
+  __nv_bfloat16* feats = static_cast<__nv_bfloat16*>(features_dev);
+  for (int64_t off = 0; off < count; off += c_max) {
+    const int c = (int)std::min<int64_t>(c_max, count - off);
+    cudaError_t e = launch_render_fused(h->vc, seed, first + (uint64_t)off, split, c, nullptr,
+                                        m->audio, params_dev ? params_dev + off * kNumParams : nullptr,
+                                        hdr, tiles, h->fused_grid, st);
+    if (e != cudaSuccess) return SYNTH_ERR_CUDA;
+    e = logmel_features_fft(m->audio, h->vc.n_samples, c, m->mel_ws, feats + off * fdim, st);
+    if (e != cudaSuccess) return SYNTH_ERR_CUDA;
+  }
+  return SYNTH_OK;
+}
+
 synth_status synth_model_forward(synth_model m, const void* features_dev, int32_t batch,
                                  float* params_out_dev, void* stream) {
   if (!m) return SYNTH_ERR_STATE;
@@ -513,7 +540,9 @@ synth_status synth_params_to_human(synth_handle h, const float* u_host, double* 
   return SYNTH_OK;
 }
 
-int32_t synth_is_test(uint64_t g) { return ((g / 1024u) % 10u) == 9u ? 1 : 0; }
+int32_t synth_is_test(uint64_t g) { return (g % kSplitPeriod) >= kSplitTrain ? 1 : 0; }
+
+uint64_t synth_split_voice(int32_t split, uint64_t i) { return split_voice(split, i); }
 
 const char* synth_status_string(synth_status s) {
   switch (s) {

@@ -85,6 +85,29 @@ def test_split_rule(pkg):
     assert flags.mean() == pytest.approx(0.1)
 
 
+def test_split_voice_enumerates_each_split_in_order(pkg):
+    """synth_split_voice(split, i) is the i-th voice of the split, checked
+    by brute-force enumeration of g with synth_is_test over three periods
+    and at indices past 2^40 (closed form against a local enumeration)."""
+    train = [g for g in range(3 * 10240) if not pkg.synth_is_test(g)]
+    test = [g for g in range(3 * 10240) if pkg.synth_is_test(g)]
+    assert [pkg.synth_split_voice(pkg.SPLIT_TRAIN, i) for i in range(len(train))] == train
+    assert [pkg.synth_split_voice(pkg.SPLIT_TEST, i) for i in range(len(test))] == test
+    assert [pkg.synth_split_voice(pkg.SPLIT_ALL, i) for i in (0, 5, 10**12)] == [0, 5, 10**12]
+    base = (1 << 40) // 10240 * 10240  # a period boundary
+    big_train = [g for g in range(base, base + 10240) if not pkg.synth_is_test(g)]
+    i0 = base // 10240 * 9216
+    assert [pkg.synth_split_voice(pkg.SPLIT_TRAIN, i0 + i) for i in range(9216)] == big_train
+    i1 = base // 10240 * 1024
+    assert pkg.synth_split_voice(pkg.SPLIT_TEST, i1) == base + 9216
+
+
+def test_stream_features_argument_errors_without_device(pkg):
+    lib = pkg.lib()
+    # a NULL model is rejected before any argument is looked at
+    assert lib.synth_stream_features(None, 0, 1, 0, 4, 0, None, None, None) == pkg.SYNTH_ERR_STATE
+
+
 def test_default_nebula_matches_oracle(pkg, oracle_mod):
     """The library's n0 table and the oracle's are written independently."""
     lib_nb = pkg.nebula_dict(pkg.synth_default_nebula())
