@@ -185,7 +185,7 @@ synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, con
  *   L_v = sum over n_fft in {512, 1024, 2048} of the mean over (bins, frames)
  *         of |log(|X| + 1e-7) - log(|Y| + 1e-7)|,
  * periodic Hann window, hop n_fft/4, centred frames with reflect padding,
- * STFT as a bf16 tensor-core GEMM with FP32 accumulation.
+ * FP32 FFTs; the gradient through the inverse transforms and an overlap-add.
  *  loss_voice_dev [batch] double (device) or NULL: L_v per voice.
  *  grad_x_dev     [batch][N] float or NULL: d(sum_v L_v)/dx.
  *  target_ready   nonzero to reuse the target spectra an earlier call with the

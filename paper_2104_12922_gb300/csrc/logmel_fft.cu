@@ -21,10 +21,13 @@
 #include <cmath>
 #include <vector>
 
+#include "fft_warp.cuh"
 #include "spectral.h"
 
 namespace synth {
 namespace {
+
+using fftw::bitrev;
 
 constexpr int kHop = kMelFFT / 4;      // 512
 constexpr int kHalf = kMelFFT / 2;     // 1024 complex points
@@ -36,59 +39,6 @@ constexpr int kLd = 33;                // padded row of the transpose buffer
 constexpr int kBuf = 32 * kLd;         // floats per warp (>= kBins)
 constexpr int kSegMax = (kGroup - 1) * kHop + kMelFFT;
 static_assert(kBuf >= kBins, "power spectrum fits the transpose buffer");
-
-// e^(-2 pi i j / 32), j = 0..15 (the values of cos and -sin at 2 pi j / 32)
-__device__ __forceinline__ float w32_re(int j) {
-  constexpr float c[16] = {1.000000000e+00f, 9.807852804e-01f, 9.238795325e-01f, 8.314696123e-01f,
-                           7.071067812e-01f, 5.555702330e-01f, 3.826834324e-01f, 1.950903220e-01f,
-                           0.0f, -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f,
-                           -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f};
-  return c[j];
-}
-__device__ __forceinline__ float w32_im(int j) {
-  constexpr float s[16] = {0.0f, -1.950903220e-01f, -3.826834324e-01f, -5.555702330e-01f,
-                           -7.071067812e-01f, -8.314696123e-01f, -9.238795325e-01f, -9.807852804e-01f,
-                           -1.000000000e+00f, -9.807852804e-01f, -9.238795325e-01f, -8.314696123e-01f,
-                           -7.071067812e-01f, -5.555702330e-01f, -3.826834324e-01f, -1.950903220e-01f};
-  return s[j];
-}
-
-__host__ __device__ constexpr int bitrev5(int r) {
-  return ((r & 1) << 4) | ((r & 2) << 2) | (r & 4) | ((r & 8) >> 2) | ((r & 16) >> 4);
-}
-
-// In-register radix-2 decimation-in-frequency 32-point DFT,
-// X[k] = sum_n x[n] e^(-2 pi i n k / 32); natural-order input, output X[k]
-// in register bitrev5(k). All indices are compile-time after unrolling, so
-// the trivial twiddles (1 and -i) cost no multiplications.
-__device__ __forceinline__ void fft32(float (&re)[32], float (&im)[32]) {
-#pragma unroll
-  for (int half = 16; half >= 1; half >>= 1) {
-#pragma unroll
-    for (int g = 0; g < 32; g += 2 * half) {
-#pragma unroll
-      for (int j = 0; j < half; ++j) {
-        const int p = g + j, q = g + j + half;
-        const float ur = re[p], ui = im[p], vr = re[q], vi = im[q];
-        re[p] = ur + vr;
-        im[p] = ui + vi;
-        const float dr = ur - vr, di = ui - vi;
-        const int tw = j * (16 / half);  // W32^tw = e^(-2 pi i j / (2 half))
-        if (tw == 0) {
-          re[q] = dr;
-          im[q] = di;
-        } else if (tw == 8) {  // -i
-          re[q] = di;
-          im[q] = -dr;
-        } else {
-          const float wr = w32_re(tw), wi = w32_im(tw);
-          re[q] = fmaf(dr, wr, -di * wi);
-          im[q] = fmaf(dr, wi, di * wr);
-        }
-      }
-    }
-  }
-}
 
 struct LmTables {
   const int* n_weights; // number of mel weights
@@ -176,11 +126,11 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
         re[a] = sv.x * wv.x;
         im[a] = sv.y * wv.y;
       }
-      fft32(re, im);  // over a: Y[k1] in register bitrev5(k1)
+      fftw::dft<32, 0>(re, im);  // over a: Y[k1] in register bitrev<32>(k1)
       // twiddle W1024^(lane k1), then the transpose: real parts, then imaginary
 #pragma unroll
       for (int r = 0; r < 32; ++r) {
-        const int k1 = bitrev5(r);
+        const int k1 = bitrev<32>(r);
         if (k1 != 0) {
           const float2 w = S.tw[32 * k1 + lane];
           const float yr = re[r], yi = im[r];
@@ -189,18 +139,18 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
         }
       }
 #pragma unroll
-      for (int r = 0; r < 32; ++r) B[bitrev5(r) * kLd + lane] = re[r];
+      for (int r = 0; r < 32; ++r) B[bitrev<32>(r) * kLd + lane] = re[r];
       __syncwarp();
 #pragma unroll
       for (int b = 0; b < 32; ++b) re[b] = B[lane * kLd + b];
       __syncwarp();
 #pragma unroll
-      for (int r = 0; r < 32; ++r) B[bitrev5(r) * kLd + lane] = im[r];
+      for (int r = 0; r < 32; ++r) B[bitrev<32>(r) * kLd + lane] = im[r];
       __syncwarp();
 #pragma unroll
       for (int b = 0; b < 32; ++b) im[b] = B[lane * kLd + b];
       __syncwarp();
-      fft32(re, im);  // over b: Z[lane + 32 k2] in register bitrev5(k2)
+      fftw::dft<32, 0>(re, im);  // over b: Z[lane + 32 k2] in register bitrev<32>(k2)
 
       // real spectrum and power; the partner Z[1024 - k] of k = lane + 32 k2 is
       // Z[(32 - lane) + 32 (31 - k2)] on lane 32 - lane, or, on lane 0,
@@ -208,12 +158,12 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
       const int src = (32 - lane) & 31;
 #pragma unroll
       for (int k2 = 0; k2 < 32; ++k2) {
-        const int r = bitrev5(k2);
-        float pr = __shfl_sync(0xffffffffu, re[bitrev5(31 - k2)], src);
-        float pi = __shfl_sync(0xffffffffu, im[bitrev5(31 - k2)], src);
+        const int r = bitrev<32>(k2);
+        float pr = __shfl_sync(0xffffffffu, re[bitrev<32>(31 - k2)], src);
+        float pi = __shfl_sync(0xffffffffu, im[bitrev<32>(31 - k2)], src);
         if (lane == 0) {
-          pr = re[bitrev5((32 - k2) & 31)];
-          pi = im[bitrev5((32 - k2) & 31)];
+          pr = re[bitrev<32>((32 - k2) & 31)];
+          pi = im[bitrev<32>((32 - k2) & 31)];
         }
         const int k = lane + 32 * k2;
         const float zr = re[r], zi = im[r];

@@ -1,178 +1,357 @@
-// spectral.cu -- STFT-as-GEMM front ends on the tcgen05 tensor cores.
+// spectral.cu -- the multi-resolution log-magnitude STFT distance (the
+// paper's multi-scale spectrogram distance, Sec. 4.4) and its gradient with
+// respect to the audio, on warp-level FP32 FFTs (fft_warp.cuh): periodic Hann
+// window, hop n/4, centred frames with reflect padding;
+// L_v = sum_n mean_(bins, frames) |log(|X| + eps) - log(|Y| + eps)|.
 //
-// * Multi-resolution log-magnitude STFT distance (the paper's "multi-scale
-//   spectrogram" distance, Sec. 4.4) and its gradient with respect to the
-//   audio: periodic Hann window, hop n/4, centred frames with reflect
-//   padding; L = sum_n mean_(bins, frames) |log(|X| + eps) - log(|Y| + eps)|,
-//   summed over voices.
-// * Log-mel features for the learned proposal: |X|^2 (n 2048, hop 512),
-//   128 Slaney-scale triangular bands, log(. + 1e-6).
-//
-// Framing: audio (FP32) -> frames (bf16, reflect-padded) -> GEMM with a
-// window-folded DFT matrix whose rows interleave cos and -sin of each bin, so
-// accumulator columns (2b, 2b+1) are (Re, Im) of bin b. The gradient runs the
-// transposed GEMM (dSpec x DFT) and an overlap-add gather that also folds the
-// reflect padding back.
+// One kernel per resolution and pass. A CTA takes a voice and a group of
+// frames, stages the padded audio the group covers in shared memory, and
+// each warp transforms 32 / R frames at a time (n = 64 R). The target pass
+// stores log(|Y| + eps) per bin; the loss pass forms d = log(|X| + eps) -
+// log(|Y| + eps), sums |d| per voice and, for the gradient, the spectrum
+// G_k = sign(d_k) / ((|X_k| + eps) |X_k|) X_k / (F bins), whose inverse real
+// DFT times the window is the gradient of the frame:
+//   dframe[t] = w[t] sum_(k = 0 .. n/2) Re(G_k e^(2 pi i k t / n)).
+// It runs the forward decomposition in reverse (a 32-point inverse DFT per
+// lane, twiddles, the transpose back, the R-point inverse DFTs) on the
+// packed sequence z[m] = dframe[2m] + i dframe[2m+1] / w. An overlap-add
+// gather then sums the frames into the audio gradient and folds the reflect
+// padding back. Also here: the Slaney mel filterbank of the log-mel features.
 
-#include <cuda_bf16.h>
+#include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <vector>
 
-#include "gemm_tc.h"
+#include "fft_warp.cuh"
 #include "spectral.h"
 
 namespace synth {
 
 namespace {
 
-// Split-bf16 products: a value a is carried as a_hi = bf16(a) and
-// a_lo = bf16(a - a_hi); a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi keeps about
-// 16 significant bits where a single bf16 product keeps 8. Laying the
-// operand A out as [hi | hi | lo] along K and B as [hi | lo | hi] makes one
-// tensor-core GEMM over 3K sum exactly those three products in FP32.
-__device__ __forceinline__ void split_bf16(float a, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16(a);
-  lo = __float2bfloat16(a - __bfloat162float(hi));
-}
+using fftw::bitrev;
 
-__device__ __forceinline__ int reflect32(int q, int N) {
-  if (q < 0) q = -q;
-  if (q >= N) q = 2 * (N - 1) - q;
-  return q;
-}
+constexpr int kWarpsMr = 8;
+constexpr int kThreadsMr = 32 * kWarpsMr;
+constexpr int kLdMr = 33;  // padded row of the per-warp transpose buffer
 
-// frames[row][seg * n_fft]: row = (voice, frame), one block per row; seg = 1
-// plain bf16, seg = 3 the [hi | hi | lo] split layout. Two samples per
-// thread and store (n_fft is even).
-__global__ void frame_reflect_bf16(const float* __restrict__ audio, int N, int n_fft, int hop,
-                                   int F, int seg, __nv_bfloat16* __restrict__ frames) {
-  const int row = blockIdx.x;
-  const int f = row % F, b = row / F;
-  const float* a = audio + (size_t)b * N;
-  const int start = f * hop - n_fft / 2;
-  __nv_bfloat16* dst = frames + (size_t)row * seg * n_fft;
-  for (int t = 2 * (int)threadIdx.x; t < n_fft; t += 2 * (int)blockDim.x) {
-    const float a0 = a[reflect32(start + t, N)], a1 = a[reflect32(start + t + 1, N)];
-    if (seg == 1) {
-      *reinterpret_cast<__nv_bfloat162*>(dst + t) = __floats2bfloat162_rn(a0, a1);
-    } else {
-      __nv_bfloat16 h0, l0, h1, l1;
-      split_bf16(a0, h0, l0);
-      split_bf16(a1, h1, l1);
-      const __nv_bfloat162 hh = __halves2bfloat162(h0, h1), ll = __halves2bfloat162(l0, l1);
-      *reinterpret_cast<__nv_bfloat162*>(dst + t) = hh;
-      *reinterpret_cast<__nv_bfloat162*>(dst + n_fft + t) = hh;
-      *reinterpret_cast<__nv_bfloat162*>(dst + 2 * n_fft + t) = ll;
-    }
+template <int R>
+struct MrCfg {
+  static constexpr int M = 32 * R;            // complex points per frame
+  static constexpr int n = 2 * M;             // n_fft
+  static constexpr int hop = n / 4;
+  static constexpr int bins = M + 1;
+  static constexpr int FPW = 32 / R;          // frames per warp pass
+  static constexpr int G = kWarpsMr * FPW * 2;  // frames per work item
+  static constexpr int seg = (G - 1) * hop + n;
+};
+
+template <int R>
+struct __align__(16) MrSmem {
+  float seg[MrCfg<R>::seg];
+  float buf[kWarpsMr][32 * kLdMr];
+  float2 win[MrCfg<R>::M];     // window at samples (2m, 2m + 1)
+  float2 tw[R * 32];           // e^(-2 pi i b k1 / M) at [k1][b]
+  float2 twi[32 * R];          // e^(+2 pi i b k1 / M) at [b][k1]
+  float2 post[MrCfg<R>::M];    // e^(-2 pi i k / n)
+  float red[kWarpsMr];
+};
+
+struct MrTables {
+  const float2* win;
+  const float2* tw;
+  const float2* twi;
+  const float2* post;
+};
+
+enum MrMode { kMrTarget = 0, kMrLoss = 1, kMrLossGrad = 2 };
+
+// Conditional move of the upper half of a lane's 32 values one slot down
+// (slot s holds k2 = s in register bitrev<32>(s)): slot 16..30 <- 17..31,
+// slot 31 <- 16, or back. On lanes with k1 = 0 this makes the partner of the
+// value in slot j (k2' = 32 - k2 mod 32) sit in slot 31 - j, as it does on
+// every other lane (k2' = 31 - k2).
+__device__ __forceinline__ void rotate_upper(float (&x)[32], bool on, bool back) {
+  if (!back) {
+    const float t = x[bitrev<32>(16)];
+#pragma unroll
+    for (int s = 16; s < 31; ++s) x[bitrev<32>(s)] = on ? x[bitrev<32>(s + 1)] : x[bitrev<32>(s)];
+    x[bitrev<32>(31)] = on ? t : x[bitrev<32>(31)];
+  } else {
+    const float t = x[bitrev<32>(31)];
+#pragma unroll
+    for (int s = 30; s >= 16; --s) x[bitrev<32>(s + 1)] = on ? x[bitrev<32>(s)] : x[bitrev<32>(s + 1)];
+    x[bitrev<32>(16)] = on ? t : x[bitrev<32>(16)];
   }
 }
 
-// fwd[2b][t] = w(t) cos(2 pi b t / n), fwd[2b+1][t] = -w(t) sin(2 pi b t / n)
-// (bins b < n/2 + 1), row stride seg * n_fft ([hi | lo | hi] when seg = 3);
-// bwd[t][2b], bwd[t][2b+1] the same values transposed, row stride seg * ld_bwd
-// with segments of ld_bwd columns (zero-padded).
-__global__ void dft_tables(int n_fft, int rows_fwd, int seg, __nv_bfloat16* fwd, int ld_bwd,
-                           __nv_bfloat16* bwd) {
-  const int nb = n_fft / 2 + 1;
-  const int64_t total = (int64_t)rows_fwd * n_fft;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(i / n_fft), t = (int)(i % n_fft);
-    const int b = r >> 1;
-    double val = 0.0;
-    if (b < nb) {
-      const double w = 0.5 - 0.5 * cospi(2.0 * (double)t / (double)n_fft);
-      const int64_t bt = ((int64_t)b * t) % n_fft;  // exact argument reduction
-      double s, c;
-      sincospi(2.0 * (double)bt / (double)n_fft, &s, &c);
-      val = (r & 1) ? -w * s : w * c;
-    }
-    __nv_bfloat16 hi, lo;
-    split_bf16((float)val, hi, lo);
-    __nv_bfloat16* f = fwd + (int64_t)r * seg * n_fft + t;
-    f[0] = hi;
-    if (seg == 3) {
-      f[n_fft] = lo;
-      f[2 * n_fft] = hi;
-    }
-    if (bwd && r < ld_bwd) {
-      __nv_bfloat16* g = bwd + (int64_t)t * seg * ld_bwd + r;
-      g[0] = hi;
-      if (seg == 3) {
-        g[ld_bwd] = lo;
-        g[2 * ld_bwd] = hi;
+template <int R>
+__global__ void __launch_bounds__(kThreadsMr, 2)
+    mr_fft_kernel(const float* __restrict__ sig, int N, int F, int batch, MrTables t, float eps,
+                  float scale, int mode, float* __restrict__ logy, double* __restrict__ loss_voice,
+                  float* __restrict__ dframes) {
+  using C = MrCfg<R>;
+  extern __shared__ __align__(16) unsigned char mr_raw[];
+  MrSmem<R>& S = *reinterpret_cast<MrSmem<R>*>(mr_raw);
+  for (int j = threadIdx.x; j < C::M; j += kThreadsMr) {
+    S.win[j] = __ldg(t.win + j);
+    S.post[j] = __ldg(t.post + j);
+  }
+  for (int j = threadIdx.x; j < 32 * R; j += kThreadsMr) {
+    S.tw[j] = __ldg(t.tw + j);
+    S.twi[j] = __ldg(t.twi + j);
+  }
+  const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(sig) & 15) == 0;
+  const int groups = (F + C::G - 1) / C::G;
+  const int items = groups * batch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int phi = lane / R, k1 = lane % R;            // this lane's frame and k1 after the transpose
+  const int src = phi * R + ((R - k1) & (R - 1));     // the lane holding Z[M - k]
+  const bool self = k1 == 0;
+  float* B = S.buf[warp];
+
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int v = item / groups, f0 = (item - v * groups) * C::G;
+    const int Gi = min(C::G, F - f0);
+    const int len = (Gi - 1) * C::hop + C::n;
+    const float* x = sig + (size_t)v * N;
+    const int base = f0 * C::hop - C::n / 2;
+    __syncthreads();  // the previous item is done with the segment and S.red
+    for (int j = 4 * threadIdx.x; j < len; j += 4 * kThreadsMr) {
+      const int i0 = base + j;
+      if (vec && i0 >= 0 && i0 + 3 < N) {
+        const unsigned int dst = (unsigned int)__cvta_generic_to_shared(S.seg + j);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(x + i0)
+                     : "memory");
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int i = i0 + q;
+          i = i < 0 ? -i : i;
+          i = i >= N ? 2 * (N - 1) - i : i;
+          S.seg[j + q] = __ldg(x + i);
+        }
       }
     }
-  }
-}
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
 
-// log-magnitude of the target: logy[row][b] = log(|Y_b| + eps)
-__global__ void spec_logmag(const float* __restrict__ spec, int ld_spec, int64_t M, int nb,
-                            float eps, float* __restrict__ logy) {
-  const int64_t total = M * nb;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i / nb;
-    const int b = (int)(i % nb);
-    const float re = spec[row * ld_spec + 2 * b], im = spec[row * ld_spec + 2 * b + 1];
-    logy[i] = logf(sqrtf(re * re + im * im) + eps);
-  }
-}
+    float acc = 0.f;  // sum of |d| over this warp's bins
+    for (int lf0 = warp * C::FPW; lf0 < Gi; lf0 += kWarpsMr * C::FPW) {
+      float re[32], im[32];
+      // ---- forward: z[32 a + lane] of frames lf0 .. lf0 + FPW - 1, windowed
+#pragma unroll
+      for (int fr = 0; fr < C::FPW; ++fr) {
+        const int lf = min(lf0 + fr, Gi - 1);
+        const float2* s2 = reinterpret_cast<const float2*>(S.seg + lf * C::hop);
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+          const float2 sv = s2[32 * a + lane];
+          const float2 wv = S.win[32 * a + lane];
+          re[fr * R + a] = sv.x * wv.x;
+          im[fr * R + a] = sv.y * wv.y;
+        }
+      }
+      fftw::dft_frames<R>(re, im);
+#pragma unroll
+      for (int fr = 0; fr < C::FPW; ++fr)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int kk = bitrev<R>(r);
+          if (kk != 0) {
+            const float2 w = S.tw[32 * kk + lane];
+            const float yr = re[fr * R + r], yi = im[fr * R + r];
+            re[fr * R + r] = fmaf(yr, w.x, -yi * w.y);
+            im[fr * R + r] = fmaf(yr, w.y, yi * w.x);
+          }
+        }
+#pragma unroll
+      for (int fr = 0; fr < C::FPW; ++fr)
+#pragma unroll
+        for (int r = 0; r < R; ++r) B[(fr * R + bitrev<R>(r)) * kLdMr + lane] = re[fr * R + r];
+      __syncwarp();
+#pragma unroll
+      for (int b = 0; b < 32; ++b) re[b] = B[lane * kLdMr + b];
+      __syncwarp();
+#pragma unroll
+      for (int fr = 0; fr < C::FPW; ++fr)
+#pragma unroll
+        for (int r = 0; r < R; ++r) B[(fr * R + bitrev<R>(r)) * kLdMr + lane] = im[fr * R + r];
+      __syncwarp();
+#pragma unroll
+      for (int b = 0; b < 32; ++b) im[b] = B[lane * kLdMr + b];
+      __syncwarp();
+      fftw::dft<32, 0>(re, im);  // Z[k1 + R k2] of frame phi in register bitrev<32>(k2)
 
-// |log(|X| + eps) - logy| summed per voice, and the gradient w.r.t. (Re, Im)
-// of X for the loss mean over (bins, frames) of one resolution. Block
-// (v, c) takes a slice of voice v's frames and adds one partial sum. The
-// gradient goes out in the split layout [hi | hi | lo] with segments of
-// ld_dspec columns; the padding columns of each segment are written as 0.
-__global__ void spec_l1_logmag_grad(const float* __restrict__ spec, int ld_spec,
-                                    const float* __restrict__ logy, int nb, int F, float eps,
-                                    float scale, double* __restrict__ loss_voice,
-                                    __nv_bfloat16* __restrict__ dspec, int ld_dspec) {
-  __shared__ float red[32];
-  const int v = blockIdx.x;
-  const int total = F * nb;
-  float local = 0.f;
-  for (int i = (int)blockIdx.y * (int)blockDim.x + (int)threadIdx.x; i < total;
-       i += (int)gridDim.y * (int)blockDim.x) {
-    const int fr = i / nb, b = i - fr * nb;
-    const size_t row = (size_t)v * F + fr;
-    const float2 x = *reinterpret_cast<const float2*>(spec + row * ld_spec + 2 * b);
-    const float mag = sqrtf(x.x * x.x + x.y * x.y);
-    const float d = logf(mag + eps) - logy[row * nb + b];
-    local += fabsf(d);
-    float gre = 0.f, gim = 0.f;
-    if (mag > 0.f && d != 0.f) {
-      const float g = (d > 0.f ? scale : -scale) / ((mag + eps) * mag);
-      gre = g * x.x;
-      gim = g * x.y;
-    }
-    __nv_bfloat16* dst = dspec + row * 3 * (size_t)ld_dspec + 2 * b;
-    __nv_bfloat16 h0, l0, h1, l1;
-    split_bf16(gre, h0, l0);
-    split_bf16(gim, h1, l1);
-    const __nv_bfloat162 hh = __halves2bfloat162(h0, h1), ll = __halves2bfloat162(l0, l1);
-    *reinterpret_cast<__nv_bfloat162*>(dst) = hh;
-    *reinterpret_cast<__nv_bfloat162*>(dst + ld_dspec) = hh;
-    *reinterpret_cast<__nv_bfloat162*>(dst + 2 * ld_dspec) = ll;
-    if (b == 0) {
-      __nv_bfloat16* prow = dspec + row * 3 * (size_t)ld_dspec;
-      for (int c = 2 * nb; c < ld_dspec; ++c) {
-        prow[c] = __float2bfloat16(0.f);
-        prow[ld_dspec + c] = __float2bfloat16(0.f);
-        prow[2 * ld_dspec + c] = __float2bfloat16(0.f);
+      const int lf = lf0 + phi;
+      const bool valid = lf < Gi;
+      const size_t row = (size_t)v * F + f0 + (valid ? lf : 0);
+      rotate_upper(re, self, false);
+      rotate_upper(im, self, false);
+      // slot pairs (j, 31 - j): their values are partners of the partner
+      // lane's slots (31 - j, j); on k1 = 0 lanes slots j and 31 - j are
+      // partners of each other (slot 0: k = 0 with the Nyquist bin; slot 31
+      // after the rotation: k = M / 2, its own partner)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int ra = bitrev<32>(j), rb = bitrev<32>(31 - j);
+        const int k2a = j, k2b = self ? (j == 0 ? 16 : 32 - j) : 31 - j;
+        float par = __shfl_sync(0xffffffffu, re[rb], src), pai = __shfl_sync(0xffffffffu, im[rb], src);
+        float pbr = __shfl_sync(0xffffffffu, re[ra], src), pbi = __shfl_sync(0xffffffffu, im[ra], src);
+        if (self) {
+          par = j == 0 ? re[ra] : re[rb];
+          pai = j == 0 ? im[ra] : im[rb];
+          pbr = j == 0 ? re[rb] : re[ra];
+          pbi = j == 0 ? im[rb] : im[ra];
+        }
+        float gr[2], gi[2];
+        float nyq_g = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int rr = h == 0 ? ra : rb;
+          const int k2 = h == 0 ? k2a : k2b;
+          const int k = k1 + R * k2;
+          const float zr = re[rr], zi = im[rr];
+          const float pr = h == 0 ? par : pbr, pi = h == 0 ? pai : pbi;
+          const float ar = zr + pr, ai = zi - pi;  // Z + conj(P)
+          const float cr = zi + pi, ci = pr - zr;  // -i (Z - conj(P))
+          const float2 w = S.post[k];
+          const float xr = 0.5f * (ar + fmaf(w.x, cr, -w.y * ci));
+          const float xi = 0.5f * (ai + fmaf(w.x, ci, w.y * cr));
+          const float mag = sqrtf(fmaf(xr, xr, xi * xi));
+          const float lm = logf(mag + eps);
+          gr[h] = 0.f;
+          gi[h] = 0.f;
+          if (mode == kMrTarget) {
+            if (valid) logy[row * C::bins + k] = lm;
+          } else {
+            const float d = lm - (valid ? logy[row * C::bins + k] : lm);
+            acc += fabsf(d);
+            if (mag > 0.f && d != 0.f) {
+              const float g = (d > 0.f ? scale : -scale) / ((mag + eps) * mag);
+              gr[h] = g * xr;
+              gi[h] = g * xi;
+            }
+          }
+          if (k == 0) {  // the Nyquist bin X[M] = Re Z[0] - Im Z[0] (real)
+            const float xn = zr - zi, mn = fabsf(xn), ln = logf(mn + eps);
+            if (mode == kMrTarget) {
+              if (valid) logy[row * C::bins + C::M] = ln;
+            } else {
+              const float d = ln - (valid ? logy[row * C::bins + C::M] : ln);
+              acc += fabsf(d);
+              if (mn > 0.f && d != 0.f) nyq_g = (d > 0.f ? scale : -scale) / ((mn + eps) * mn) * xn;
+            }
+          }
+        }
+        if (mode == kMrLossGrad) {
+          // inverse packing: Zp_k = A_k + i B_k with A_k = (G_k + conj G_(M-k)) / 2,
+          // B_k = (G_k - conj G_(M-k)) / 2 e^(2 pi i k / n); k = 0 pairs with
+          // the Nyquist bin: A_0 = Re G_0 + G_M, B_0 = Re G_0 - G_M
+          float qar = __shfl_sync(0xffffffffu, gr[1], src), qai = __shfl_sync(0xffffffffu, gi[1], src);
+          float qbr = __shfl_sync(0xffffffffu, gr[0], src), qbi = __shfl_sync(0xffffffffu, gi[0], src);
+          if (self) {
+            qar = j == 0 ? gr[0] : gr[1];
+            qai = j == 0 ? gi[0] : gi[1];
+            qbr = j == 0 ? gr[1] : gr[0];
+            qbi = j == 0 ? gi[1] : gi[0];
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int rr = h == 0 ? ra : rb;
+            const int k2 = h == 0 ? k2a : k2b;
+            const int k = k1 + R * k2;
+            const float g_r = gr[h], g_i = gi[h];
+            const float q_r = h == 0 ? qar : qbr, q_i = h == 0 ? qai : qbi;
+            float Ar = 0.5f * (g_r + q_r), Ai = 0.5f * (g_i - q_i);
+            const float Dr = 0.5f * (g_r - q_r), Di = 0.5f * (g_i + q_i);
+            const float2 w = S.post[k];  // e^(2 pi i k / n) = conj(w)
+            float Br = fmaf(Dr, w.x, Di * w.y), Bi = fmaf(Di, w.x, -Dr * w.y);
+            if (k == 0) {
+              Ar = g_r + nyq_g;
+              Ai = 0.f;
+              Br = g_r - nyq_g;
+              Bi = 0.f;
+            }
+            re[rr] = Ar - Bi;  // A + i B
+            im[rr] = Ai + Br;
+          }
+        }
+      }
+      if (mode != kMrLossGrad) continue;
+
+      // ---- inverse: z[m] = sum_k Zp_k e^(2 pi i k m / M), m = 32 a + b
+      rotate_upper(re, self, true);
+      rotate_upper(im, self, true);
+      // 32-point inverse DFT over k2 (the swap of real and imaginary parts
+      // turns the forward transform into the inverse one)
+      {
+        float tr[32], ti[32];
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) {
+          tr[k2] = re[bitrev<32>(k2)];
+          ti[k2] = im[bitrev<32>(k2)];
+        }
+        fftw::dft<32, 0>(ti, tr);  // T[b] in register bitrev<32>(b)
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const int b = bitrev<32>(r);
+          float yr = tr[r], yi = ti[r];
+          if (b != 0 && k1 != 0) {
+            const float2 w = S.twi[b * R + k1];
+            const float t0 = fmaf(yr, w.x, -yi * w.y);
+            yi = fmaf(yr, w.y, yi * w.x);
+            yr = t0;
+          }
+          re[b] = yr;
+          im[b] = yi;
+        }
+      }
+      // transpose back: lane (phi, k1) row, column b
+#pragma unroll
+      for (int b = 0; b < 32; ++b) B[lane * kLdMr + b] = re[b];
+      __syncwarp();
+#pragma unroll
+      for (int fr = 0; fr < C::FPW; ++fr)
+#pragma unroll
+        for (int q = 0; q < R; ++q) re[fr * R + q] = B[(fr * R + q) * kLdMr + lane];
+      __syncwarp();
+#pragma unroll
+      for (int b = 0; b < 32; ++b) B[lane * kLdMr + b] = im[b];
+      __syncwarp();
+#pragma unroll
+      for (int fr = 0; fr < C::FPW; ++fr)
+#pragma unroll
+        for (int q = 0; q < R; ++q) im[fr * R + q] = B[(fr * R + q) * kLdMr + lane];
+      __syncwarp();
+      fftw::dft_frames<R>(im, re);  // z[32 a + lane] of frame fr in register fr R + bitrev<R>(a)
+#pragma unroll
+      for (int fr = 0; fr < C::FPW; ++fr) {
+        if (lf0 + fr >= Gi) continue;
+        float2* out = reinterpret_cast<float2*>(dframes + ((size_t)v * F + f0 + lf0 + fr) * C::n);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int m = 32 * bitrev<R>(r) + lane;
+          const float2 wv = S.win[m];
+          out[m] = make_float2(re[fr * R + r] * wv.x, im[fr * R + r] * wv.y);
+        }
       }
     }
-  }
-  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)red[w];
-    atomicAdd(&loss_voice[v], t * scale);
+    if (mode != kMrTarget) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) S.red[warp] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tot = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarpsMr; ++w) tot += (double)S.red[w];
+        atomicAdd(loss_voice + v, tot * (double)scale);
+      }
+    }
   }
 }
 
@@ -208,46 +387,92 @@ __global__ void overlap_add_reflect(const float* __restrict__ dframes, int N, in
   }
 }
 
-int grid_of(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (int)(b < 152 * 64 ? b : 152 * 64);
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// FFT tables of one resolution (n = 64 R), built on the host in FP64.
+size_t mr_table_bytes(int R) {
+  const int M = 32 * R;
+  return al256(sizeof(float2) * M) * 2 + al256(sizeof(float2) * 32 * R) * 2;
 }
 
-size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+MrTables mr_tables(int R, const char* p) {
+  const int M = 32 * R;
+  MrTables t;
+  t.win = reinterpret_cast<const float2*>(p);
+  t.post = reinterpret_cast<const float2*>(p + al256(sizeof(float2) * M));
+  t.tw = reinterpret_cast<const float2*>(p + 2 * al256(sizeof(float2) * M));
+  t.twi = reinterpret_cast<const float2*>(p + 2 * al256(sizeof(float2) * M) +
+                                          al256(sizeof(float2) * 32 * R));
+  return t;
+}
+
+cudaError_t mr_tables_fill(int R, void* dst, cudaStream_t st) {
+  const double pi = 3.14159265358979323846;
+  const int M = 32 * R, n = 2 * M;
+  std::vector<char> host(mr_table_bytes(R), 0);
+  const MrTables t = mr_tables(R, host.data());
+  float2* win = const_cast<float2*>(t.win);
+  float2* post = const_cast<float2*>(t.post);
+  float2* tw = const_cast<float2*>(t.tw);
+  float2* twi = const_cast<float2*>(t.twi);
+  for (int m = 0; m < M; ++m) {
+    win[m] = make_float2((float)(0.5 - 0.5 * std::cos(2.0 * pi * (2 * m) / n)),
+                         (float)(0.5 - 0.5 * std::cos(2.0 * pi * (2 * m + 1) / n)));
+    const double a = -2.0 * pi * m / n;
+    post[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  for (int k1 = 0; k1 < R; ++k1)
+    for (int b = 0; b < 32; ++b) {
+      const double a = 2.0 * pi * (double)((b * k1) % M) / M;
+      tw[32 * k1 + b] = make_float2((float)std::cos(a), (float)-std::sin(a));
+      twi[b * R + k1] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+  return cudaMemcpyAsync(dst, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+}
+
+int r_of(int n_fft) { return n_fft == 512 ? 8 : n_fft == 1024 ? 16 : n_fft == 2048 ? 32 : 0; }
+
+template <int R>
+cudaError_t mr_launch(const float* sig, int N, int F, int batch, const char* tables, float eps,
+                      float scale, int mode, float* logy, double* loss_voice, float* dframes,
+                      cudaStream_t st) {
+  const int smem = (int)sizeof(MrSmem<R>);
+  static int grid_cap = 0;
+  if (grid_cap == 0) {
+    cudaError_t e =
+        cudaFuncSetAttribute(mr_fft_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mr_fft_kernel<R>, kThreadsMr,
+                                                           smem)) != cudaSuccess)
+      return e;
+    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int64_t items = (int64_t)((F + MrCfg<R>::G - 1) / MrCfg<R>::G) * batch;
+  if (items >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<int64_t>(items, grid_cap);
+  mr_fft_kernel<R><<<grid, kThreadsMr, smem, st>>>(sig, N, F, batch, mr_tables(R, tables), eps,
+                                                   scale, mode, logy, loss_voice, dframes);
+  return cudaGetLastError();
+}
+
+cudaError_t mr_pass(int n_fft, const float* sig, int N, int F, int batch, const char* tables,
+                    float eps, float scale, int mode, float* logy, double* loss_voice,
+                    float* dframes, cudaStream_t st) {
+  switch (r_of(n_fft)) {
+    case 8: return mr_launch<8>(sig, N, F, batch, tables, eps, scale, mode, logy, loss_voice, dframes, st);
+    case 16: return mr_launch<16>(sig, N, F, batch, tables, eps, scale, mode, logy, loss_voice, dframes, st);
+    case 32: return mr_launch<32>(sig, N, F, batch, tables, eps, scale, mode, logy, loss_voice, dframes, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 }  // namespace
 
 int stft_frames(int64_t N, int n_fft) { return 1 + (int)(N / (n_fft / 4)); }
-
-// ------------------------------------------------------------------ tables
-size_t dft_bytes(int n_fft, int seg) {
-  const int nb = n_fft / 2 + 1;
-  const int rows = 2 * nb;
-  const int ld_bwd = (rows + 7) & ~7;
-  return al256(sizeof(__nv_bfloat16) * (size_t)rows * seg * n_fft) +
-         al256(sizeof(__nv_bfloat16) * (size_t)n_fft * seg * ld_bwd);
-}
-
-DftTables dft_carve(int n_fft, void* mem, int seg) {
-  DftTables t;
-  t.n_fft = n_fft;
-  t.seg = seg;
-  t.nb = n_fft / 2 + 1;
-  t.rows = 2 * t.nb;
-  t.ld_bwd = (t.rows + 7) & ~7;
-  char* p = static_cast<char*>(mem);
-  t.fwd = reinterpret_cast<__nv_bfloat16*>(p);
-  t.bwd = reinterpret_cast<__nv_bfloat16*>(
-      p + al256(sizeof(__nv_bfloat16) * (size_t)t.rows * seg * n_fft));
-  return t;
-}
-
-cudaError_t dft_fill(const DftTables& t, cudaStream_t st) {
-  cudaMemsetAsync(t.bwd, 0, sizeof(__nv_bfloat16) * (size_t)t.n_fft * t.seg * t.ld_bwd, st);
-  dft_tables<<<grid_of((int64_t)t.rows * t.n_fft), 256, 0, st>>>(t.n_fft, t.rows, t.seg, t.fwd,
-                                                                 t.ld_bwd, t.bwd);
-  return cudaGetLastError();
-}
 
 // Slaney mel filterbank [n_mels][ld] (bf16, zero-padded), built on the host in
 // FP64: triangles between mel-spaced edges from 0 to SR/2, unit area in Hz.
@@ -275,18 +500,9 @@ std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld)
 }
 
 // ---------------------------------------------------------------- MR-STFT
-// The distance and its gradient use split-bf16 operands (3 products, about
-// 16 significant bits): d log(|X| + eps) / d|X| = 1/(|X| + eps) weights the
-// quiet bins heavily, and a single bf16 rounding of frames and DFT weights
-// leaves those bins with noise only.
 namespace {
-constexpr int kSplit = 3;
-
 struct MrLayout {
-  DftTables tabs[8];
-  __nv_bfloat16* frames;
-  float* spec;
-  __nv_bfloat16* dspec;
+  char* tables[8];
   float* dframes;
   float* logy[8];
   double* loss_voice;
@@ -297,28 +513,20 @@ MrLayout mr_layout(int64_t N, int batch, const int* n_ffts, int n_res, void* ws)
   MrLayout L;
   char* base = static_cast<char*>(ws);
   size_t off = 0;
-  int64_t max_frames = 0, max_spec = 0, max_dspec = 0, max_dfr = 0, max_nb = 0;
-  for (int r = 0; r < n_res; ++r) {
-    const int n = n_ffts[r];
-    L.tabs[r] = dft_carve(n, base ? base + off : nullptr, kSplit);
-    off += dft_bytes(n, kSplit);
-    const int64_t M = (int64_t)batch * stft_frames(N, n);
-    max_frames = std::max<int64_t>(max_frames, M * kSplit * n);
-    max_spec = std::max<int64_t>(max_spec, M * L.tabs[r].ld_bwd);
-    max_dspec = std::max<int64_t>(max_dspec, M * kSplit * L.tabs[r].ld_bwd);
-    max_dfr = std::max<int64_t>(max_dfr, M * n);
-    max_nb = std::max<int64_t>(max_nb, M * L.tabs[r].nb);
-  }
   auto take = [&](size_t bytes) {
     char* p = base ? base + off : nullptr;
     off += al256(bytes);
     return p;
   };
-  L.frames = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * max_frames));
-  L.spec = reinterpret_cast<float*>(take(sizeof(float) * max_spec));
-  L.dspec = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * max_dspec));
+  int64_t max_dfr = 0;
+  for (int r = 0; r < n_res; ++r) {
+    const int n = n_ffts[r];
+    L.tables[r] = take(mr_table_bytes(std::max(1, r_of(n))));
+    const int64_t M = (int64_t)batch * stft_frames(N, n);
+    max_dfr = std::max<int64_t>(max_dfr, M * n);
+    L.logy[r] = reinterpret_cast<float*>(take(sizeof(float) * M * (n / 2 + 1)));
+  }
   L.dframes = reinterpret_cast<float*>(take(sizeof(float) * max_dfr));
-  for (int r = 0; r < n_res; ++r) L.logy[r] = reinterpret_cast<float*>(take(sizeof(float) * max_nb));
   L.loss_voice = reinterpret_cast<double*>(take(sizeof(double) * batch));
   L.total = off;
   return L;
@@ -331,53 +539,32 @@ size_t mrstft_workspace_bytes(int64_t N, int batch, const int* n_ffts, int n_res
 
 cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batch,
                              const int* n_ffts, int n_res, float eps, bool target_ready,
-                             double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
-                             cudaStream_t st) {
+                             double* loss_voice_out, float* grad_x, void* ws, cudaStream_t st) {
   if (n_res < 1 || n_res > 8) return cudaErrorInvalidValue;
   for (int r = 0; r < n_res; ++r)  // reflect padding needs more samples than half a frame
-    if (N <= n_ffts[r] / 2 || N >= (int64_t)1 << 31) return cudaErrorInvalidValue;
+    if (r_of(n_ffts[r]) == 0 || N <= n_ffts[r] / 2 || N >= (int64_t)1 << 31)
+      return cudaErrorInvalidValue;
+  if (batch <= 0) return cudaSuccess;
   MrLayout L = mr_layout(N, batch, n_ffts, n_res, ws);
   cudaError_t e;
-  auto spectrum = [&](const float* sig, int r) -> cudaError_t {
-    const int n = n_ffts[r], F = stft_frames(N, n);
-    const int64_t M = (int64_t)batch * F;
-    frame_reflect_bf16<<<(unsigned)M, 256, 0, st>>>(sig, (int)N, n, n / 4, F, kSplit, L.frames);
-    GemmEpilogue ep;
-    ep.kind = kEpiStoreF32;
-    ep.out_f32 = L.spec;
-    ep.ldc = L.tabs[r].ld_bwd;
-    return gemm_bf16(L.frames, kSplit * n, L.tabs[r].fwd, kSplit * n, (int)M, L.tabs[r].rows,
-                     kSplit * n, ep, err, st);
-  };
   if (!target_ready) {
     for (int r = 0; r < n_res; ++r) {
-      if ((e = dft_fill(L.tabs[r], st)) != cudaSuccess) return e;
-      if ((e = spectrum(y, r)) != cudaSuccess) return e;
-      const int64_t M = (int64_t)batch * stft_frames(N, n_ffts[r]);
-      spec_logmag<<<grid_of(M * L.tabs[r].nb), 256, 0, st>>>(L.spec, L.tabs[r].ld_bwd, M,
-                                                            L.tabs[r].nb, eps, L.logy[r]);
+      const int n = n_ffts[r];
+      if ((e = mr_tables_fill(r_of(n), L.tables[r], st)) != cudaSuccess) return e;
+      if ((e = mr_pass(n, y, (int)N, stft_frames(N, n), batch, L.tables[r], eps, 0.f, kMrTarget,
+                       L.logy[r], nullptr, nullptr, st)) != cudaSuccess)
+        return e;
     }
   }
-  cudaMemsetAsync(L.loss_voice, 0, sizeof(double) * batch, st);
+  if ((e = cudaMemsetAsync(L.loss_voice, 0, sizeof(double) * batch, st)) != cudaSuccess) return e;
   for (int r = 0; r < n_res; ++r) {
     const int n = n_ffts[r], F = stft_frames(N, n);
-    const int64_t M = (int64_t)batch * F;
-    const int ld = L.tabs[r].ld_bwd;
-    if ((e = spectrum(x, r)) != cudaSuccess) return e;
-    const float scale = 1.0f / (float)((int64_t)F * L.tabs[r].nb);
-    const int64_t per_voice = (int64_t)F * L.tabs[r].nb;
-    dim3 gl(batch, (unsigned)std::min<int64_t>(64, (per_voice + 255) / 256));
-    spec_l1_logmag_grad<<<gl, 256, 0, st>>>(L.spec, ld, L.logy[r], L.tabs[r].nb, F, eps, scale,
-                                            L.loss_voice, L.dspec, ld);
+    const float scale = 1.0f / (float)((int64_t)F * (n / 2 + 1));
+    if ((e = mr_pass(n, x, (int)N, F, batch, L.tables[r], eps, scale,
+                     grad_x ? kMrLossGrad : kMrLoss, L.logy[r], L.loss_voice, L.dframes, st)) !=
+        cudaSuccess)
+      return e;
     if (grad_x) {
-      // dFrames[M][n] = dSpec[M][3 ld] * bwd[n][3 ld]^T
-      GemmEpilogue eb;
-      eb.kind = kEpiStoreF32;
-      eb.out_f32 = L.dframes;
-      eb.ldc = n;
-      if ((e = gemm_bf16(L.dspec, kSplit * ld, L.tabs[r].bwd, kSplit * ld, (int)M, n, kSplit * ld,
-                         eb, err, st)) != cudaSuccess)
-        return e;
       dim3 go((unsigned)std::min<int64_t>((N + 255) / 256, 1024), (unsigned)batch);
       overlap_add_reflect<<<go, 256, 0, st>>>(L.dframes, (int)N, n, n / 4, F, r > 0 ? 1 : 0,
                                               grad_x);

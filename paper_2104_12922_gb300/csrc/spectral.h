@@ -1,5 +1,5 @@
-// spectral.h -- spectral front ends: the STFT-as-GEMM MR-STFT distance
-// (spectral.cu) and the FFT log-mel features (logmel_fft.cu).
+// spectral.h -- spectral front ends on warp-level FFTs: the MR-STFT distance
+// and its gradient (spectral.cu) and the log-mel features (logmel_fft.cu).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -22,26 +22,15 @@ constexpr float kFeatureScale = 6.0f;
 // Centred frames of an N-sample signal at hop n/4.
 int stft_frames(int64_t N, int n_fft);
 
-// seg = 1: plain bf16 tables; seg = 3: split-bf16 layouts along K.
-struct DftTables {
-  int n_fft, seg, nb, rows, ld_bwd;
-  __nv_bfloat16* fwd;  // [rows = 2 nb][seg n_fft]: (w cos, -w sin) interleaved per bin
-  __nv_bfloat16* bwd;  // [n_fft][seg ld_bwd]: the same, transposed, zero-padded columns
-};
-size_t dft_bytes(int n_fft, int seg);
-DftTables dft_carve(int n_fft, void* mem, int seg);
-cudaError_t dft_fill(const DftTables& t, cudaStream_t st);
-
 // Multi-resolution log-magnitude distance between x and y ([batch][N] FP32,
-// device) and its gradient w.r.t. x. loss_voice_out [batch] (device, FP64,
-// may be NULL); grad_x [batch][N] or NULL. With target_ready the tables and
+// device) and its gradient w.r.t. x; n_ffts from {512, 1024, 2048}.
+// loss_voice_out [batch] (device, FP64, may be NULL); grad_x [batch][N] or NULL. With target_ready the tables and
 // the target log-magnitudes left in ws by an earlier call for the same y are
 // reused.
 size_t mrstft_workspace_bytes(int64_t N, int batch, const int* n_ffts, int n_res);
 cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batch,
                              const int* n_ffts, int n_res, float eps, bool target_ready,
-                             double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
-                             cudaStream_t st);
+                             double* loss_voice_out, float* grad_x, void* ws, cudaStream_t st);
 
 // Slaney mel filterbank [n_mels][ld] (unit-area triangles over 0 .. sr/2).
 std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld);

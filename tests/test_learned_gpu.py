@@ -1,10 +1,9 @@
 """GPU spectral front ends and the learned proposal against the FP64 oracle.
 
 Tolerances follow from the arithmetic of each path: the MR-STFT distance
-runs on split-bf16 tensor-core GEMMs (about 16 significant bits), the
-log-mel features on an FP32 FFT with a bf16 output, and the MLP on bf16
-operands with FP32 accumulation (a relative rounding of at most 2^-9 per
-operand).
+and its gradient run on FP32 FFTs, the log-mel features on an FP32 FFT with
+a bf16 output, and the MLP on bf16 operands with FP32 accumulation (a
+relative rounding of at most 2^-9 per operand).
 """
 import numpy as np
 import pytest
@@ -35,15 +34,20 @@ def test_mrstft_loss_matches_oracle_on_voices(env):
     loss, _ = mr(x, y)
     syn.sync()
     ref_voice = sp.mrstft_loss(x.cpu().numpy(), y.cpu().numpy(), per_voice=True).numpy()
-    assert np.allclose(loss.cpu().numpy(), ref_voice, rtol=2e-2)
+    # FP32 spectra: |X| carries an absolute error of about 1e-7 of the frame's
+    # norm, which moves log(|X| + 1e-7) by O(1) only in bins near silence;
+    # averaged over ~1e5 bins that stays below 1e-4 relative (measured 2e-7)
+    assert np.allclose(loss.cpu().numpy(), ref_voice, rtol=1e-4)
     syn.close()
 
 
 def test_mrstft_gradient_matches_oracle(env):
     """Gradient on broadband signals: d log(|X| + eps) / d|X| = 1 / (|X| + eps)
-    weights near-silent bins by up to 1/eps, where a bf16 STFT has only its
-    rounding noise, so the gradient is compared where every bin carries
-    energy (seeded Gaussian noise)."""
+    weights near-silent bins by up to 1/eps, so the gradient is compared where
+    every bin carries energy (seeded Gaussian noise). FP32 FFTs: the loss
+    within 1e-5 relative, the gradient within 1e-3 in relative norm (the
+    small-|X| bins, weighted by 1/|X|, carry most of the rounding; measured
+    2.5e-7 and 2.7e-5)."""
     from oracle import spectral as sp
     torch, pkg = env
     syn = pkg.Synth(seconds=0.1, max_batch=2)
@@ -55,11 +59,9 @@ def test_mrstft_gradient_matches_oracle(env):
     loss, gx = mr(x, y)
     syn.sync()
     ref_loss, ref_g = sp.mrstft_loss_and_grad(x.cpu().numpy(), y.cpu().numpy())
-    assert float(loss.sum()) == pytest.approx(ref_loss, rel=2e-2)
     g = gx.cpu().numpy().astype(np.float64)
-    cos = float(np.sum(g * ref_g) / np.sqrt(np.sum(g * g) * np.sum(ref_g * ref_g)))
-    assert cos > 0.98
-    assert np.linalg.norm(g - ref_g) <= 0.2 * np.linalg.norm(ref_g)
+    assert float(loss.sum()) == pytest.approx(ref_loss, rel=1e-5)
+    assert np.linalg.norm(g - ref_g) <= 1e-3 * np.linalg.norm(ref_g)
     # the target spectra kept in the workspace give the same result
     loss2, gx2 = mr(x, y, target_ready=True)
     syn.sync()
