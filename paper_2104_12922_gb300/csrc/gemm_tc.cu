@@ -2,7 +2,7 @@
 //
 // C[M][N] = A[M][K] * B[N][K]^T, A and B bf16 and K-contiguous, FP32
 // accumulation in tensor memory (TMEM), a fused epilogue. Used for the
-// STFT-as-GEMM, the mel projection and the proposal MLP.
+// proposal MLP (and exposed as synth_gemm_bf16).
 //
 // Persistent: one CTA per SM walks the 128 x BN output tiles (N fastest, so
 // neighbouring CTAs share A rows in L2) with 6 warps:
@@ -269,30 +269,6 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
               if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + col] = b;
               if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ldc_t + row] = b;
               if (epi.out_f32) epi.out_f32[(size_t)row * epi.ldc + col] = z;
-            }
-            break;
-          }
-          case kEpiPowerPairs: {
-            // columns (2b, 2b+1) hold (re, im) of bin b: out[row][b] = re^2 + im^2
-#pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-              const int bin = (col0 + i) >> 1;
-              if (col0 + i + 1 < N && bin < epi.n_valid) {
-                const float pw = v[i] * v[i] + v[i + 1] * v[i + 1];
-                if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + bin] = __float2bfloat16(pw);
-                else epi.out_f32[(size_t)row * epi.ldc + bin] = pw;
-              }
-            }
-            break;
-          }
-          case kEpiLogBF16: {
-            // features = alpha (log(acc + eps) - shift) in bf16
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int col = col0 + i;
-              if (col < N && col < epi.n_valid)
-                epi.out_bf16[(size_t)row * epi.ldc + col] =
-                    __float2bfloat16(epi.alpha * (__logf(v[i] + epi.eps) - epi.shift));
             }
             break;
           }

@@ -9,8 +9,6 @@ namespace synth {
 enum GemmEpiKind : int {
   kEpiStoreF32 = 0,     // out_f32[row][col] = alpha * acc
   kEpiBiasActBF16 = 1,  // z = act(acc + bias[col]) -> out_bf16 / out_bf16_t (transposed) / out_f32
-  kEpiPowerPairs = 2,   // out_f32[row][b] = acc[2b]^2 + acc[2b+1]^2 for b < n_valid
-  kEpiLogBF16 = 3,      // out_bf16[row][col] = alpha (log(acc + eps) - shift), col < n_valid
 };
 enum GemmAct : int { kActNone = 0, kActRelu = 1, kActSigmoid = 2 };
 
@@ -23,10 +21,7 @@ struct GemmEpilogue {
   const float* bias = nullptr;
   int ldc = 0;      // row stride (elements) of out_f32 / out_bf16
   int ldc_t = 0;    // row stride of the transposed copy
-  int n_valid = 0;  // valid output columns (power pairs: bins; log: columns)
   float alpha = 1.f;
-  float eps = 0.f;
-  float shift = 0.f;
 };
 
 // C = A[M][K] * B[N][K]^T on the tensor cores; A, B bf16 with row strides lda,
