@@ -14,9 +14,12 @@
 //   dframe[t] = w[t] sum_(k = 0 .. n/2) Re(G_k e^(2 pi i k t / n)).
 // It runs the forward decomposition in reverse (a 32-point inverse DFT per
 // lane, twiddles, the transpose back, the R-point inverse DFTs) on the
-// packed sequence z[m] = dframe[2m] + i dframe[2m+1] / w. An overlap-add
-// gather then sums the frames into the audio gradient and folds the reflect
-// padding back. Also here: the Slaney mel filterbank of the log-mel features.
+// packed sequence z[m] = dframe[2m] + i dframe[2m+1] / w. The CTA sums its
+// frames' gradients into the padded segment they cover (in shared memory)
+// and writes that partial; one gather over all resolutions then adds the
+// partials of the (at most two) segments covering each padded position and
+// folds the reflect padding back. Also here: the Slaney mel filterbank of
+// the log-mel features.
 
 #include <cuda_runtime.h>
 
@@ -26,6 +29,7 @@
 #include <vector>
 
 #include "fft_warp.cuh"
+#include "mbarrier.cuh"
 #include "spectral.h"
 
 namespace synth {
@@ -43,22 +47,26 @@ struct MrCfg {
   static constexpr int M = 32 * R;            // complex points per frame
   static constexpr int n = 2 * M;             // n_fft
   static constexpr int hop = n / 4;
-  static constexpr int bins = M + 1;
+  static constexpr int ldl = M + 4;  // row stride of the target log-magnitudes (bins M + 1,
+                                     // padded to a 16-byte multiple for bulk copies)
   static constexpr int FPW = 32 / R;          // frames per warp pass
-  static constexpr int G = kWarpsMr * FPW * 2;  // frames per work item
+  static constexpr int G = kWarpsMr * FPW;    // frames per work item: one pass per warp
   static constexpr int seg = (G - 1) * hop + n;
 };
 
 template <int R>
 struct __align__(16) MrSmem {
-  float seg[MrCfg<R>::seg];
+  float seg[2][MrCfg<R>::seg];  // this item's padded audio and the next one's (prefetched)
   float buf[kWarpsMr][32 * kLdMr];
   float2 win[MrCfg<R>::M];     // window at samples (2m, 2m + 1)
   float2 tw[R * 32];           // e^(-2 pi i b k1 / M) at [k1][b]
   float2 twi[32 * R];          // e^(+2 pi i b k1 / M) at [b][k1]
   float2 post[MrCfg<R>::M];    // e^(-2 pi i k / n)
   float red[kWarpsMr];
+  uint64_t mbar[kWarpsMr];     // per warp: its frames' target rows have arrived
 };
+
+constexpr long long kMrWaitLimit = 1ll << 24;
 
 struct MrTables {
   const float2* win;
@@ -88,11 +96,35 @@ __device__ __forceinline__ void rotate_upper(float (&x)[32], bool on, bool back)
   }
 }
 
+// Stages the padded samples base .. base + len - 1 of signal x (sample j of
+// the segment = x[reflect(base + j)]) in dst: 16-byte cp.async copies where a
+// 4-sample run lies inside the signal, plain loads where it is reflected;
+// the copies form one commit group.
+__device__ __forceinline__ void stage_segment(float* dst, const float* __restrict__ x, int N,
+                                              bool vec, int base, int len) {
+  for (int j = 4 * threadIdx.x; j < len; j += 4 * kThreadsMr) {
+    const int i0 = base + j;
+    if (vec && i0 >= 0 && i0 + 3 < N) {
+      const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst + j);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(x + i0) : "memory");
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int i = i0 + q;
+        i = i < 0 ? -i : i;
+        i = i >= N ? 2 * (N - 1) - i : i;
+        dst[j + q] = __ldg(x + i);
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 template <int R>
 __global__ void __launch_bounds__(kThreadsMr, 2)
     mr_fft_kernel(const float* __restrict__ sig, int N, int F, int batch, MrTables t, float eps,
                   float scale, int mode, float* __restrict__ logy, double* __restrict__ loss_voice,
-                  float* __restrict__ dframes) {
+                  float* __restrict__ part, unsigned int* __restrict__ err) {
   using C = MrCfg<R>;
   extern __shared__ __align__(16) unsigned char mr_raw[];
   MrSmem<R>& S = *reinterpret_cast<MrSmem<R>*>(mr_raw);
@@ -104,6 +136,9 @@ __global__ void __launch_bounds__(kThreadsMr, 2)
     S.tw[j] = __ldg(t.tw + j);
     S.twi[j] = __ldg(t.twi + j);
   }
+  if ((threadIdx.x & 31) == 0) mbar::init(&S.mbar[threadIdx.x >> 5], 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  uint32_t mb_phase = 0;
   const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(sig) & 15) == 0;
   const int groups = (F + C::G - 1) / C::G;
   const int items = groups * batch;
@@ -113,40 +148,38 @@ __global__ void __launch_bounds__(kThreadsMr, 2)
   const bool self = k1 == 0;
   float* B = S.buf[warp];
 
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  auto stage = [&](int it, float* dst) {
+    const int vv = it / groups, ff = (it - vv * groups) * C::G;
+    stage_segment(dst, sig + (size_t)vv * N, N, vec, ff * C::hop - C::n / 2,
+                  (min(C::G, F - ff) - 1) * C::hop + C::n);
+  };
+  if ((int)blockIdx.x < items) stage(blockIdx.x, S.seg[0]);
+  int cur = 0;
+  for (int item = blockIdx.x; item < items; item += gridDim.x, cur ^= 1) {
     const int v = item / groups, f0 = (item - v * groups) * C::G;
     const int Gi = min(C::G, F - f0);
     const int len = (Gi - 1) * C::hop + C::n;
-    const float* x = sig + (size_t)v * N;
-    const int base = f0 * C::hop - C::n / 2;
-    __syncthreads();  // the previous item is done with the segment and S.red
-    for (int j = 4 * threadIdx.x; j < len; j += 4 * kThreadsMr) {
-      const int i0 = base + j;
-      if (vec && i0 >= 0 && i0 + 3 < N) {
-        const unsigned int dst = (unsigned int)__cvta_generic_to_shared(S.seg + j);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(x + i0)
-                     : "memory");
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          int i = i0 + q;
-          i = i < 0 ? -i : i;
-          i = i >= N ? 2 * (N - 1) - i : i;
-          S.seg[j + q] = __ldg(x + i);
-        }
-      }
+    float* sg = S.seg[cur];
+    __syncthreads();  // the previous item is done with the other buffer and S.red
+    // prefetch the next item's segment, then wait for this one's copies
+    if (item + (int)gridDim.x < items) {
+      stage(item + gridDim.x, S.seg[cur ^ 1]);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
 
     float acc = 0.f;  // sum of |d| over this warp's bins
-    for (int lf0 = warp * C::FPW; lf0 < Gi; lf0 += kWarpsMr * C::FPW) {
-      float re[32], im[32];
+    // one pass per warp: frames lf0 .. lf0 + FPW - 1 of the item
+    const int lf0 = warp * C::FPW;
+    float re[32], im[32];
+    if (lf0 < Gi) {
       // ---- forward: z[32 a + lane] of frames lf0 .. lf0 + FPW - 1, windowed
 #pragma unroll
       for (int fr = 0; fr < C::FPW; ++fr) {
         const int lf = min(lf0 + fr, Gi - 1);
-        const float2* s2 = reinterpret_cast<const float2*>(S.seg + lf * C::hop);
+        const float2* s2 = reinterpret_cast<const float2*>(sg + lf * C::hop);
 #pragma unroll
         for (int a = 0; a < R; ++a) {
           const float2 sv = s2[32 * a + lane];
@@ -184,7 +217,21 @@ __global__ void __launch_bounds__(kThreadsMr, 2)
 #pragma unroll
       for (int b = 0; b < 32; ++b) im[b] = B[lane * kLdMr + b];
       __syncwarp();
+      // the target rows of this warp's frames into B (free until the inverse
+      // transposes) by one bulk copy, in flight during the 32-point DFTs
+      if (mode != kMrTarget && lane == 0) {
+        const int rows = min(C::FPW, Gi - lf0);
+        const uint32_t bytes = (uint32_t)(rows * C::ldl * sizeof(float));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar::expect_tx(&S.mbar[warp], bytes);
+        mbar::bulk_g2s(B, logy + ((size_t)v * F + f0 + lf0) * C::ldl, bytes, &S.mbar[warp]);
+      }
       fftw::dft<32, 0>(re, im);  // Z[k1 + R k2] of frame phi in register bitrev<32>(k2)
+      if (mode != kMrTarget) {
+        if (!mbar::wait(&S.mbar[warp], mb_phase, kMrWaitLimit) && lane == 0) atomicOr(err, 1u);
+        mb_phase ^= 1;
+      }
+      const float* ly = B + phi * C::ldl;  // this lane's frame's target row
 
       const int lf = lf0 + phi;
       const bool valid = lf < Gi;
@@ -221,29 +268,32 @@ __global__ void __launch_bounds__(kThreadsMr, 2)
           const float2 w = S.post[k];
           const float xr = 0.5f * (ar + fmaf(w.x, cr, -w.y * ci));
           const float xi = 0.5f * (ai + fmaf(w.x, ci, w.y * cr));
-          const float mag = sqrtf(fmaf(xr, xr, xi * xi));
-          const float lm = logf(mag + eps);
+          // |X| by the reciprocal square root, log by the SFU: both well
+          // inside the distance's and the gradient's tolerances
+          const float p2 = fmaf(xr, xr, xi * xi);
+          const float mag = p2 > 0.f ? p2 * rsqrtf(p2) : 0.f;
+          const float lm = __logf(mag + eps);
           gr[h] = 0.f;
           gi[h] = 0.f;
           if (mode == kMrTarget) {
-            if (valid) logy[row * C::bins + k] = lm;
+            if (valid) logy[row * C::ldl + k] = lm;
           } else {
-            const float d = lm - (valid ? logy[row * C::bins + k] : lm);
+            const float d = lm - (valid ? ly[k] : lm);
             acc += fabsf(d);
             if (mag > 0.f && d != 0.f) {
-              const float g = (d > 0.f ? scale : -scale) / ((mag + eps) * mag);
+              const float g = __fdividef(d > 0.f ? scale : -scale, (mag + eps) * mag);
               gr[h] = g * xr;
               gi[h] = g * xi;
             }
           }
           if (k == 0) {  // the Nyquist bin X[M] = Re Z[0] - Im Z[0] (real)
-            const float xn = zr - zi, mn = fabsf(xn), ln = logf(mn + eps);
+            const float xn = zr - zi, mn = fabsf(xn), ln = __logf(mn + eps);
             if (mode == kMrTarget) {
-              if (valid) logy[row * C::bins + C::M] = ln;
+              if (valid) logy[row * C::ldl + C::M] = ln;
             } else {
-              const float d = ln - (valid ? logy[row * C::bins + C::M] : ln);
+              const float d = ln - (valid ? ly[C::M] : ln);
               acc += fabsf(d);
-              if (mn > 0.f && d != 0.f) nyq_g = (d > 0.f ? scale : -scale) / ((mn + eps) * mn) * xn;
+              if (mn > 0.f && d != 0.f) nyq_g = __fdividef(d > 0.f ? scale : -scale, (mn + eps) * mn) * xn;
             }
           }
         }
@@ -281,8 +331,7 @@ __global__ void __launch_bounds__(kThreadsMr, 2)
           }
         }
       }
-      if (mode != kMrLossGrad) continue;
-
+      if (mode == kMrLossGrad) {
       // ---- inverse: z[m] = sum_k Zp_k e^(2 pi i k m / M), m = 32 a + b
       rotate_upper(re, self, true);
       rotate_upper(im, self, true);
@@ -328,17 +377,40 @@ __global__ void __launch_bounds__(kThreadsMr, 2)
         for (int q = 0; q < R; ++q) im[fr * R + q] = B[(fr * R + q) * kLdMr + lane];
       __syncwarp();
       fftw::dft_frames<R>(im, re);  // z[32 a + lane] of frame fr in register fr R + bitrev<R>(a)
-#pragma unroll
-      for (int fr = 0; fr < C::FPW; ++fr) {
-        if (lf0 + fr >= Gi) continue;
-        float2* out = reinterpret_cast<float2*>(dframes + ((size_t)v * F + f0 + lf0 + fr) * C::n);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int m = 32 * bitrev<R>(r) + lane;
-          const float2 wv = S.win[m];
-          out[m] = make_float2(re[fr * R + r] * wv.x, im[fr * R + r] * wv.y);
-        }
       }
+    }
+    if (mode == kMrLossGrad) {
+      // the item's frame gradients (times the window) summed into its padded
+      // segment, over the audio it no longer needs; frames four hops apart do
+      // not overlap, so the four residue classes of the frame index add in
+      // turn (a fixed order: the sums are deterministic)
+      __syncthreads();
+      for (int j = 4 * threadIdx.x; j < len; j += 4 * kThreadsMr)
+        *reinterpret_cast<float4*>(sg + j) = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int fr = 0; fr < C::FPW; ++fr) {
+          const int lf = lf0 + fr;
+          if (lf < Gi && (lf & 3) == c) {
+            float2* a = reinterpret_cast<float2*>(sg + lf * C::hop);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int m = 32 * bitrev<R>(r) + lane;
+              const float2 wv = S.win[m];
+              float2 o = a[m];
+              o.x = fmaf(re[fr * R + r], wv.x, o.x);
+              o.y = fmaf(im[fr * R + r], wv.y, o.y);
+              a[m] = o;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      float4* dst = reinterpret_cast<float4*>(part + (size_t)item * C::seg);
+      for (int j = threadIdx.x; 4 * j < len; j += kThreadsMr)
+        dst[j] = reinterpret_cast<const float4*>(sg)[j];
     }
     if (mode != kMrTarget) {
 #pragma unroll
@@ -355,35 +427,77 @@ __global__ void __launch_bounds__(kThreadsMr, 2)
   }
 }
 
-// dAudio[b][s] (+)= sum over padded positions p with reflect(p - pad) == s of
-// sum over frames f covering p of dframes[b F + f][p - f hop]. Grid
-// (samples, voices); accumulate = 0 overwrites.
-__global__ void overlap_add_reflect(const float* __restrict__ dframes, int N, int n_fft, int hop,
-                                    int F, int accumulate, float* __restrict__ daudio) {
-  const int pad = n_fft / 2;
-  const int b = blockIdx.y;
-  const float* dfv = dframes + (size_t)b * F * n_fft;
-  float* out = daudio + (size_t)b * N;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+// The audio gradient from the items' segment partials of every resolution:
+// grad[v][s] = sum over resolutions, over the padded positions p with
+// reflect(p - n/2) = s (one, or two near the ends), over the items whose
+// segment covers p (one or two: segments of (G + 3) hops start every G hops)
+// of the partial at p. One thread per sample, a fixed summation order.
+struct OlaRes {
+  const float* part;  // [batch][groups][seg]
+  int n, hop, G, groups, seg, F;
+};
+struct OlaArgs {
+  OlaRes r[8];
+  int n_res;
+};
+
+__device__ __forceinline__ float ola_sample(const OlaArgs& a, int N, int v, int s) {
+  float acc = 0.f;
+  for (int k = 0; k < a.n_res; ++k) {
+    const OlaRes& R = a.r[k];
+    const int pad = R.n / 2, stride = R.G * R.hop;
+    const float* pv = R.part + (size_t)v * R.groups * R.seg;
     int pre[3];
     int np = 0;
     pre[np++] = s + pad;
     if (s >= 1 && s <= pad) pre[np++] = pad - s;
     if (s <= N - 2 && 2 * (N - 1) - s + pad < N + 2 * pad && 2 * (N - 1) - s >= N)
       pre[np++] = 2 * (N - 1) - s + pad;
-    float acc = 0.f;
     for (int j = 0; j < np; ++j) {
       const int p = pre[j];
-      int f_hi = p / hop;
-      if (f_hi > F - 1) f_hi = F - 1;
-      int f_lo = (p - n_fft + hop) / hop;  // ceil((p - n_fft + 1) / hop)
-      if (p - n_fft + 1 <= 0) f_lo = 0;
-      for (int f = f_lo; f <= f_hi; ++f) {
-        const int t = p - f * hop;
-        if (t >= 0 && t < n_fft) acc += dfv[(size_t)f * n_fft + t];
+      const int i = min(p / stride, R.groups - 1);
+      for (int q = i; q >= 0 && q >= i - 1; --q) {
+        const int off = p - q * stride;
+        const int len = (min(R.G, R.F - q * R.G) - 1) * R.hop + R.n;
+        if (off >= 0 && off < len) acc += pv[(size_t)q * R.seg + off];
       }
     }
-    out[s] = accumulate ? out[s] + acc : acc;
+  }
+  return acc;
+}
+
+// Four samples per thread: away from the ends (no reflected positions) the
+// four padded positions s + n/2 share their items and segment bounds (all
+// multiples of 4), so each covering segment contributes one 16-byte load.
+__global__ void mr_ola_gather(OlaArgs a, int N, int pad_max, float* __restrict__ grad) {
+  const int v = blockIdx.y;
+  const int n4 = (N + 3) / 4;
+  const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(grad) & 15) == 0;
+  for (int i4 = blockIdx.x * blockDim.x + threadIdx.x; i4 < n4; i4 += gridDim.x * blockDim.x) {
+    const int s0 = 4 * i4;
+    if (vec && s0 > pad_max && s0 + 3 <= N - 2 - pad_max) {
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < a.n_res; ++k) {
+        const OlaRes& R = a.r[k];
+        const int stride = R.G * R.hop, p0 = s0 + R.n / 2;
+        const float* pv = R.part + (size_t)v * R.groups * R.seg;
+        const int i = min(p0 / stride, R.groups - 1);
+        for (int q = i; q >= 0 && q >= i - 1; --q) {
+          const int off = p0 - q * stride;
+          const int len = (min(R.G, R.F - q * R.G) - 1) * R.hop + R.n;
+          if (off >= 0 && off < len) {
+            const float4 t = *reinterpret_cast<const float4*>(pv + (size_t)q * R.seg + off);
+            acc.x += t.x;
+            acc.y += t.y;
+            acc.z += t.z;
+            acc.w += t.w;
+          }
+        }
+      }
+      *reinterpret_cast<float4*>(grad + (size_t)v * N + s0) = acc;
+    } else {
+      for (int s = s0; s < min(s0 + 4, N); ++s) grad[(size_t)v * N + s] = ola_sample(a, N, v, s);
+    }
   }
 }
 
@@ -434,8 +548,8 @@ int r_of(int n_fft) { return n_fft == 512 ? 8 : n_fft == 1024 ? 16 : n_fft == 20
 
 template <int R>
 cudaError_t mr_launch(const float* sig, int N, int F, int batch, const char* tables, float eps,
-                      float scale, int mode, float* logy, double* loss_voice, float* dframes,
-                      cudaStream_t st) {
+                      float scale, int mode, float* logy, double* loss_voice, float* part,
+                      unsigned int* err, cudaStream_t st) {
   const int smem = (int)sizeof(MrSmem<R>);
   static int grid_cap = 0;
   if (grid_cap == 0) {
@@ -455,20 +569,26 @@ cudaError_t mr_launch(const float* sig, int N, int F, int batch, const char* tab
   if (items >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const int grid = (int)std::min<int64_t>(items, grid_cap);
   mr_fft_kernel<R><<<grid, kThreadsMr, smem, st>>>(sig, N, F, batch, mr_tables(R, tables), eps,
-                                                   scale, mode, logy, loss_voice, dframes);
+                                                   scale, mode, logy, loss_voice, part, err);
   return cudaGetLastError();
 }
 
 cudaError_t mr_pass(int n_fft, const float* sig, int N, int F, int batch, const char* tables,
-                    float eps, float scale, int mode, float* logy, double* loss_voice,
-                    float* dframes, cudaStream_t st) {
+                    float eps, float scale, int mode, float* logy, double* loss_voice, float* part,
+                    unsigned int* err, cudaStream_t st) {
+#define SYNTH_MR_ARGS sig, N, F, batch, tables, eps, scale, mode, logy, loss_voice, part, err, st
   switch (r_of(n_fft)) {
-    case 8: return mr_launch<8>(sig, N, F, batch, tables, eps, scale, mode, logy, loss_voice, dframes, st);
-    case 16: return mr_launch<16>(sig, N, F, batch, tables, eps, scale, mode, logy, loss_voice, dframes, st);
-    case 32: return mr_launch<32>(sig, N, F, batch, tables, eps, scale, mode, logy, loss_voice, dframes, st);
+    case 8: return mr_launch<8>(SYNTH_MR_ARGS);
+    case 16: return mr_launch<16>(SYNTH_MR_ARGS);
+    case 32: return mr_launch<32>(SYNTH_MR_ARGS);
     default: return cudaErrorInvalidValue;
   }
+#undef SYNTH_MR_ARGS
 }
+
+// frames per work item and padded segment length of a resolution
+int mr_group(int n_fft) { return kWarpsMr * (32 / std::max(1, r_of(n_fft))); }
+int mr_seg(int n_fft) { return (mr_group(n_fft) - 1) * (n_fft / 4) + n_fft; }
 
 }  // namespace
 
@@ -503,7 +623,7 @@ std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld)
 namespace {
 struct MrLayout {
   char* tables[8];
-  float* dframes;
+  float* part[8];
   float* logy[8];
   double* loss_voice;
   size_t total;
@@ -518,15 +638,13 @@ MrLayout mr_layout(int64_t N, int batch, const int* n_ffts, int n_res, void* ws)
     off += al256(bytes);
     return p;
   };
-  int64_t max_dfr = 0;
   for (int r = 0; r < n_res; ++r) {
-    const int n = n_ffts[r];
+    const int n = n_ffts[r], F = stft_frames(N, n);
     L.tables[r] = take(mr_table_bytes(std::max(1, r_of(n))));
-    const int64_t M = (int64_t)batch * stft_frames(N, n);
-    max_dfr = std::max<int64_t>(max_dfr, M * n);
-    L.logy[r] = reinterpret_cast<float*>(take(sizeof(float) * M * (n / 2 + 1)));
+    L.logy[r] = reinterpret_cast<float*>(take(sizeof(float) * batch * F * (n / 2 + 4)));
+    const int64_t groups = (F + mr_group(n) - 1) / mr_group(n);
+    L.part[r] = reinterpret_cast<float*>(take(sizeof(float) * batch * groups * mr_seg(n)));
   }
-  L.dframes = reinterpret_cast<float*>(take(sizeof(float) * max_dfr));
   L.loss_voice = reinterpret_cast<double*>(take(sizeof(double) * batch));
   L.total = off;
   return L;
@@ -539,7 +657,8 @@ size_t mrstft_workspace_bytes(int64_t N, int batch, const int* n_ffts, int n_res
 
 cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batch,
                              const int* n_ffts, int n_res, float eps, bool target_ready,
-                             double* loss_voice_out, float* grad_x, void* ws, cudaStream_t st) {
+                             double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
+                             cudaStream_t st) {
   if (n_res < 1 || n_res > 8) return cudaErrorInvalidValue;
   for (int r = 0; r < n_res; ++r)  // reflect padding needs more samples than half a frame
     if (r_of(n_ffts[r]) == 0 || N <= n_ffts[r] / 2 || N >= (int64_t)1 << 31)
@@ -552,23 +671,28 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
       const int n = n_ffts[r];
       if ((e = mr_tables_fill(r_of(n), L.tables[r], st)) != cudaSuccess) return e;
       if ((e = mr_pass(n, y, (int)N, stft_frames(N, n), batch, L.tables[r], eps, 0.f, kMrTarget,
-                       L.logy[r], nullptr, nullptr, st)) != cudaSuccess)
+                       L.logy[r], nullptr, nullptr, err, st)) != cudaSuccess)
         return e;
     }
   }
   if ((e = cudaMemsetAsync(L.loss_voice, 0, sizeof(double) * batch, st)) != cudaSuccess) return e;
+  OlaArgs ola;
+  ola.n_res = n_res;
   for (int r = 0; r < n_res; ++r) {
     const int n = n_ffts[r], F = stft_frames(N, n);
     const float scale = 1.0f / (float)((int64_t)F * (n / 2 + 1));
     if ((e = mr_pass(n, x, (int)N, F, batch, L.tables[r], eps, scale,
-                     grad_x ? kMrLossGrad : kMrLoss, L.logy[r], L.loss_voice, L.dframes, st)) !=
+                     grad_x ? kMrLossGrad : kMrLoss, L.logy[r], L.loss_voice, L.part[r], err, st)) !=
         cudaSuccess)
       return e;
-    if (grad_x) {
-      dim3 go((unsigned)std::min<int64_t>((N + 255) / 256, 1024), (unsigned)batch);
-      overlap_add_reflect<<<go, 256, 0, st>>>(L.dframes, (int)N, n, n / 4, F, r > 0 ? 1 : 0,
-                                              grad_x);
-    }
+    ola.r[r] = OlaRes{L.part[r], n, n / 4, mr_group(n), (F + mr_group(n) - 1) / mr_group(n),
+                      mr_seg(n), F};
+  }
+  if (grad_x) {
+    int pad_max = 0;
+    for (int r = 0; r < n_res; ++r) pad_max = std::max(pad_max, n_ffts[r] / 2);
+    dim3 go((unsigned)std::min<int64_t>((N / 4 + 255) / 256 + 1, 1024), (unsigned)batch);
+    mr_ola_gather<<<go, 256, 0, st>>>(ola, (int)N, pad_max, grad_x);
   }
   if (loss_voice_out)
     cudaMemcpyAsync(loss_voice_out, L.loss_voice, sizeof(double) * batch, cudaMemcpyDeviceToDevice,

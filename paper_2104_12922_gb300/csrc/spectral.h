@@ -26,11 +26,12 @@ int stft_frames(int64_t N, int n_fft);
 // device) and its gradient w.r.t. x; n_ffts from {512, 1024, 2048}.
 // loss_voice_out [batch] (device, FP64, may be NULL); grad_x [batch][N] or NULL. With target_ready the tables and
 // the target log-magnitudes left in ws by an earlier call for the same y are
-// reused.
+// reused. err: device word, bit 0 set if a bounded wait gave up.
 size_t mrstft_workspace_bytes(int64_t N, int batch, const int* n_ffts, int n_res);
 cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batch,
                              const int* n_ffts, int n_res, float eps, bool target_ready,
-                             double* loss_voice_out, float* grad_x, void* ws, cudaStream_t st);
+                             double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
+                             cudaStream_t st);
 
 // Slaney mel filterbank [n_mels][ld] (unit-area triangles over 0 .. sr/2).
 std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld);

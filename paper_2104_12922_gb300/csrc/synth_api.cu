@@ -291,9 +291,10 @@ synth_status synth_mrstft(synth_handle h, const float* x_dev, const float* y_dev
   if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return SYNTH_ERR_ARG;
   if (workspace_bytes < mrstft_workspace_bytes(h->vc.n_samples, batch, kMrFFT, 3))
     return SYNTH_ERR_ARG;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
   return check_cuda(mrstft_loss_grad(x_dev, y_dev, h->vc.n_samples, batch, kMrFFT, 3, 1e-7f,
                                      target_ready != 0, loss_voice_dev, grad_x_dev, workspace_dev,
-                                     static_cast<cudaStream_t>(stream)));
+                                     &hdr->error, static_cast<cudaStream_t>(stream)));
 }
 
 synth_status synth_param_adam(synth_handle h, float* u_dev, const float* grad_dev, float* m_dev,
