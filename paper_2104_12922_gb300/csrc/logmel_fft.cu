@@ -14,7 +14,9 @@
 // b. The real spectrum follows from Z[k] and Z[1024 - k] (a lane shuffle):
 // X[k] = E[k] + W2048^k O[k] with E = (Z[k] + conj Z[1024-k]) / 2 and
 // O = (Z[k] - conj Z[1024-k]) / 2i. The 1/2 of E and O is folded into the
-// mel weights (a factor 1/4 on |X|^2).
+// mel weights (a factor 1/4 on |X|^2). The window comes from the SFU cosine
+// and each mel weight from its band's two triangle lines, so the shared
+// memory traffic is the transform's own.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -41,27 +43,26 @@ constexpr int kSegMax = (kGroup - 1) * kHop + kMelFFT;
 static_assert(kBuf >= kBins, "power spectrum fits the transpose buffer");
 
 struct LmTables {
-  const int* n_weights; // number of mel weights
-  const float2* win;    // [1024]: periodic Hann at samples (2m, 2m + 1)
   const float2* tw;     // [32][32]: e^(-2 pi i b k1 / 1024) at [k1][b]
   const float2* post;   // [1024]: e^(-2 pi i k / 2048)
-  const int* band;      // [128][2]: first bin, bin count
-  const int* woff;      // [128]: offset of the band's weights
-  const float* w;       // mel weights x 1/4, consecutive bins per band
+  const int2* band;     // [128]: first non-zero bin, bin count
+  const float4* line;   // [128]: mel weight x 1/4 of bin k = max(0, min(x k + y, z k + w))
 };
-
-constexpr int kMaxWeights = 2560;  // mel weights held in shared memory (the bank has ~2100)
 
 struct __align__(16) LmSmem {
   float seg[kSegMax];           // the group's padded audio
   float buf[kWarpsLm][kBuf];    // per warp: transpose, then power spectrum, then bands
-  float2 win[kHalf];
   float2 tw[32 * 32];
   float2 post[kHalf];
-  int band[2 * kMelBands];
-  int woff[kMelBands];
-  float w[kMaxWeights];
+  int2 band[kMelBands];
+  float4 line[kMelBands];
 };
+
+// Periodic Hann window at sample k of the 2048-point frame from the SFU
+// cosine on [-pi, pi): 0.5 - 0.5 cos(2 pi k / n) = 0.5 + 0.5 cos(2 pi k / n - pi).
+__device__ __forceinline__ float hann2048(int k) {
+  return fmaf(0.5f, __cosf(fmaf((float)k, 0.0030679615757712823f, -3.14159265358979f)), 0.5f);
+}
 
 __global__ void __launch_bounds__(kThreadsLm, 2)
     logmel_fft_kernel(const float* __restrict__ audio, int N, int F, int batch, LmTables t,
@@ -69,15 +70,12 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
                       __nv_bfloat16* __restrict__ features) {
   extern __shared__ __align__(16) unsigned char lm_raw[];
   LmSmem& S = *reinterpret_cast<LmSmem*>(lm_raw);
-  for (int j = threadIdx.x; j < kHalf; j += kThreadsLm) {
-    S.win[j] = __ldg(t.win + j);
-    S.post[j] = __ldg(t.post + j);
-  }
+  for (int j = threadIdx.x; j < kHalf; j += kThreadsLm) S.post[j] = __ldg(t.post + j);
   for (int j = threadIdx.x; j < 32 * 32; j += kThreadsLm) S.tw[j] = __ldg(t.tw + j);
-  for (int j = threadIdx.x; j < 2 * kMelBands; j += kThreadsLm) S.band[j] = __ldg(t.band + j);
-  for (int j = threadIdx.x; j < kMelBands; j += kThreadsLm) S.woff[j] = __ldg(t.woff + j);
-  const int n_weights = min(__ldg(t.n_weights), kMaxWeights);
-  for (int j = threadIdx.x; j < n_weights; j += kThreadsLm) S.w[j] = __ldg(t.w + j);
+  for (int j = threadIdx.x; j < kMelBands; j += kThreadsLm) {
+    S.band[j] = __ldg(t.band + j);
+    S.line[j] = __ldg(t.line + j);
+  }
   const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(audio) & 15) == 0;
   const int groups = (F + kGroup - 1) / kGroup;
   const int items = groups * batch;
@@ -122,9 +120,8 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
 #pragma unroll
       for (int a = 0; a < 32; ++a) {
         const float2 sv = s2[32 * a + lane];
-        const float2 wv = S.win[32 * a + lane];
-        re[a] = sv.x * wv.x;
-        im[a] = sv.y * wv.y;
+        re[a] = sv.x * hann2048(2 * (32 * a + lane));
+        im[a] = sv.y * hann2048(2 * (32 * a + lane) + 1);
       }
       fftw::dft<32, 0>(re, im);  // over a: Y[k1] in register bitrev<32>(k1)
       // twiddle W1024^(lane k1), then the transpose: real parts, then imaginary
@@ -185,12 +182,15 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int m = q == 0 ? lane : q == 1 ? 63 - lane : q == 2 ? 64 + lane : 127 - lane;
-        const int k0 = S.band[2 * m], cnt = S.band[2 * m + 1];
-        const float* wm = S.w + S.woff[m];
-        float acc = 0.f;
+        const int2 br = S.band[m];
+        const float4 ln = S.line[m];
+        float acc = 0.f, kf = (float)br.x;
 #pragma unroll 4
-        for (int j = 0; j < cnt; ++j) acc = fmaf(wm[j], B[k0 + j], acc);
-        mel[q] = (logf(acc + eps) - shift) * inv_scale;
+        for (int j = 0; j < br.y; ++j, kf += 1.f) {
+          const float w = fmaxf(0.f, fminf(fmaf(kf, ln.x, ln.y), fmaf(kf, ln.z, ln.w)));
+          acc = fmaf(w, B[br.x + j], acc);
+        }
+        mel[q] = (__logf(acc + eps) - shift) * inv_scale;
       }
       __syncwarp();
       B[lane] = mel[0];
@@ -212,63 +212,28 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
 size_t al256b(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct LmLayout {
-  size_t count, win, tw, post, band, woff, w, total;
+  size_t tw, post, band, line, total;
 };
 
-LmLayout lm_layout(int n_weights) {
+LmLayout lm_layout() {
   LmLayout L{};
   size_t o = 0;
-  L.count = o; o += 256;
-  L.win = o;  o += al256b(sizeof(float2) * kHalf);
   L.tw = o;   o += al256b(sizeof(float2) * 32 * 32);
   L.post = o; o += al256b(sizeof(float2) * kHalf);
-  L.band = o; o += al256b(sizeof(int) * 2 * kMelBands);
-  L.woff = o; o += al256b(sizeof(int) * kMelBands);
-  L.w = o;    o += al256b(sizeof(float) * n_weights);
+  L.band = o; o += al256b(sizeof(int2) * kMelBands);
+  L.line = o; o += al256b(sizeof(float4) * kMelBands);
   L.total = o;
   return L;
 }
 
-// The mel bank's non-zero weights per band (each band's bins are contiguous).
-void mel_sparse(double sample_rate, std::vector<int>& band, std::vector<int>& woff,
-                std::vector<float>& w) {
-  const std::vector<float> fb = mel_filterbank_host(kMelFFT, kMelBands, sample_rate, kBins);
-  band.assign(2 * kMelBands, 0);
-  woff.assign(kMelBands, 0);
-  w.clear();
-  for (int m = 0; m < kMelBands; ++m) {
-    int lo = -1, hi = -1;
-    for (int k = 0; k < kBins; ++k)
-      if (fb[(size_t)m * kBins + k] != 0.f) {
-        if (lo < 0) lo = k;
-        hi = k;
-      }
-    woff[m] = (int)w.size();
-    if (lo < 0) continue;
-    band[2 * m] = lo;
-    band[2 * m + 1] = hi - lo + 1;
-    for (int k = lo; k <= hi; ++k) w.push_back(0.25f * fb[(size_t)m * kBins + k]);
-  }
-}
-
 }  // namespace
 
-size_t logmel_fft_table_bytes() { return lm_layout(kMaxWeights).total; }
+size_t logmel_fft_table_bytes() { return lm_layout().total; }
 
 cudaError_t logmel_fft_init(double sample_rate, void* tables, cudaStream_t st) {
   const double pi = 3.14159265358979323846;
-  std::vector<int> band, woff;
-  std::vector<float> w;
-  mel_sparse(sample_rate, band, woff, w);
-  if (w.size() > (size_t)kMaxWeights) return cudaErrorInvalidValue;
-  const LmLayout L = lm_layout((int)w.size());
+  const LmLayout L = lm_layout();
   std::vector<char> host(L.total, 0);
-  *reinterpret_cast<int*>(host.data() + L.count) = (int)w.size();
-  float2* win = reinterpret_cast<float2*>(host.data() + L.win);
-  for (int m = 0; m < kHalf; ++m) {
-    win[m].x = (float)(0.5 - 0.5 * std::cos(2.0 * pi * (2 * m) / kMelFFT));
-    win[m].y = (float)(0.5 - 0.5 * std::cos(2.0 * pi * (2 * m + 1) / kMelFFT));
-  }
   float2* tw = reinterpret_cast<float2*>(host.data() + L.tw);
   for (int k1 = 0; k1 < 32; ++k1)
     for (int b = 0; b < 32; ++b) {
@@ -280,9 +245,27 @@ cudaError_t logmel_fft_init(double sample_rate, void* tables, cudaStream_t st) {
     const double a = -2.0 * pi * (double)k / kMelFFT;
     post[k] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
-  std::copy(band.begin(), band.end(), reinterpret_cast<int*>(host.data() + L.band));
-  std::copy(woff.begin(), woff.end(), reinterpret_cast<int*>(host.data() + L.woff));
-  std::copy(w.begin(), w.end(), reinterpret_cast<float*>(host.data() + L.w));
+  // each band: the bins where the FP64 bank is non-zero, and the two lines of
+  // its triangle (rising edge, falling edge) in the bin index, with the unit
+  // area normalisation and the 1/4 of the packed transform folded in
+  const std::vector<float> fb = mel_filterbank_host(kMelFFT, kMelBands, sample_rate, kBins);
+  const std::vector<double> edges = mel_edges_host(kMelBands, sample_rate);
+  const double df = sample_rate / kMelFFT;
+  int2* band = reinterpret_cast<int2*>(host.data() + L.band);
+  float4* line = reinterpret_cast<float4*>(host.data() + L.line);
+  for (int m = 0; m < kMelBands; ++m) {
+    int lo = -1, hi = -1;
+    for (int k = 0; k < kBins; ++k)
+      if (fb[(size_t)m * kBins + k] != 0.f) {
+        if (lo < 0) lo = k;
+        hi = k;
+      }
+    band[m] = lo < 0 ? make_int2(0, 0) : make_int2(lo, hi - lo + 1);
+    const double e0 = edges[m], c = edges[m + 1], e1 = edges[m + 2];
+    const double norm = 0.25 * 2.0 / (e1 - e0);
+    line[m] = make_float4((float)(norm * df / (c - e0)), (float)(-norm * e0 / (c - e0)),
+                          (float)(-norm * df / (e1 - c)), (float)(norm * e1 / (e1 - c)));
+  }
   cudaError_t e = cudaMemcpyAsync(tables, host.data(), L.total, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
@@ -293,17 +276,13 @@ cudaError_t logmel_features_fft(const float* audio, int64_t N, int batch, const 
   if (N <= kMelFFT / 2 || N >= (int64_t)1 << 31) return cudaErrorInvalidValue;
   if (batch <= 0) return cudaSuccess;
   const int F = stft_frames(N, kMelFFT);
-  // the weight count is not needed for the offsets of the other tables
-  const LmLayout L = lm_layout(0);
+  const LmLayout L = lm_layout();
   const char* b = static_cast<const char*>(tables);
   LmTables t;
-  t.n_weights = reinterpret_cast<const int*>(b + L.count);
-  t.win = reinterpret_cast<const float2*>(b + L.win);
   t.tw = reinterpret_cast<const float2*>(b + L.tw);
   t.post = reinterpret_cast<const float2*>(b + L.post);
-  t.band = reinterpret_cast<const int*>(b + L.band);
-  t.woff = reinterpret_cast<const int*>(b + L.woff);
-  t.w = reinterpret_cast<const float*>(b + L.w);
+  t.band = reinterpret_cast<const int2*>(b + L.band);
+  t.line = reinterpret_cast<const float4*>(b + L.line);
   const int smem = (int)sizeof(LmSmem);
   static int grid_cap = 0;  // resident CTAs on the device
   if (grid_cap == 0) {

@@ -594,19 +594,26 @@ int mr_seg(int n_fft) { return (mr_group(n_fft) - 1) * (n_fft / 4) + n_fft; }
 
 int stft_frames(int64_t N, int n_fft) { return 1 + (int)(N / (n_fft / 4)); }
 
-// Slaney mel filterbank [n_mels][ld] (bf16, zero-padded), built on the host in
-// FP64: triangles between mel-spaced edges from 0 to SR/2, unit area in Hz.
-std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld) {
+// Slaney mel band edges in Hz: n_mels + 2 points equally spaced on the mel
+// scale (linear below 1 kHz, logarithmic above) from 0 to sr / 2.
+std::vector<double> mel_edges_host(int n_mels, double sr) {
   auto hz_to_mel = [](double f) {
     return f < 1000.0 ? 3.0 * f / 200.0 : 15.0 + 27.0 * std::log(f / 1000.0) / std::log(6.4);
   };
   auto mel_to_hz = [](double m) {
     return m < 15.0 ? 200.0 * m / 3.0 : 1000.0 * std::exp((m - 15.0) * std::log(6.4) / 27.0);
   };
-  const int nb = n_fft / 2 + 1;
   std::vector<double> edges(n_mels + 2);
   const double m_hi = hz_to_mel(sr / 2.0);
   for (int i = 0; i < n_mels + 2; ++i) edges[i] = mel_to_hz(m_hi * i / (n_mels + 1));
+  return edges;
+}
+
+// Slaney mel filterbank [n_mels][ld], built on the host in FP64: triangles
+// between the mel-spaced edges, unit area in Hz.
+std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld) {
+  const int nb = n_fft / 2 + 1;
+  const std::vector<double> edges = mel_edges_host(n_mels, sr);
   std::vector<float> fb((size_t)n_mels * ld, 0.f);
   for (int i = 0; i < n_mels; ++i) {
     const double lo = edges[i], c = edges[i + 1], hi = edges[i + 2];

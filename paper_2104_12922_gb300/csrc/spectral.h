@@ -33,8 +33,10 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
                              double* loss_voice_out, float* grad_x, void* ws, unsigned int* err,
                              cudaStream_t st);
 
-// Slaney mel filterbank [n_mels][ld] (unit-area triangles over 0 .. sr/2).
+// Slaney mel filterbank [n_mels][ld] (unit-area triangles over 0 .. sr/2)
+// and its n_mels + 2 band edges in Hz.
 std::vector<float> mel_filterbank_host(int n_fft, int n_mels, double sr, int ld);
+std::vector<double> mel_edges_host(int n_mels, double sr);
 
 // Log-mel features [batch][frames][128] (bf16, flattened per voice) through a
 // shared-memory FFT (logmel_fft.cu): tables (logmel_fft_table_bytes, filled
