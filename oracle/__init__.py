@@ -122,9 +122,21 @@ def num_samples(cfg: Config) -> int:
     return int(round(cfg.seconds * cfg.sample_rate))
 
 
+def rate_ratio(sample_rate: float, control_rate: float) -> tuple[int, int]:
+    """R = SR / CR as A / B in lowest terms: an integer R, or, for a
+    fractional R, integer rates in Hz (the only fractional ratios rendered)."""
+    from fractions import Fraction
+    r = sample_rate / control_rate
+    if round(r) >= 1 and abs(r - round(r)) <= 1e-9:
+        return int(round(r)), 1
+    f = Fraction(int(round(sample_rate)), int(round(control_rate)))
+    return f.numerator, f.denominator
+
+
 def num_control_points(cfg: Config) -> int:
-    R = int(round(cfg.sample_rate / cfg.control_rate))
-    return (num_samples(cfg) + R - 1) // R + 1
+    """K + 1 points: K = floor((N - 1) B / A) + 1 intervals hold the samples."""
+    a, b = rate_ratio(cfg.sample_rate, cfg.control_rate)
+    return (num_samples(cfg) - 1) * b // a + 2
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

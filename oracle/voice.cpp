@@ -229,10 +229,16 @@ T lfo_shape(int shape, T p) {
 template <class T>
 T midi_to_hz(T m) { return T(440.0) * t_exp2((m - T(69.0)) / T(12.0)); }
 
+// Samples per control interval R = SR / CR = A / B in lowest terms: an
+// integer R (B = 1), or, for a fractional R, integer rates in Hz. Control
+// point k sits at sample position k A / B; sample n lies in interval
+// k = floor(n B / A) at the fraction u = (n B - k A) / A of the way from point
+// k to point k + 1 (for an integer R: k = n div R, u = (n mod R) / R).
 struct Geometry {
   int64_t N;   // samples per voice, round(seconds * SR)
-  int64_t R;   // samples per control interval, SR / CR (an integer)
-  int64_t K;   // control intervals, ceil(N / R); K + 1 control points
+  int64_t A;   // R = A / B
+  int64_t B;
+  int64_t K;   // control intervals holding samples, floor((N - 1) B / A) + 1; K + 1 points
 };
 
 bool geometry(const oracle_config* cfg, Geometry* g) {
@@ -240,11 +246,26 @@ bool geometry(const oracle_config* cfg, Geometry* g) {
   if (!(sr > 0) || !(cr > 0) || !(cfg->seconds > 0)) return false;
   double r = sr / cr;
   double n = cfg->seconds * sr;
-  g->R = (int64_t)std::llround(r);
   g->N = (int64_t)std::llround(n);
-  if (g->R < 1 || std::fabs(r - (double)g->R) > 1e-9) return false;
   if (std::fabs(n - (double)g->N) > 1e-6 || g->N < 1) return false;
-  g->K = (g->N + g->R - 1) / g->R;  // a ragged last interval still ends on point K
+  const int64_t ri = (int64_t)std::llround(r);
+  if (ri >= 1 && std::fabs(r - (double)ri) <= 1e-9) {
+    g->A = ri;
+    g->B = 1;
+  } else {
+    const int64_t si = (int64_t)std::llround(sr), ci = (int64_t)std::llround(cr);
+    if (std::fabs(sr - (double)si) > 1e-9 || std::fabs(cr - (double)ci) > 1e-9) return false;
+    int64_t a = si, b = ci;
+    while (b != 0) {
+      const int64_t t = a % b;
+      a = b;
+      b = t;
+    }
+    g->A = si / a;
+    g->B = ci / a;
+    if (g->A < g->B) return false;  // at least one sample per control interval
+  }
+  g->K = (g->N - 1) * g->B / g->A + 1;
   return true;
 }
 
@@ -329,8 +350,9 @@ void map_params(const oracle_config* cfg, const T* u_in, T* y) {
 }
 
 // One voice, every audio sample in order (Sec. 3.2 routing):
-//  * upsampling: sample n = kR + j takes c_k + (j/R)(c_{k+1} - c_k) of each
-//    control signal (linear, control point k at sample kR);
+//  * upsampling: sample n in interval k at fraction u (see Geometry; for an
+//    integer R, n = kR + j and u = j/R) takes c_k + u (c_{k+1} - c_k) of each
+//    control signal (linear between the control points);
 //  * VCO pitch in midi: m(n) = midi_f0 + tune + depth * pitch_dest(n), capped
 //    at the Nyquist pitch 69 + 12 log2(SR/2/440); f = 440 * 2^((m - 69)/12);
 //  * phase in cycles, exclusive running sum: phi(0) = frac(phase0 / 2pi),
@@ -377,9 +399,8 @@ int render_voice(const oracle_config* cfg, const T* u_in, uint64_t seed, uint64_
   uint32_t noise_words[4] = {0, 0, 0, 0};
 
   for (int64_t n = 0; n < geo.N; ++n) {
-    const int64_t k = n / geo.R;
-    const int64_t j = n % geo.R;
-    const double frac_j = (double)j / (double)geo.R;
+    const int64_t k = n * geo.B / geo.A;
+    const double frac_j = (double)(n * geo.B - k * geo.A) / (double)geo.A;
     auto upsample = [&](const std::vector<T>& c) { return c[k] + T(frac_j) * (c[k + 1] - c[k]); };
 
     T f[2];

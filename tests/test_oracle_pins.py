@@ -256,9 +256,16 @@ def test_constant_pitch_sine_closed_form(oracle_mod):
         assert np.max(np.abs(out - want)) < 1e-9
 
 
-def test_linear_glide_sine_closed_form(oracle_mod):
+@pytest.mark.parametrize("sr,cr", [(44100.0, 441.0), (16000.0, 441.0), (22050.0, 441.0),
+                                   (8000.0, 441.0), (48000.0, 400.0)])
+def test_linear_glide_sine_closed_form(oracle_mod, sr, cr):
     """Linear midi glide m(n) = m0 + D n / (a SR): the phase is the geometric
-    sum phi(n) = phi0 + (f0/SR) (r^n - 1)/(r - 1), r = 2^(D/(12 a SR))."""
+    sum phi(n) = phi0 + (f0/SR) (r^n - 1)/(r - 1), r = 2^(D/(12 a SR)). The
+    pitch is linear in time at the control points (an attack ramp), and
+    linear interpolation between control points keeps it linear at every
+    sample only if each sample takes its own fraction of its interval: so
+    the closed form holds for any R = SR / CR, integer (100, 50, 120) or not
+    (36.28..., 18.14...)."""
     secs, m0, D = 2.0, 50.0, 30.0
     extra = {si.MIDI: m0, si.SINE + 1: D, si.SINE + 2: 0.0,
              si.ADSR + 0: secs, si.ADSR + 4: 1.0,
@@ -268,14 +275,53 @@ def test_linear_glide_sine_closed_form(oracle_mod):
     pins[si.mod_slot(0, 1)] = 0.0
     pins[si.mod_slot(1, 1)] = 1.0   # ADSR1 = constant 1 drives the amplitude
     pins[si.mod_slot(0, 0)] = 1.0   # ADSR0 = linear ramp drives the pitch
-    cfg = oracle_mod.default_config(seconds=secs, nebula=_base_nebula(oracle_mod, pins))
+    cfg = oracle_mod.default_config(seconds=secs, sample_rate=sr, control_rate=cr,
+                                    nebula=_base_nebula(oracle_mod, pins))
     out = oracle_mod.render_voice(cfg, np.full(78, 0.5), 0, 0)
+    assert len(out) == int(secs * sr)
     f0 = 440.0 * 2 ** ((m0 - 69.0) / 12.0)
     n = np.arange(len(out), dtype=np.float64)
-    lr = D / (12.0 * secs * 44100.0) * math.log(2.0)
-    phi = f0 / 44100.0 * np.expm1(n * lr) / math.expm1(lr)
+    lr = D / (12.0 * secs * sr) * math.log(2.0)
+    phi = f0 / sr * np.expm1(n * lr) / math.expm1(lr)
     want = np.sin(2 * math.pi * np.mod(phi, 1.0))
     assert np.max(np.abs(out - want)) < 1e-8
+
+
+@pytest.mark.parametrize("sr,cr", [(16000.0, 441.0), (44100.0, 441.0), (11025.0, 400.0)])
+def test_amplitude_ramp_is_linear_at_every_sample(oracle_mod, sr, cr):
+    """A linear attack ramp routed to the sine's amplitude, at constant
+    pitch: out(n) = (t_n / a) sin(2 pi f n / SR) with t_n = n / SR, for any
+    R = SR / CR (the upsampling fraction of sample n is n B / A - k)."""
+    secs, a = 1.0, 1.0
+    f = 440.0
+    pins = _const_source_pins(1, {si.MIX: 1.0, si.MIX + 1: 0.0, si.MIX + 2: 0.0,
+                                  si.SINE + 1: 0.0, si.MIDI: 69.0, si.SINE: 0.0,
+                                  si.SINE + 2: 0.0, si.ADSR + 0: a, si.ADSR + 4: 1.0})
+    cfg = oracle_mod.default_config(seconds=secs, sample_rate=sr, control_rate=cr,
+                                    nebula=_base_nebula(oracle_mod, pins))
+    out = oracle_mod.render_voice(cfg, np.full(78, 0.5), 0, 0)
+    n = np.arange(len(out), dtype=np.float64)
+    want = np.minimum(n / sr / a, 1.0) * np.sin(2 * math.pi * np.mod(f * n / sr, 1.0))
+    assert np.max(np.abs(out - want)) < 1e-9
+
+
+def test_fractional_rate_geometry(oracle_mod):
+    """R = 16000 / 441: K = floor((N - 1) B / A) + 1 intervals, each of
+    floor(R) or ceil(R) samples (counted by brute force over n); an
+    unsupported non-integer pair of non-integer rates is refused."""
+    a, b = oracle_mod.rate_ratio(16000.0, 441.0)
+    assert (a, b) == (16000, 441)
+    assert oracle_mod.rate_ratio(44100.0, 441.0) == (100, 1)
+    N = 16000
+    k = np.arange(N, dtype=np.int64) * b // a
+    counts = np.bincount(k)
+    assert len(counts) == (N - 1) * b // a + 1
+    assert set(counts[:-1].tolist()) <= {36, 37} and 1 <= counts[-1] <= 37
+    cfg = oracle_mod.default_config(seconds=1.0, sample_rate=16000.0, control_rate=441.0)
+    assert oracle_mod.num_control_points(cfg) == len(counts) + 1
+    bad = oracle_mod.default_config(seconds=2.0, sample_rate=16000.5, control_rate=441.3)
+    with pytest.raises(ValueError):
+        oracle_mod.render_voice(bad, np.full(78, 0.5), 0, 0)
 
 
 def test_square_saw_spot_values(oracle_mod):
