@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-normalized", action="store_true")
     ap.add_argument("--no-generator", action="store_true")
+    ap.add_argument("--no-rates", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -220,6 +221,42 @@ def adjoint_leg(pkg, torch, dev, steps: int = 20):
             "config": "batch 64 x 1 s; per step: render, MR-STFT distance (n_fft 512/1024/2048, "
                       "hop n_fft/4) and its gradient, adjoint render, Adam on the 78 parameters",
             "steps": steps}
+
+
+def rates_leg(pkg, torch, stream, steps: int = 64):
+    """The fused render at a fractional samples-per-interval ratio: batch 128 x
+    4 s at 16 kHz with the 441 Hz control rate (R = 36.28..), outputs rotated
+    over 4 buffers; CUDA events around `steps` renders captured in a graph."""
+    sr, B, seconds = 16000.0, 128, 4.0
+    syn = pkg.Synth(seconds=seconds, max_batch=B, sample_rate=sr, control_rate=441.0)
+    n = syn.num_samples
+    outs = [torch.empty((B, n), dtype=torch.float32, device=syn.device) for _ in range(4)]
+    pout = torch.empty((B, 78), dtype=torch.float32, device=syn.device)
+
+    def record(k):
+        for s in range(k):
+            syn.render(s, s, B, out=outs[s % 4], params_out=pout, stream=stream)
+    with torch.cuda.stream(stream):
+        record(3)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        record(steps)
+    with torch.cuda.stream(stream):
+        g.replay()
+    stream.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        g.replay()
+        end.record(stream)
+    end.synchronize()
+    ms = start.elapsed_time(end) / steps
+    del g
+    syn.sync(stream)
+    syn.close()
+    return {"value": B * n / (ms / 1e3) / 1e6, "unit": "MHz", "ms_per_step": ms, "steps": steps,
+            "config": "batch 128 x 4 s at 16 kHz, control rate 441 Hz (R = 16000/441)"}
 
 
 def generator_leg(pkg, torch, syn, stream, count: int = 8192):
@@ -482,6 +519,7 @@ def run_ours(args):
         cpu = cpu_oracle_baseline(args.cpu_seconds)
     adjoint = None if args.no_adjoint else adjoint_leg(pkg, torch, dev)
     generator = None if args.no_generator else generator_leg(pkg, torch, syn, stream)
+    rates = None if args.no_rates else rates_leg(pkg, torch, stream)
     line = {"metric": METRIC, "value": value, "unit": "MHz", "n_gpus": ws, "steps": steps,
             "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
@@ -496,6 +534,7 @@ def run_ours(args):
             "plain": plain, "fused_over_plain": (value / plain["value"]) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "adjoint": adjoint, "normalized": normalized, "generator": generator,
+            "fractional_rate": rates,
             "gpu_launches": steps}
     print(json.dumps(line), flush=True)
     if ws > 1:

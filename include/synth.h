@@ -67,8 +67,13 @@ typedef struct {
 
 typedef struct {
   double sample_rate;   /* Hz; Sec. 3.1 default 44100 */
-  double control_rate;  /* Hz; Sec. 3.1 default 441. sample_rate/control_rate
-                           must be an integer multiple of 4, at most 65532 */
+  double control_rate;  /* Hz; Sec. 3.1 default 441. R = sample_rate/control_rate
+                           in [4, 65532]: an integer, or a fraction of two
+                           integer rates (e.g. 16000 / 441). Sample n then lies
+                           in control interval k = floor(n CR / SR), at the
+                           fraction n CR / SR - k between points k and k + 1.
+                           The plain and adjoint renders and FP32 carries need
+                           R an integer multiple of 4. */
   double seconds;       /* voice length; Abstract: 4 s */
   int32_t max_batch;    /* largest batch any call on this handle will use */
   int32_t carry;        /* SYNTH_CARRY_FIXED64 (default) or SYNTH_CARRY_FP32 */
@@ -84,9 +89,11 @@ void synth_default_config(synth_config* out);
 void synth_default_nebula(synth_nebula* out);
 
 /* Allocates the handle and its device scratch on the current CUDA device.
- * Errors: SYNTH_ERR_ARG (NULL pointers, non-integer or non-multiple-of-4
- * sample_rate/control_rate, seconds <= 0, max_batch < 1),
- * SYNTH_ERR_OOM, SYNTH_ERR_CUDA. */
+ * Errors: SYNTH_ERR_ARG (NULL pointers, rates or seconds <= 0, max_batch < 1,
+ * an unknown carry), SYNTH_ERR_UNSUPPORTED (R outside [4, 65532], a
+ * fractional R from rates that are not integers in Hz, seconds * sample_rate
+ * not an integer or >= 2^31, FP32 carries with R not an integer multiple of
+ * 4), SYNTH_ERR_OOM, SYNTH_ERR_CUDA. */
 synth_status synth_create(const synth_config* cfg, synth_handle* out);
 synth_status synth_destroy(synth_handle h);
 
@@ -136,6 +143,7 @@ synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t bat
  * module, every control-rate and audio-rate intermediate in a caller-owned
  * workspace in device memory), the torchsynth-style design of Sec. 3.1.
  * Same results as synth_render to within floating-point reordering.
+ * SYNTH_ERR_UNSUPPORTED unless R is an integer multiple of 4.
  * workspace_dev must hold synth_render_plain_workspace_size(h, batch) bytes
  * (256-byte aligned). Errors as synth_render, plus SYNTH_ERR_ARG when the
  * workspace is NULL or too small. */
@@ -159,7 +167,8 @@ synth_status synth_render_plain(synth_handle h, uint64_t seed, uint64_t batch_in
  *                  256-byte aligned, caller-owned.
  * The forward control rate is recomputed from the parameters; its
  * per-interval phase descriptions are the checkpoints from which every
- * audio sample is rebuilt. Errors as synth_render_plain; SYNTH_ERR_UNSUPPORTED
+ * audio sample is rebuilt. Errors as synth_render_plain (R an integer
+ * multiple of 4); SYNTH_ERR_UNSUPPORTED
  * when sample_rate/control_rate > 128. */
 synth_status synth_render_backward_workspace_size(synth_handle h, int32_t batch, size_t* bytes);
 synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch_index,
@@ -280,8 +289,9 @@ synth_status synth_model_load(synth_model m, const char* path);
  *  with the same results.
  * Scratch: a fixed 256 KiB device array inside the library, which every GPU
  * that loads the library holds until the process exits. It needs
- * 256 + 48 * batch * ceil(ceil(seconds * sample_rate / R) / 255) bytes
- * (R = sample_rate / control_rate); for 4 s at 44.1 kHz that allows batch
+ * 256 + 48 * batch * ceil(K / 255) bytes, K = floor((N - 1) / R) + 1 control
+ * intervals (N = seconds * sample_rate, R = sample_rate / control_rate); for
+ * 4 s at 44.1 kHz that allows batch
  * <= 779. Larger requests return SYNTH_ERR_ARG before any launch.
  * The first call on a device (with that device current) looks up the
  * array's device address; make that first call before any stream capture.

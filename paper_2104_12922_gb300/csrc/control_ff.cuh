@@ -171,7 +171,7 @@ __device__ __forceinline__ ff geo_sum_ff(ff c, ff x, int k, const FFTables& T) {
 // the phase advanced (cycles) and, in *inc_first, the increment of the
 // interval's first sample (cycles per sample, capped at 1/2). Sample j of the
 // interval has pitch m_a + (j / R)(m_b - m_a), capped at the Nyquist pitch.
-__device__ inline ff vco_interval_ff(ff m_a, ff m_b, int R, int Rk, ff inv_R, ff ln2_12R,
+__device__ inline ff vco_interval_ff(ff m_a, ff m_b, float R, int Rk, ff inv_R, ff ln2_12R,
                                      ff m_nyq, ff log2_440_over_sr, const FFTables& T,
                                      SegVco* out, float* inc_first) {
   const ff dm = ff_sub(m_b, m_a);
@@ -196,7 +196,7 @@ __device__ inline ff vco_interval_ff(ff m_a, ff m_b, int R, int Rk, ff inv_R, ff
   // one geometric piece: its first pitch m_g and length k_g.
   int jc = Rk;
   if (c_first != c_last) {
-    const float js = (m_nyq.hi - m_a.hi) * (float)R / dm.hi;
+    const float js = (m_nyq.hi - m_a.hi) * R / dm.hi;
     jc = (int)fminf(fmaxf(ceilf(js), 0.f), (float)(Rk - 1));
     if (!c_first) {  // rising: first capped sample
       while (jc > 0 && capped(jc - 1)) --jc;

@@ -47,7 +47,12 @@ struct __align__(16) Smem {
   FFTables T;
   union {
     ff env[6][P];            // the 6 ADSRs at the control points (steps 2-3)
-    SegVco seg[2][TI];       // VCO interval descriptions (steps 4-5)
+    struct {
+      SegVco seg[2][TI];     // VCO interval descriptions (steps 4-5)
+      int sst[P];            // fractional R: first sample of each interval (tile-relative),
+                             // sst[nseg] = the tile's sample count
+      float u0f[TI];         // fractional R: fraction of each interval's first sample
+    };
   };
   float4 sq[TI];             // square-saw constants per interval: k2, c1, c2 (square_saw_sc)
   float4 ampv[P];            // gain x amplitude at the control points: sine, square-saw (gain
@@ -127,6 +132,27 @@ __device__ __forceinline__ void block_scan2_f32(float& a, float& b, float (*buf)
   tot1 = tb;
 }
 
+// The tile's peak (a block maximum of the threads' largest |sample|),
+// published in its tile record behind a done flag once every thread's
+// stores are visible at device scope.
+__device__ __forceinline__ void publish_tile_peak(Smem& s, TileState* me, float vmax,
+                                                  unsigned int epoch) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  if ((tid & 31) == 0) s.warp_max[tid >> 5] = vmax;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    float m = s.warp_max[0];
+#pragma unroll
+    for (int i = 1; i < kWarps; ++i) m = fmaxf(m, s.warp_max[i]);
+    me->peak = __float_as_uint(m);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(me->done);
+    f.store(((epoch & 0x3fffffffu) << 2) | 3u, cuda::memory_order_release);
+  }
+}
+
 // One normalisation work item: chunk c (kNormChunkSamples samples) of voice
 // v. Waits, with a spin limit, for the done flags of the voice's render
 // tiles, takes the largest of their peaks, and scales the chunk by 1 / peak
@@ -195,7 +221,7 @@ __device__ __noinline__ void normalize_chunk(Smem& s, float* __restrict__ audio,
   }
 }
 
-template <bool kCarryF32, bool kPeak>
+template <bool kCarryF32, bool kPeak, bool kGenR>
 __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t first, int split, int batch,
     const float* __restrict__ params_in, float* __restrict__ audio, float* __restrict__ params_out,
@@ -353,17 +379,49 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
 
     // ---- 4. VCO phase over each control interval, scanned -----------------
     ff tot[2] = {ff_make(0.f), ff_make(0.f)};
+    // the tile's first sample: interval k starts at sample ceil(k a / b)
+    const int64_t s_tile =
+        kGenR ? ((int64_t)k0 * vc.rate_a + vc.rate_b - 1) / vc.rate_b : (int64_t)k0 * R;
     if (tid < nseg) {
-      const int64_t rem = N - (int64_t)(k0 + tid) * R;
-      const int Rk = rem < R ? (int)rem : R;
       float inc1 = 0.5f;
+      if constexpr (kGenR) {
+        const int64_t k = k0 + tid;
+        const int64_t sk = (k * vc.rate_a + vc.rate_b - 1) / vc.rate_b;
+        const int64_t sk1 = min(((k + 1) * vc.rate_a + vc.rate_b - 1) / vc.rate_b, N);
+        const int Rk = (int)(sk1 - sk);
+        // fraction of the way from point k to point k + 1: (s_k b - k a) / a
+        const ff u0 = ff_mul_f(vc.inv_a, (float)(sk * vc.rate_b - k * vc.rate_a));
+        s.sst[tid] = (int)(sk - s_tile);
+        s.u0f[tid] = ff_to_float(u0);
+        if (tid == nseg - 1) s.sst[nseg] = (int)(sk1 - s_tile);
+        // the pitch at the interval's first sample, and the end point that
+        // keeps the slope (m_(k+1) - m_k) / R per sample
 #pragma unroll 1
-      for (int o = 0; o < 2; ++o) {
-        float inc;
-        const ff t_o = vco_interval_ff(s.m[o][tid], s.m[o][tid + 1], R, Rk, vc.inv_R, vc.ln2_12R,
-                                       vc.m_nyq_ff, vc.log2_440_over_sr, s.T, &s.seg[o][tid], &inc);
-        if (o == 0) tot[0] = t_o; else { tot[1] = t_o; inc1 = inc; }
+        for (int o = 0; o < 2; ++o) {
+          const ff dm = ff_sub(s.m[o][tid + 1], s.m[o][tid]);
+          const ff mf = ff_add(s.m[o][tid], ff_mul(dm, u0));
+          float inc;
+          const ff t_o = vco_interval_ff(mf, ff_add(mf, dm), vc.r_f, Rk, vc.inv_R, vc.ln2_12R,
+                                         vc.m_nyq_ff, vc.log2_440_over_sr, s.T, &s.seg[o][tid],
+                                         &inc);
+          if (o == 0) tot[0] = t_o; else tot[1] = t_o;
+        }
+      } else {
+        const int64_t rem = N - (int64_t)(k0 + tid) * R;
+        const int Rk = rem < R ? (int)rem : R;
+#pragma unroll 1
+        for (int o = 0; o < 2; ++o) {
+          float inc;
+          const ff t_o = vco_interval_ff(s.m[o][tid], s.m[o][tid + 1], (float)R, Rk, vc.inv_R,
+                                         vc.ln2_12R, vc.m_nyq_ff, vc.log2_440_over_sr, s.T,
+                                         &s.seg[o][tid], &inc);
+          if (o == 0) tot[0] = t_o; else { tot[1] = t_o; inc1 = inc; }
+        }
       }
+      if constexpr (kGenR)  // kappa follows the (capped) frequency at the control point
+        inc1 = ff_gt(s.m[1][tid], vc.m_nyq_ff)
+                   ? 0.5f
+                   : ff_to_float(inc_at_ff(s.m[1][tid], vc.log2_440_over_sr, s.T));
       // square-saw drive from the (capped) frequency at the interval start:
       // kappa = 1 + SR / (8 f) = 1 + 1 / (8 inc), at most 50
       const float kap = fminf((float)kBrightnessMax, 1.f + 0.125f / inc1);
@@ -406,7 +464,73 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     __syncthreads();
 
     // ---- 5. audio ----------------------------------------------------------
-    {
+    if constexpr (kGenR) {
+      // fractional R: quads of the voice's own 4-sample grid, each sample in
+      // the interval whose start it has passed (a quad meets at most two
+      // intervals since R >= 4); the tile writes only its own samples
+      const int n_t = s.sst[nseg];
+      float* out_v = audio + (size_t)v * (size_t)N;
+      const int64_t q_lo = s_tile >> 2;
+      const int nq = (int)(((s_tile + n_t + 3) >> 2) - q_lo);
+      const float invRg = ff_to_float(vc.inv_R);
+      float vmax = 0.f;
+      for (int q = tid; q < nq; q += NT) {
+        const int64_t n0 = (q_lo + q) << 2;
+        const int rel0 = (int)(n0 - s_tile);  // -3 .. 0 on the first quad
+        const int r0 = max(rel0, 0);
+        int si = min((int)((float)r0 * invRg), nseg - 1);
+        while (si + 1 < nseg && s.sst[si + 1] <= r0) ++si;
+        while (si > 0 && s.sst[si] > r0) --si;
+        const int b1 = s.sst[si + 1];
+        const bool two = si + 1 < nseg && rel0 + 3 >= b1;
+        float psA[4], pqA[4], psB[4], pqB[4];
+        vco_quad<false>(s.seg[0][si], rel0 - s.sst[si], psA);
+        vco_quad<false>(s.seg[1][si], rel0 - s.sst[si], pqA);
+        if (two) {
+          vco_quad<false>(s.seg[0][si + 1], rel0 - b1, psB);
+          vco_quad<false>(s.seg[1][si + 1], rel0 - b1, pqB);
+        }
+        const uint4 nz = philox4x32_10(
+            make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(q_lo + q), kStreamNoise), key);
+        const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
+        float out4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int rel = rel0 + i;
+          const bool in_b = two && rel >= b1;
+          const int ii = in_b ? si + 1 : si;
+          const float ps = in_b ? psB[i] : psA[i], pq = in_b ? pqB[i] : pqA[i];
+          const float4 sq = s.sq[ii];
+          const float4 A = s.ampv[ii], Bn = s.ampv[ii + 1];
+          const float fj = fmaf((float)(rel - s.sst[ii]), invRg, s.u0f[ii]);
+          const float x_sin = __sinf(kTwoPiF * ps);
+          float sn, cs;
+          __sincosf(kTwoPiF * pq, &sn, &cs);
+          const float x_sq = square_saw_sc(sn, cs, sq.x, sq.y, sq.z);
+          const float x_nz = fmaf((float)(nw[i] >> 8), 0x1p-23f, -1.f);
+          out4[i] = fmaf(fmaf(fj, Bn.x - A.x, A.x), x_sin,
+                         fmaf(fmaf(fj, Bn.y - A.y, A.y), x_sq, fmaf(fj, Bn.z - A.z, A.z) * x_nz));
+        }
+        if (vec_ok && rel0 >= 0 && rel0 + 3 < n_t) {
+          if (kPeak) {
+            *reinterpret_cast<float4*>(out_v + n0) = make_float4(out4[0], out4[1], out4[2], out4[3]);
+            vmax = fmaxf(fmaxf(vmax, fmaxf(fabsf(out4[0]), fabsf(out4[1]))),
+                         fmaxf(fabsf(out4[2]), fabsf(out4[3])));
+          } else {
+            __stcs(reinterpret_cast<float4*>(out_v + n0),
+                   make_float4(out4[0], out4[1], out4[2], out4[3]));
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (rel0 + i >= 0 && rel0 + i < n_t) {
+              out_v[n0 + i] = out4[i];
+              if (kPeak) vmax = fmaxf(vmax, fabsf(out4[i]));
+            }
+        }
+      }
+      if (kPeak) publish_tile_peak(s, vt + w, vmax, epoch);
+    } else {
       const int64_t t0 = (int64_t)k0 * R;                     // first sample of the tile
       float* out_t = audio + (size_t)v * (size_t)N + (size_t)t0;
       const int n_t = (int)min((int64_t)nseg * R, N - t0);   // samples in the tile
@@ -466,24 +590,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
         jq += dq_j;
         if (jq >= qps) { jq -= qps; ++si; }
       }
-      if (kPeak) {
-        // the tile's peak (a block maximum), published with a flag once
-        // every thread's stores are visible at device scope
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        if ((tid & 31) == 0) s.warp_max[tid >> 5] = vmax;
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-          float m = s.warp_max[0];
-#pragma unroll
-          for (int i = 1; i < kWarps; ++i) m = fmaxf(m, s.warp_max[i]);
-          TileState* me = vt + w;
-          me->peak = __float_as_uint(m);
-          cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(me->done);
-          f.store(((epoch & 0x3fffffffu) << 2) | 3u, cuda::memory_order_release);
-        }
-      }
+      if (kPeak) publish_tile_peak(s, vt + w, vmax, epoch);
     }
   }
   persistent_finish(hdr);
@@ -493,7 +600,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
 
 int fused_max_active_blocks_per_sm() {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false, false>, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false, false, false>, NT, 0);
   return n;
 }
 
@@ -507,12 +614,15 @@ cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t fi
   const PeakNormArgs nz = norm ? *norm : PeakNormArgs{0.f, nullptr, nullptr};
 #define SYNTH_FUSED_ARGS vc, seed, first, split, batch, params_in, audio, params_out, hdr, tiles, \
                          n_windows, nz
-  if (vc.carry_fp32) {
-    if (norm) render_fused_kernel<true, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
-    else render_fused_kernel<true, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+  if (vc.general_r) {  // fractional R (never with FP32 carries)
+    if (norm) render_fused_kernel<false, true, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    else render_fused_kernel<false, false, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+  } else if (vc.carry_fp32) {
+    if (norm) render_fused_kernel<true, true, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    else render_fused_kernel<true, false, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
   } else {
-    if (norm) render_fused_kernel<false, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
-    else render_fused_kernel<false, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    if (norm) render_fused_kernel<false, true, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    else render_fused_kernel<false, false, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
   }
 #undef SYNTH_FUSED_ARGS
   return cudaGetLastError();

@@ -60,14 +60,8 @@ synth_status voice_const_from_config(const synth_config* cfg, VoiceConst* vc) {
   const double sr = cfg->sample_rate, cr = cfg->control_rate;
   if (!(sr > 0.0) || !(cr > 0.0) || !(cfg->seconds > 0.0)) return SYNTH_ERR_ARG;
   if (cfg->carry != SYNTH_CARRY_FIXED64 && cfg->carry != SYNTH_CARRY_FP32) return SYNTH_ERR_ARG;
-  const double r = sr / cr;
-  const long long R = std::llround(r);
-  const double n = cfg->seconds * sr;
-  const long long N = std::llround(n);
-  // R < 2^16: an interval description keeps its in-interval sample index in 16 bits
-  if (R < 4 || R > 65532 || std::fabs(r - (double)R) > 1e-9 || (R & 3) != 0)
-    return SYNTH_ERR_UNSUPPORTED;
-  if (std::fabs(n - (double)N) > 1e-6 || N < 1 || N > (1LL << 31)) return SYNTH_ERR_UNSUPPORTED;
+  if (!voice_geometry(*vc, sr, cr, cfg->seconds)) return SYNTH_ERR_UNSUPPORTED;
+  if (vc->general_r && cfg->carry == SYNTH_CARRY_FP32) return SYNTH_ERR_UNSUPPORTED;
   synth_nebula nb;
   if (cfg->nebula) nb = *cfg->nebula;
   else synth_default_nebula(&nb);
@@ -81,9 +75,6 @@ synth_status voice_const_from_config(const synth_config* cfg, VoiceConst* vc) {
   vc->sample_rate = sr;
   vc->control_rate = cr;
   vc->m_nyq = 69.0 + 12.0 * std::log2(0.5 * sr / 440.0);
-  vc->n_samples = N;
-  vc->R = (int32_t)R;
-  vc->K = (int32_t)((N + R - 1) / R);
   vc->carry_fp32 = cfg->carry == SYNTH_CARRY_FP32 ? 1 : 0;
   voice_const_derive(*vc);
   return SYNTH_OK;

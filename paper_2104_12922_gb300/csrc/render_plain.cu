@@ -191,7 +191,7 @@ __global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const
     const ff mb = ff_add(V.pitch_base[o], ff_mul(V.depth[o], pd[k + 1]));
     float inc_first;
     seg_sum[((size_t)v * 2 + o) * K + k] = ff_to_double(
-        vco_interval_ff(ma, mb, vc.R, Rk, vc.inv_R, vc.ln2_12R, vc.m_nyq_ff, vc.log2_440_over_sr, T,
+        vco_interval_ff(ma, mb, (float)vc.R, Rk, vc.inv_R, vc.ln2_12R, vc.m_nyq_ff, vc.log2_440_over_sr, T,
                         &seg[((size_t)v * 2 + o) * K + k], &inc_first));
     if (o == 1) {  // drive 1 + SR / (8 f) at the (capped) frequency of the interval start
       const float kap = fminf((float)kBrightnessMax, 1.f + 0.125f / inc_first);

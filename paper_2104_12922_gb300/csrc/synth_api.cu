@@ -110,14 +110,9 @@ synth_status synth_create(const synth_config* cfg, synth_handle* out) {
   if (!(sr > 0.0) || !(cr > 0.0) || !(cfg->seconds > 0.0) || cfg->max_batch < 1)
     return SYNTH_ERR_ARG;
   if (cfg->carry != SYNTH_CARRY_FIXED64 && cfg->carry != SYNTH_CARRY_FP32) return SYNTH_ERR_ARG;
-  const double r = sr / cr;
-  const long long R = std::llround(r);
-  const double n = cfg->seconds * sr;
-  const long long N = std::llround(n);
-  // R < 2^16: an interval description keeps its in-interval sample index in 16 bits
-  if (R < 4 || R > 65532 || std::fabs(r - (double)R) > 1e-9 || (R & 3) != 0)
-    return SYNTH_ERR_UNSUPPORTED;
-  if (std::fabs(n - (double)N) > 1e-6 || N < 1 || N > (1LL << 31)) return SYNTH_ERR_UNSUPPORTED;
+  VoiceConst geo{};
+  if (!voice_geometry(geo, sr, cr, cfg->seconds)) return SYNTH_ERR_UNSUPPORTED;
+  if (geo.general_r && cfg->carry == SYNTH_CARRY_FP32) return SYNTH_ERR_UNSUPPORTED;
   synth_handle h = new (std::nothrow) synth_handle_s();
   if (!h) return SYNTH_ERR_OOM;
   h->cfg = *cfg;
@@ -134,9 +129,12 @@ synth_status synth_create(const synth_config* cfg, synth_handle* out) {
   h->vc.sample_rate = sr;
   h->vc.control_rate = cr;
   h->vc.m_nyq = 69.0 + 12.0 * std::log2(0.5 * sr / 440.0);
-  h->vc.n_samples = N;
-  h->vc.R = (int32_t)R;
-  h->vc.K = (int32_t)((N + R - 1) / R);
+  h->vc.n_samples = geo.n_samples;
+  h->vc.rate_a = geo.rate_a;
+  h->vc.rate_b = geo.rate_b;
+  h->vc.general_r = geo.general_r;
+  h->vc.R = geo.R;
+  h->vc.K = geo.K;
   h->vc.carry_fp32 = cfg->carry == SYNTH_CARRY_FP32 ? 1 : 0;
   voice_const_derive(h->vc);
   if (cudaGetDevice(&h->device) != cudaSuccess ||
@@ -208,6 +206,7 @@ synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t bat
 synth_status synth_render_plain_workspace_size(synth_handle h, int32_t batch, size_t* bytes) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
   if (!bytes || batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (h->vc.general_r) return SYNTH_ERR_UNSUPPORTED;
   *bytes = plain_workspace_bytes(h->vc, batch);
   return SYNTH_OK;
 }
@@ -217,6 +216,7 @@ synth_status synth_render_plain(synth_handle h, uint64_t seed, uint64_t batch_in
                                 void* workspace_dev, size_t workspace_bytes, void* stream) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
   if (batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (h->vc.general_r) return SYNTH_ERR_UNSUPPORTED;
   if (batch == 0) return SYNTH_OK;
   if (!audio_dev || !workspace_dev) return SYNTH_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return SYNTH_ERR_ARG;
@@ -231,6 +231,7 @@ synth_status synth_render_plain(synth_handle h, uint64_t seed, uint64_t batch_in
 synth_status synth_render_backward_workspace_size(synth_handle h, int32_t batch, size_t* bytes) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
   if (!bytes || batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (h->vc.general_r) return SYNTH_ERR_UNSUPPORTED;
   *bytes = backward_workspace_bytes(h->vc, batch);
   return SYNTH_OK;
 }
@@ -241,6 +242,7 @@ synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch
                                    void* workspace_dev, size_t workspace_bytes, void* stream) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
   if (batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (h->vc.general_r) return SYNTH_ERR_UNSUPPORTED;
   if (batch == 0) return SYNTH_OK;
   if (!params_dev || !grad_audio_dev || !grad_params_dev || !workspace_dev) return SYNTH_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return SYNTH_ERR_ARG;

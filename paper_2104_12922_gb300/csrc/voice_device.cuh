@@ -11,6 +11,8 @@
 // module is stated at its function below.
 #pragma once
 
+#include <cmath>
+
 #include <cstdint>
 
 #include "ff.cuh"
@@ -48,20 +50,68 @@ struct VoiceConst {
   double sample_rate, control_rate;
   double m_nyq;      // Nyquist pitch in midi, 69 + 12 log2(SR / 2 / 440)
   int64_t n_samples; // N
-  int32_t R;         // samples per control interval (multiple of 4)
-  int32_t K;         // control intervals, ceil(N / R)
+  int32_t R;         // samples per control interval (general_r: ceil(a / b))
+  int32_t K;         // control intervals holding samples, floor((N - 1) b / a) + 1
   int32_t carry_fp32;
   // Sec. 3.3 map as y = map_base + map_scale a^curve (range_map_ff)
   ff map_base[kNumParams], map_scale[kNumParams], map_curve[kNumParams];
   int32_t map_code[kNumParams];  // 1, 2, 3 for those integer curves, else 0
   ff inv_cr;            // 1 / control rate
-  ff inv_R;             // 1 / R
+  ff inv_R;             // 1 / R = b / a
   ff ln2_12R;           // ln 2 / (12 R)
+  ff inv_a;             // 1 / a
+  float r_f;            // R
   ff m_nyq_ff;          // m_nyq
   ff log2_440_over_sr;  // log2(440 / SR)
   ff inv_2pi;           // 1 / (2 pi)
   alignas(16) FFTables T;
+  // Samples per control interval R = SR / CR = rate_a / rate_b in lowest
+  // terms: an integer R, or, for a fractional R, integer rates in Hz. Sample n
+  // lies in interval k = floor(n b / a) at the fraction (n b - k a) / a; the
+  // interval starts at sample ceil(k a / b).
+  int64_t rate_a, rate_b;
+  int32_t general_r; // 0: R is an integer multiple of 4 (quads align with intervals)
 };
+
+// The render geometry of sample rate sr, control rate cr and duration
+// `seconds` (host): n_samples, rate_a / rate_b, general_r, R and K. Returns
+// false for what the renders do not support: N not an integer or >= 2^31, a
+// fractional R from rates that are not integers in Hz, R < 4 (a 4-sample
+// quad then spans at most two intervals), or R > 65532 (an interval's sample
+// index fits 16 bits).
+inline bool voice_geometry(VoiceConst& vc, double sr, double cr, double seconds) {
+  const double n = seconds * sr;
+  const long long N = std::llround(n);
+  if (std::fabs(n - (double)N) > 1e-6 || N < 1 || N > (1LL << 31)) return false;
+  const double r = sr / cr;
+  const long long ri = std::llround(r);
+  long long a, b;
+  if (ri >= 1 && std::fabs(r - (double)ri) <= 1e-9) {
+    a = ri;
+    b = 1;
+  } else {
+    const long long si = std::llround(sr), ci = std::llround(cr);
+    if (std::fabs(sr - (double)si) > 1e-9 || std::fabs(cr - (double)ci) > 1e-9) return false;
+    long long x = si, y = ci;
+    while (y != 0) {
+      const long long t = x % y;
+      x = y;
+      y = t;
+    }
+    a = si / x;
+    b = ci / x;
+  }
+  if (a < 4 * b || a > 65532 * b || a >= (1LL << 31) || b >= (1LL << 31)) return false;
+  vc.n_samples = N;
+  vc.rate_a = a;
+  vc.rate_b = b;
+  vc.general_r = (b != 1 || (a & 3) != 0) ? 1 : 0;
+  vc.R = (int32_t)((a + b - 1) / b);
+  const long long K = (N - 1) * b / a + 1;
+  if (K >= (1LL << 31)) return false;
+  vc.K = (int32_t)K;
+  return true;
+}
 
 // Fills the derived fields of vc from its FP64 fields (host).
 inline void voice_const_derive(VoiceConst& vc) {
@@ -75,8 +125,10 @@ inline void voice_const_derive(VoiceConst& vc) {
     vc.map_code[p] = c == 1.0 ? 1 : (c == 2.0 ? 2 : (c == 3.0 ? 3 : 0));
   }
   vc.inv_cr = ff_from_double(1.0 / vc.control_rate);
-  vc.inv_R = ff_from_double(1.0 / (double)vc.R);
-  vc.ln2_12R = ff_from_double(0.69314718055994530942 / (12.0 * (double)vc.R));
+  vc.inv_R = ff_from_double((double)vc.rate_b / (double)vc.rate_a);
+  vc.ln2_12R = ff_from_double(0.69314718055994530942 * (double)vc.rate_b / (12.0 * (double)vc.rate_a));
+  vc.inv_a = ff_from_double(1.0 / (double)vc.rate_a);
+  vc.r_f = (float)((double)vc.rate_a / (double)vc.rate_b);
   vc.m_nyq_ff = ff_from_double(vc.m_nyq);
   vc.log2_440_over_sr = ff_from_double(log2(440.0 / vc.sample_rate));
   vc.inv_2pi = ff_from_double(0.15915494309189533577);

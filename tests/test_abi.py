@@ -60,7 +60,13 @@ def test_create_rejects_bad_config_without_device(pkg):
         setattr(c, field, bad)
         assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_ARG
     c = pkg.synth_default_config()
-    c.control_rate = 441.0 * 100 / 98  # R = 98 is not a multiple of 4
+    c.control_rate = 441.3  # fractional R from a control rate that is not an integer in Hz
+    assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_UNSUPPORTED
+    c = pkg.synth_default_config()
+    c.control_rate = 44100.0 / 3  # R = 3 < 4
+    assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_UNSUPPORTED
+    c = pkg.synth_default_config()
+    c.sample_rate, c.carry = 16000.0, pkg.SYNTH_CARRY_FP32  # FP32 carries need integer R % 4 == 0
     assert L.synth_create(ctypes.byref(c), ctypes.byref(h)) == pkg.SYNTH_ERR_UNSUPPORTED
     c = pkg.synth_default_config()
     c.control_rate = 44100.0 / 65536  # R = 2^16: above the 16-bit in-interval index
