@@ -27,6 +27,24 @@ struct SegVco {
   int jc_flags;  // jc | (A linear) << 16 | (B linear) << 17 | (A capped) << 18 | (B capped) << 19
 };
 
+// expm1(z) for the in-interval phase of a geometric piece, z = d x (d samples
+// into the piece, x the log of the per-sample increment ratio). |z| < 1/4
+// covers nearly every quad: the Taylor series to z^7, whose remainder is
+// below z^7 / 8! < 2e-9 relative there, in Horner form; larger |z| (steep
+// pitch sweeps) takes the library expm1f.
+__device__ __forceinline__ float expm1_phase(float z) {
+  if (fabsf(z) < 0.25f) {
+    float p = fmaf(z, 1.f / 5040.f, 1.f / 720.f);
+    p = fmaf(z, p, 1.f / 120.f);
+    p = fmaf(z, p, 1.f / 24.f);
+    p = fmaf(z, p, 1.f / 6.f);
+    p = fmaf(z, p, 0.5f);
+    p = fmaf(z, p, 1.f);
+    return z * p;
+  }
+  return expm1f(z);
+}
+
 // Per-sample phase increments (cycles/sample) of samples j0..j0+3 and whether
 // each sample's pitch is capped at Nyquist (used by the adjoint).
 __device__ __forceinline__ void vco_inc_quad(const SegVco& s, int j0, float inc[4], bool capped[4]) {
@@ -69,7 +87,7 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
       g = c;
       e1 = 1.f; e2 = 2.f; e3 = 3.f;
     } else {
-      const float E0 = expm1f((float)d0 * s.x);
+      const float E0 = expm1_phase((float)d0 * s.x);
       const float cE = c * s.invE;
       base = s.phase0 + fmaf(cE, E0, L);
       g = fmaf(cE, E0, cE);
@@ -92,7 +110,7 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
       const float c = in_b ? s.cB : s.cA;
       const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
       const int d = j - (in_b ? jc : 0);
-      const float loc = lin ? fmaf(c, (float)d, L) : fmaf(c * s.invE, expm1f((float)d * s.x), L);
+      const float loc = lin ? fmaf(c, (float)d, L) : fmaf(c * s.invE, expm1_phase((float)d * s.x), L);
       const float p = s.phase0 + loc;
       ph[i] = p - rintf(p);
     }
