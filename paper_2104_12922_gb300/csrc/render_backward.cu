@@ -135,11 +135,12 @@ __global__ void __launch_bounds__(kBT) bwd_samples(const __grid_constant__ Voice
       float A[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) A[c] = fmaf(fj, a1[c] - a0[c], a0[c]);
+      // SFU sine, cosine and tanh, as in the forward render
       float xs, xc;
-      sincosf(kTwoPiF * ps[i], &xs, &xc);
+      __sincosf(kTwoPiF * ps[i], &xs, &xc);
       float sn, cs;
-      sincosf(kTwoPiF * pq[i], &sn, &cs);
-      const float th = tanhf(kap * sn);
+      __sincosf(kTwoPiF * pq[i], &sn, &cs);
+      const float th = tanh_from_y(kTwoLog2e * kap * sn);
       const float shp = fmaf(sigma, cs, 1.f);
       const float xq = th * itk * shp * ip;
       const float xn = fmaf(2.f, u01f(nw[i]), -1.f);

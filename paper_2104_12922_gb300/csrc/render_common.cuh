@@ -57,7 +57,7 @@ __device__ __forceinline__ void vco_inc_quad(const SegVco& s, int j0, float inc[
     const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
     capped[i] = (s.jc_flags >> (in_b ? 19 : 18)) & 1;
     const int d = j - (in_b ? jc : 0);
-    inc[i] = lin ? c : c * (1.f + expm1f((float)d * s.x));
+    inc[i] = lin ? c : c * (1.f + expm1_phase((float)d * s.x));
   }
 }
 
