@@ -85,6 +85,12 @@ def lib():
         L.oracle_render_vjp.argtypes = [P(Config), P(d), u64, u64, P(d), P(d), i32]
         L.oracle_render_vjp.restype = i32
         L.oracle_hardware_threads.restype = i32
+        L.oracle_fm_draw_params.argtypes = [u64, u64, P(d)]
+        L.oracle_fm_render_voice.argtypes = [P(Config), P(d), P(d)]
+        L.oracle_fm_render_voice.restype = i32
+        L.oracle_fm_render_batch.argtypes = [P(Config), u64, u64, i32, P(d), P(ctypes.c_float),
+                                             P(ctypes.c_float), i32]
+        L.oracle_fm_render_batch.restype = i32
         _lib = L
     return _lib
 
@@ -212,6 +218,42 @@ def render_voice(cfg: Config, u, seed: int, g: int, flags: int = 0) -> np.ndarra
     if rc != 0:
         raise ValueError("oracle_render_voice: configuration not representable")
     return out
+
+
+FM_NUM_PARAMS = 30
+
+
+def fm_draw_params(seed: int, g: int) -> np.ndarray:
+    u = np.zeros(FM_NUM_PARAMS)
+    lib().oracle_fm_draw_params(seed, g, _p(u, ctypes.c_double))
+    return u
+
+
+def fm_render_voice(cfg: Config, u) -> np.ndarray:
+    """4-operator FM voice (the library's reading, see oracle.h), FP64."""
+    out = np.zeros(num_samples(cfg))
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    if lib().oracle_fm_render_voice(ctypes.byref(cfg), _p(u, ctypes.c_double),
+                                    _p(out, ctypes.c_double)) != 0:
+        raise ValueError("oracle_fm_render_voice: configuration not representable")
+    return out
+
+
+def fm_render_batch(cfg: Config, seed: int, batch_index: int, batch: int, u_in=None,
+                    threads: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """FM audio [batch][N] float32 and normalized params [batch][30] float32."""
+    N = num_samples(cfg)
+    audio = np.zeros((batch, N), dtype=np.float32)
+    params = np.zeros((batch, FM_NUM_PARAMS), dtype=np.float32)
+    up = None
+    if u_in is not None:
+        u_in = np.ascontiguousarray(u_in, dtype=np.float64).reshape(batch, FM_NUM_PARAMS)
+        up = _p(u_in, ctypes.c_double)
+    if lib().oracle_fm_render_batch(ctypes.byref(cfg), seed, batch_index, batch, up,
+                                    _p(audio, ctypes.c_float), _p(params, ctypes.c_float),
+                                    threads) != 0:
+        raise ValueError("oracle_fm_render_batch failed")
+    return audio, params
 
 
 def vco_phase(cfg: Config, u, vco: int) -> np.ndarray:

@@ -23,6 +23,7 @@ extern "C" {
 #endif
 
 #define ORACLE_NUM_PARAMS 78
+#define ORACLE_FM_NUM_PARAMS 30
 
 /* Range-map hyper-parameters of one nebula (Sec. 3.3): per parameter the
  * human range [lo, hi], the curve exponent and the symmetric flag. */
@@ -108,6 +109,18 @@ int32_t oracle_render_vjp(const oracle_config* cfg, const double u[ORACLE_NUM_PA
                           int32_t threads);
 
 int32_t oracle_hardware_threads(void);
+
+/* 4-operator FM voice (the library's reading of the FM architecture that
+ * Sec. 3.2 names as in development; the formulas are in voice.cpp):
+ * 30 normalized parameters, drawn from Philox stream 2; serial phase
+ * modulation op3 -> op2 -> op1 -> op0, each operator a sine at f0 x ratio
+ * with its own ADSR. cfg: rates and length (its nebula is not used). */
+void oracle_fm_draw_params(uint64_t seed, uint64_t g, double u[ORACLE_FM_NUM_PARAMS]);
+int32_t oracle_fm_render_voice(const oracle_config* cfg, const double u[ORACLE_FM_NUM_PARAMS],
+                               double* out);
+int32_t oracle_fm_render_batch(const oracle_config* cfg, uint64_t seed, uint64_t batch_index,
+                               int32_t batch, const double* u_in, float* audio, float* params_out,
+                               int32_t threads);
 
 #ifdef __cplusplus
 }

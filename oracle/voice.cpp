@@ -461,6 +461,100 @@ void parallel_for(int64_t n, int threads, F fn) {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// 4-operator FM voice. Sec. 3.2 names a 4-operator frequency-modulation
+// architecture (after Chowning 1973) as in development and gives nothing
+// more; everything below is the library's reading:
+//  * 30 parameters, normalized u in [0,1] mapped by y = lo + (hi - lo) u^c:
+//    midi f0 [0, 127]; note-on duration [0, 4] s; then for operator i = 0..3
+//    (0 the carrier) at 2 + 7 i: frequency ratio [0.5, 8] (c = 2); level,
+//    the carrier's amplitude [0, 1] or a modulator's index in radians
+//    [0, 8] (c = 2); the Voice's ADSR: attack [0, 2] s, decay [0, 2] s
+//    (c = 2), sustain [0, 1], release [0, 5] s (c = 2), alpha [0.1, 6]
+//    (c = 2), gated by the note-on duration.
+//  * drawn from Philox4x32-10 stream 2: counter (g lo, g hi, block, 2), key
+//    (seed lo, seed hi), 4 words per block, u = u01(word).
+//  * envelopes E_i at the control points t_k = k / CR, upsampled linearly
+//    as the Voice's control signals;
+//  * operator phase phi_i(n) = frac(n f0 ratio_i / SR) (phase 0 at n = 0,
+//    constant pitch);
+//  * serial stack op 3 -> op 2 -> op 1 -> op 0 (phase modulation):
+//    y_4 = 0, y_i(n) = level_i E_i(n) sin(2 pi phi_i(n) + y_(i+1)(n)),
+//    out(n) = y_0(n).
+// ---------------------------------------------------------------------------
+constexpr int kFmNP = 30;
+constexpr uint32_t kStreamFmParam = 2;
+
+struct FmRange {
+  double lo, hi, curve;
+};
+
+FmRange fm_range(int p) {
+  if (p == 0) return {0.0, 127.0, 1.0};
+  if (p == 1) return {0.0, 4.0, 1.0};
+  const int i = (p - 2) / 7, q = (p - 2) % 7;
+  switch (q) {
+    case 0: return {0.5, 8.0, 2.0};
+    case 1: return i == 0 ? FmRange{0.0, 1.0, 1.0} : FmRange{0.0, 8.0, 2.0};
+    case 2: return {0.0, 2.0, 2.0};
+    case 3: return {0.0, 2.0, 2.0};
+    case 4: return {0.0, 1.0, 1.0};
+    case 5: return {0.0, 5.0, 2.0};
+    default: return {0.1, 6.0, 2.0};
+  }
+}
+
+// frac(n x) with the product's rounding error carried (fma), so that the
+// phase stays exact to ~1e-16 cycles at any n
+double frac_prod(int64_t n, double x) {
+  const double nd = (double)n;
+  const double p = nd * x;
+  const double e = std::fma(nd, x, -p);
+  const double f = (p - std::floor(p)) + e;
+  return f - std::floor(f);
+}
+
+int fm_render_voice(const oracle_config* cfg, const double* u_in, double* out) {
+  Geometry geo;
+  if (!geometry(cfg, &geo)) return -1;
+  const double two_pi = 6.28318530717958647692;
+  double y[kFmNP];
+  for (int p = 0; p < kFmNP; ++p) {
+    double u = u_in[p];
+    if (u < 0.0) u = 0.0;
+    if (u > 1.0) u = 1.0;
+    const FmRange r = fm_range(p);
+    y[p] = range_map<double>(u, r.lo, r.hi, r.curve, 0);
+  }
+  const double f0 = midi_to_hz<double>(y[0]), d = y[1];
+  const int64_t P = geo.K + 1;
+  std::vector<double> env[4];
+  double inc[4], level[4];
+  for (int i = 0; i < 4; ++i) {
+    const double* o = y + 2 + 7 * i;
+    inc[i] = f0 * o[0] / cfg->sample_rate;
+    level[i] = o[1];
+    env[i].resize(P);
+    for (int64_t k = 0; k < P; ++k)
+      env[i][k] = adsr<double>((double)k / cfg->control_rate, o[2], o[3], o[4], o[5], o[6], d);
+  }
+  for (int64_t n = 0; n < geo.N; ++n) {
+    const int64_t k = n * geo.B / geo.A;
+    const double u = (double)(n * geo.B - k * geo.A) / (double)geo.A;
+    double yv = 0.0;
+    for (int i = 3; i >= 0; --i) {
+      const double e = env[i][k] + u * (env[i][k + 1] - env[i][k]);
+      yv = level[i] * e * std::sin(two_pi * frac_prod(n, inc[i]) + yv);
+    }
+    out[n] = yv;
+  }
+  return 0;
+}
+
+}  // namespace
+
 extern "C" {
 
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
@@ -608,6 +702,43 @@ int32_t oracle_render_vjp(const oracle_config* cfg, const double u[ORACLE_NUM_PA
     double acc = 0.0;
     for (int64_t n = 0; n < geo.N; ++n) acc += w[n] * out[n].d;
     grad[p] = acc;
+  });
+  return failed ? -1 : 0;
+}
+
+void oracle_fm_draw_params(uint64_t seed, uint64_t g, double u[ORACLE_FM_NUM_PARAMS]) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int b = 0; 4 * b < kFmNP; ++b) {
+    const uint32_t ctr[4] = {(uint32_t)g, (uint32_t)(g >> 32), (uint32_t)b, kStreamFmParam};
+    uint32_t w[4];
+    philox(ctr, key, w);
+    for (int l = 0; l < 4; ++l)
+      if (4 * b + l < kFmNP) u[4 * b + l] = u01(w[l]);
+  }
+}
+
+int32_t oracle_fm_render_voice(const oracle_config* cfg, const double u[ORACLE_FM_NUM_PARAMS],
+                               double* out) {
+  return fm_render_voice(cfg, u, out);
+}
+
+int32_t oracle_fm_render_batch(const oracle_config* cfg, uint64_t seed, uint64_t batch_index,
+                               int32_t batch, const double* u_in, float* audio, float* params_out,
+                               int32_t threads) {
+  Geometry geo;
+  if (!geometry(cfg, &geo) || batch < 0) return -1;
+  std::atomic<int> failed(0);
+  parallel_for(batch, threads, [&](int64_t v) {
+    const uint64_t g = batch_index * (uint64_t)batch + (uint64_t)v;
+    double u[kFmNP];
+    if (u_in) std::memcpy(u, u_in + v * kFmNP, sizeof(u));
+    else oracle_fm_draw_params(seed, g, u);
+    if (params_out)
+      for (int p = 0; p < kFmNP; ++p) params_out[v * kFmNP + p] = (float)u[p];
+    std::vector<double> buf(geo.N);
+    if (fm_render_voice(cfg, u, buf.data()) != 0) { failed = 1; return; }
+    if (audio)
+      for (int64_t n = 0; n < geo.N; ++n) audio[v * geo.N + n] = (float)buf[n];
   });
   return failed ? -1 : 0;
 }

@@ -458,3 +458,74 @@ def test_peak_normalize_pins(oracle_mod):
     # a voice below the threshold is returned unchanged
     out_q, _, sil_q = oracle_mod.peak_normalize(x[3:] * 0.5, 1e-3)
     assert sil_q[0] and np.array_equal(out_q[0], (x[3] * 0.5).astype(np.float64))
+
+
+# ---- 4-operator FM voice -----------------------------------------------------
+def _fm_u(midi, ops, duration=4.0):
+    """Normalized FM parameters from human values: ops[i] = (ratio, level,
+    attack, decay, sustain, release, alpha), inverted through y = lo +
+    (hi - lo) u^c with the FM ranges."""
+    def inv(y, lo, hi, c):
+        return ((y - lo) / (hi - lo)) ** (1.0 / c)
+    u = [inv(midi, 0.0, 127.0, 1.0), inv(duration, 0.0, 4.0, 1.0)]
+    for i, (ratio, level, a, dc, s, r, alpha) in enumerate(ops):
+        u += [inv(ratio, 0.5, 8.0, 2.0),
+              inv(level, 0.0, 1.0, 1.0) if i == 0 else inv(level, 0.0, 8.0, 2.0),
+              inv(a, 0.0, 2.0, 2.0), inv(dc, 0.0, 2.0, 2.0), inv(s, 0.0, 1.0, 1.0),
+              inv(r, 0.0, 5.0, 2.0), inv(alpha, 0.1, 6.0, 2.0)]
+    return np.array(u)
+
+
+def _fm_y(u, p):
+    """The mapped value of parameter p (same map, for closed forms)."""
+    lo, hi, c = ((0.0, 127.0, 1.0) if p == 0 else (0.0, 4.0, 1.0) if p == 1 else
+                 [(0.5, 8.0, 2.0), (0.0, 1.0, 1.0) if (p - 2) // 7 == 0 else (0.0, 8.0, 2.0),
+                  (0.0, 2.0, 2.0), (0.0, 2.0, 2.0), (0.0, 1.0, 1.0), (0.0, 5.0, 2.0),
+                  (0.1, 6.0, 2.0)][(p - 2) % 7])
+    return lo + (hi - lo) * u[p] ** c
+
+
+FLAT = (0.0, 0.0, 1.0, 0.0, 1.0)  # attack, decay, sustain, release, alpha: E = 1 while held
+
+
+def test_fm_two_operators_match_jacobi_anger(oracle_mod):
+    """Carrier at f0, one modulator at 2 f0 with index b, flat envelopes:
+    sin(2 pi fc t + b sin(2 pi fm t)) = sum_k J_k(b) sin(2 pi (fc + k fm) t)
+    (Jacobi-Anger; Chowning 1973). Pins the phase-modulation structure."""
+    special = pytest.importorskip("scipy.special")
+    cfg = oracle_mod.default_config(seconds=0.25)
+    for b in (0.5, 2.0, 5.0):
+        u = _fm_u(57.0, [(1.0, 1.0) + FLAT, (2.0, b) + FLAT, (1.0, 0.0) + FLAT, (1.0, 0.0) + FLAT])
+        out = oracle_mod.fm_render_voice(cfg, u)
+        f0 = 440.0 * 2 ** ((_fm_y(u, 0) - 69.0) / 12.0)
+        fc, fm, idx = f0 * _fm_y(u, 2), f0 * _fm_y(u, 9), _fm_y(u, 10)
+        t = np.arange(len(out)) / 44100.0
+        want = sum(special.jv(k, idx) * np.sin(2 * math.pi * (fc + k * fm) * t)
+                   for k in range(-30, 31))
+        assert np.max(np.abs(out - want)) < 1e-9, b
+
+
+def test_fm_carrier_alone_and_chain_order(oracle_mod):
+    """Modulator levels 0 give the carrier's sine; a zero-level op1 cuts
+    op2 and op3 off from the carrier (modulation flows only down the
+    serial chain); the carrier's attack ramp scales it linearly."""
+    cfg = oracle_mod.default_config(seconds=0.5)
+    base = [(3.0, 0.75) + FLAT, (1.0, 0.0) + FLAT, (1.5, 7.0) + FLAT, (4.0, 6.0) + FLAT]
+    out = oracle_mod.fm_render_voice(cfg, _fm_u(60.0, base))
+    u = _fm_u(60.0, base)
+    f = 440.0 * 2 ** ((_fm_y(u, 0) - 69.0) / 12.0) * _fm_y(u, 2)
+    n = np.arange(len(out))
+    assert np.max(np.abs(out - _fm_y(u, 3) * np.sin(2 * math.pi * np.mod(f * n / 44100.0, 1.0)))) < 1e-9
+    ramp = [(3.0, 0.75, 1.0, 0.0, 1.0, 0.0, 1.0)] + base[1:]  # a 1 s attack: no kink in 0.5 s
+    u2 = _fm_u(60.0, ramp)
+    out2 = oracle_mod.fm_render_voice(cfg, u2)
+    a = _fm_y(u2, 4)
+    env = np.minimum(n / 44100.0 / a, 1.0)
+    assert np.max(np.abs(out2 - env * _fm_y(u2, 3) * np.sin(2 * math.pi * np.mod(f * n / 44100.0, 1.0)))) < 1e-9
+
+
+def test_fm_param_draw_stream(oracle_mod):
+    """FM parameters are Philox stream 2 words: u = (w >> 8) / 2^24."""
+    u = oracle_mod.fm_draw_params(7, 123)
+    words = np.concatenate([oracle_mod.philox4x32_10([123, 0, b, 2], [7, 0]) for b in range(8)])
+    assert np.array_equal(u, (words[:30] >> 8) / 2.0 ** 24)
