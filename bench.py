@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-normalized", action="store_true")
     ap.add_argument("--no-generator", action="store_true")
     ap.add_argument("--no-rates", action="store_true")
+    ap.add_argument("--no-fm", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -257,6 +258,38 @@ def rates_leg(pkg, torch, stream, steps: int = 64):
     syn.close()
     return {"value": B * n / (ms / 1e3) / 1e6, "unit": "MHz", "ms_per_step": ms, "steps": steps,
             "config": "batch 128 x 4 s at 16 kHz, control rate 441 Hz (R = 16000/441)"}
+
+
+def fm_leg(pkg, torch, syn, stream, steps: int = 64):
+    """The 4-operator FM voice at the bench workload (batch 128 x 4 s,
+    44.1 kHz), outputs rotated over 4 buffers; CUDA events around `steps`
+    renders captured in a graph."""
+    B, n = BATCH, N_SAMPLES
+    outs = [torch.empty((B, n), dtype=torch.float32, device=syn.device) for _ in range(4)]
+    pout = torch.empty((B, 30), dtype=torch.float32, device=syn.device)
+
+    def record(k):
+        for s in range(k):
+            syn.fm_render(s, s, B, out=outs[s % 4], params_out=pout, stream=stream)
+    with torch.cuda.stream(stream):
+        record(3)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        record(steps)
+    with torch.cuda.stream(stream):
+        g.replay()
+    stream.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        g.replay()
+        end.record(stream)
+    end.synchronize()
+    ms = start.elapsed_time(end) / steps
+    del g
+    return {"value": B * n / (ms / 1e3) / 1e6, "unit": "MHz", "ms_per_step": ms, "steps": steps,
+            "config": "4-operator FM voice, batch 128 x 4 s at 44.1 kHz"}
 
 
 def generator_leg(pkg, torch, syn, stream, count: int = 8192):
@@ -520,6 +553,7 @@ def run_ours(args):
     adjoint = None if args.no_adjoint else adjoint_leg(pkg, torch, dev)
     generator = None if args.no_generator else generator_leg(pkg, torch, syn, stream)
     rates = None if args.no_rates else rates_leg(pkg, torch, stream)
+    fm = None if args.no_fm else fm_leg(pkg, torch, syn, stream)
     line = {"metric": METRIC, "value": value, "unit": "MHz", "n_gpus": ws, "steps": steps,
             "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
@@ -534,7 +568,7 @@ def run_ours(args):
             "plain": plain, "fused_over_plain": (value / plain["value"]) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "adjoint": adjoint, "normalized": normalized, "generator": generator,
-            "fractional_rate": rates,
+            "fractional_rate": rates, "fm_voice": fm,
             "gpu_launches": steps}
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -139,6 +139,28 @@ synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t bat
                                     float* params_out_dev, float threshold, float* peak_out_dev,
                                     int32_t* silent_out_dev, void* stream);
 
+/* 4-operator FM voice. Sec. 3.2 names a 4-operator frequency-modulation
+ * architecture as in development and specifies no more; this is the
+ * library's own: four sine operators in a serial phase-modulation stack
+ * op3 -> op2 -> op1 -> op0, out(n) = y_0(n), y_4 = 0,
+ * y_i(n) = level_i E_i(n) sin(2 pi frac(n f0 ratio_i / SR) + y_(i+1)(n)),
+ * E_i the Voice's ADSR at the control points, linearly upsampled.
+ * SYNTH_FM_NUM_PARAMS normalized parameters per voice, u in [0, 1] mapped by
+ * y = lo + (hi - lo) u^c: [0] midi f0 [0, 127]; [1] note-on duration [0, 4] s;
+ * then for operator i (0 = carrier) at 2 + 7 i: ratio [0.5, 8] (c = 2), level
+ * (carrier: amplitude [0, 1]; modulators: index [0, 8] rad, c = 2), attack
+ * [0, 2] s (c = 2), decay [0, 2] s (c = 2), sustain [0, 1], release [0, 5] s
+ * (c = 2), alpha [0.1, 6] (c = 2). Drawn parameters come from Philox4x32-10
+ * stream 2 (counter (g lo, g hi, block, 2), key = seed).
+ *  params_in_dev  [batch][30] float or NULL (NULL = draw); clamped to [0, 1].
+ *  audio_dev      [batch][N] float, required; params_out_dev [batch][30] or NULL.
+ * Any rates the handle accepts. Errors: SYNTH_ERR_ARG (batch < 0, > max_batch
+ * or > 65535, NULL audio_dev), SYNTH_ERR_CUDA. */
+#define SYNTH_FM_NUM_PARAMS 30
+synth_status synth_fm_render(synth_handle h, uint64_t seed, uint64_t batch_index, int32_t batch,
+                             const float* params_in_dev, float* audio_dev, float* params_out_dev,
+                             void* stream);
+
 /* The same render as a plain, unfused sequence of module kernels (one per
  * module, every control-rate and audio-rate intermediate in a caller-owned
  * workspace in device memory), the torchsynth-style design of Sec. 3.1.

@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.synth_params_to_human.argtypes = [vp, vp, vp, i32]
         L.synth_is_test.argtypes = [u64]
         L.synth_is_test.restype = i32
+        L.synth_fm_render.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp]
+        L.synth_fm_render.restype = ctypes.c_int
         L.synth_split_voice.argtypes = [i32, u64]
         L.synth_split_voice.restype = u64
         L.synth_stream_features.argtypes = [vp, u64, i32, u64, ctypes.c_int64, i32, vp, vp, vp]
@@ -186,6 +188,7 @@ def synth_is_test(g: int) -> bool:
 
 
 SPLIT_ALL, SPLIT_TRAIN, SPLIT_TEST = 0, 1, 2
+FM_NUM_PARAMS = 30
 
 
 def synth_split_voice(split: int, i: int) -> int:
@@ -317,6 +320,23 @@ class Synth:
                                                _stream_ptr(stream))
         _check(status, "synth_render_normalized")
         return out, params_out, peak, silent
+
+    def fm_render(self, seed: int, batch_index: int, batch: int, params_in=None, out=None,
+                  params_out=None, stream=None):
+        """4-operator FM voices g = batch_index * batch + v (synth_fm_render);
+        returns (audio, params [batch][30])."""
+        import torch
+        if out is None:
+            out = torch.empty((batch, self.num_samples), dtype=torch.float32, device=self.device)
+        if params_out is None:
+            params_out = torch.empty((batch, FM_NUM_PARAMS), dtype=torch.float32, device=self.device)
+        self._check_tensor(out, (batch, self.num_samples), "out")
+        self._check_tensor(params_out, (batch, FM_NUM_PARAMS), "params_out")
+        self._check_tensor(params_in, (batch, FM_NUM_PARAMS), "params_in")
+        _check(lib().synth_fm_render(self.handle, seed, batch_index, batch, _ptr(params_in),
+                                     _ptr(out), _ptr(params_out), _stream_ptr(stream)),
+               "synth_fm_render")
+        return out, params_out
 
     def sync(self, stream=None) -> None:
         _check(synth_sync(self.handle, _stream_ptr(stream)), "synth_sync")

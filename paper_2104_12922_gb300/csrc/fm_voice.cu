@@ -1,0 +1,217 @@
+// fm_voice.cu -- the 4-operator FM voice: four sine operators in a serial
+// phase-modulation stack op3 -> op2 -> op1 -> op0 (Chowning's FM as phase
+// modulation), each at f0 x ratio_i with the Voice's ADSR gated by the
+// keyboard's note-on duration; out(n) = y_0(n) with y_4 = 0 and
+// y_i(n) = level_i E_i(n) sin(2 pi phi_i(n) + y_(i+1)(n)). The paper names a
+// 4-operator FM architecture as in development (Sec. 3.2) and specifies no
+// more; parameter ranges and the stack are this library's choices.
+//
+// One CTA renders one voice's chunk of kFmChunk samples: it draws (or loads)
+// the 30 normalized parameters, maps them, turns each operator's frequency
+// into a 64-bit fixed-point phase increment (the phase of sample n is the
+// exact product n x inc mod 2^64), evaluates the four envelopes at the
+// control points the chunk spans, and then renders 4-sample quads.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "voice_device.cuh"
+
+namespace synth {
+namespace {
+
+constexpr int kFmThreads = 256;
+constexpr int kFmChunk = 4096;                  // samples per CTA (a multiple of 4)
+constexpr int kFmMaxPts = kFmChunk / 4 + 3;     // control points a chunk can span (R >= 4)
+constexpr uint32_t kStreamFmParam = 2;
+
+struct FmConst {
+  int64_t N, rate_a, rate_b;  // samples; R = rate_a / rate_b samples per control interval
+  double sample_rate, control_rate;
+};
+
+// Normalized parameter p -> human value, y = lo + (hi - lo) u^c with c = 1
+// or 2 (exact products). Layout: midi f0, note-on duration, then per
+// operator (0 = carrier) ratio, level, attack, decay, sustain, release, alpha.
+__host__ __device__ inline void fm_range(int p, float& lo, float& hi, int& c) {
+  if (p < 2) {
+    lo = 0.f;
+    hi = p == 0 ? 127.f : 4.f;
+    c = 1;
+    return;
+  }
+  const int i = (p - 2) / 7, q = (p - 2) % 7;
+  const float los[7] = {0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.1f};
+  const float his[7] = {8.f, 8.f, 2.f, 2.f, 1.f, 5.f, 6.f};
+  const int cs[7] = {2, 2, 2, 2, 1, 2, 2};
+  lo = los[q];
+  hi = (q == 1 && i == 0) ? 1.f : his[q];  // the carrier's level is an amplitude in [0, 1]
+  c = (q == 1 && i == 0) ? 1 : cs[q];
+}
+
+// The Voice's ADSR (attack (t/a)^alpha, decay to s, release from the level at
+// note-off d), in FP32; zero-length sections are skipped.
+__device__ __forceinline__ float fm_gate_on(float t, float a, float dc, float s, float alpha) {
+  if (t < a) return powf(t / a, alpha);
+  if (t < a + dc) return 1.f - (1.f - s) * powf((t - a) / dc, alpha);
+  return s;
+}
+__device__ __forceinline__ float fm_adsr(float t, const float* o, float d) {
+  if (t < d) return fm_gate_on(t, o[2], o[3], o[4], o[6]);
+  const float level = fm_gate_on(d, o[2], o[3], o[4], o[6]);
+  const float tau = t - d;
+  if (tau < o[5]) return level * (1.f - powf(tau / o[5], o[6]));
+  return 0.f;
+}
+
+struct __align__(16) FmSmem {
+  float u[32];
+  float y[kNumFmParams];
+  unsigned long long inc[4];
+  float env[4][kFmMaxPts];
+  int sst[kFmMaxPts];    // first sample of each interval, relative to the chunk start
+  float u0[kFmMaxPts];   // fraction of the interval's first sample
+};
+
+__global__ void __launch_bounds__(kFmThreads) fm_render_kernel(FmConst fc, uint64_t seed,
+                                                               uint64_t batch_index, int batch,
+                                                               const float* __restrict__ params_in,
+                                                               float* __restrict__ audio,
+                                                               float* __restrict__ params_out) {
+  __shared__ FmSmem S;
+  const int tid = threadIdx.x;
+  const int v = blockIdx.y;
+  const uint64_t g = batch_index * (uint64_t)batch + (uint64_t)v;
+  const int64_t s0 = (int64_t)blockIdx.x * kFmChunk;
+  const int64_t N = fc.N;
+  const int64_t s1 = min(s0 + (int64_t)kFmChunk, N);
+  // ---- parameters
+  if (params_in == nullptr) {
+    if (tid < 8) {
+      const uint4 r = philox4x32_10(
+          make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)tid, kStreamFmParam),
+          make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+      S.u[4 * tid + 0] = u01f(r.x);
+      S.u[4 * tid + 1] = u01f(r.y);
+      S.u[4 * tid + 2] = u01f(r.z);
+      S.u[4 * tid + 3] = u01f(r.w);
+    }
+  } else if (tid < kNumFmParams) {
+    S.u[tid] = fminf(fmaxf(params_in[(size_t)v * kNumFmParams + tid], 0.f), 1.f);
+  }
+  __syncthreads();
+  if (tid < kNumFmParams) {
+    const float u = S.u[tid];
+    if (blockIdx.x == 0 && params_out) params_out[(size_t)v * kNumFmParams + tid] = u;
+    float lo, hi;
+    int c;
+    fm_range(tid, lo, hi, c);
+    S.y[tid] = fmaf(hi - lo, c == 2 ? u * u : u, lo);
+  }
+  if (tid < 4) {
+    // the operator's increment in cycles per sample, in FP64 once per CTA,
+    // reduced mod 1 and scaled to 2^64: phase(n) = n inc mod 2^64 exactly
+    const double u0 = (double)S.u[0], ur = (double)S.u[2 + 7 * tid];
+    const double f0 = 440.0 * exp2((127.0 * u0 - 69.0) / 12.0);
+    const double inc = f0 * (0.5 + 7.5 * ur * ur) / fc.sample_rate;
+    const double fr = inc - floor(inc);
+    const double scaled = ldexp(fr, 64);
+    S.inc[tid] = scaled >= 18446744073709551615.0 ? 0ull : __double2ull_rn(scaled);
+  }
+  __syncthreads();
+  // ---- envelopes at the control points the chunk spans
+  const int64_t k_lo = s0 * fc.rate_b / fc.rate_a;
+  const int64_t k_hi = (s1 - 1) * fc.rate_b / fc.rate_a + 1;
+  const int npts = (int)(k_hi - k_lo + 1);
+  const float inv_cr = (float)(1.0 / fc.control_rate);
+  const float dur = S.y[1];
+  for (int j = tid; j < npts; j += kFmThreads) {
+    const int64_t k = k_lo + j;
+    const float t = (float)k * inv_cr;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) S.env[i][j] = fm_adsr(t, S.y + 2 + 7 * i, dur);
+    const int64_t sk = (k * fc.rate_a + fc.rate_b - 1) / fc.rate_b;
+    S.sst[j] = (int)(sk - s0);
+    S.u0[j] = (float)(sk * fc.rate_b - k * fc.rate_a) / (float)fc.rate_a;
+  }
+  __syncthreads();
+  // ---- audio
+  const float lev[4] = {S.y[3], S.y[10], S.y[17], S.y[24]};
+  const float invR = (float)fc.rate_b / (float)fc.rate_a;
+  const float kInv2Pi = 0.15915494309189535f;
+  const int n_c = (int)(s1 - s0);
+  float* out = audio + (size_t)v * (size_t)N + (size_t)s0;
+  const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(audio) & 15) == 0;
+  for (int q = tid; 4 * q < n_c; q += kFmThreads) {
+    const int r0 = 4 * q;
+    int j = min((int)((float)r0 * invR), npts - 2);
+    while (j + 1 < npts - 1 && S.sst[j + 1] <= r0) ++j;
+    while (j > 0 && S.sst[j] > r0) --j;
+    const unsigned long long n0 = (unsigned long long)(s0 + r0);
+    // per operator: the quad's first phase (one 64-bit product, then sums),
+    // and the envelope of the quad's interval(s) (it meets at most two)
+    unsigned long long ph[4];
+    float ea[4], da[4], eb[4], db[4];
+    const bool two = j + 1 < npts - 1 && r0 + 3 >= S.sst[j + 1];
+#pragma unroll
+    for (int op = 0; op < 4; ++op) {
+      ph[op] = n0 * S.inc[op];
+      ea[op] = S.env[op][j];
+      da[op] = S.env[op][j + 1] - ea[op];
+      eb[op] = two ? S.env[op][j + 1] : ea[op];
+      db[op] = two ? S.env[op][j + 2] - eb[op] : da[op];
+    }
+    float o4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + i;
+      const bool in_b = two && r >= S.sst[j + 1];
+      const int jj = in_b ? j + 1 : j;
+      const float fu = fmaf((float)(r - S.sst[jj]), invR, S.u0[jj]);
+      float yv = 0.f;
+#pragma unroll
+      for (int op = 3; op >= 0; --op) {
+        // the phase's top 24 bits are exact in a float; add the modulation
+        // (radians -> cycles) and reduce to [-1/2, 1/2] before the sine
+        float t = fmaf(yv, kInv2Pi, (float)(ph[op] >> 40) * 0x1p-24f);
+        t -= rintf(t);
+        const float e = in_b ? fmaf(fu, db[op], eb[op]) : fmaf(fu, da[op], ea[op]);
+        // a modulator's sine error is amplified by the levels below it: the
+        // accurate sine there; the carrier's is not: the SFU sine
+        const float sn = op == 0 ? __sinf(6.283185307179586f * t) : sinpif(2.f * t);
+        yv = lev[op] * e * sn;
+        ph[op] += S.inc[op];
+      }
+      o4[i] = yv;
+    }
+    if (vec && r0 + 3 < n_c) {
+      __stcs(reinterpret_cast<float4*>(out + r0), make_float4(o4[0], o4[1], o4[2], o4[3]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (r0 + i < n_c) out[r0 + i] = o4[i];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fm_render(const VoiceConst& vc, uint64_t seed, uint64_t batch_index, int batch,
+                             const float* params_in, float* audio, float* params_out,
+                             cudaStream_t stream) {
+  if (batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  FmConst fc;
+  fc.N = vc.n_samples;
+  fc.rate_a = vc.rate_a;
+  fc.rate_b = vc.rate_b;
+  fc.sample_rate = vc.sample_rate;
+  fc.control_rate = vc.control_rate;
+  const dim3 grid((unsigned)((vc.n_samples + kFmChunk - 1) / kFmChunk), (unsigned)batch);
+  fm_render_kernel<<<grid, kFmThreads, 0, stream>>>(fc, seed, batch_index, batch, params_in, audio,
+                                                    params_out);
+  return cudaGetLastError();
+}
+
+}  // namespace synth

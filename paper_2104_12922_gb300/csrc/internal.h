@@ -75,6 +75,11 @@ cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t fi
                                 const PeakNormArgs* norm = nullptr);
 int fused_max_active_blocks_per_sm();
 
+// The 4-operator FM voice (fm_voice.cu): voices g = batch_index * batch + v.
+cudaError_t launch_fm_render(const VoiceConst& vc, uint64_t seed, uint64_t batch_index, int batch,
+                             const float* params_in, float* audio, float* params_out,
+                             cudaStream_t stream);
+
 // Plain (unfused) form.
 size_t plain_workspace_bytes(const VoiceConst& vc, int batch);
 cudaError_t launch_render_plain(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,

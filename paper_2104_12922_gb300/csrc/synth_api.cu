@@ -203,6 +203,17 @@ synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t bat
                                         h->fused_grid, static_cast<cudaStream_t>(stream), &norm));
 }
 
+synth_status synth_fm_render(synth_handle h, uint64_t seed, uint64_t batch_index, int32_t batch,
+                             const float* params_in_dev, float* audio_dev, float* params_out_dev,
+                             void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (batch < 0 || batch > h->cfg.max_batch || batch > 65535) return SYNTH_ERR_ARG;
+  if (batch == 0) return SYNTH_OK;
+  if (!audio_dev) return SYNTH_ERR_ARG;
+  return check_cuda(launch_fm_render(h->vc, seed, batch_index, batch, params_in_dev, audio_dev,
+                                     params_out_dev, static_cast<cudaStream_t>(stream)));
+}
+
 synth_status synth_render_plain_workspace_size(synth_handle h, int32_t batch, size_t* bytes) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
   if (!bytes || batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;

@@ -20,6 +20,7 @@
 namespace synth {
 
 constexpr int kNumParams = 78;
+constexpr int kNumFmParams = 30;  // the 4-operator FM voice (fm_voice.cu)
 
 // Parameter slots of the Voice.
 enum : int {
