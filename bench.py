@@ -114,6 +114,21 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_batch_index(step: int, ws: int, rank: int) -> int:
+    """Replicas: step s of rank r renders batch index s * ws + r, so the
+    ranks' batches are disjoint and together cover 0 .. steps * ws - 1."""
+    return step * ws + rank
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (an all-reduce MAX, then a barrier)."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 FUSED_SOURCES = ["render_fused.cu", "render_common.cuh", "control_ff.cuh", "ff.cuh",
                  "voice_device.cuh", "internal.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "render_fused_batch128x4s.md")
@@ -381,7 +396,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
 
     def batch_index(step):
-        return step * ws + rank
+        return rank_batch_index(step, ws, rank)
 
     def record(g_steps, plain=False):
         for s in range(g_steps):
@@ -423,10 +438,7 @@ def run_ours(args):
             sampler.__exit__(None, None, None)
         ms = start.elapsed_time(end)
         if ws > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.barrier()
-            ms = float(t.item())
+            ms = max_over_ranks(ms, dist, dev)
         return ms, (sampler.summary() if sampler else None)
 
     # untimed replays (about 1 s of load), then exactly K timed steps
