@@ -10,11 +10,13 @@
 // the 30 normalized parameters, maps them, turns each operator's frequency
 // into a 64-bit fixed-point phase increment (the phase of sample n is the
 // exact product n x inc mod 2^64), evaluates the four envelopes at the
-// control points the chunk spans, and then renders 4-sample quads.
+// control points the chunk spans, and then renders 4-sample quads. No FP64:
+// the increments come from the float-float exp2 of the Voice's control chain.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
+#include "control_ff.cuh"
 #include "internal.h"
 #include "voice_device.cuh"
 
@@ -22,13 +24,15 @@ namespace synth {
 namespace {
 
 constexpr int kFmThreads = 256;
-constexpr int kFmChunk = 4096;                  // samples per CTA (a multiple of 4)
-constexpr int kFmMaxPts = kFmChunk / 4 + 3;     // control points a chunk can span (R >= 4)
+constexpr int kFmChunk = 8192;                  // samples per CTA (a multiple of 4)
 constexpr uint32_t kStreamFmParam = 2;
 
 struct FmConst {
   int64_t N, rate_a, rate_b;  // samples; R = rate_a / rate_b samples per control interval
-  double sample_rate, control_rate;
+  double control_rate;
+  int max_pts;                // control points a chunk can span
+  ff log2_440_over_sr;        // log2(440 / SR)
+  alignas(16) FFTables T;     // float-float exp2 tables
 };
 
 // Normalized parameter p -> human value, y = lo + (hi - lo) u^c with c = 1
@@ -69,17 +73,44 @@ struct __align__(16) FmSmem {
   float u[32];
   float y[kNumFmParams];
   unsigned long long inc[4];
-  float env[4][kFmMaxPts];
-  int sst[kFmMaxPts];    // first sample of each interval, relative to the chunk start
-  float u0[kFmMaxPts];   // fraction of the interval's first sample
 };
 
-__global__ void __launch_bounds__(kFmThreads) fm_render_kernel(FmConst fc, uint64_t seed,
+// sin(2 pi t) for |t| <= 1/2: a quarter-turn reduction t = q/4 + r,
+// |r| <= 1/8, then sin(2 pi t) = sin x, cos x, -sin x, -cos x (x = 2 pi r)
+// for q = 0, 1, 2, 3 (mod 4), with the Taylor series of sin to x^9 and of
+// cos to x^10 in Horner form (truncation below 2e-9 at |x| = pi/4).
+__device__ __forceinline__ float sin2pi_poly(float t) {
+  const float q = rintf(4.f * t);
+  const float x = fmaf(q, -0.25f, t) * 6.28318530717958648f;
+  const float z = x * x;
+  float ps = fmaf(z, 1.f / 362880.f, -1.f / 5040.f);
+  ps = fmaf(z, ps, 1.f / 120.f);
+  ps = fmaf(z, ps, -1.f / 6.f);
+  const float sn = fmaf(z * x, ps, x);
+  float pc = fmaf(z, -1.f / 3628800.f, 1.f / 40320.f);
+  pc = fmaf(z, pc, -1.f / 720.f);
+  pc = fmaf(z, pc, 1.f / 24.f);
+  pc = fmaf(z, pc, -0.5f);
+  const float cs = fmaf(z, pc, 1.f);
+  const int qi = (int)q & 3;
+  const float v = (qi & 1) ? cs : sn;
+  return (qi & 2) ? -v : v;
+}
+
+__global__ void __launch_bounds__(kFmThreads) fm_render_kernel(const __grid_constant__ FmConst fc,
+                                                               uint64_t seed,
                                                                uint64_t batch_index, int batch,
                                                                const float* __restrict__ params_in,
                                                                float* __restrict__ audio,
                                                                float* __restrict__ params_out) {
   __shared__ FmSmem S;
+  // per control point the chunk spans: the four envelopes, the first sample
+  // of its interval (chunk-relative) and that sample's fraction
+  extern __shared__ __align__(16) float fm_dyn[];
+  const int max_pts = fc.max_pts;
+  float* env = fm_dyn;                                         // [4][max_pts]
+  int* sst = reinterpret_cast<int*>(fm_dyn + 4 * max_pts);     // [max_pts]
+  float* fr0 = fm_dyn + 5 * max_pts;                           // [max_pts]
   const int tid = threadIdx.x;
   const int v = blockIdx.y;
   const uint64_t g = batch_index * (uint64_t)batch + (uint64_t)v;
@@ -110,14 +141,13 @@ __global__ void __launch_bounds__(kFmThreads) fm_render_kernel(FmConst fc, uint6
     S.y[tid] = fmaf(hi - lo, c == 2 ? u * u : u, lo);
   }
   if (tid < 4) {
-    // the operator's increment in cycles per sample, in FP64 once per CTA,
-    // reduced mod 1 and scaled to 2^64: phase(n) = n inc mod 2^64 exactly
-    const double u0 = (double)S.u[0], ur = (double)S.u[2 + 7 * tid];
-    const double f0 = 440.0 * exp2((127.0 * u0 - 69.0) / 12.0);
-    const double inc = f0 * (0.5 + 7.5 * ur * ur) / fc.sample_rate;
-    const double fr = inc - floor(inc);
-    const double scaled = ldexp(fr, 64);
-    S.inc[tid] = scaled >= 18446744073709551615.0 ? 0ull : __double2ull_rn(scaled);
+    // the operator's increment in cycles per sample, f0 ratio / SR with
+    // f0 = 440 2^((m - 69)/12), in float-float (relative error ~1e-14), then
+    // its fraction as 64-bit fixed point: phase(n) = n inc mod 2^64 exactly
+    const float ur = S.u[2 + 7 * tid];
+    const ff m = ff_mul_f(ff_make(127.f), S.u[0]);
+    const ff ratio = ff_add_f(ff_mul_f(ff_mul_f(ff_make(ur), ur), 7.5f), 0.5f);
+    S.inc[tid] = ff_to_fix64(ff_mul(inc_at_ff(m, fc.log2_440_over_sr, fc.T), ratio));
   }
   __syncthreads();
   // ---- envelopes at the control points the chunk spans
@@ -130,10 +160,10 @@ __global__ void __launch_bounds__(kFmThreads) fm_render_kernel(FmConst fc, uint6
     const int64_t k = k_lo + j;
     const float t = (float)k * inv_cr;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) S.env[i][j] = fm_adsr(t, S.y + 2 + 7 * i, dur);
+    for (int i = 0; i < 4; ++i) env[i * max_pts + j] = fm_adsr(t, S.y + 2 + 7 * i, dur);
     const int64_t sk = (k * fc.rate_a + fc.rate_b - 1) / fc.rate_b;
-    S.sst[j] = (int)(sk - s0);
-    S.u0[j] = (float)(sk * fc.rate_b - k * fc.rate_a) / (float)fc.rate_a;
+    sst[j] = (int)(sk - s0);
+    fr0[j] = (float)(sk * fc.rate_b - k * fc.rate_a) / (float)fc.rate_a;
   }
   __syncthreads();
   // ---- audio
@@ -146,29 +176,29 @@ __global__ void __launch_bounds__(kFmThreads) fm_render_kernel(FmConst fc, uint6
   for (int q = tid; 4 * q < n_c; q += kFmThreads) {
     const int r0 = 4 * q;
     int j = min((int)((float)r0 * invR), npts - 2);
-    while (j + 1 < npts - 1 && S.sst[j + 1] <= r0) ++j;
-    while (j > 0 && S.sst[j] > r0) --j;
+    while (j + 1 < npts - 1 && sst[j + 1] <= r0) ++j;
+    while (j > 0 && sst[j] > r0) --j;
     const unsigned long long n0 = (unsigned long long)(s0 + r0);
     // per operator: the quad's first phase (one 64-bit product, then sums),
     // and the envelope of the quad's interval(s) (it meets at most two)
     unsigned long long ph[4];
     float ea[4], da[4], eb[4], db[4];
-    const bool two = j + 1 < npts - 1 && r0 + 3 >= S.sst[j + 1];
+    const bool two = j + 1 < npts - 1 && r0 + 3 >= sst[j + 1];
 #pragma unroll
     for (int op = 0; op < 4; ++op) {
       ph[op] = n0 * S.inc[op];
-      ea[op] = S.env[op][j];
-      da[op] = S.env[op][j + 1] - ea[op];
-      eb[op] = two ? S.env[op][j + 1] : ea[op];
-      db[op] = two ? S.env[op][j + 2] - eb[op] : da[op];
+      ea[op] = env[op * max_pts + j];
+      da[op] = env[op * max_pts + j + 1] - ea[op];
+      eb[op] = two ? env[op * max_pts + j + 1] : ea[op];
+      db[op] = two ? env[op * max_pts + j + 2] - eb[op] : da[op];
     }
     float o4[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = r0 + i;
-      const bool in_b = two && r >= S.sst[j + 1];
+      const bool in_b = two && r >= sst[j + 1];
       const int jj = in_b ? j + 1 : j;
-      const float fu = fmaf((float)(r - S.sst[jj]), invR, S.u0[jj]);
+      const float fu = fmaf((float)(r - sst[jj]), invR, fr0[jj]);
       float yv = 0.f;
 #pragma unroll
       for (int op = 3; op >= 0; --op) {
@@ -177,9 +207,10 @@ __global__ void __launch_bounds__(kFmThreads) fm_render_kernel(FmConst fc, uint6
         float t = fmaf(yv, kInv2Pi, (float)(ph[op] >> 40) * 0x1p-24f);
         t -= rintf(t);
         const float e = in_b ? fmaf(fu, db[op], eb[op]) : fmaf(fu, da[op], ea[op]);
-        // a modulator's sine error is amplified by the levels below it: the
-        // accurate sine there; the carrier's is not: the SFU sine
-        const float sn = op == 0 ? __sinf(6.283185307179586f * t) : sinpif(2.f * t);
+        // a modulator's sine error is amplified by the levels below it: a
+        // sine accurate to an ulp or two there; the carrier's is not: the
+        // SFU sine
+        const float sn = op == 0 ? __sinf(6.283185307179586f * t) : sin2pi_poly(t);
         yv = lev[op] * e * sn;
         ph[op] += S.inc[op];
       }
@@ -206,11 +237,21 @@ cudaError_t launch_fm_render(const VoiceConst& vc, uint64_t seed, uint64_t batch
   fc.N = vc.n_samples;
   fc.rate_a = vc.rate_a;
   fc.rate_b = vc.rate_b;
-  fc.sample_rate = vc.sample_rate;
   fc.control_rate = vc.control_rate;
+  fc.log2_440_over_sr = vc.log2_440_over_sr;
+  fc.T = vc.T;
+  fc.max_pts = (int)((int64_t)kFmChunk * vc.rate_b / vc.rate_a) + 3;
+  const size_t smem = sizeof(float) * 6 * (size_t)fc.max_pts;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(fm_render_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   const dim3 grid((unsigned)((vc.n_samples + kFmChunk - 1) / kFmChunk), (unsigned)batch);
-  fm_render_kernel<<<grid, kFmThreads, 0, stream>>>(fc, seed, batch_index, batch, params_in, audio,
-                                                    params_out);
+  fm_render_kernel<<<grid, kFmThreads, smem, stream>>>(fc, seed, batch_index, batch, params_in,
+                                                       audio, params_out);
   return cudaGetLastError();
 }
 
