@@ -86,3 +86,15 @@ def test_fm_argument_errors(pkg):
     assert L.synth_fm_render(syn.handle, 0, 0, 2, None, None, None, None) == pkg.SYNTH_ERR_ARG
     assert L.synth_fm_render(syn.handle, 0, 0, 0, None, None, None, None) == pkg.SYNTH_OK
     syn.close()
+
+
+def test_fm_index_rule_across_batch_sizes(pkg):
+    """Voice g = batch_index * batch + v depends on (seed, g) only: voices
+    16..23 of one batch of 32 equal batch index 2 of batches of 8."""
+    import torch
+    syn = pkg.Synth(seconds=0.5, max_batch=32)
+    a32, p32 = syn.fm_render(9, 0, 32)
+    a8, p8 = syn.fm_render(9, 2, 8)
+    syn.sync()
+    assert torch.equal(p32[16:24], p8) and torch.equal(a32[16:24], a8)
+    syn.close()

@@ -70,3 +70,20 @@ def test_noalloc_rejects_batches_beyond_its_scratch(env):
     assert st == pkg.SYNTH_ERR_ARG
     assert L.synth_render_noalloc(None, 0, 0, 1, None, out.data_ptr(), None, None) == pkg.SYNTH_ERR_ARG
     assert L.synth_render_noalloc(ctypes.byref(cfg), 0, 0, 0, None, None, None, None) == pkg.SYNTH_OK
+
+
+def test_noalloc_at_a_fractional_rate(env):
+    """16 kHz at the 441 Hz control rate (R = 16000/441): the handle-free
+    entry takes the same general-R kernel as synth_render."""
+    torch, pkg, L = env
+    batch, seconds = 8, 1.0
+    syn = pkg.Synth(seconds=seconds, max_batch=batch, sample_rate=16000.0)
+    ref_a, ref_p = syn.render(2, 6, batch)
+    syn.sync()
+    cfg = pkg.synth_default_config()
+    cfg.seconds, cfg.sample_rate = seconds, 16000.0
+    a, p = _noalloc(torch, pkg, L, cfg, 2, 6, batch, syn.num_samples)
+    assert torch.equal(p, ref_p)
+    err = float((a - ref_a).abs().max())
+    assert np.isfinite(err) and err <= TOL, err
+    syn.close()
