@@ -9,9 +9,13 @@ Our arm (default) times the fused persistent kernel (and, beside it, the
 plain unfused module-by-module form on the same GPU). ``--impl reference``
 times the FP64 CPU oracle as it stands on the host cores.
 
+The timed loop renders 8 consecutive batches per launch
+(synth_render_batches, each batch with seed = its index); the same render
+with one launch per batch is reported beside it.
+
 Under torchrun (N > 1) every rank renders its own batches (batch indices
-rank, rank + N, ...): voices are independent, so there is no collective on
-the data path; the timing is the max over ranks.
+rank * K .. rank * K + K - 1): voices are independent, so there is no
+collective on the data path; the timing is the max over ranks.
 """
 from __future__ import annotations
 
@@ -27,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BATCH = 128
+GROUP = 8  # consecutive batches per launch of the timed loop
 SECONDS = 4.0
 SR = 44100.0
 N_SAMPLES = int(SECONDS * SR)
@@ -114,10 +119,11 @@ def dist_env():
     return ws, rank, local
 
 
-def rank_batch_index(step: int, ws: int, rank: int) -> int:
-    """Replicas: step s of rank r renders batch index s * ws + r, so the
-    ranks' batches are disjoint and together cover 0 .. steps * ws - 1."""
-    return step * ws + rank
+def rank_batch_index(step: int, ws: int, rank: int, steps: int) -> int:
+    """Replicas: step s of rank r renders batch index r * steps + s, so each
+    rank's batches are consecutive (several go into one launch), the ranks'
+    batches are disjoint and together they cover 0 .. steps * ws - 1."""
+    return rank * steps + step
 
 
 def max_over_ranks(value: float, dist, device) -> float:
@@ -388,17 +394,31 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     dev = torch.device("cuda", local)
-    syn = pkg.Synth(seconds=SECONDS, max_batch=BATCH)
     K, W = args.steps, max(3, args.warmup)
+    syn = pkg.Synth(seconds=SECONDS, max_batch=BATCH * GROUP)
     n_buf = 4  # 4 x 90.3 MB rotating outputs: > L2 (129 MB), writes reach HBM
     outs = [torch.empty((BATCH, N_SAMPLES), dtype=torch.float32, device=dev) for _ in range(n_buf)]
     pouts = [torch.empty((BATCH, 78), dtype=torch.float32, device=dev) for _ in range(n_buf)]
+    # GROUP consecutive batches per launch into 2 rotating 723 MB outputs
+    outs_g = [torch.empty((BATCH * GROUP, N_SAMPLES), dtype=torch.float32, device=dev)
+              for _ in range(2)]
+    pouts_g = [torch.empty((BATCH * GROUP, 78), dtype=torch.float32, device=dev) for _ in range(2)]
     stream = torch.cuda.Stream(device=dev)
 
     def batch_index(step):
-        return rank_batch_index(step, ws, rank)
+        return rank_batch_index(step, ws, rank, K)
 
-    def record(g_steps, plain=False):
+    def record(g_steps):
+        """g_steps batches, GROUP per launch (seed = batch index)"""
+        for s0 in range(0, g_steps, GROUP):
+            c = min(GROUP, g_steps - s0)
+            bi = batch_index(s0)
+            i = (s0 // GROUP) % 2
+            syn.render_batches(bi, 1, bi, BATCH, c, out=outs_g[i][:c * BATCH],
+                               params_out=pouts_g[i][:c * BATCH], stream=stream)
+
+    def record_single(g_steps, plain=False):
+        """one launch per batch"""
         for s in range(g_steps):
             bi = batch_index(s)
             syn.render(bi, bi, BATCH, out=outs[s % n_buf], params_out=pouts[s % n_buf],
@@ -406,7 +426,7 @@ def run_ours(args):
 
     # warm-up (untimed), then capture K steps in one graph
     with torch.cuda.stream(stream):
-        record(W)
+        record(W * GROUP)
     stream.synchronize()
     syn.sync(stream)
     graph = torch.cuda.CUDAGraph()
@@ -456,16 +476,32 @@ def run_ours(args):
     value = samples_total / (ms / 1e3) / 1e6
     ms_per_step = ms / steps
 
+    # the same fused render with one launch per batch
+    Ks = min(K, 256)
+    with torch.cuda.stream(stream):
+        record_single(2)
+    stream.synchronize()
+    gs = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gs, stream=stream):
+        record_single(Ks)
+    with torch.cuda.stream(stream):
+        gs.replay()
+    stream.synchronize()
+    mss, _ = timed(lambda: gs.replay())
+    single = {"value": Ks * BATCH * N_SAMPLES * ws / (mss / 1e3) / 1e6, "unit": "MHz",
+              "ms_per_step": mss / Ks, "steps": Ks, "launches_per_step": 1}
+    del gs
+
     # plain unfused form on the same GPU (same workload)
     plain = None
     if not args.no_plain:
         Kp = min(K, 64)
         with torch.cuda.stream(stream):
-            record(2, plain=True)
+            record_single(2, plain=True)
         stream.synchronize()
         gp = torch.cuda.CUDAGraph()
         with torch.cuda.graph(gp, stream=stream):
-            record(Kp, plain=True)
+            record_single(Kp, plain=True)
         with torch.cuda.stream(stream):
             gp.replay()
         stream.synchronize()
@@ -571,17 +607,19 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (synth1B1 workload: parameters drawn per voice from seed and voice index)",
             "config": {"workload": "Voice batch 128 x 4 s @ 44.1 kHz, FP32 out, seed = batch index, "
-                                   f"{K} batches per CUDA graph", "global_batch": BATCH * ws,
+                                   f"{K} batches per CUDA graph, {GROUP} per launch "
+                                   "(synth_render_batches)", "global_batch": BATCH * ws,
                        "seconds": SECONDS, "sample_rate": SR,
-                       "l2": "4 rotating 90.3 MB output buffers (> 129 MB L2)",
+                       "l2": "2 rotating 723 MB outputs of 8 batches (> 129 MB L2)",
                        "parallelism": f"replicas x{ws} (disjoint batch indices)"},
             "x_realtime": value * 1e6 / SR,
             "paper_context": {"value": PAPER_MHZ, "unit": "MHz", "hardware": "single V100 (Sec. 2.2)"},
+            "one_launch_per_batch": single,
             "plain": plain, "fused_over_plain": (value / plain["value"]) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "adjoint": adjoint, "normalized": normalized, "generator": generator,
             "fractional_rate": rates, "fm_voice": fm,
-            "gpu_launches": steps}
+            "gpu_launches": (steps + GROUP - 1) // GROUP}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()

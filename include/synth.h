@@ -117,6 +117,19 @@ synth_status synth_render(synth_handle h, uint64_t seed, uint64_t batch_index, i
                           const float* params_in_dev, float* audio_dev, float* params_out_dev,
                           void* stream);
 
+/* `count` consecutive batches in one persistent launch: batch k (k < count)
+ * is synth_render(seed + k * seed_step, batch_index + k, batch) (its voices
+ * g = (batch_index + k) * batch + v, the same voices and results), written
+ * to audio_dev + k * batch * N and params_out_dev + k * batch * 78.
+ * seed_step = 1 with seed = batch_index gives each batch the seed equal to
+ * its index. One launch spreads the tiles of all batches over the GPU, so
+ * the tail of one batch's tiles overlaps the next batch's.
+ * Errors: as synth_render, with batch * count <= max_batch. */
+synth_status synth_render_batches(synth_handle h, uint64_t seed, uint64_t seed_step,
+                                  uint64_t batch_index, int32_t batch, int32_t count,
+                                  const float* params_in_dev, float* audio_dev,
+                                  float* params_out_dev, void* stream);
+
 /* Render with per-voice peak normalisation and silence rejection. Sec. 2
  * names nearly silent renders among the undesirable products of sampling
  * parameters uniformly; this is the library's reading of a remedy, not a

@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.synth_params_to_human.argtypes = [vp, vp, vp, i32]
         L.synth_is_test.argtypes = [u64]
         L.synth_is_test.restype = i32
+        L.synth_render_batches.argtypes = [vp, u64, u64, u64, i32, i32, vp, vp, vp, vp]
+        L.synth_render_batches.restype = ctypes.c_int
         L.synth_fm_render.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp]
         L.synth_fm_render.restype = ctypes.c_int
         L.synth_split_voice.argtypes = [i32, u64]
@@ -320,6 +322,25 @@ class Synth:
                                                _stream_ptr(stream))
         _check(status, "synth_render_normalized")
         return out, params_out, peak, silent
+
+    def render_batches(self, seed: int, seed_step: int, batch_index: int, batch: int, count: int,
+                       params_in=None, out=None, params_out=None, stream=None):
+        """`count` consecutive batches in one launch (synth_render_batches):
+        batch k = render(seed + k seed_step, batch_index + k, batch); returns
+        (audio [count * batch][N], params [count * batch][78])."""
+        import torch
+        total = batch * count
+        if out is None:
+            out = torch.empty((total, self.num_samples), dtype=torch.float32, device=self.device)
+        if params_out is None:
+            params_out = torch.empty((total, NUM_PARAMS), dtype=torch.float32, device=self.device)
+        self._check_tensor(out, (total, self.num_samples), "out")
+        self._check_tensor(params_out, (total, NUM_PARAMS), "params_out")
+        self._check_tensor(params_in, (total, NUM_PARAMS), "params_in")
+        _check(lib().synth_render_batches(self.handle, seed, seed_step, batch_index, batch, count,
+                                          _ptr(params_in), _ptr(out), _ptr(params_out),
+                                          _stream_ptr(stream)), "synth_render_batches")
+        return out, params_out
 
     def fm_render(self, seed: int, batch_index: int, batch: int, params_in=None, out=None,
                   params_out=None, stream=None):

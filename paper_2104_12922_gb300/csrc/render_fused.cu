@@ -225,13 +225,13 @@ template <bool kCarryF32, bool kPeak, bool kGenR>
 __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t first, int split, int batch,
     const float* __restrict__ params_in, float* __restrict__ audio, float* __restrict__ params_out,
-    ScratchHeader* hdr, TileState* tiles, int n_windows, const PeakNormArgs norm) {
+    ScratchHeader* hdr, TileState* tiles, int n_windows, const PeakNormArgs norm,
+    uint64_t seed_step, int sub_batch) {
   __shared__ Smem s;
   const int tid = threadIdx.x;
   const int total_tiles = batch * n_windows;
   const int R = vc.R, K = vc.K;
   const int64_t N = vc.n_samples;
-  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   const int qps = R >> 2;             // quads per control interval
   const int dq_s = NT / qps;          // a thread's quad stride NT as (intervals, quads)
   const int dq_j = NT - dq_s * qps;
@@ -257,6 +257,10 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     }
     const int v = t % batch, w = t / batch;
     const uint64_t g = split_voice(split, first + (uint64_t)v);
+    // consecutive sub-batches of sub_batch voices may each have their own
+    // seed: seed + (v / sub_batch) seed_step
+    const uint64_t sd = seed + (uint64_t)(v / sub_batch) * seed_step;
+    const uint2 key = make_uint2((uint32_t)sd, (uint32_t)(sd >> 32));
     const int k0 = w * TI;
     const int nseg = min(TI, K - k0);
     TileState* vt = tiles + (size_t)v * n_windows;
@@ -607,13 +611,15 @@ int fused_max_active_blocks_per_sm() {
 cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t first, int split,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
-                                int grid, cudaStream_t stream, const PeakNormArgs* norm) {
+                                int grid, cudaStream_t stream, const PeakNormArgs* norm,
+                                uint64_t seed_step, int sub_batch) {
   const int n_windows = windows_per_voice(vc.K);
   const int total = batch * n_windows;
   grid = grid < total ? grid : total;
   const PeakNormArgs nz = norm ? *norm : PeakNormArgs{0.f, nullptr, nullptr};
+  if (sub_batch <= 0) sub_batch = batch;
 #define SYNTH_FUSED_ARGS vc, seed, first, split, batch, params_in, audio, params_out, hdr, tiles, \
-                         n_windows, nz
+                         n_windows, nz, seed_step, sub_batch
   if (vc.general_r) {  // fractional R (never with FP32 carries)
     if (norm) render_fused_kernel<false, true, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
     else render_fused_kernel<false, false, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);

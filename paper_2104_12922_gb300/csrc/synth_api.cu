@@ -186,6 +186,23 @@ synth_status synth_render(synth_handle h, uint64_t seed, uint64_t batch_index, i
                                         h->fused_grid, static_cast<cudaStream_t>(stream)));
 }
 
+synth_status synth_render_batches(synth_handle h, uint64_t seed, uint64_t seed_step,
+                                  uint64_t batch_index, int32_t batch, int32_t count,
+                                  const float* params_in_dev, float* audio_dev,
+                                  float* params_out_dev, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (batch < 0 || count < 0 || (int64_t)batch * count > h->cfg.max_batch) return SYNTH_ERR_ARG;
+  if (batch == 0 || count == 0) return SYNTH_OK;
+  if (!audio_dev) return SYNTH_ERR_ARG;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
+  return check_cuda(launch_render_fused(h->vc, seed, batch_index * (uint64_t)batch, 0,
+                                        batch * count, params_in_dev, audio_dev, params_out_dev,
+                                        hdr, tiles, h->fused_grid,
+                                        static_cast<cudaStream_t>(stream), nullptr, seed_step,
+                                        batch));
+}
+
 synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t batch_index,
                                     int32_t batch, const float* params_in_dev, float* audio_dev,
                                     float* params_out_dev, float threshold, float* peak_out_dev,

@@ -197,3 +197,22 @@ def test_params_to_human_matches_oracle(synth4, oracle_mod):
             want = oracle_mod.range_map(float(u[i, p]), nb["lo"][p], nb["hi"][p], nb["curve"][p],
                                         nb["symmetric"][p])
             assert y[i, p] == pytest.approx(want, rel=1e-15, abs=1e-15)
+
+
+def test_render_batches_equals_separate_renders(torch_cuda):
+    """synth_render_batches(seed, step, bi, batch, count): batch k is
+    synth_render(seed + k step, bi + k, batch) -- bit-exact, including a
+    ragged batch count and a seed step of 0."""
+    import paper_2104_12922_gb300 as pkg
+    torch = torch_cuda
+    syn = pkg.Synth(seconds=0.5, max_batch=40)
+    for seed, step, bi, batch, count in [(7, 1, 7, 8, 5), (3, 0, 11, 13, 3)]:
+        a, p = syn.render_batches(seed, step, bi, batch, count)
+        for k in range(count):
+            ak, pk = syn.render(seed + k * step, bi + k, batch)
+            assert torch.equal(a[k * batch:(k + 1) * batch], ak), (seed, k)
+            assert torch.equal(p[k * batch:(k + 1) * batch], pk), (seed, k)
+    syn.sync()
+    L = pkg.lib()
+    assert L.synth_render_batches(syn.handle, 0, 1, 0, 8, 6, None, a.data_ptr(), None, None) == pkg.SYNTH_ERR_ARG
+    syn.close()

@@ -1,5 +1,5 @@
 """The multi-GPU path is replicas (voices are independent): rank r renders
-batch indices s * ws + r and the reported time is the slowest rank's. The
+batch indices r * steps + s and the reported time is the slowest rank's. The
 host logic of that path is checked here on CPU with two gloo ranks."""
 import os
 import socket
@@ -23,7 +23,7 @@ def _worker(rank, ws, port, steps, out):
                        "WORLD_SIZE": str(ws), "RANK": str(rank), "LOCAL_RANK": str(rank)})
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     assert bench.dist_env() == (ws, rank, rank)
-    mine = torch.tensor([bench.rank_batch_index(s, ws, rank) for s in range(steps)])
+    mine = torch.tensor([bench.rank_batch_index(s, ws, rank, steps) for s in range(steps)])
     gathered = [torch.zeros_like(mine) for _ in range(ws)]
     dist.all_gather(gathered, mine)
     slowest = bench.max_over_ranks(10.0 + rank, dist, torch.device("cpu"))
