@@ -29,7 +29,7 @@ constexpr uint32_t kStreamFmParam = 2;
 
 struct FmConst {
   int64_t N, rate_a, rate_b;  // samples; R = rate_a / rate_b samples per control interval
-  double control_rate;
+  float inv_cr;               // 1 / control rate
   int max_pts;                // control points a chunk can span
   ff log2_440_over_sr;        // log2(440 / SR)
   alignas(16) FFTables T;     // float-float exp2 tables
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kFmThreads) fm_render_kernel(const __grid_cons
   const int64_t k_lo = s0 * fc.rate_b / fc.rate_a;
   const int64_t k_hi = (s1 - 1) * fc.rate_b / fc.rate_a + 1;
   const int npts = (int)(k_hi - k_lo + 1);
-  const float inv_cr = (float)(1.0 / fc.control_rate);
+  const float inv_cr = fc.inv_cr;
   const float dur = S.y[1];
   for (int j = tid; j < npts; j += kFmThreads) {
     const int64_t k = k_lo + j;
@@ -202,9 +202,10 @@ __global__ void __launch_bounds__(kFmThreads) fm_render_kernel(const __grid_cons
       float yv = 0.f;
 #pragma unroll
       for (int op = 3; op >= 0; --op) {
-        // the phase's top 24 bits are exact in a float; add the modulation
-        // (radians -> cycles) and reduce to [-1/2, 1/2] before the sine
-        float t = fmaf(yv, kInv2Pi, (float)(ph[op] >> 40) * 0x1p-24f);
+        // the phase's top 24 bits are exact in a float (converted from 32
+        // bits: a 64-bit conversion would take the FP64 pipe); add the
+        // modulation (radians -> cycles), reduce to [-1/2, 1/2]
+        float t = fmaf(yv, kInv2Pi, (float)(uint32_t)(ph[op] >> 40) * 0x1p-24f);
         t -= rintf(t);
         const float e = in_b ? fmaf(fu, db[op], eb[op]) : fmaf(fu, da[op], ea[op]);
         // a modulator's sine error is amplified by the levels below it: a
@@ -237,7 +238,7 @@ cudaError_t launch_fm_render(const VoiceConst& vc, uint64_t seed, uint64_t batch
   fc.N = vc.n_samples;
   fc.rate_a = vc.rate_a;
   fc.rate_b = vc.rate_b;
-  fc.control_rate = vc.control_rate;
+  fc.inv_cr = (float)(1.0 / vc.control_rate);
   fc.log2_440_over_sr = vc.log2_440_over_sr;
   fc.T = vc.T;
   fc.max_pts = (int)((int64_t)kFmChunk * vc.rate_b / vc.rate_a) + 3;
