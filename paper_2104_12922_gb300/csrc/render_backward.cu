@@ -540,16 +540,18 @@ __global__ void bwd_range_map(const __grid_constant__ VoiceConst vc, const float
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= batch * kNumParams) return;
   const int p = i % kNumParams;
-  const double u = (double)fminf(fmaxf(u_in[i], 0.f), 1.f);
-  const double c = vc.curve[p], span = vc.hi[p] - vc.lo[p];
-  double dydu;
+  // FP32 (the FP64 pipe is narrow on this GPU; the gradient needs ~1e-6)
+  const float u = fminf(fmaxf(u_in[i], 0.f), 1.f);
+  const float c = ff_to_float(vc.map_curve[p]);
+  const float span = vc.sym[p] ? 2.f * ff_to_float(vc.map_scale[p]) : ff_to_float(vc.map_scale[p]);
+  float dydu;
   if (!vc.sym[p]) {
-    dydu = u <= 0.0 ? 0.0 : span * c * pow(u, c - 1.0);
+    dydu = u <= 0.f ? 0.f : span * c * powf(u, c - 1.f);
   } else {
-    const double s = fabs(2.0 * u - 1.0);
-    dydu = s <= 0.0 ? 0.0 : span * c * pow(s, c - 1.0);
+    const float s = fabsf(2.f * u - 1.f);
+    dydu = s <= 0.f ? 0.f : span * c * powf(s, c - 1.f);
   }
-  grad[i] = (float)((double)grad[i] * dydu);
+  grad[i] *= dydu;
 }
 
 }  // namespace
