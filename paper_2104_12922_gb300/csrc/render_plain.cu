@@ -98,7 +98,7 @@ __global__ void plain_adsr(const __grid_constant__ VoiceConst vc, const VoiceFF*
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 6 * P) return;
   const int a = i / P, k = i - a * P;
-  const ff tk = ff_mul_f(ff_from_double(1.0 / vc.control_rate), (float)k);
+  const ff tk = ff_mul_f(vc.inv_cr, (float)k);
   env[((size_t)v * 6 + a) * P + k] = adsr_ff(tk, a, vff[v], T);
 }
 
@@ -110,7 +110,7 @@ __global__ void plain_lfo_rate(const __grid_constant__ VoiceConst vc, const Voic
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P) return;
   const VoiceFF& V = vff[v];
-  const ff inv_cr = ff_from_double(1.0 / vc.control_rate);
+  const ff inv_cr = vc.inv_cr;
   for (int l = 0; l < 2; ++l) {
     const ff e = env[((size_t)v * 6 + 2 + 2 * l) * P + k];
     const ff rate = ff_min(ff_max(ff_add(V.lfo_freq[l], ff_mul(V.lfo_depth[l], e)), ff_make(0.f)),
