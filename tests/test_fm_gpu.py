@@ -98,3 +98,23 @@ def test_fm_index_rule_across_batch_sizes(pkg):
     syn.sync()
     assert torch.equal(p32[16:24], p8) and torch.equal(a32[16:24], a8)
     syn.close()
+
+
+def test_fm_full_size_sampled(pkg, oracle_mod):
+    """The FM throughput workload: batch 128 x 4 s at 44.1 kHz, seed = batch
+    index = 5, voices g = 5 * 128 + v; sampled voices vs the oracle."""
+    import seeded_inputs as si
+    syn = pkg.Synth(seconds=4.0, max_batch=128)
+    audio, params = syn.fm_render(5, 5, 128)
+    syn.sync()
+    cfg = oracle_mod.default_config(seconds=4.0)
+    a = audio.cpu().numpy()
+    p = params.cpu().numpy()
+    assert np.all(np.isfinite(a))
+    for v in si.sample_voices(5, 128, 5):
+        u = oracle_mod.fm_draw_params(5, 5 * 128 + int(v))
+        assert np.array_equal(p[v], u.astype(np.float32)), v
+        ref = oracle_mod.fm_render_voice(cfg, u)
+        err = float(np.max(np.abs(a[v] - ref)))
+        assert err <= _bar(u), (int(v), err, _levels(u))
+    syn.close()

@@ -89,3 +89,33 @@ def test_normalized_argument_errors(env):
     assert L.synth_render_normalized(syn.handle, 0, 0, 0, None, None, None, 1e-3, None, None,
                                      None) == pkg.SYNTH_OK
     syn.close()
+
+
+def test_normalized_full_size_sampled(env, oracle_mod):
+    """The normalised throughput workload: batch 128 x 4 s drawn voices, seed =
+    batch index = 21, threshold 1e-3; peaks and flags of all voices are
+    checked through the unnormalised render, sampled voices against the
+    oracle's render + peak_normalize."""
+    torch, pkg = env
+    syn = pkg.Synth(seconds=4.0, max_batch=128)
+    a, p, peak, silent = syn.render_normalized(21, 21, 128, threshold=TAU)
+    raw, _ = syn.render(21, 21, 128)
+    syn.sync()
+    raw_peak = raw.abs().amax(dim=1)
+    assert torch.equal(peak, raw_peak)
+    assert torch.equal(silent.bool(), ~((raw_peak >= TAU) & (raw_peak > 0)))
+    rows = si.sample_voices(21, 128, 6)
+    cfg = oracle_mod.default_config(seconds=4.0)
+    ref_a, ref_p = oracle_mod.render_batch(cfg, 21, 21, 128, voices=rows)
+    ref_n, ref_peak, ref_silent = oracle_mod.peak_normalize(ref_a[rows], TAU)
+    assert np.array_equal(p.cpu().numpy()[rows], ref_p[rows])
+    peak_r = peak.cpu().numpy()[rows]
+    a_r = a.cpu().numpy()[rows]
+    assert np.max(np.abs(peak_r - ref_peak)) <= 2e-4
+    for i in range(len(rows)):
+        if ref_silent[i]:
+            assert np.max(np.abs(a_r[i] - ref_a[rows[i]])) <= 2e-4
+        else:
+            err = np.max(np.abs(a_r[i] - ref_n[i]))
+            assert err <= 4e-4 / ref_peak[i] + 1e-6, (int(rows[i]), err, ref_peak[i])
+    syn.close()

@@ -68,3 +68,21 @@ def test_normalized_and_unsupported_paths_at_fractional_rate(pkg):
     assert L.synth_render_plain_workspace_size(syn.handle, 8, ctypes.byref(b)) == pkg.SYNTH_ERR_UNSUPPORTED
     assert L.synth_render_backward_workspace_size(syn.handle, 8, ctypes.byref(b)) == pkg.SYNTH_ERR_UNSUPPORTED
     syn.close()
+
+
+def test_fractional_rate_full_size_sampled(pkg, oracle_mod):
+    """The fractional-rate throughput workload: batch 128 x 4 s at 16 kHz with
+    the 441 Hz control rate, seed = batch index; sampled voices vs the oracle."""
+    import seeded_inputs as si
+    syn = pkg.Synth(seconds=4.0, max_batch=128, sample_rate=16000.0, control_rate=441.0)
+    audio, params = syn.render(9, 9, 128)
+    syn.sync()
+    rows = si.sample_voices(9, 128, 6)
+    cfg = oracle_mod.default_config(seconds=4.0, sample_rate=16000.0, control_rate=441.0)
+    ref_a, ref_p = oracle_mod.render_batch(cfg, 9, 9, 128, voices=rows)
+    assert np.array_equal(params.cpu().numpy()[rows], ref_p[rows])
+    a = audio.cpu().numpy()[rows]
+    assert np.all(np.isfinite(a))
+    err = float(np.max(np.abs(a - ref_a[rows])))
+    assert err <= TOL, f"max-abs error {err:.3e}"
+    syn.close()

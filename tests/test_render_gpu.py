@@ -216,3 +216,28 @@ def test_render_batches_equals_separate_renders(torch_cuda):
     L = pkg.lib()
     assert L.synth_render_batches(syn.handle, 0, 1, 0, 8, 6, None, a.data_ptr(), None, None) == pkg.SYNTH_ERR_ARG
     syn.close()
+
+
+def test_render_batches_full_size_sampled(torch_cuda, oracle_mod):
+    """The throughput launch itself: 8 consecutive batches of 128 x 4 s in one
+    synth_render_batches call, batch k with seed = batch index = 16 + k. A
+    sample of voices of the first and last batch is checked against the
+    oracle (parameters bit-exact, audio within the 2e-4 bar)."""
+    import paper_2104_12922_gb300 as pkg
+    torch = torch_cuda
+    syn = pkg.Synth(seconds=4.0, max_batch=1024)
+    bi = 16
+    audio, params = syn.render_batches(bi, 1, bi, 128, 8)
+    syn.sync()
+    assert audio.shape == (1024, syn.num_samples)
+    for k in (0, 7):
+        rows = si.sample_voices(bi + k, 128, 6)
+        idx = torch.as_tensor(k * 128 + rows, device=audio.device, dtype=torch.long)
+        a = audio.index_select(0, idx).cpu().numpy()
+        p = params.index_select(0, idx).cpu().numpy()
+        ref_a, ref_p = _oracle_batch(oracle_mod, 4.0, bi + k, bi + k, 128, voices=rows)
+        assert np.array_equal(p, ref_p[rows]), f"batch {k}: parameter draw must be bit-exact"
+        assert np.all(np.isfinite(a))
+        err = float(np.max(np.abs(a - ref_a[rows])))
+        assert err <= TOL, f"batch {k}: max-abs error {err:.3e}"
+    syn.close()
