@@ -29,7 +29,7 @@ constexpr uint32_t kStreamFmParam = 2;
 
 struct FmConst {
   int64_t N, rate_a, rate_b;  // samples; R = rate_a / rate_b samples per control interval
-  float inv_cr;               // 1 / control rate
+  ff inv_cr;                  // 1 / control rate
   int max_pts;                // control points a chunk can span
   ff log2_440_over_sr;        // log2(440 / SR)
   alignas(16) FFTables T;     // float-float exp2 tables
@@ -55,18 +55,44 @@ __host__ __device__ inline void fm_range(int p, float& lo, float& hi, int& c) {
 }
 
 // The Voice's ADSR (attack (t/a)^alpha, decay to s, release from the level at
-// note-off d), in FP32; zero-length sections are skipped.
-__device__ __forceinline__ float fm_gate_on(float t, float a, float dc, float s, float alpha) {
-  if (t < a) return powf(t / a, alpha);
-  if (t < a + dc) return 1.f - (1.f - s) * powf((t - a) / dc, alpha);
-  return s;
+// note-off d); zero-length sections are skipped. The section lengths, the
+// note-on duration and the time are float-float, and so are the section
+// choice and the time into the section (t - a, t - d): the argument x of
+// x^alpha then carries a relative error of a few float roundings wherever
+// the section falls in the note. (In FP32 the time alone is off by up to
+// t 2^-24 s, which near a section start with alpha < 1 -- where x^alpha is
+// steep -- moves the envelope by 1e-5 and more.) x^alpha itself is FP32.
+struct FmEnv {
+  ff a, dc, r, d;  // attack, decay, release, note-on duration (s)
+  float s, alpha;  // sustain level, curve exponent
+};
+__device__ __forceinline__ float fm_gate_on(ff t, const FmEnv& E) {
+  if (ff_lt(t, E.a)) return powf(ff_to_float(t) / ff_to_float(E.a), E.alpha);
+  const ff ta = ff_sub(t, E.a);
+  if (ff_lt(ta, E.dc)) return 1.f - (1.f - E.s) * powf(ff_to_float(ta) / ff_to_float(E.dc), E.alpha);
+  return E.s;
 }
-__device__ __forceinline__ float fm_adsr(float t, const float* o, float d) {
-  if (t < d) return fm_gate_on(t, o[2], o[3], o[4], o[6]);
-  const float level = fm_gate_on(d, o[2], o[3], o[4], o[6]);
-  const float tau = t - d;
-  if (tau < o[5]) return level * (1.f - powf(tau / o[5], o[6]));
-  return 0.f;
+__device__ __forceinline__ float fm_adsr(ff t, const FmEnv& E) {
+  if (ff_lt(t, E.d)) return fm_gate_on(t, E);
+  const ff tau = ff_sub(t, E.d);
+  if (!ff_lt(tau, E.r)) return 0.f;
+  return fm_gate_on(E.d, E) * (1.f - powf(ff_to_float(tau) / ff_to_float(E.r), E.alpha));
+}
+
+// Operator i's envelope constants from its normalized parameters uo (ratio,
+// level, attack, decay, sustain, release, alpha) and the duration parameter
+// ud: attack and decay 2 u^2, release 5 u^2 (u^2 exact as a float-float
+// product), duration 4 u, sustain u; alpha = 0.1 + 5.9 u^2 as in the
+// parameter map.
+__device__ __forceinline__ FmEnv fm_env(const float* uo, float ud) {
+  FmEnv E;
+  E.a = ff_mul_f(two_prod(uo[2], uo[2]), 2.f);
+  E.dc = ff_mul_f(two_prod(uo[3], uo[3]), 2.f);
+  E.r = ff_mul_f(two_prod(uo[5], uo[5]), 5.f);
+  E.d = ff_make(4.f * ud);
+  E.s = uo[4];
+  E.alpha = fmaf(6.f - 0.1f, uo[6] * uo[6], 0.1f);
+  return E;
 }
 
 struct __align__(16) FmSmem {
@@ -154,13 +180,11 @@ __global__ void __launch_bounds__(kFmThreads) fm_render_kernel(const __grid_cons
   const int64_t k_lo = s0 * fc.rate_b / fc.rate_a;
   const int64_t k_hi = (s1 - 1) * fc.rate_b / fc.rate_a + 1;
   const int npts = (int)(k_hi - k_lo + 1);
-  const float inv_cr = fc.inv_cr;
-  const float dur = S.y[1];
   for (int j = tid; j < npts; j += kFmThreads) {
     const int64_t k = k_lo + j;
-    const float t = (float)k * inv_cr;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) env[i * max_pts + j] = fm_adsr(t, S.y + 2 + 7 * i, dur);
+    const ff t = ff_mul_f(fc.inv_cr, (float)k);  // k < 2^24: exact in a float
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) env[i * max_pts + j] = fm_adsr(t, fm_env(S.u + 2 + 7 * i, S.u[1]));
     const int64_t sk = (k * fc.rate_a + fc.rate_b - 1) / fc.rate_b;
     sst[j] = (int)(sk - s0);
     fr0[j] = (float)(sk * fc.rate_b - k * fc.rate_a) / (float)fc.rate_a;
@@ -238,7 +262,7 @@ cudaError_t launch_fm_render(const VoiceConst& vc, uint64_t seed, uint64_t batch
   fc.N = vc.n_samples;
   fc.rate_a = vc.rate_a;
   fc.rate_b = vc.rate_b;
-  fc.inv_cr = (float)(1.0 / vc.control_rate);
+  fc.inv_cr = ff_from_double(1.0 / vc.control_rate);
   fc.log2_440_over_sr = vc.log2_440_over_sr;
   fc.T = vc.T;
   fc.max_pts = (int)((int64_t)kFmChunk * vc.rate_b / vc.rate_a) + 3;
