@@ -16,14 +16,15 @@ namespace synth {
 // cap, after which it is the constant 1/2. The interval is therefore at most
 // two pieces, A for j < jc and B for j >= jc, each either geometric (first
 // increment c, ratio e^x) or linear (constant increment c).
-struct SegVco {
+struct __align__(16) SegVco {
   float phase0;  // phase in cycles at the interval's first sample, in [0, 1)
   float cA;      // first increment of piece A
   float cB;      // first increment of piece B
   float LB;      // phase advanced over piece A (cycles) = local phase where B starts
   float x;       // log of the per-sample increment ratio
-  float E1;      // expm1(x)
   float invE;    // 1 / expm1(x)
+  float q2, q3;  // 1 + r and 1 + r + r^2 with r = e^x (a quad's phase steps, in units of
+                 // its first increment)
   int jc_flags;  // jc | (A linear) << 16 | (B linear) << 17 | (A capped) << 18 | (B capped) << 19
 };
 
@@ -65,8 +66,10 @@ constexpr double kLn2 = 0.69314718055994530942;
 
 // Phases (cycles, wrapped to [-1/2, 1/2]) of samples j0..j0+3 of an interval.
 // Inside one piece the phase of sample j0 + i is base + g e_i: linear pieces
-// have g = c and e_i = i; geometric pieces phase0 + L + (c/E)(r^(d0+i) - 1)
-// = [phase0 + L + (c/E) E0] + (c/E)(1 + E0) expm1(i x), E0 = expm1(d0 x).
+// have g = c and e_i = i; geometric pieces (E = expm1(x), r = e^x)
+// phase0 + L + (c/E)(r^(d0+i) - 1) = [phase0 + L + (c/E) E0] + c r^d0 q_i
+// with E0 = expm1(d0 x), c r^d0 = c + c E0 and q_i = (r^i - 1)/(r - 1) =
+// 1 + r + ... + r^(i-1): q_1 = 1 and the interval's q_2, q_3.
 // The base is wrapped once (exactly), so each sample adds a term below
 // 2 cycles to a number below 1/2 and wraps again.
 // With kWrap = false the phases are left in (-1/2, 2) (the wrapped base plus
@@ -90,10 +93,10 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
       const float E0 = expm1_phase((float)d0 * s.x);
       const float cE = c * s.invE;
       base = s.phase0 + fmaf(cE, E0, L);
-      g = fmaf(cE, E0, cE);
-      e1 = s.E1;
-      e2 = e1 * (2.f + e1);
-      e3 = fmaf(e1, 1.f + e2, e2);
+      g = fmaf(c, E0, c);
+      e1 = 1.f;
+      e2 = s.q2;
+      e3 = s.q3;
     }
     base -= rintf(base);
     ph[0] = base;

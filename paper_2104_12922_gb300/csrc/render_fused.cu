@@ -49,9 +49,15 @@ struct __align__(16) Smem {
     ff env[6][P];            // the 6 ADSRs at the control points (steps 2-3)
     struct {
       SegVco seg[2][TI];     // VCO interval descriptions (steps 4-5)
-      int sst[P];            // fractional R: first sample of each interval (tile-relative),
+      union {
+        float4 aslope[TI];   // R a multiple of 4: amplitude change per sample over each
+                             // interval, (ampv[k + 1] - ampv[k]) / R
+        struct {
+          int sst[P];        // fractional R: first sample of each interval (tile-relative),
                              // sst[nseg] = the tile's sample count
-      float u0f[TI];         // fractional R: fraction of each interval's first sample
+          float u0f[TI];     // fractional R: fraction of each interval's first sample
+        };
+      };
     };
   };
   float4 sq[TI];             // square-saw constants per interval: k2, c1, c2 (square_saw_sc)
@@ -72,6 +78,8 @@ struct __align__(16) Smem {
   int tile;
   unsigned int epoch;
 };
+// static shared memory is capped at 48 KB per block; 4 blocks per SM fit
+static_assert(sizeof(Smem) <= 48 * 1024, "shared-memory layout exceeds the static limit");
 
 // Exclusive block scan of two fixed-point values (exact, any order). After
 // the barrier inside, warp 0 receives the block totals in tot0/tot1 (all
@@ -413,6 +421,10 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       } else {
         const int64_t rem = N - (int64_t)(k0 + tid) * R;
         const int Rk = rem < R ? (int)rem : R;
+        {  // the amplitudes' change per sample over this interval (linear upsampling)
+          const float4 a = s.ampv[tid], b = s.ampv[tid + 1];
+          s.aslope[tid] = make_float4((b.x - a.x) * invR, (b.y - a.y) * invR, (b.z - a.z) * invR, 0.f);
+        }
 #pragma unroll 1
         for (int o = 0; o < 2; ++o) {
           float inc;
@@ -551,24 +563,25 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
           vco_quad<false>(s.seg[0][si], j0, ps);
           vco_quad<false>(s.seg[1][si], j0, pq);
           const float4 sq = s.sq[si];
-          const float4 A = s.ampv[si], B = s.ampv[si + 1];
+          const float4 A = s.ampv[si], D = s.aslope[si];
           const uint4 nz = philox4x32_10(
               make_uint4((uint32_t)g, (uint32_t)(g >> 32), q_t + (uint32_t)(off >> 2), kStreamNoise),
               key);
           const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
-          const float d0 = B.x - A.x, d1 = B.y - A.y, d2 = B.z - A.z;
-          const float fj0 = (float)j0 * invR;
+          // amplitudes at the quad's first sample, then one step of the slope per sample
+          const float fj0 = (float)j0;
+          const float a0x = fmaf(fj0, D.x, A.x), a0y = fmaf(fj0, D.y, A.y), a0z = fmaf(fj0, D.z, A.z);
           float out4[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const float fj = fmaf((float)i, invR, fj0);
             const float x_sin = __sinf(kTwoPiF * ps[i]);
             float sn, cs;
             __sincosf(kTwoPiF * pq[i], &sn, &cs);
             const float x_sq = square_saw_sc(sn, cs, sq.x, sq.y, sq.z);
             const float x_nz = fmaf((float)(nw[i] >> 8), 0x1p-23f, -1.f);  // 2u - 1, exact
-            out4[i] = fmaf(fmaf(fj, d0, A.x), x_sin,
-                           fmaf(fmaf(fj, d1, A.y), x_sq, fmaf(fj, d2, A.z) * x_nz));
+            const float fi = (float)i;
+            out4[i] = fmaf(fmaf(fi, D.x, a0x), x_sin,
+                           fmaf(fmaf(fi, D.y, a0y), x_sq, fmaf(fi, D.z, a0z) * x_nz));
           }
           if (vec_ok && off + 3 < n_t) {
             // streaming stores, except when the scaling pass reads the audio
