@@ -104,8 +104,8 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
     ph[1] = kWrap ? p1 - rintf(p1) : p1;
     ph[2] = kWrap ? p2 - rintf(p2) : p2;
     ph[3] = kWrap ? p3 - rintf(p3) : p3;
-  } else {  // the quad straddles the piece boundary
-#pragma unroll
+  } else {  // the quad straddles the piece boundary (rare): one rolled loop
+#pragma unroll 1
     for (int i = 0; i < 4; ++i) {
       const int j = j0 + i;
       const bool in_b = j >= jc;
@@ -115,7 +115,11 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
       const int d = j - (in_b ? jc : 0);
       const float loc = lin ? fmaf(c, (float)d, L) : fmaf(c * s.invE, expm1_phase((float)d * s.x), L);
       const float p = s.phase0 + loc;
-      ph[i] = p - rintf(p);
+      const float w = p - rintf(p);
+      if (i == 0) ph[0] = w;
+      if (i == 1) ph[1] = w;
+      if (i == 2) ph[2] = w;
+      if (i == 3) ph[3] = w;
     }
   }
 }
