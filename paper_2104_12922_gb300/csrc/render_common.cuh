@@ -75,7 +75,23 @@ constexpr double kLn2 = 0.69314718055994530942;
 // With kWrap = false the phases are left in (-1/2, 2) (the wrapped base plus
 // at most three increments of at most 1/2), which the sine unit takes as
 // they are after scaling by 2 pi.
-template <bool kWrap = true>
+// Wrapped phase of sample j of an interval (pieces split at jc), evaluated on
+// its own.
+__device__ __forceinline__ float vco_phase_at(const SegVco& s, int jc, int j) {
+  const bool in_b = j >= jc;
+  const float L = in_b ? s.LB : 0.f;
+  const float c = in_b ? s.cB : s.cA;
+  const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
+  const int d = j - (in_b ? jc : 0);
+  const float loc = lin ? fmaf(c, (float)d, L) : fmaf(c * s.invE, expm1_phase((float)d * s.x), L);
+  const float p = s.phase0 + loc;
+  return p - rintf(p);
+}
+
+// kRolled: a quad that straddles the piece boundary is evaluated by a rolled
+// loop (one copy of the per-sample code: a smaller loop body where such quads
+// are rare, i.e. whenever quads align with the intervals); unrolled otherwise.
+template <bool kWrap = true, bool kRolled = true>
 __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
   const int jc = s.jc_flags & 0xffff;
   if (j0 + 3 < jc || j0 >= jc) {
@@ -104,23 +120,18 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
     ph[1] = kWrap ? p1 - rintf(p1) : p1;
     ph[2] = kWrap ? p2 - rintf(p2) : p2;
     ph[3] = kWrap ? p3 - rintf(p3) : p3;
-  } else {  // the quad straddles the piece boundary (rare): one rolled loop
+  } else if (kRolled) {  // the quad straddles the piece boundary: one rolled loop
 #pragma unroll 1
     for (int i = 0; i < 4; ++i) {
-      const int j = j0 + i;
-      const bool in_b = j >= jc;
-      const float L = in_b ? s.LB : 0.f;
-      const float c = in_b ? s.cB : s.cA;
-      const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
-      const int d = j - (in_b ? jc : 0);
-      const float loc = lin ? fmaf(c, (float)d, L) : fmaf(c * s.invE, expm1_phase((float)d * s.x), L);
-      const float p = s.phase0 + loc;
-      const float w = p - rintf(p);
+      const float w = vco_phase_at(s, jc, j0 + i);
       if (i == 0) ph[0] = w;
       if (i == 1) ph[1] = w;
       if (i == 2) ph[2] = w;
       if (i == 3) ph[3] = w;
     }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ph[i] = vco_phase_at(s, jc, j0 + i);
   }
 }
 

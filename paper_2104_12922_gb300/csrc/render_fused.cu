@@ -500,11 +500,11 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
         const int b1 = s.sst[si + 1];
         const bool two = si + 1 < nseg && rel0 + 3 >= b1;
         float psA[4], pqA[4], psB[4], pqB[4];
-        vco_quad<false>(s.seg[0][si], rel0 - s.sst[si], psA);
-        vco_quad<false>(s.seg[1][si], rel0 - s.sst[si], pqA);
+        vco_quad<false, false>(s.seg[0][si], rel0 - s.sst[si], psA);
+        vco_quad<false, false>(s.seg[1][si], rel0 - s.sst[si], pqA);
         if (two) {
-          vco_quad<false>(s.seg[0][si + 1], rel0 - b1, psB);
-          vco_quad<false>(s.seg[1][si + 1], rel0 - b1, pqB);
+          vco_quad<false, false>(s.seg[0][si + 1], rel0 - b1, psB);
+          vco_quad<false, false>(s.seg[1][si + 1], rel0 - b1, pqB);
         }
         const uint4 nz = philox4x32_10(
             make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(q_lo + q), kStreamNoise), key);
@@ -560,8 +560,9 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
         const int off = si * R + j0;
         if (off < n_t) {
           float ps[4], pq[4];
-          vco_quad<false>(s.seg[0][si], j0, ps);
-          vco_quad<false>(s.seg[1][si], j0, pq);
+          // (the peak variant keeps the unrolled straddle code: measured faster there)
+          vco_quad<false, !kPeak>(s.seg[0][si], j0, ps);
+          vco_quad<false, !kPeak>(s.seg[1][si], j0, pq);
           const float4 sq = s.sq[si];
           const float4 A = s.ampv[si], D = s.aslope[si];
           const uint4 nz = philox4x32_10(
