@@ -14,9 +14,10 @@
 // b. The real spectrum follows from Z[k] and Z[1024 - k] (a lane shuffle):
 // X[k] = E[k] + W2048^k O[k] with E = (Z[k] + conj Z[1024-k]) / 2 and
 // O = (Z[k] - conj Z[1024-k]) / 2i. The 1/2 of E and O is folded into the
-// mel weights (a factor 1/4 on |X|^2). The window comes from the SFU cosine
-// and each mel weight from its band's two triangle lines, so the shared
-// memory traffic is the transform's own.
+// mel weights (a factor 1/4 on |X|^2). The window is a shared-memory table
+// each CTA fills once from the SFU cosine (evaluated per frame, the cosines
+// competed with the transform for registers and spilled), and each mel
+// weight comes from its band's two triangle lines.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -54,6 +55,7 @@ struct __align__(16) LmSmem {
   float buf[kWarpsLm][kBuf];    // per warp: transpose, then power spectrum, then bands
   float2 tw[32 * 32];
   float2 post[kHalf];
+  float2 hann[kHalf];           // Hann window at samples 2m, 2m + 1
   int2 band[kMelBands];
   float4 line[kMelBands];
 };
@@ -70,7 +72,10 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
                       __nv_bfloat16* __restrict__ features) {
   extern __shared__ __align__(16) unsigned char lm_raw[];
   LmSmem& S = *reinterpret_cast<LmSmem*>(lm_raw);
-  for (int j = threadIdx.x; j < kHalf; j += kThreadsLm) S.post[j] = __ldg(t.post + j);
+  for (int j = threadIdx.x; j < kHalf; j += kThreadsLm) {
+    S.post[j] = __ldg(t.post + j);
+    S.hann[j] = make_float2(hann2048(2 * j), hann2048(2 * j + 1));
+  }
   for (int j = threadIdx.x; j < 32 * 32; j += kThreadsLm) S.tw[j] = __ldg(t.tw + j);
   for (int j = threadIdx.x; j < kMelBands; j += kThreadsLm) {
     S.band[j] = __ldg(t.band + j);
@@ -119,9 +124,9 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
       // z[32 a + lane], windowed
 #pragma unroll
       for (int a = 0; a < 32; ++a) {
-        const float2 sv = s2[32 * a + lane];
-        re[a] = sv.x * hann2048(2 * (32 * a + lane));
-        im[a] = sv.y * hann2048(2 * (32 * a + lane) + 1);
+        const float2 sv = s2[32 * a + lane], w = S.hann[32 * a + lane];
+        re[a] = sv.x * w.x;
+        im[a] = sv.y * w.y;
       }
       fftw::dft<32, 0>(re, im);  // over a: Y[k1] in register bitrev<32>(k1)
       // twiddle W1024^(lane k1), then the transpose: real parts, then imaginary
