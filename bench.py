@@ -316,13 +316,15 @@ def fm_leg(pkg, torch, syn, stream, steps: int = 64):
 def generator_leg(pkg, torch, syn, stream, count: int = 8192):
     """Streaming synth1B1 generator: log-mel features and parameters of
     `count` train-split voices (4 s), rendered and transformed chunk by
-    chunk; CUDA events around one call per chunk size."""
-    model = pkg.ProposalModel(syn, max_batch=BATCH, seed=0)
+    chunk; CUDA events around one call per chunk size. Larger chunks fill
+    the GPU's last wave of render tiles better; smaller ones keep the chunk's
+    audio in L2 between the two kernels."""
+    model = pkg.ProposalModel(syn, max_batch=min(512, syn.max_batch), seed=0)
     dev = syn.device
     feats = torch.empty((count, model.feature_dim), dtype=torch.bfloat16, device=dev)
     params = torch.empty((count, 78), dtype=torch.float32, device=dev)
     out = {}
-    for chunk in (128, 64):
+    for chunk in (c for c in (512, 256, 128, 64) if c <= model.max_batch):
         with torch.cuda.stream(stream):
             model.stream_features(0, pkg.SPLIT_TRAIN, 0, 4 * chunk, chunk=chunk,
                                   features=feats[:4 * chunk], params=params[:4 * chunk],
