@@ -344,6 +344,17 @@ synth_status synth_render_noalloc(const synth_config* cfg, uint64_t seed, uint64
  * wait gave up, SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. */
 synth_status synth_sync(synth_handle h, void* stream);
 
+/* Failure-detection self-test (the library's own; the paper has no device
+ * waits). Runs, on `stream`, one look-back wait of the fused render against
+ * a window record that nothing ever publishes: the wait gives up after its
+ * bounded spin (well under a second) and records a timeout in the handle,
+ * exactly as a render whose earlier window never published would. Returns
+ * after the stream is idle; the next synth_sync(h, stream) then returns
+ * SYNTH_ERR_TIMEOUT and clears the record, and the handle stays usable.
+ * Allocates and frees a 2-record device buffer. Errors: SYNTH_ERR_STATE
+ * (invalid handle), SYNTH_ERR_CUDA. */
+synth_status synth_selftest_wait_timeout(synth_handle h, void* stream);
+
 /* Host-side range map of normalized parameters (Sec. 3.3): y[count][78]
  * from u[count][78] under the handle's nebula. Host pointers. */
 synth_status synth_params_to_human(synth_handle h, const float* u_host, double* y_host,

@@ -107,6 +107,8 @@ def lib() -> ctypes.CDLL:
         L.synth_split_voice.argtypes = [i32, u64]
         L.synth_split_voice.restype = u64
         L.synth_stream_features.argtypes = [vp, u64, i32, u64, ctypes.c_int64, i32, vp, vp, vp]
+        L.synth_selftest_wait_timeout.argtypes = [vp, vp]
+        L.synth_selftest_wait_timeout.restype = ctypes.c_int
         L.synth_status_string.argtypes = [ctypes.c_int]
         L.synth_status_string.restype = ctypes.c_char_p
         for name in ("synth_create", "synth_destroy", "synth_render", "synth_render_normalized",

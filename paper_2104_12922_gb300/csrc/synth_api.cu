@@ -12,6 +12,7 @@
 #include "gemm_tc.h"
 #include "internal.h"
 #include "mlp.h"
+#include "render_common.cuh"
 #include "spectral.h"
 #include "synth.h"
 
@@ -554,6 +555,38 @@ synth_status synth_sync(synth_handle h, void* stream) {
     return SYNTH_ERR_TIMEOUT;
   }
   return SYNTH_OK;
+}
+
+namespace {
+// One warp runs the fused render's look-back wait against a window record
+// whose flag is never set (probe[0], zeroed by the caller): the bounded wait
+// gives up and records kErrLookbackTimeout in the header, as a render whose
+// earlier window never published would. Lane 0 alone touches probe[0]
+// (window 0 of 1); probe[1] takes the (unused) result.
+__global__ void wait_probe_kernel(TileState* probe, ScratchHeader* hdr) {
+  unsigned long long e0, e1;
+  lookback_consume<unsigned long long>(probe, 1, 0, 1u, e0, e1, hdr);
+  if (threadIdx.x == 0) {
+    probe[1].agg[0][0] = e0;
+    probe[1].agg[0][1] = e1;
+  }
+}
+}  // namespace
+
+synth_status synth_selftest_wait_timeout(synth_handle h, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  TileState* probe = nullptr;
+  if (cudaMalloc(&probe, 2 * sizeof(TileState)) != cudaSuccess) return SYNTH_ERR_CUDA;
+  cudaError_t e = cudaMemsetAsync(probe, 0, 2 * sizeof(TileState), st);
+  if (e == cudaSuccess) {
+    wait_probe_kernel<<<1, 32, 0, st>>>(probe, hdr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const cudaError_t f = cudaFree(probe);
+  return (e == cudaSuccess && f == cudaSuccess) ? SYNTH_OK : SYNTH_ERR_CUDA;
 }
 
 synth_status synth_params_to_human(synth_handle h, const float* u_host, double* y_host,

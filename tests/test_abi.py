@@ -80,6 +80,7 @@ def test_calls_on_null_handle_return_status(pkg):
     L = pkg.lib()
     assert L.synth_render(None, 0, 0, 1, None, None, None, None) == pkg.SYNTH_ERR_STATE
     assert L.synth_sync(None, None) == pkg.SYNTH_ERR_STATE
+    assert L.synth_selftest_wait_timeout(None, None) == pkg.SYNTH_ERR_STATE
     assert L.synth_destroy(None) == pkg.SYNTH_ERR_ARG
 
 
