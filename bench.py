@@ -168,6 +168,24 @@ def profiled_traffic():
         return None
 
 
+def profiled_instructions():
+    """Warp instructions per launch of the fused kernel (8 batches) from the
+    committed ncu summary, or None when it was taken on other sources."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    if f"kernel_sources_sha256: `{fused_source_digest()}`" not in text:
+        return None
+    for ln in text.splitlines():
+        if ln.startswith("| `smsp__inst_executed.sum` |"):
+            try:
+                return float(ln.split("|")[2].split()[0])
+            except (IndexError, ValueError):
+                return None
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -596,7 +614,20 @@ def run_ours(args):
                 "unit": "Gsample/s", "frac": per_gpu_rate / alu_peak, "traffic": profiled_traffic(),
                 "peak_source": f"{num_sms} SMs x 16 transcendentals/clk x {sm_max:.0f} MHz / 4 per sample",
                 "hbm": {"achieved": per_gpu_rate * 4 / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": per_gpu_rate / hbm_peak_samples, "peak_source": peak_src}}
+                        "frac": per_gpu_rate / hbm_peak_samples, "peak_source": peak_src},
+                # the same bound counting 6 transcendentals per sample (tanh as
+                # exp2 + reciprocal, plus an exp2 of the pitch per sample)
+                "t6": {"peak": alu_peak * 4 / 6 / 1e9, "frac": per_gpu_rate / (alu_peak * 4 / 6)}}
+    inst = profiled_instructions()
+    if inst is not None:
+        # instruction issue: one warp instruction per clock per scheduler, 4 per SM
+        issue_peak = num_sms * 4 * sm_max * 1e6
+        per_batch = inst / GROUP
+        roofline["issue"] = {"warp_instructions_per_batch": per_batch,
+                             "achieved": per_batch / (ms_per_step / 1e3) / 1e9,
+                             "peak": issue_peak / 1e9, "unit": "G warp instructions/s",
+                             "frac": per_batch / (ms_per_step / 1e3) / issue_peak,
+                             "source": "smsp__inst_executed.sum of the committed ncu summary"}
     cpu = None
     if not args.no_cpu:
         cpu = cpu_oracle_baseline(args.cpu_seconds)
