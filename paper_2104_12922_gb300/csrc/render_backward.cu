@@ -195,13 +195,26 @@ __global__ void __launch_bounds__(kBT) bwd_samples(const __grid_constant__ Voice
     acc[5 * o + 3] += M2;
     acc[5 * o + 4] += F2;
   }
+  // butterfly reduce-scatter of the kStat (<= 32) sums over the warp: at
+  // step s a lane keeps half of its slots (the upper half when bit s of its
+  // lane index is set) and adds its partner's copy of that half; after 31
+  // shuffles lane i holds the warp's total of sum i (instead of 5 shuffles
+  // for each of the kStat sums)
+  static_assert(kStat <= 32, "one sum per lane");
+  float r[32];
 #pragma unroll
-  for (int i = 0; i < kStat; ++i) acc[i] = warp_sum(acc[i]);
-  if (lane == 0) {
-    float* out = stat + ((size_t)v * K + k) * kStat;
+  for (int i = 0; i < 32; ++i) r[i] = i < kStat ? acc[i] : 0.f;
 #pragma unroll
-    for (int i = 0; i < kStat; ++i) out[i] = acc[i];
+  for (int sh = 16; sh >= 1; sh >>= 1) {
+    const bool up = (lane & sh) != 0;
+#pragma unroll
+    for (int i = 0; i < sh; ++i) {
+      const float send = up ? r[i] : r[i + sh];
+      const float keep = up ? r[i + sh] : r[i];
+      r[i] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+    }
   }
+  if (lane < kStat) stat[((size_t)v * K + k) * kStat + lane] = r[0];
 }
 
 // ---------------------------------------------------------------------------
