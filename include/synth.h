@@ -190,7 +190,7 @@ synth_status synth_render_plain(synth_handle h, uint64_t seed, uint64_t batch_in
 /* Adjoint of synth_render (reverse mode): for every voice,
  * grad_params[v][p] = sum_n grad_audio[v][n] * d audio[v][n] / d u[v][p],
  * the derivative with respect to the normalized parameters u. The paper
- * lists differentiable modules as future work (Sec. 6); where the render
+ * lists differentiable modules as future work (Sec. 7); where the render
  * branches (envelope section, clamp, Nyquist cap, square LFO) this is the
  * derivative of the branch taken, and it is 0 at u = 0 for curve exponents
  * whose derivative is unbounded there.
@@ -224,7 +224,7 @@ synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, con
                              int32_t k, float alpha, void* stream);
 
 /* Multi-resolution log-magnitude STFT distance (the paper's multi-scale
- * spectrogram distance, Sec. 4.4) between x and y, both [batch][N] float
+ * spectrogram distance, Sec. 4, Table 2) between x and y, both [batch][N] float
  * device arrays of the handle's voice length (N >= 2048):
  *   L_v = sum over n_fft in {512, 1024, 2048} of the mean over (bins, frames)
  *         of |log(|X| + 1e-7) - log(|Y| + 1e-7)|,

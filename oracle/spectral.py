@@ -1,6 +1,6 @@
 """Spectral parts of the oracle -- TEST INFRASTRUCTURE (plain PyTorch CPU ops, FP64).
 
-* Multi-resolution log-magnitude STFT distance (Sec. 4.4 "multi-scale
+* Multi-resolution log-magnitude STFT distance (Sec. 4, Table 2 "multi-scale
   spectrogram" of the paper, after Engel et al. DDSP): periodic Hann window,
   hop n_fft/4, centred frames (reflect padding by n_fft/2),
   L = sum over n_fft of mean over (bins, frames) |log(|X| + eps) - log(|Y| + eps)|.
@@ -112,4 +112,4 @@ def mlp_loss_and_grads(x, target, weights, biases):
     y = mlp_forward(x, ws, bs)
     loss = ((y - _as64(target)) ** 2).mean()
     loss.backward()
-    return float(loss), [w.grad.numpy() for w in ws], [b.grad.numpy() for b in bs]
+    return float(loss.detach()), [w.grad.numpy() for w in ws], [b.grad.numpy() for b in bs]

@@ -2,7 +2,7 @@
 // grad_audio for the 78 normalized parameters of every voice.
 //
 // "Stress-tested differentiable modules" are future work in the paper
-// (Sec. 6); this is the reverse-mode derivative of the library's own render.
+// (Sec. 7); this is the reverse-mode derivative of the library's own render.
 // Where the forward takes a branch (envelope section, clamp, Nyquist cap,
 // square LFO) the derivative is that of the branch taken.
 //

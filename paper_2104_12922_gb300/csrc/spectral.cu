@@ -1,5 +1,5 @@
 // spectral.cu -- the multi-resolution log-magnitude STFT distance (the
-// paper's multi-scale spectrogram distance, Sec. 4.4) and its gradient with
+// paper's multi-scale spectrogram distance, Sec. 4, Table 2) and its gradient with
 // respect to the audio, on warp-level FP32 FFTs (fft_warp.cuh): periodic Hann
 // window, hop n/4, centred frames with reflect padding;
 // L_v = sum_n mean_(bins, frames) |log(|X| + eps) - log(|Y| + eps)|.

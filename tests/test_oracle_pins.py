@@ -194,6 +194,91 @@ def test_lfo_constant_rate_phase_is_exclusive_sum(oracle_mod):
     assert np.allclose(lfo[0], 2 * theta - 1, atol=1e-12)
 
 
+def _lfo_pins(l, F, D, ph0, weights, rate_env, amp_level=1.0):
+    """Pins for LFO ``l`` (0 or 1): frequency F, rate depth D, initial phase
+    ph0, shape weights (sin, tri, saw, rsaw, sqr); its rate ADSR is either a
+    constant 1 (``rate_env = "one"``) or the linear ramp t / 2 over the voice
+    (``"ramp"``: attack 2 s, alpha 1, note held); its amplitude ADSR is the
+    constant ``amp_level`` (zero attack and decay, sustain = amp_level)."""
+    rate_adsr = si.ADSR + 5 * (2 + 2 * l)
+    amp_adsr = si.ADSR + 5 * (3 + 2 * l)
+    pins = {si.DURATION: 10.0}
+    if rate_env == "one":
+        pins.update({rate_adsr + 0: 0.0, rate_adsr + 1: 0.0, rate_adsr + 2: 1.0})
+    else:
+        pins.update({rate_adsr + 0: 2.0, rate_adsr + 1: 0.0, rate_adsr + 2: 1.0})
+    pins.update({rate_adsr + 3: 0.0, rate_adsr + 4: 1.0,
+                 amp_adsr + 0: 0.0, amp_adsr + 1: 0.0, amp_adsr + 2: amp_level,
+                 amp_adsr + 3: 0.0, amp_adsr + 4: 1.0})
+    b = si.LFO + 8 * l
+    pins.update({b + 0: F, b + 1: D, b + 2: ph0})
+    pins.update({b + 3 + s: w for s, w in enumerate(weights)})
+    return pins
+
+
+def _circ(a, b):
+    d = np.abs(np.mod(a - b, 1.0))
+    return np.minimum(d, 1.0 - d)
+
+
+@pytest.mark.parametrize("lfo", [0, 1])
+def test_lfo_rate_modulation_by_its_rate_adsr(oracle_mod, lfo):
+    """rate_k = F + D ADSR_rate(t_k): with the rate ADSR a linear ramp
+    t_k / 2 the exclusive phase sum has the closed form
+    theta_k = ph0 / 2pi + k F / CR + D k (k - 1) / (4 CR^2), read back from
+    a saw LFO (lfo = 2 theta - 1). A wrong sign of D, the amplitude ADSR in
+    place of the rate ADSR, or the other LFO's ADSR fails it."""
+    F, D, ph0, CR = 3.25, 9.5, -1.3, 441.0
+    pins = _lfo_pins(lfo, F, D, ph0, (0, 0, 1, 0, 0), "ramp")
+    cfg = oracle_mod.default_config(seconds=1.0, nebula=_base_nebula(oracle_mod, pins))
+    _, out, _ = oracle_mod.control(cfg, np.full(78, 0.5))
+    k = np.arange(out.shape[1], dtype=np.float64)
+    theta = ph0 / (2 * math.pi) + k * F / CR + D * k * (k - 1) / (4 * CR * CR)
+    assert np.max(_circ((out[lfo] + 1) / 2, theta)) < 1e-10
+
+
+@pytest.mark.parametrize("lfo", [0, 1])
+@pytest.mark.parametrize("F,D,rate", [(6.0, 5.5, 11.5), (15.0, 12.0, 20.0), (5.0, -12.0, 0.0),
+                                      (20.0, -20.0, 0.0), (0.0, 20.0, 20.0)])
+def test_lfo_rate_is_clamped_to_0_20_hz(oracle_mod, lfo, F, D, rate):
+    """Constant rate ADSR 1: rate = clamp(F + D, 0, 20 Hz), so the saw's phase
+    is ph0/2pi + k rate / CR; above 20 Hz it runs at exactly 20 Hz, below 0
+    it stands still (no negative rates)."""
+    ph0, CR = 0.9, 441.0
+    pins = _lfo_pins(lfo, F, D, ph0, (0, 0, 1, 0, 0), "one")
+    cfg = oracle_mod.default_config(seconds=0.5, nebula=_base_nebula(oracle_mod, pins))
+    _, out, _ = oracle_mod.control(cfg, np.full(78, 0.5))
+    k = np.arange(out.shape[1], dtype=np.float64)
+    theta = ph0 / (2 * math.pi) + k * rate / CR
+    assert np.max(_circ((out[lfo] + 1) / 2, theta)) < 1e-11
+
+
+@pytest.mark.parametrize("lfo", [0, 1])
+def test_lfo_shape_mix_divides_by_weight_sum(oracle_mod, lfo):
+    """A standing LFO (rate 0) at phase p gives amp * sum_s w_s shape_s(p) /
+    sum_s w_s, with the shapes' own values at the quarter points: sin 1, 0,
+    -1; tri 0, 1, 0 (p = 1/4, 1/2, 3/4); saw 2p - 1; rsaw 1 - 2p; square +1
+    for p < 1/2 else -1. Weights summing to less than 1 are normalised too
+    (a lone weight of 0.1 gives the full shape), and the amplitude ADSR
+    scales the mix."""
+    shapes = {0.25: (1.0, 0.0, -0.5, 0.5, 1.0), 0.5: (0.0, 1.0, 0.0, 0.0, -1.0),
+              0.75: (-1.0, 0.0, 0.5, -0.5, -1.0)}
+    ph0_of = {0.25: math.pi / 2, 0.5: math.pi, 0.75: -math.pi / 2}
+    for weights in [(0.2, 0.5, 0.3, 0.7, 0.1), (0.1, 0.0, 0.0, 0.0, 0.0),
+                    (0.0, 0.05, 0.0, 0.0, 0.15), (1.0, 1.0, 1.0, 1.0, 1.0)]:
+        for p, vals in shapes.items():
+            pins = _lfo_pins(lfo, 0.0, 0.0, ph0_of[p], weights, "one", amp_level=0.6)
+            cfg = oracle_mod.default_config(seconds=0.05, nebula=_base_nebula(oracle_mod, pins))
+            _, out, _ = oracle_mod.control(cfg, np.full(78, 0.5))
+            want = 0.6 * sum(w * v for w, v in zip(weights, vals)) / sum(weights)
+            assert np.allclose(out[lfo], want, atol=1e-12), (weights, p)
+    # all weights 0: the LFO is silent
+    pins = _lfo_pins(lfo, 3.0, 0.0, 0.3, (0, 0, 0, 0, 0), "one")
+    cfg = oracle_mod.default_config(seconds=0.05, nebula=_base_nebula(oracle_mod, pins))
+    _, out, _ = oracle_mod.control(cfg, np.full(78, 0.5))
+    assert np.all(out[lfo] == 0.0)
+
+
 def test_mod_matrix_one_hot_routes_source(oracle_mod):
     """dest_j = sum_i W[i][j] src_i / max(1, sum_i W[i][j]): one-hot W[i][j]
     copies source i to destination j and leaves the others at 0; the
@@ -345,6 +430,56 @@ def test_square_saw_spot_values(oracle_mod):
         assert out[1] == pytest.approx(want1, abs=1e-9)
         if shape == 0.0:
             assert np.allclose(out[4:400], -out[0:396], atol=1e-9)
+
+
+def _square_saw_patch(oracle_mod, seconds, midi, tune, depth, ph0, shape, pitch_dest):
+    """Square-saw alone (levels 0, 1, 0; amplitude from ADSR0 = 1 through
+    destination 3); ADSR0 also routed with weight 1 to ``pitch_dest``."""
+    pins = _const_source_pins(3, {si.MIX: 0.0, si.MIX + 1: 1.0, si.MIX + 2: 0.0,
+                                  si.MIDI: midi, si.SQR: tune, si.SQR + 1: depth,
+                                  si.SQR + 2: ph0, si.SQR + 3: shape, si.SINE + 1: 0.0})
+    if pitch_dest is not None:
+        pins[si.mod_slot(0, pitch_dest)] = 1.0
+    return oracle_mod.default_config(seconds=seconds, nebula=_base_nebula(oracle_mod, pins))
+
+
+def _square_saw_closed_form(f, ph0, shape, n, sr=44100.0, kappa=None):
+    th = 2 * math.pi * np.mod(f * n / sr + ph0 / (2 * math.pi), 1.0)
+    if kappa is None:
+        kappa = min(50.0, 1.0 + sr / (8.0 * f))
+    return (np.tanh(kappa * np.sin(th)) / math.tanh(kappa)
+            * (1.0 + shape * np.cos(th)) / (1.0 + shape))
+
+
+@pytest.mark.parametrize("f,kappa", [(44100.0 / 16, 3.0), (44100.0 / 32, 5.0), (44100.0 / 64, 9.0),
+                                     (55.0, 50.0), (20.0, 50.0)])
+def test_square_saw_drive_follows_pitch_and_is_capped(oracle_mod, f, kappa):
+    """kappa = min(50, 1 + SR / (8 f)): 3, 5 and 9 at 16, 32 and 64 samples
+    per cycle, and the cap 50 at low pitch (55 Hz would give 101.2 and 20 Hz
+    276.6 without it). Checked against the closed form at constant pitch with
+    kappa stated numerically, over the first 2000 samples."""
+    midi = 69.0 + 12.0 * math.log2(f / 440.0)
+    for shape in (0.0, 0.4):
+        cfg = _square_saw_patch(oracle_mod, 0.05, midi, 0.0, 0.0, 0.0, shape, None)
+        out = oracle_mod.render_voice(cfg, np.full(78, 0.5), 0, 0)
+        n = np.arange(2000)
+        want = _square_saw_closed_form(f, 0.0, shape, n, kappa=kappa)
+        assert np.max(np.abs(out[:2000] - want)) < 1e-9, (f, shape)
+
+
+def test_square_saw_pitch_comes_from_destination_2(oracle_mod):
+    """The square-saw's pitch is midi + tune + depth * dest_2: with ADSR0 = 1
+    routed to destination 2 it sounds at 440 * 2^((midi + tune + depth - 69)/12)
+    (drive kappa from that pitch); routed to destination 0 (the sine's pitch)
+    instead it stays at midi + tune."""
+    n = np.arange(4410)
+    for midi, tune, depth, ph0 in [(60.0, 2.0, 7.0, 0.4), (81.0, -5.0, -13.5, -2.2)]:
+        for dest, m in [(2, midi + tune + depth), (0, midi + tune)]:
+            cfg = _square_saw_patch(oracle_mod, 0.1, midi, tune, depth, ph0, 0.3, dest)
+            out = oracle_mod.render_voice(cfg, np.full(78, 0.5), 0, 0)
+            f = 440.0 * 2 ** ((m - 69.0) / 12.0)
+            want = _square_saw_closed_form(f, ph0, 0.3, n)
+            assert np.max(np.abs(out - want)) < 1e-8, (midi, dest)
 
 
 def test_nyquist_cap(oracle_mod):

@@ -127,3 +127,82 @@ def test_mlp_gradients_match_finite_differences():
         wm[l][i, j] -= h
         fd = (sp.mlp_loss_and_grads(x, tgt, wp, bs)[0] - sp.mlp_loss_and_grads(x, tgt, wm, bs)[0]) / (2 * h)
         assert gw[l][i, j] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_mrstft_loss_of_a_scaled_copy():
+    """L(c x, x) = sum over the three resolutions of the mean over (bins,
+    frames) of |ln(c|X| + eps) - ln(|X| + eps)|, which is 3 |ln c| wherever
+    |X| >> eps. Broadband noise keeps every bin far above eps = 1e-7 (the
+    smallest |X| is ~1e-2, so the eps terms move the value by < 1e-4 of it).
+    Per voice, each voice's own factor; over the batch, the voices' mean.
+    Summing instead of averaging, a dropped resolution, |X|^2 instead of |X|
+    or a base-10 log all miss this value."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((3, 8192)) * 0.3
+    c = np.array([2.0, 0.25, 1.5])
+    per = sp.mrstft_loss(c[:, None] * x, x, per_voice=True).numpy()
+    assert np.allclose(per, 3 * np.abs(np.log(c)), rtol=1e-4)
+    whole = float(sp.mrstft_loss(c[:, None] * x, x))
+    assert whole == pytest.approx(3 * np.mean(np.abs(np.log(c))), rel=1e-4)
+    # one resolution alone: |ln c|
+    one = sp.mrstft_loss(2.0 * x, x, n_ffts=(1024,), per_voice=True).numpy()
+    assert np.allclose(one, math.log(2.0), rtol=1e-4)
+    # both silent: every bin at the floor, distance 0; one silent: the
+    # distance is the mean of ln((|X| + eps) / eps) over the other's bins
+    z = np.zeros((1, 4096))
+    assert float(sp.mrstft_loss(z, z)) == 0.0
+    y = x[:1, :4096]
+    want = 0.0
+    for n in (512, 1024, 2048):
+        mag = sp.stft(y, n).abs().numpy()
+        want += np.mean(np.log((mag + sp.MR_EPS) / sp.MR_EPS))
+    assert float(sp.mrstft_loss(y, z)) == pytest.approx(want, rel=1e-12)
+
+
+def test_mlp_forward_hand_set_two_layer_net():
+    """x = (1, -2); W1 = [[1, 0], [0, 1], [1, 1]], b1 = (0, 0, 0.5):
+    z1 = (1, -2, -0.5), ReLU zeroes the last two; W2 = [[2, 3, 4]], b2 = -1:
+    z2 = 1, sigmoid(1) = 1 / (1 + e^-1) = 0.7310585786300049. A ReLU on the
+    output (1.0), a sigmoid on the hidden layer, or a transposed W all give
+    other values. The MSE against a target t is (y - t)^2 averaged."""
+    w1 = np.array([[1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    b1 = np.array([0.0, 0.0, 0.5])
+    w2 = np.array([[2.0, 3.0, 4.0]])
+    b2 = np.array([-1.0])
+    y = sp.mlp_forward(np.array([[1.0, -2.0]]), [w1, w2], [b1, b2]).numpy()
+    assert y.shape == (1, 1)
+    assert y[0, 0] == pytest.approx(0.7310585786300049, abs=1e-15)
+    # a row with every hidden unit active: z1 = (0.5, 0.25, 1.25),
+    # z2 = 1 + 0.75 + 5 - 1 = 5.75
+    y2 = sp.mlp_forward(np.array([[0.5, 0.25]]), [w1, w2], [b1, b2]).numpy()[0, 0]
+    assert y2 == pytest.approx(1.0 / (1.0 + math.exp(-5.75)), abs=1e-15)
+    loss, _, _ = sp.mlp_loss_and_grads(np.array([[1.0, -2.0], [0.5, 0.25]]),
+                                       np.array([[0.5], [1.0]]), [w1, w2], [b1, b2])
+    want = ((0.7310585786300049 - 0.5) ** 2 + (y2 - 1.0) ** 2) / 2
+    assert loss == pytest.approx(want, rel=1e-12)
+
+
+def test_log_mel_floor_and_power_scale():
+    """Silence gives ln(1e-6) in every band and frame. A tone's mel energies
+    are a power spectrum: doubling the amplitude adds ln 4 in the bands that
+    hold it (far above the floor). Its absolute value follows from the DFT of
+    a bin-centred tone under the periodic Hann window (|X| = A n / 4 at its
+    bin, A n / 8 at the two neighbours, 0 elsewhere) weighted by the
+    filterbank, in frames clear of the reflect padding."""
+    silent = sp.log_mel(np.zeros((2, 8192))).numpy()
+    assert silent.shape == (2, 17, 128)
+    assert np.all(silent == math.log(1e-6))
+    sr, n = 44100.0, 2048
+    kbin, A = 139, 0.5                      # 2993 Hz, exactly on bin 139
+    t = np.arange(22050)
+    x = A * np.cos(2 * math.pi * kbin * t / n)
+    m1 = sp.log_mel(x[None, :]).numpy()[0]
+    m2 = sp.log_mel(2 * x[None, :]).numpy()[0]
+    fb = sp.mel_filterbank(n, 128, sr)
+    loud = fb[:, kbin] > 0
+    assert np.allclose(m2[10:30][:, loud] - m1[10:30][:, loud], math.log(4.0), atol=1e-9)
+    power = np.zeros(n // 2 + 1)
+    power[kbin] = (A * n / 4) ** 2
+    power[kbin - 1] = power[kbin + 1] = (A * n / 8) ** 2
+    want = np.log(fb @ power + 1e-6)
+    assert np.allclose(m1[10:30][:, loud], want[loud], atol=1e-9)
