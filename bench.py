@@ -52,7 +52,17 @@ def parse():
     ap.add_argument("--no-generator", action="store_true")
     ap.add_argument("--no-rates", action="store_true")
     ap.add_argument("--no-fm", action="store_true")
+    ap.add_argument("--no-proposal", action="store_true")
+    ap.add_argument("--no-sfu", action="store_true")
+    ap.add_argument("--no-mmd", action="store_true")
+    ap.add_argument("--no-cfg5", action="store_true")
+    ap.add_argument("--cfg5-train-steps", type=int, default=78125)  # 10 M voices
+    ap.add_argument("--cfg5-voices", type=int, default=4096)
+    ap.add_argument("--cfg5-refine", type=int, default=50)
+    ap.add_argument("--cfg5-judge", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--load-seconds", type=float, default=1.0,
+                    help="untimed load before and after the timed region (clock sampling)")
     return ap.parse_args()
 
 
@@ -194,17 +204,61 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_oracle_baseline(budget_s: float):
-    """The FP64 oracle as it stands on this host's cores: batches of 128 x 4 s
-    voices (seed = batch index) until about budget_s of wall time is spent."""
+def oracle_judge(finals, judge_voices: int, cores: int):
+    """Oracle re-synthesis of the proposal evaluation's fitted parameters:
+    for the first judge_voices evaluated voices, the FP64 oracle renders the
+    target (its drawn parameters, seed 0) and both fits (the refinement's
+    noise seed 1), and measures the FP64 MR-STFT distance of each fit."""
+    import numpy as np
+
     import oracle
+    from oracle import spectral as osp
+    cfg = oracle.default_config(seconds=SECONDS)
+    t0 = time.perf_counter()
+    d = {"proposal": [], "random": []}
+    done = 0
+    for i, bi in enumerate(finals["target_batch"]):
+        if done >= judge_voices:
+            break
+        n = min(len(finals["proposal"][i]), judge_voices - done)
+        rows = list(range(n))
+        target, _ = oracle.render_batch(cfg, 0, bi, BATCH, threads=cores, voices=rows)
+        for arm in ("proposal", "random"):
+            u = np.zeros((BATCH, 78))
+            u[:n] = np.clip(finals[arm][i][:n].numpy().astype(np.float64), 0.0, 1.0)
+            fit, _ = oracle.render_batch(cfg, 1, bi, BATCH, u_in=u, threads=cores, voices=rows)
+            d[arm].extend(osp.mrstft_loss(fit[:n], target[:n], per_voice=True).numpy().tolist())
+        done += n
+    return {"voices": done, "seconds": time.perf_counter() - t0,
+            "oracle_distance_mean": {k: float(np.mean(v)) for k, v in d.items()},
+            "proposal_better_fraction": float(np.mean(np.array(d["proposal"]) <
+                                                      np.array(d["random"])))}
+
+
+def cpu_oracle_baseline(budget_s: float, gpu, cfg5_finals=None, judge_voices: int = 256):
+    """The FP64 oracle as it stands on this host's cores: batches of 128 x 4 s
+    voices (seed = batch index) until about budget_s of wall time is spent;
+    one thread on the small configuration (16 voices x 4 s); and the
+    precision configuration (32 voices x 60 s, sine-only patch, constant
+    pitch and linear glide). The GPU renders the same voices beside it, so the
+    same oracle runs also give the GPU's max-abs error per configuration.
+    ``gpu(kind, ...)`` renders them through the library."""
+    import math
+
+    import numpy as np
+
+    import oracle
+    import seeded_inputs as si
     cfg = oracle.default_config(seconds=SECONDS)
     cores = oracle.hardware_threads()
     t0 = time.perf_counter()
     done = 0
     b = 0
+    first = None
     while True:
-        oracle.render_batch(cfg, b, b, BATCH, threads=cores)
+        audio, params = oracle.render_batch(cfg, b, b, BATCH, threads=cores)
+        if first is None:
+            first = (audio, params)
         done += 1
         b += 1
         el = time.perf_counter() - t0
@@ -214,13 +268,46 @@ def cpu_oracle_baseline(budget_s: float):
     mhz = done * BATCH * N_SAMPLES / el / 1e6
     # one thread on the small configuration: 16 voices x 4 s, seed 0, batch index 0
     t1 = time.perf_counter()
-    oracle.render_batch(cfg, 0, 0, 16, threads=1)
+    small, small_p = oracle.render_batch(cfg, 0, 0, 16, threads=1)
     el1 = time.perf_counter() - t1
+    errors = {}
+    ga, gp = gpu("render", 0, 0, 16)
+    errors["batch16x4s_all_voices"] = {"max_abs": float(np.abs(ga - small).max()),
+                                       "params_bit_exact": bool(np.array_equal(gp, small_p))}
+    ga, gp = gpu("render", 0, 0, BATCH)
+    errors["batch128x4s_batch0_all_voices"] = {
+        "max_abs": float(np.abs(ga - first[0]).max()),
+        "params_bit_exact": bool(np.array_equal(gp, first[1]))}
+    # precision configuration: 32 x 60 s, sine only, fixed-point carries
+    secs, nb32 = 60.0, 32
+    lo = 69.0 + 12.0 * math.log2(20.0 / 440.0)
+    hi = 69.0 + 12.0 * math.log2(8000.0 / 440.0)
+    nb = si.precision_patch_nebula(oracle.default_nebula(), secs, lo, hi, hi - lo)
+    pcfg = oracle.default_config(seconds=secs, nebula=nb)
+    prec = {}
+    t2 = time.perf_counter()
+    for glide in (False, True):
+        u, _ = si.precision_patch_params(31 if glide else 30, nb32, lo, hi, hi - lo, glide)
+        u = u.astype(np.float32).astype(np.float64)
+        ref, _ = oracle.render_batch(pcfg, 0, 0, nb32, u_in=u, threads=cores)
+        ga = gpu("precision", nb, u)
+        err = np.abs(ga - ref)
+        prec["glide" if glide else "constant"] = {
+            "max_abs": float(err.max()),
+            "drift_cycles_last_1s": float(err[:, -44100:].max() / (2 * math.pi))}
+    el2 = time.perf_counter() - t2
+    errors["precision_32x60s"] = prec
+    judge = oracle_judge(cfg5_finals, judge_voices, cores) if cfg5_finals else None
     return {"value": mhz, "unit": "MHz", "cores": cores, "kind": "oracle",
+            "proposal_judge": judge,
             "sample": f"{done} batch(es) of {BATCH} voices x {SECONDS:g} s (seed = batch index), "
                       f"{el:.1f} s wall on {cores} threads",
             "single_thread": {"value": 16 * N_SAMPLES / el1 / 1e6, "unit": "MHz", "cores": 1,
-                              "sample": f"16 voices x {SECONDS:g} s, seed 0, {el1:.2f} s wall"}}
+                              "sample": f"16 voices x {SECONDS:g} s, seed 0, {el1:.2f} s wall"},
+            "precision_config": {"value": 2 * nb32 * int(secs * SR) / el2 / 1e6, "unit": "MHz",
+                                 "cores": cores,
+                                 "sample": "32 voices x 60 s, constant pitch and glide"},
+            "gpu_vs_oracle": errors}
 
 
 def adjoint_leg(pkg, torch, dev, steps: int = 20):
@@ -261,6 +348,242 @@ def adjoint_leg(pkg, torch, dev, steps: int = 20):
             "config": "batch 64 x 1 s; per step: render, MR-STFT distance (n_fft 512/1024/2048, "
                       "hop n_fft/4) and its gradient, adjoint render, Adam on the 78 parameters",
             "steps": steps}
+
+
+def _events_ms(torch, fn, reps: int) -> float:
+    """Device milliseconds per call of fn (CUDA events on the current stream,
+    after one untimed call)."""
+    fn(0)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for r in range(reps):
+        fn(r)
+    end.record()
+    end.synchronize()
+    return start.elapsed_time(end) / reps
+
+
+def proposal_leg(pkg, torch, dev, peaks, steps: int = 20):
+    """The learned proposal's training step at batch 128 x 4 s (render on the
+    fly, log-mel features, the 4-layer network's forward, backward and Adam),
+    its parts, and the two large contractions alone on the tensor cores: the
+    first layer's forward product 128 x 1024 x 44160 (split-K) and its weight
+    gradient 1024 x 44160 x 128 (1,384 output tiles). Weights rotate over 3
+    copies (270 MB > L2) so that the timed products read them from HBM."""
+    B = 128
+    syn = pkg.Synth(seconds=SECONDS, max_batch=B)
+    model = pkg.ProposalModel(syn, max_batch=B, seed=0)
+    loss = torch.zeros(1, device=dev)
+    audio = torch.empty((B, N_SAMPLES), device=dev)
+    params = torch.empty((B, 78), device=dev)
+    feats = torch.empty((B, model.feature_dim), dtype=torch.bfloat16, device=dev)
+    for s in range(3):
+        model.train_step(0, s, B, 1e-4, loss=loss)
+    step_ms = _events_ms(torch, lambda r: model.train_step(0, 10 + r, B, 1e-4, loss=loss), steps)
+    render_ms = _events_ms(torch, lambda r: syn.render(r, r, B, out=audio, params_out=params), steps)
+    st0 = torch.cuda.current_stream().cuda_stream
+    feat_ms = _events_ms(torch, lambda r: pkg.lib().synth_model_features(
+        model.handle, audio.data_ptr(), B, feats.data_ptr(), st0), steps)
+    mlp_ms = _events_ms(torch, lambda r: model.train_features(feats, params, 1e-4, loss=loss), steps)
+    syn.sync()
+    L = pkg.lib()
+    import ctypes
+    k_in = model.feature_dim
+    w = [torch.randn(1024, k_in, device=dev).to(torch.bfloat16) for _ in range(3)]
+    x = torch.randn(B, k_in, device=dev).to(torch.bfloat16)
+    xt = x.t().contiguous()
+    dzt = torch.randn(1024, B, device=dev).to(torch.bfloat16)
+    c1 = torch.empty(B, 1024, device=dev)
+    c2 = torch.empty(1024, k_in, device=dev)
+    nb = ctypes.c_size_t()
+    L.synth_gemm_bf16_workspace_size(syn.handle, B, 1024, ctypes.byref(nb))
+    ws = torch.empty(nb.value // 4 + 1, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+    fwd_ms = _events_ms(torch, lambda r: L.synth_gemm_bf16_splitk(
+        syn.handle, x.data_ptr(), k_in, w[r % 3].data_ptr(), k_in, c1.data_ptr(), 1024, B, 1024,
+        k_in, 1.0, ws.data_ptr(), nb.value, st), 30)
+    dw_ms = _events_ms(torch, lambda r: L.synth_gemm_bf16(
+        syn.handle, dzt.data_ptr(), B, xt.data_ptr(), B, c2.data_ptr(), k_in, 1024, k_in, B, 1.0,
+        st), 30)
+    syn.sync()
+    model.close()
+    syn.close()
+    flop = 2.0 * B * 1024 * k_in
+    tf = peaks.get("bf16_tflops", 1900.0)
+    hbm = peaks["hbm_gbs"]
+    return {"ms_per_step": step_ms, "voices_per_s": B / (step_ms / 1e3),
+            "parts_ms": {"render": render_ms, "features": feat_ms, "network_train": mlp_ms},
+            "config": "batch 128 x 4 s voices rendered on the fly, log-mel 345 x 128, "
+                      "MLP 44160-1024-1024-1024-78 (bf16 tcgen05 GEMMs, FP32 Adam)",
+            "gemm_first_layer_forward": {
+                "shape": [B, 1024, k_in], "ms": fwd_ms, "tflops": flop / fwd_ms / 1e9,
+                "frac_tensor": flop / fwd_ms / 1e9 / tf,
+                "hbm_gbs": 2.0 * 1024 * k_in / fwd_ms / 1e6,
+                "frac_hbm": 2.0 * 1024 * k_in / fwd_ms / 1e6 / hbm,
+                "bound": "hbm (the bf16 weights, 90 MB, read once: 128 FLOP per weight byte "
+                         "is below the tensor/HBM ratio)"},
+            "gemm_first_layer_weight_grad": {
+                "shape": [1024, k_in, B], "ms": dw_ms, "tflops": flop / dw_ms / 1e9,
+                "frac_tensor": flop / dw_ms / 1e9 / tf,
+                "hbm_gbs": 4.0 * 1024 * k_in / dw_ms / 1e6,
+                "frac_hbm": 4.0 * 1024 * k_in / dw_ms / 1e6 / hbm,
+                "bound": "hbm (the FP32 gradient, 181 MB, written once)"},
+            "peaks": {"bf16_tflops": tf, "hbm_gbs": hbm}}
+
+
+def sfu_leg(pkg, torch, dev, num_sms: int):
+    """Measured special-function-unit rate: each probe (sin, cos, ex2, rcp,
+    tanh: the .approx forms the render issues) runs ~0.25 s of launches of
+    8 independent chains per thread on a full grid; CUDA events give the
+    time, nvidia-smi samples taken meanwhile the SM clock."""
+    L = pkg.lib()
+    import ctypes
+    sink = torch.zeros(256, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+    blocks, iters = num_sms * 8, 4096
+    ops = ctypes.c_int64()
+    out = {}
+    for name, op in (("sin", pkg.SFU_SIN), ("cos", pkg.SFU_COS), ("ex2", pkg.SFU_EX2),
+                     ("rcp", pkg.SFU_RCP), ("tanh", pkg.SFU_TANH)):
+        L.synth_sfu_probe(op, blocks, iters, sink.data_ptr(), ctypes.byref(ops), st)
+        torch.cuda.synchronize()
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        L.synth_sfu_probe(op, blocks, iters, sink.data_ptr(), None, st)
+        t1.record()
+        t1.synchronize()
+        reps = max(4, int(250.0 / max(t0.elapsed_time(t1), 1e-3)))
+        with ClockSampler(dev.index if dev.index is not None else 0) as cs:
+            time.sleep(0.05)
+            t0.record()
+            for _ in range(reps):
+                L.synth_sfu_probe(op, blocks, iters, sink.data_ptr(), None, st)
+            t1.record()
+            t1.synchronize()
+        ms = t0.elapsed_time(t1)
+        clk = cs.summary()
+        mhz = clk["sm_mhz"] or 0.0
+        rate = ops.value * reps / (ms / 1e3)
+        out[name] = {"gops_per_s": rate / 1e9, "sm_mhz": mhz,
+                     "per_clk_per_sm": rate / (num_sms * mhz * 1e6) if mhz else None}
+    return out
+
+
+def mmd_leg(pkg, torch, dev, num_sms: int, sm_mhz: float, per_corpus: int = 1024, n: int = 512,
+            trials: int = 100):
+    """Corpus similarity (Sec. 5): log-mel embeddings (44160 bf16 values per
+    4 s sound) of three corpora -- Voice sounds, 4-operator FM sounds, and
+    white noise (the Voice with only its noise oscillator sounding) -- the
+    pooled l1 distance matrix on the GPU, and MMD trials: within each corpus
+    (random n / n splits) and between each pair (n sounds from each)."""
+    import numpy as np
+
+    import seeded_inputs as si
+    B = 128
+    syn = pkg.Synth(seconds=SECONDS, max_batch=B)
+    model = pkg.ProposalModel(syn, max_batch=B, seed=0)
+    m = 3 * per_corpus
+    emb = torch.empty((m, model.feature_dim), dtype=torch.bfloat16, device=dev)
+    noise_u = np.full((B, 78), 0.5)
+    noise_u[:, si.MIX], noise_u[:, si.MIX + 1], noise_u[:, si.MIX + 2] = 0.0, 0.0, 1.0
+    noise_u[:, si.DURATION] = 1.0
+    noise_u[:, si.ADSR:si.ADSR + 5] = [0.0, 0.0, 1.0, 1.0, 1.0]
+    for src in range(4):
+        noise_u[:, si.mod_slot(src, 4)] = 0.0
+    noise_u[:, si.mod_slot(0, 4)] = 1.0
+    pin = torch.tensor(noise_u, dtype=torch.float32, device=dev)
+    for c in range(3):
+        for b in range(per_corpus // B):
+            if c == 0:
+                audio, _ = syn.render(7, b, B)
+            elif c == 1:
+                audio, _ = syn.fm_render(7, b, B)
+            else:
+                audio, _ = syn.render(7, b, B, params_in=pin)
+            lo = c * per_corpus + b * B
+            emb[lo:lo + B] = model.features(audio)
+    dist = torch.empty((m, m), dtype=torch.float32, device=dev)
+    pkg.l1_distances(syn, emb, out=dist)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for _ in range(3):
+        pkg.l1_distances(syn, emb, out=dist)
+    end.record()
+    end.synchronize()
+    dist_ms = start.elapsed_time(end) / 3
+    names = ("voice", "fm", "noise")
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    labels = np.concatenate([si.mmd_labels(100 + i, trials, [per_corpus] * 3, p, n)
+                             for i, p in enumerate(pairs)])
+    lab = torch.tensor(labels, device=dev)
+    start.record()
+    mm = pkg.mmd_trials(syn, dist, lab)
+    end.record()
+    end.synchronize()
+    trials_ms = start.elapsed_time(end)
+    mm = mm.cpu().numpy().reshape(len(pairs), trials)
+    syn.sync()
+    model.close()
+    syn.close()
+    dim = emb.shape[1]
+    pair_elems = m * (m + 1) / 2 * dim  # upper triangle incl. the diagonal tiles' halves
+    # FP32 pipe: 128 lanes per SM per clock, 2 instructions per element pair
+    peak = num_sms * 128 * sm_mhz * 1e6 / 2
+    return {"corpora": {nm: per_corpus for nm in names}, "n_per_set": n, "trials_per_pair": trials,
+            "embedding": "log-mel features (345 frames x 128 bands, bf16), l1 distance",
+            "mmd": {f"{names[a]}/{names[b]}": {"mean": float(mm[i].mean()),
+                                                "std": float(mm[i].std())}
+                    for i, (a, b) in enumerate(pairs)},
+            "distance_matrix": {"m": m, "ms": dist_ms,
+                                "g_pair_elements_per_s": pair_elems / (dist_ms / 1e3) / 1e9,
+                                "roofline": {"bound": "alu", "peak_g_per_s": peak / 1e9,
+                                             "frac": pair_elems / (dist_ms / 1e3) / peak,
+                                             "peak_source": f"{num_sms} SMs x 128 FP32 lanes x "
+                                                            f"{sm_mhz:.0f} MHz / 2 instructions "
+                                                            "per element pair"}},
+            "trials_ms": trials_ms}
+
+
+def proposal_eval_leg(pkg, torch, train_steps: int, voices: int, refine_steps: int):
+    """The learned proposal's evaluation (inverse synthesis): the network is
+    trained on train_steps batches of 128 voices (4 s) rendered on the fly,
+    then `voices` held-out test-split voices are fitted by refine_steps
+    adjoint refinement steps on the MR-STFT distance, once from the
+    network's proposal and once from random parameters. Reported: GPU time
+    of the training, the mean distance per step and GPU seconds (CUDA
+    events, the proposal's inference included) until each arm first
+    reaches a stated distance (the random-start arm's final one). The fitted
+    parameters go to the oracle leg, whose re-synthesis judges them."""
+    from paper_2104_12922_gb300 import proposal as pr
+    syn = pkg.Synth(seconds=SECONDS, max_batch=BATCH)
+    model = pkg.ProposalModel(syn, max_batch=BATCH, seed=0)
+    tr = pr.train(model, train_steps, BATCH, log_every=max(1, train_steps // 10))
+    res, finals = pr.evaluate(model, voices, refine_steps, batch=BATCH)
+    summ = pr.summarize(res)
+    model.close()
+    syn.close()
+    keep = [0, refine_steps // 10, refine_steps // 2, refine_steps]
+    arms = {}
+    for k in ("proposal", "random"):
+        a = summ[k]
+        arms[k] = {"distance_at_steps": {str(i): a["distance"][i] for i in keep},
+                   "steps_to_goal": a["steps_to_goal"],
+                   "gpu_s_to_goal": a["gpu_ms_to_goal"] / 1e3 if a["gpu_ms_to_goal"] else None,
+                   "gpu_s_all_steps": a["gpu_ms"][-1] / 1e3}
+    g_p, g_r = arms["proposal"]["gpu_s_to_goal"], arms["random"]["gpu_s_to_goal"]
+    return ({"train": {"voices": train_steps * BATCH, "steps": train_steps,
+                       "gpu_s": tr["gpu_ms"] / 1e3, "wall_s": tr["seconds"],
+                       "ms_per_step": tr["gpu_ms"] / train_steps,
+                       "loss_first_last": [tr["loss"][0][1], tr["loss"][-1][1]]},
+             "eval": {"voices": voices, "refine_steps": refine_steps,
+                      "goal_distance": summ["goal_distance"],
+                      "goal": "the random-start arm's mean MR-STFT distance after all steps",
+                      "arms": arms,
+                      "gpu_time_ratio_random_over_proposal": (g_r / g_p) if g_p and g_r else None}},
+            finals)
 
 
 def rates_leg(pkg, torch, stream, steps: int = 64):
@@ -456,7 +779,7 @@ def run_ours(args):
         graph.replay()  # untimed replay primes the graph
     stream.synchronize()
 
-    def timed(fn, clocks=False, preload=None):
+    def timed(fn, clocks=False, preload=None, postload=None):
         # graph replays and eager renders both go to `stream`, where the
         # events are recorded
         if ws > 1:
@@ -466,12 +789,15 @@ def run_ours(args):
         sampler = ClockSampler(local) if clocks else None
         if sampler:
             sampler.__enter__()
+            time.sleep(0.05)
         with torch.cuda.stream(stream):
             if preload is not None:  # untimed load so the clock samples see a busy GPU
                 preload()
             start.record(stream)
             fn()
             end.record(stream)
+            if postload is not None:
+                postload()
         end.synchronize()
         torch.cuda.synchronize()
         if sampler:
@@ -481,15 +807,23 @@ def run_ours(args):
             ms = max_over_ranks(ms, dist, dev)
         return ms, (sampler.summary() if sampler else None)
 
-    # untimed replays (about 1 s of load), then exactly K timed steps
+    # exactly K timed steps (one replay of the K-step graph), inside at least
+    # 1 s of identical untimed load before and after it, so that the clock
+    # samples taken meanwhile see the GPU as busy as the timed region does
     ms1, _ = timed(lambda: graph.replay())
-    n_pre = max(1, min(20, int(1000 / max(ms1, 1.0))))
+    n_load = max(1, int(1000.0 * args.load_seconds / max(ms1, 1e-3)) + 1)
 
-    def preload():
-        for _ in range(n_pre):
+    def load():
+        for _ in range(n_load):
             graph.replay()
 
-    ms, clocks = timed(lambda: graph.replay(), clocks=True, preload=preload)
+    ms, clocks = timed(lambda: graph.replay(), clocks=True, preload=load, postload=load)
+    # the same replays for at least 1 s, timed as a whole (a steady figure
+    # beside the exact-K one)
+    ms_long, clocks_long = timed(load, clocks=True)
+    sustained = {"value": n_load * K * BATCH * N_SAMPLES * ws / (ms_long / 1e3) / 1e6,
+                 "unit": "MHz", "ms_per_step": ms_long / (n_load * K), "steps": n_load * K,
+                 "seconds": ms_long / 1e3, "clocks": clocks_long}
     syn.sync(stream)
     steps = K
     samples_total = steps * BATCH * N_SAMPLES * ws
@@ -605,14 +939,19 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # transcendental issue bound: 4 per sample (sine sin; square-saw sin, cos,
-    # tanh) at 16 per clock per SM, at the maximum SM clock
-    alu_peak = num_sms * 16 * sm_max * 1e6 / 4
+    # transcendental bound: 4 per sample (sine sin; square-saw sin, cos, tanh)
+    # at the MUFU rate measured by the probe (sin.approx per clock per SM),
+    # at the maximum SM clock
+    sfu = None if args.no_sfu else sfu_leg(pkg, torch, dev, num_sms)
+    sfu_rate = (sfu or {}).get("sin", {}).get("per_clk_per_sm") or 16.0
+    alu_peak = num_sms * sfu_rate * sm_max * 1e6 / 4
     per_gpu_rate = BATCH * N_SAMPLES / (ms_per_step / 1e3)
     hbm_peak_samples = peaks["hbm_gbs"] * 1e9 / 4
     roofline = {"bound": "alu", "achieved": per_gpu_rate / 1e9, "peak": alu_peak / 1e9,
                 "unit": "Gsample/s", "frac": per_gpu_rate / alu_peak, "traffic": profiled_traffic(),
-                "peak_source": f"{num_sms} SMs x 16 transcendentals/clk x {sm_max:.0f} MHz / 4 per sample",
+                "peak_source": f"{num_sms} SMs x {sfu_rate:.2f} sin.approx/clk/SM "
+                               f"({'measured by the SFU probe' if sfu else 'assumed'}) x "
+                               f"{sm_max:.0f} MHz / 4 per sample",
                 "hbm": {"achieved": per_gpu_rate * 4 / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": per_gpu_rate / hbm_peak_samples, "peak_source": peak_src},
                 # the same bound counting 6 transcendentals per sample (tanh as
@@ -628,13 +967,36 @@ def run_ours(args):
                              "peak": issue_peak / 1e9, "unit": "G warp instructions/s",
                              "frac": per_batch / (ms_per_step / 1e3) / issue_peak,
                              "source": "smsp__inst_executed.sum of the committed ncu summary"}
+    def gpu_render(kind, *a):
+        """Renders through the library for the oracle leg's comparisons."""
+        import numpy as np
+        if kind == "render":
+            seed, bi, nb = a
+            audio, params = syn.render(seed, bi, nb)
+            syn.sync()
+            return audio.cpu().numpy(), params.cpu().numpy()
+        nebula, u = a
+        ps = pkg.Synth(seconds=60.0, max_batch=u.shape[0], nebula=nebula)
+        audio, _ = ps.render(0, 0, u.shape[0],
+                             params_in=torch.tensor(u, dtype=torch.float32, device=dev))
+        ps.sync()
+        out = audio.cpu().numpy()
+        ps.close()
+        return out
+
+    cfg5, finals = (None, None)
+    if not args.no_cfg5:
+        cfg5, finals = proposal_eval_leg(pkg, torch, args.cfg5_train_steps, args.cfg5_voices,
+                                         args.cfg5_refine)
     cpu = None
     if not args.no_cpu:
-        cpu = cpu_oracle_baseline(args.cpu_seconds)
+        cpu = cpu_oracle_baseline(args.cpu_seconds, gpu_render, finals, args.cfg5_judge)
     adjoint = None if args.no_adjoint else adjoint_leg(pkg, torch, dev)
     generator = None if args.no_generator else generator_leg(pkg, torch, syn, stream)
     rates = None if args.no_rates else rates_leg(pkg, torch, stream)
     fm = None if args.no_fm else fm_leg(pkg, torch, syn, stream)
+    proposal = None if args.no_proposal else proposal_leg(pkg, torch, dev, peaks)
+    mmd = None if args.no_mmd else mmd_leg(pkg, torch, dev, num_sms, sm_max)
     line = {"metric": METRIC, "value": value, "unit": "MHz", "n_gpus": ws, "steps": steps,
             "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
@@ -650,8 +1012,10 @@ def run_ours(args):
             "one_launch_per_batch": single,
             "plain": plain, "fused_over_plain": (value / plain["value"]) if plain else None,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "sustained": sustained, "sfu_probe": sfu,
             "adjoint": adjoint, "normalized": normalized, "generator": generator,
-            "fractional_rate": rates, "fm_voice": fm,
+            "fractional_rate": rates, "fm_voice": fm, "proposal_step": proposal,
+            "mmd_diversity": mmd, "proposal_eval": cfg5,
             "gpu_launches": (steps + GROUP - 1) // GROUP}
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -222,6 +222,19 @@ synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch
 synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, const void* b_dev,
                              int32_t ldb, float* c_dev, int32_t ldc, int32_t m, int32_t n,
                              int32_t k, float alpha, void* stream);
+/* The same product split along K when it has fewer 128-row output tiles than
+ * the GPU has SMs (e.g. the proposal network's first layer, 128 x 1024 x
+ * 44160): each SM takes a (tile, K-slice) pair and stores its FP32 partial
+ * product in workspace_dev; a second kernel adds the slices in slice order
+ * (deterministic) into C. workspace_dev: caller-owned device memory of at
+ * least synth_gemm_bf16_workspace_size(h, m, n) bytes for the full split
+ * (less splits less; NULL or 0 bytes: no split), 16-byte aligned.
+ * Errors as synth_gemm_bf16. */
+synth_status synth_gemm_bf16_workspace_size(synth_handle h, int32_t m, int32_t n, size_t* bytes);
+synth_status synth_gemm_bf16_splitk(synth_handle h, const void* a_dev, int32_t lda,
+                                    const void* b_dev, int32_t ldb, float* c_dev, int32_t ldc,
+                                    int32_t m, int32_t n, int32_t k, float alpha,
+                                    void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* Multi-resolution log-magnitude STFT distance (the paper's multi-scale
  * spectrogram distance, Sec. 4, Table 2) between x and y, both [batch][N] float
@@ -240,6 +253,32 @@ synth_status synth_mrstft_workspace_size(synth_handle h, int32_t batch, size_t* 
 synth_status synth_mrstft(synth_handle h, const float* x_dev, const float* y_dev, int32_t batch,
                           int32_t target_ready, double* loss_voice_dev, float* grad_x_dev,
                           void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Corpus similarity by maximum mean discrepancy (Sec. 5, the MMD equation):
+ * MMD(X, Y) = 1/(n n) sum over i, j < n of [2 d(x_i, y_j) - d(x_i, x_j)
+ * - d(y_i, y_j)], d an l1 distance between embeddings of the sounds (the
+ * library's embedding: the network input features of synth_model_features,
+ * 44160 bf16 values for a 4 s voice).
+ *
+ * synth_l1_distances: the pooled distance matrix dist_dev [m][m] FP32,
+ * dist[i][j] = sum_k |e_i[k] - e_j[k]| over the rows of emb_dev [m][ld]
+ * (bf16, row stride ld elements: a multiple of 8 and >= dim; 16-byte
+ * aligned base), FP32 sums on the CUDA cores; symmetric, zero diagonal.
+ * Errors: SYNTH_ERR_ARG (bad sizes or pointers), SYNTH_ERR_CUDA. */
+synth_status synth_l1_distances(synth_handle h, const void* emb_dev, int64_t ld, int32_t m,
+                                int32_t dim, float* dist_dev, void* stream);
+/* synth_mmd_trials: one MMD per trial over a pooled distance matrix
+ * dist_dev [m][m]. labels_dev [trials][m] int8: 0 puts sound j in X, 1 in Y,
+ * any other value leaves it out. mmd_dev [trials] FP64 receives
+ * 2 S_xy / (n_x n_y) - S_xx / n_x^2 - S_yy / n_y^2 (S_ab the sum of d over
+ * ordered pairs, diagonal included; the paper's statistic when n_x = n_y),
+ * or 0 when X or Y is empty. Sums in a fixed order: repeatable bit for bit.
+ * Diversity within a corpus: X, Y a random 50/50 partition of it; between
+ * corpora: n sounds drawn from each. m <= 49152.
+ * Errors: SYNTH_ERR_ARG, SYNTH_ERR_CUDA. */
+synth_status synth_mmd_trials(synth_handle h, const float* dist_dev, int32_t m,
+                              const int8_t* labels_dev, int32_t trials, double* mmd_dev,
+                              void* stream);
 
 /* One Adam step (Kingma & Ba; beta 0.9 / 0.999, eps 1e-8, step >= 1) on
  * normalized parameters u[count] with gradient grad[count] and moments m, v
@@ -305,8 +344,11 @@ synth_status synth_stream_features(synth_model m, uint64_t seed, int32_t split, 
 synth_status synth_propose(synth_handle h, synth_model m, const float* audio_dev, int32_t batch,
                            float* params_out_dev, void* stream);
 /* Copies an FP32 tensor out of the model: which = 0 weights [out][in],
- * 1 biases [out], 2 last weight gradients, 3 last bias gradients; layer 0..3;
- * count must equal the tensor's size. */
+ * 1 biases [out], 2 last weight gradients, 3 last bias gradients (layer
+ * 0..3); 4 the hidden activations H_layer (layer 1..3, the output of layer
+ * layer - 1 after the ReLU, as the GEMMs read them: bf16 values widened to
+ * FP32) of the last forward or training step, [batch][1024] for that call's
+ * batch. count must equal the tensor's size. */
 synth_status synth_model_get_tensor(synth_model m, int32_t which, int32_t layer, float* dst_dev,
                                     size_t count, void* stream);
 /* Checkpoint: every model tensor (weights, Adam moments) and the step count
@@ -330,19 +372,49 @@ synth_status synth_model_load(synth_model m, const char* path);
  * <= 779. Larger requests return SYNTH_ERR_ARG before any launch.
  * The first call on a device (with that device current) looks up the
  * array's device address; make that first call before any stream capture.
- * All calls share the one array and each clears the part it uses: calls
- * whose kernels overlap on the GPU (other streams, other threads) race and
- * must be serialized by the caller. A device-side wait that gives up is not
- * reported by this entry point (it has no handle to record it in).
+ * Calls outside capture look it up again (after cudaDeviceReset the array
+ * may have moved); a call captured after a device reset, with no call in
+ * between, would use the stale address. All calls share the one array and
+ * each clears the part it uses: calls whose kernels overlap on the GPU
+ * (other streams, other threads) race and must be serialized by the caller.
+ * A device-side wait that gives up sets an error word in the array, which
+ * synth_noalloc_status reads (the next call clears it).
  * Errors: SYNTH_ERR_ARG, SYNTH_ERR_UNSUPPORTED, SYNTH_ERR_CUDA. */
 synth_status synth_render_noalloc(const synth_config* cfg, uint64_t seed, uint64_t batch_index,
                                   int32_t batch, const float* params_in_dev, float* audio_dev,
                                   float* params_out_dev, void* stream);
+/* Status of the last synth_render_noalloc call on the current device: waits
+ * for `stream`, then returns SYNTH_ERR_TIMEOUT (and clears the record) if a
+ * bounded device-side wait of that render gave up (its audio is invalid),
+ * SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. Allocates nothing; call it
+ * after the render and before the next synth_render_noalloc. The paper has
+ * no counterpart to this call either. */
+synth_status synth_noalloc_status(void* stream);
 
 /* Waits for the stream, then reports (and clears) a device-side error
  * recorded by any earlier call on this handle: SYNTH_ERR_TIMEOUT if a bounded
  * wait gave up, SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. */
 synth_status synth_sync(synth_handle h, void* stream);
+
+/* Special-function-unit (MUFU) throughput probe, for the render's
+ * transcendental roofline (the paper reports no roofline; this is the
+ * library's own measurement aid). Launches `blocks` CTAs of 256 threads on
+ * `stream`; every thread runs 8 independent chains of `iters` applications
+ * of one approximate special function (sin, cos, ex2, rcp, lg2 or tanh, the
+ * .approx PTX forms the render uses), so the unit's rate, not one chain's
+ * latency, bounds the time. *ops_out (host, nullable) receives the number of
+ * operations issued. sink_dev: a device buffer of at least 256 floats (only
+ * written when a result could otherwise be optimised away). Time the call
+ * with CUDA events; ops / time / SMs / SM clock = operations per clock per SM.
+ * Errors: SYNTH_ERR_ARG, SYNTH_ERR_CUDA. */
+#define SYNTH_SFU_SIN 0
+#define SYNTH_SFU_COS 1
+#define SYNTH_SFU_EX2 2
+#define SYNTH_SFU_RCP 3
+#define SYNTH_SFU_LG2 4
+#define SYNTH_SFU_TANH 5
+synth_status synth_sfu_probe(int32_t op, int32_t blocks, int32_t iters, float* sink_dev,
+                             int64_t* ops_out, void* stream);
 
 /* Failure-detection self-test (the library's own; the paper has no device
  * waits). Runs, on `stream`, one look-back wait of the fused render against

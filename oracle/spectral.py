@@ -113,3 +113,45 @@ def mlp_loss_and_grads(x, target, weights, biases):
     loss = ((y - _as64(target)) ** 2).mean()
     loss.backward()
     return float(loss.detach()), [w.grad.numpy() for w in ws], [b.grad.numpy() for b in bs]
+
+
+def mlp_trace(x, target, weights, biases, masks=None):
+    """The same network and MSE loss with every intermediate kept, the
+    backward written out by the chain rule (FP64):
+      Z_l = H_(l-1) W_l^T + b_l, H_l = relu(Z_l) (hidden), Y = sigmoid(Z_L);
+      dZ_L = 2 (Y - target) / (B P) * Y (1 - Y);
+      dW_l = dZ_l^T H_(l-1), db_l = sum over the batch of dZ_l;
+      dH_(l-1) = dZ_l W_l, dZ_(l-1) = dH_(l-1) * [Z_(l-1) > 0].
+    ``masks`` (optional, one boolean array per hidden layer) replaces the
+    ReLU decisions [Z_l > 0] of the backward by given ones: at Z = 0 the
+    derivative is a choice, and near it a rounding of Z may take it either
+    way. Returns a dict of lists indexed by layer: Z, H (H[l] is the input of
+    layer l, H[0] = x), dZ, dH (dH[l] is the gradient of H[l], l >= 1), gW,
+    gb, and Y and the loss."""
+    x = _as64(x).numpy()
+    t = _as64(target).numpy()
+    ws = [_as64(w).numpy() for w in weights]
+    bs = [_as64(b).numpy() for b in biases]
+    L = len(ws)
+    H, Z = [x], []
+    for l in range(L):
+        z = H[l] @ ws[l].T + bs[l]
+        Z.append(z)
+        if l < L - 1:
+            H.append(np.maximum(z, 0.0))
+    Y = 1.0 / (1.0 + np.exp(-Z[-1]))
+    B, P = Y.shape
+    loss = float(np.mean((Y - t) ** 2))
+    dZ = [None] * L
+    dH = [None] * L
+    gW = [None] * L
+    gb = [None] * L
+    dZ[L - 1] = 2.0 * (Y - t) / (B * P) * Y * (1.0 - Y)
+    for l in range(L - 1, -1, -1):
+        gW[l] = dZ[l].T @ H[l]
+        gb[l] = dZ[l].sum(axis=0)
+        if l > 0:
+            dH[l] = dZ[l] @ ws[l]
+            mask = (Z[l - 1] > 0.0) if masks is None else masks[l - 1]
+            dZ[l - 1] = dH[l] * mask
+    return {"Z": Z, "H": H, "Y": Y, "dZ": dZ, "dH": dH, "gW": gW, "gb": gb, "loss": loss}

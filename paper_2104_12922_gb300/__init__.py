@@ -75,6 +75,11 @@ def lib() -> ctypes.CDLL:
         L.synth_gemm_bf16.argtypes = [vp, vp, i32, vp, i32, vp, i32, i32, i32, i32,
                                       ctypes.c_float, vp]
         L.synth_gemm_bf16.restype = ctypes.c_int
+        L.synth_gemm_bf16_workspace_size.argtypes = [vp, i32, i32, P(ctypes.c_size_t)]
+        L.synth_gemm_bf16_workspace_size.restype = ctypes.c_int
+        L.synth_gemm_bf16_splitk.argtypes = [vp, vp, i32, vp, i32, vp, i32, i32, i32, i32,
+                                             ctypes.c_float, vp, ctypes.c_size_t, vp]
+        L.synth_gemm_bf16_splitk.restype = ctypes.c_int
         L.synth_mrstft_workspace_size.argtypes = [vp, i32, P(ctypes.c_size_t)]
         L.synth_mrstft.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, ctypes.c_size_t, vp]
         L.synth_param_adam.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.c_float, vp]
@@ -107,6 +112,12 @@ def lib() -> ctypes.CDLL:
         L.synth_split_voice.argtypes = [i32, u64]
         L.synth_split_voice.restype = u64
         L.synth_stream_features.argtypes = [vp, u64, i32, u64, ctypes.c_int64, i32, vp, vp, vp]
+        L.synth_sfu_probe.argtypes = [i32, i32, i32, vp, P(i64), vp]
+        L.synth_sfu_probe.restype = ctypes.c_int
+        L.synth_l1_distances.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+        L.synth_l1_distances.restype = ctypes.c_int
+        L.synth_mmd_trials.argtypes = [vp, vp, i32, vp, i32, vp, vp]
+        L.synth_mmd_trials.restype = ctypes.c_int
         L.synth_selftest_wait_timeout.argtypes = [vp, vp]
         L.synth_selftest_wait_timeout.restype = ctypes.c_int
         L.synth_status_string.argtypes = [ctypes.c_int]
@@ -192,6 +203,7 @@ def synth_is_test(g: int) -> bool:
 
 
 SPLIT_ALL, SPLIT_TRAIN, SPLIT_TEST = 0, 1, 2
+SFU_SIN, SFU_COS, SFU_EX2, SFU_RCP, SFU_LG2, SFU_TANH = 0, 1, 2, 3, 4, 5
 FM_NUM_PARAMS = 30
 
 
@@ -429,6 +441,34 @@ class MRSTFT:
         return self.loss, gx
 
 
+def l1_distances(synth: Synth, emb, out=None, stream=None):
+    """Pooled pairwise l1 distances [m][m] (FP32) of bf16 embeddings [m][dim]
+    (synth_l1_distances)."""
+    import torch
+    m, dim = emb.shape
+    if emb.dtype != torch.bfloat16 or emb.stride(1) != 1:
+        raise ValueError("emb must be a bf16 tensor with contiguous rows")
+    if out is None:
+        out = torch.empty((m, m), dtype=torch.float32, device=emb.device)
+    _check(lib().synth_l1_distances(synth.handle, _ptr(emb), emb.stride(0), m, dim, _ptr(out),
+                                    _stream_ptr(stream)), "synth_l1_distances")
+    return out
+
+
+def mmd_trials(synth: Synth, dist, labels, out=None, stream=None):
+    """One MMD per row of labels [trials][m] (int8: 0 in X, 1 in Y, else out)
+    over the pooled distance matrix (synth_mmd_trials); FP64 [trials]."""
+    import torch
+    trials, m = labels.shape
+    if labels.dtype != torch.int8 or not labels.is_contiguous():
+        raise ValueError("labels must be a contiguous int8 tensor")
+    if out is None:
+        out = torch.empty(trials, dtype=torch.float64, device=dist.device)
+    _check(lib().synth_mmd_trials(synth.handle, _ptr(dist), m, _ptr(labels), trials, _ptr(out),
+                                  _stream_ptr(stream)), "synth_mmd_trials")
+    return out
+
+
 def param_adam(synth: Synth, u, grad, m, v, step: int, lr: float, stream=None) -> None:
     _check(lib().synth_param_adam(synth.handle, _ptr(u), _ptr(grad), _ptr(m), _ptr(v), u.numel(),
                                   step, lr, _stream_ptr(stream)), "synth_param_adam")
@@ -506,10 +546,15 @@ class ProposalModel:
                                    _ptr(out), _stream_ptr(stream)), "synth_propose")
         return out
 
-    def tensor(self, which: int, layer: int):
+    def tensor(self, which: int, layer: int, batch: int | None = None):
+        """which 0..3: weights, biases, weight / bias gradients of a layer;
+        4: hidden activations H_layer [batch][1024] of the last call."""
         import torch
         dims = [self.feature_dim, 1024, 1024, 1024, NUM_PARAMS]
-        shape = (dims[layer + 1], dims[layer]) if which in (0, 2) else (dims[layer + 1],)
+        if which == 4:
+            shape = (batch, 1024)
+        else:
+            shape = (dims[layer + 1], dims[layer]) if which in (0, 2) else (dims[layer + 1],)
         t = torch.empty(shape, dtype=torch.float32, device=self.synth.device)
         _check(lib().synth_model_get_tensor(self.handle, which, layer, _ptr(t), t.numel(),
                                             _stream_ptr(None)), "synth_model_get_tensor")

@@ -4,8 +4,14 @@
 // accumulation in tensor memory (TMEM), a fused epilogue. Used for the
 // proposal MLP (and exposed as synth_gemm_bf16).
 //
-// Persistent: one CTA per SM walks the 128 x BN output tiles (N fastest, so
-// neighbouring CTAs share A rows in L2) with 6 warps:
+// Persistent: one CTA per SM walks work items -- 128 x BN output tiles (N
+// fastest, so neighbouring CTAs share A rows in L2), or, when the output has
+// fewer tiles than the GPU has SMs and a partial-sum workspace is given,
+// (tile, K-slice) pairs of a split-K product, K-slice major so that the CTAs
+// working on one slice at a time share its A columns in L2. Each split-K item
+// stores its raw FP32 partial tile; splitk_reduce then adds the slices in
+// slice order (the same sum whichever CTA finished first: deterministic) and
+// applies the epilogue. 6 warps per CTA:
 //   warp 0      TMA producer: cp.async.bulk.tensor loads of 128x64 A and BNx64 B
 //               tiles (128-byte swizzle) into a STAGES-deep shared-memory ring
 //               that runs on across tiles;
@@ -24,7 +30,9 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "gemm_tc.h"
 
@@ -147,10 +155,31 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __device__ __forceinline__ float sigmoidf(float x) { return 1.f / (1.f + __expf(-x)); }
 
+// Work item -> output tile, K-slice and its k-block range [kb0, kb1).
+struct GemmItem {
+  int m0, n0, split, kb0, kb1;
+};
+
+__device__ __forceinline__ GemmItem gemm_item(int item, int n_tiles, int tiles_n, int bn,
+                                              int kb_per, int nk) {
+  GemmItem g;
+  const int tile = item % n_tiles;
+  g.split = item / n_tiles;
+  g.m0 = (tile / tiles_n) * BM;
+  g.n0 = (tile % tiles_n) * bn;
+  g.kb0 = g.split * kb_per;
+  g.kb1 = min(nk, g.kb0 + kb_per);
+  return g;
+}
+
+// part == nullptr: the epilogue `epi` is applied to each finished tile.
+// Otherwise (split-K, `splits` slices of kb_per k-blocks each) the raw
+// accumulator of slice s goes to part[s][M][N].
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
     const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-    GemmEpilogue epi, int M, int N, int K, unsigned int* err) {
+    GemmEpilogue epi, int M, int N, int K, int splits, int kb_per, float* part,
+    unsigned int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   GemmSmem<BN>& sm = *reinterpret_cast<GemmSmem<BN>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -158,6 +187,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
   const int nk = (K + BK - 1) / BK;
   const int tiles_n = (N + BN - 1) / BN;
   const int n_tiles = tiles_n * ((M + BM - 1) / BM);
+  const int n_items = n_tiles * splits;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -186,28 +216,29 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
   if (warp == 0 && lane == 0) {
     // producer: the stage ring runs on across this CTA's tiles
     int it = 0;
-    for (int tile = blockIdx.x; tile < n_tiles && !sm.failed; tile += gridDim.x) {
-      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-      for (int kb = 0; kb < nk; ++kb, ++it) {
+    for (int item = blockIdx.x; item < n_items && !sm.failed; item += gridDim.x) {
+      const GemmItem g = gemm_item(item, n_tiles, tiles_n, BN, kb_per, nk);
+      for (int kb = g.kb0; kb < g.kb1; ++kb, ++it) {
         const int s = it % kStages;
         const uint32_t ph = (uint32_t)(it / kStages) & 1u;
         if (!mbar_wait(&sm.empty[s], ph ^ 1u)) { sm.failed = 1; break; }
         mbar_expect_tx(&sm.full[s], (uint32_t)((BM + BN) * BK * 2));
-        tma_load_2d(sm.a[s], &map_a, &sm.full[s], kb * BK, m0);
-        tma_load_2d(sm.b[s], &map_b, &sm.full[s], kb * BK, n0);
+        tma_load_2d(sm.a[s], &map_a, &sm.full[s], kb * BK, g.m0);
+        tma_load_2d(sm.b[s], &map_b, &sm.full[s], kb * BK, g.n0);
       }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: tile t of this CTA accumulates in TMEM buffer t & 1
     constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
     int it = 0, t = 0;
-    for (int tile = blockIdx.x; tile < n_tiles && !sm.failed; tile += gridDim.x, ++t) {
+    for (int item = blockIdx.x; item < n_items && !sm.failed; item += gridDim.x, ++t) {
+      const GemmItem g = gemm_item(item, n_tiles, tiles_n, BN, kb_per, nk);
       const int buf = t & 1;
       const uint32_t use = (uint32_t)(t >> 1);
       if (!mbar_wait(&sm.acc_empty[buf], (use & 1u) ^ 1u)) { sm.failed = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t acc = tmem + (uint32_t)(buf * BN);
-      for (int kb = 0; kb < nk; ++kb, ++it) {
+      for (int kb = g.kb0; kb < g.kb1; ++kb, ++it) {
         const int s = it % kStages;
         const uint32_t ph = (uint32_t)(it / kStages) & 1u;
         if (!mbar_wait(&sm.full[s], ph)) { sm.failed = 1; break; }
@@ -216,7 +247,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
           umma_bf16(acc, smem_desc_sw128(a0 + kk * 32), smem_desc_sw128(b0 + kk * 32), idesc,
-                    (kb | kk) != 0 ? 1u : 0u);
+                    (kb != g.kb0 || kk != 0) ? 1u : 0u);
         umma_commit(&sm.empty[s]);
       }
       umma_commit(&sm.acc_full[buf]);
@@ -225,21 +256,36 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
     // epilogue
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     int t = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++t) {
+      const GemmItem g = gemm_item(item, n_tiles, tiles_n, BN, kb_per, nk);
       const int buf = t & 1;
       const uint32_t use = (uint32_t)(t >> 1);
       const bool ok = mbar_wait(&sm.acc_full[buf], use & 1u);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) { sm.failed = 1; break; }
-      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-      const int row = m0 + 32 * q + lane;
+      const int row = g.m0 + 32 * q + lane;
       const uint32_t acc = tmem + (uint32_t)(buf * BN) + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         tmem_ld16(acc + (uint32_t)c, v);
         if (row >= M) continue;
-        const int col0 = n0 + c;
+        const int col0 = g.n0 + c;
+        if (part) {
+          // split-K: the raw partial sums of this K-slice
+          float* out = part + ((size_t)g.split * M + row) * N;
+          if (col0 + 15 < N && (N & 3) == 0) {
+            float4* o4 = reinterpret_cast<float4*>(out + col0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (col0 + i < N) out[col0 + i] = v[i];
+          }
+          continue;
+        }
         switch (epi.kind) {
           case kEpiStoreF32: {
             float* out = epi.out_f32 + (size_t)row * epi.ldc;
@@ -292,22 +338,64 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
   }
 }
 
+// Split-K reduction with the fused epilogue: C = sum over slices s = 0, 1, ...
+// of part[s] in that order, then the epilogue of `epi`. A block covers a
+// 32 x 32 output tile (32 x 8 threads, 4 rows each); the transposed bf16
+// copy goes through shared memory so both of its stores are coalesced.
+__global__ void __launch_bounds__(256) splitk_reduce(const float* __restrict__ part, int splits,
+                                                     int M, int N, GemmEpilogue epi) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx, r0 = blockIdx.y * 32;
+  const size_t slice = (size_t)M * N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 8 * i;
+    float z = 0.f;
+    if (r < M && c < N) {
+      const float* p = part + (size_t)r * N + c;
+      float acc = 0.f;
+      for (int k = 0; k < splits; ++k) acc += p[(size_t)k * slice];
+      if (epi.kind == kEpiStoreF32) {
+        epi.out_f32[(size_t)r * epi.ldc + c] = acc * epi.alpha;
+      } else {
+        z = acc + (epi.bias ? epi.bias[c] : 0.f);
+        if (epi.act == kActRelu) z = fmaxf(z, 0.f);
+        else if (epi.act == kActSigmoid) z = sigmoidf(z);
+        const __nv_bfloat16 b = __float2bfloat16(z);
+        if (epi.out_bf16) epi.out_bf16[(size_t)r * epi.ldc + c] = b;
+        if (epi.out_f32) epi.out_f32[(size_t)r * epi.ldc + c] = z;
+        z = __bfloat162float(b);
+      }
+    }
+    tile[ty + 8 * i][tx] = z;
+  }
+  if (epi.kind != kEpiBiasActBF16 || !epi.out_bf16_t) return;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int cc = blockIdx.x * 32 + ty + 8 * i, r = r0 + tx;
+    if (cc < N && r < M)
+      epi.out_bf16_t[(size_t)cc * epi.ldc_t + r] = __float2bfloat16(tile[tx][ty + 8 * i]);
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  // looked up once (thread-safe initialisation of a function-local static)
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) ==
-            cudaSuccess &&
+                                         &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -326,39 +414,103 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Per-device launch facts, set up once per device under a lock: the SM count
+// and whether each instantiation's dynamic shared-memory limit is raised.
+struct GemmDevice {
+  int sms = 0;
+  bool attr128 = false, attr256 = false;
+};
+constexpr int kGemmMaxDevices = 64;
+std::mutex g_gemm_mutex;
+GemmDevice g_gemm_dev[kGemmMaxDevices];
+
+template <int BN>
+cudaError_t gemm_device_setup(int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kGemmMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_gemm_mutex);
+  GemmDevice& d = g_gemm_dev[dev];
+  bool& attr = BN == 256 ? d.attr256 : d.attr128;
+  if (!attr) {
+    e = cudaFuncSetAttribute(gemm_bf16_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(GemmSmem<BN>) + 1024));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (d.sms == 0) {
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  *sms = d.sms;
+  return cudaSuccess;
+}
+
+// K-slices for a product with `tiles` output tiles and nk k-blocks: enough
+// to give every SM an item, at least 4 k-blocks per slice, within the
+// workspace. Returns 1 (no split) when the tiles alone fill the GPU.
+int choose_splits(int tiles, int nk, int sms, size_t slice_bytes, size_t ws_bytes, int* kb_per) {
+  *kb_per = nk;
+  if (tiles >= sms || slice_bytes == 0) return 1;
+  int s = sms / tiles;
+  s = std::min(s, (nk + 3) / 4);
+  s = (int)std::min<size_t>((size_t)s, ws_bytes / slice_bytes);
+  if (s <= 1) return 1;
+  *kb_per = (nk + s - 1) / s;
+  return (nk + *kb_per - 1) / *kb_per;
+}
+
 template <int BN>
 cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEpilogue& epi, int M,
-                      int N, int K, unsigned int* err, cudaStream_t st) {
+                      int N, int K, float* ws, size_t ws_bytes, unsigned int* err,
+                      cudaStream_t st) {
+  int sms = 0;
+  cudaError_t e = gemm_device_setup<BN>(&sms);
+  if (e != cudaSuccess) return e;
   const size_t smem = sizeof(GemmSmem<BN>) + 1024;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(gemm_bf16_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = true;
-  }
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 1;
-  }
+  const int nk = (K + BK - 1) / BK;
   const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  const int grid = (int)(tiles < sms ? tiles : sms);  // persistent: one CTA per SM
-  gemm_bf16_tc<BN><<<grid, kGemmThreads, smem, st>>>(ma, mb, epi, M, N, K, err);
+  int kb_per = nk;
+  const int splits =
+      ws ? choose_splits((int)std::min<long long>(tiles, 1 << 30), nk, sms,
+                         sizeof(float) * (size_t)M * N, ws_bytes, &kb_per)
+         : 1;
+  const long long items = tiles * splits;
+  const int grid = (int)(items < sms ? items : sms);  // persistent: one CTA per SM
+  gemm_bf16_tc<BN><<<grid, kGemmThreads, smem, st>>>(ma, mb, epi, M, N, K, splits, kb_per,
+                                                     splits > 1 ? ws : nullptr, err);
+  if ((e = cudaGetLastError()) != cudaSuccess || splits == 1) return e;
+  const dim3 rgrid((N + 31) / 32, (M + 31) / 32);
+  splitk_reduce<<<rgrid, 256, 0, st>>>(ws, splits, M, N, epi);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
-                      int N, int K, const GemmEpilogue& epi, unsigned int* err, cudaStream_t st) {
+                      int N, int K, const GemmEpilogue& epi, unsigned int* err, cudaStream_t st,
+                      float* splitk_ws, size_t splitk_bytes) {
   if (M <= 0 || N <= 0 || K <= 0 || (K % 8) != 0) return cudaErrorInvalidValue;
   const int bn = N > 128 ? 256 : 128;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, K, lda, BM) || !make_map(&mb, B, N, K, ldb, bn))
     return cudaErrorInvalidValue;
-  if (bn == 256) return launch_bn<256>(ma, mb, epi, M, N, K, err, st);
-  return launch_bn<128>(ma, mb, epi, M, N, K, err, st);
+  if (bn == 256) return launch_bn<256>(ma, mb, epi, M, N, K, splitk_ws, splitk_bytes, err, st);
+  return launch_bn<128>(ma, mb, epi, M, N, K, splitk_ws, splitk_bytes, err, st);
+}
+
+size_t gemm_splitk_workspace_bytes(int max_m, int max_n) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  // splits <= sms / tiles with tiles >= ceil(M / 128) ceil(N / 256): at most
+  // sms slices of one 128 x 256 tile's worth of the output each
+  const size_t tiles = (size_t)((max_m + BM - 1) / BM) * (size_t)((max_n + 255) / 256);
+  const size_t per_slice = sizeof(float) * (size_t)max_m * max_n;
+  const size_t slices = tiles >= (size_t)sms ? 1 : (size_t)sms / tiles;
+  return slices * per_slice;
 }
 
 }  // namespace synth

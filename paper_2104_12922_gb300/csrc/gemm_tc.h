@@ -27,7 +27,16 @@ struct GemmEpilogue {
 // C = A[M][K] * B[N][K]^T on the tensor cores; A, B bf16 with row strides lda,
 // ldb (elements, multiples of 8), K a multiple of 8, 16-byte aligned bases.
 // err: device word, bit 0 set if a bounded wait gave up.
+// splitk_ws (splitk_bytes, device, 16-byte aligned) or NULL: when the output
+// has fewer 128 x BN tiles than the GPU has SMs, K is split into slices whose
+// FP32 partial products go there and a second kernel adds them in slice
+// order (deterministic) before the epilogue. NULL: no split.
 cudaError_t gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
-                      int N, int K, const GemmEpilogue& epi, unsigned int* err, cudaStream_t st);
+                      int N, int K, const GemmEpilogue& epi, unsigned int* err, cudaStream_t st,
+                      float* splitk_ws = nullptr, size_t splitk_bytes = 0);
+
+// Workspace that lets gemm_bf16 split every product of at most max_m x max_n
+// outputs as far as it would (0 if the device cannot be queried).
+size_t gemm_splitk_workspace_bytes(int max_m, int max_n);
 
 }  // namespace synth

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "voice_device.cuh"
@@ -88,6 +89,13 @@ cudaError_t launch_render_plain(const VoiceConst& vc, uint64_t seed, uint64_t ba
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, void* workspace, ScratchHeader* hdr,
                                 TileState* tiles, cudaStream_t stream);
+
+// Corpus similarity (mmd.cu): pooled pairwise l1 distances of bf16
+// embeddings [m][ld], and the MMD statistic of labelled trials over them.
+cudaError_t launch_l1_distances(const __nv_bfloat16* emb, int64_t ld, int m, int dim, float* dist,
+                                cudaStream_t st);
+cudaError_t launch_mmd_trials(const float* dist, int m, const int8_t* labels, int trials,
+                              double* mmd, cudaStream_t st);
 
 // Adjoint.
 size_t backward_workspace_bytes(const VoiceConst& vc, int batch);

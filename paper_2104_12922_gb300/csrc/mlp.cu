@@ -72,20 +72,26 @@ __global__ void transpose_bf16(const __nv_bfloat16* __restrict__ in, int rows, i
 
 // Output layer: MSE against the target (mean over batch x outputs) through
 // the sigmoid: dZ = 2 (y - u) / (B P) * y (1 - y); writes dZ and dZ^T (bf16,
-// zero-padded to P_pad columns / rows) and the loss sum.
-__global__ void mse_sigmoid_grad(const float* __restrict__ y, const float* __restrict__ target,
-                                 int batch, int P, int P_pad, __nv_bfloat16* __restrict__ dz,
-                                 __nv_bfloat16* __restrict__ dzt, float* __restrict__ dzf,
-                                 float* __restrict__ loss) {
+// zero-padded to P_pad columns / rows), the FP32 dZ, and the loss. One
+// element per thread; each block leaves its partial sum of squares in
+// part[block], and the block that finishes last (a counter it resets) adds
+// the partials in block order, so the loss does not depend on which block
+// came last.
+__global__ void __launch_bounds__(256) mse_sigmoid_grad(
+    const float* __restrict__ y, const float* __restrict__ target, int batch, int P, int P_pad,
+    __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt, float* __restrict__ dzf,
+    float* __restrict__ part, unsigned int* __restrict__ counter, float* __restrict__ loss) {
   __shared__ float red[8];
-  float local = 0.f;
+  __shared__ bool last;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const float scale = 2.f / (float)(batch * P);
-  for (int i = threadIdx.x; i < batch * P_pad; i += blockDim.x) {
+  float local = 0.f;
+  if (i < batch * P_pad) {
     const int b = i / P_pad, p = i % P_pad;
     float g = 0.f;
     if (p < P) {
       const float yy = y[b * P + p], d = yy - target[b * P + p];
-      local += d * d;
+      local = d * d;
       g = scale * d * yy * (1.f - yy);
     }
     dz[i] = __float2bfloat16(g);
@@ -95,26 +101,52 @@ __global__ void mse_sigmoid_grad(const float* __restrict__ y, const float* __res
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
   __syncthreads();
-  if (threadIdx.x == 0 && loss) {
+  if (threadIdx.x == 0) {
     float t = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    *loss = t / (float)(batch * P);
+    part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  float t = 0.f;
+  for (unsigned int k = 0; k < gridDim.x; ++k) t += reinterpret_cast<volatile float*>(part)[k];
+  *counter = 0u;
+  if (loss) *loss = t / (float)(batch * P);
 }
 
-// Hidden layer: dZ = dH * relu'(Z) with relu'(Z) = (H > 0); writes dZ, dZ^T.
-__global__ void relu_grad(const float* __restrict__ dh, const __nv_bfloat16* __restrict__ h, int batch,
-                          int width, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt,
-                          float* __restrict__ dzf) {
-  const int64_t total = (int64_t)batch * width;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(i / width), c = (int)(i % width);
-    const float g = __bfloat162float(h[i]) > 0.f ? dh[i] : 0.f;
-    const __nv_bfloat16 gb = __float2bfloat16(g);
-    dz[i] = gb;
-    dzt[(int64_t)c * batch + b] = gb;
-    dzf[i] = g;
+// Hidden layer: dZ = dH * relu'(Z) with relu'(Z) = (H > 0); writes dZ, dZ^T
+// and the FP32 dZ. A block covers 32 batch rows x 32 columns (32 x 8
+// threads); the transposed copy goes through shared memory so that its
+// stores are coalesced too.
+__global__ void __launch_bounds__(256) relu_grad(const float* __restrict__ dh,
+                                                 const __nv_bfloat16* __restrict__ h, int batch,
+                                                 int width, __nv_bfloat16* __restrict__ dz,
+                                                 __nv_bfloat16* __restrict__ dzt,
+                                                 float* __restrict__ dzf) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx, b0 = blockIdx.y * 32;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int b = b0 + ty + 8 * k;
+    __nv_bfloat16 gb = __float2bfloat16(0.f);
+    if (b < batch && c < width) {
+      const int64_t i = (int64_t)b * width + c;
+      const float g = __bfloat162float(h[i]) > 0.f ? dh[i] : 0.f;
+      gb = __float2bfloat16(g);
+      dz[i] = gb;
+      dzf[i] = g;
+    }
+    tile[ty + 8 * k][tx] = gb;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int cc = blockIdx.x * 32 + ty + 8 * k, b = b0 + tx;
+    if (cc < width && b < batch) dzt[(int64_t)cc * batch + b] = tile[tx][ty + 8 * k];
   }
 }
 
@@ -129,33 +161,97 @@ __global__ void bias_grad(const float* __restrict__ dz, int batch, int width, in
 }
 
 // Adam (Kingma & Ba, 2015) on FP32 master values; also refreshes the bf16
-// copy (and its transpose) the GEMMs read. rows x cols, row-major.
-__global__ void adam_update(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int64_t rows, int cols, float lr, float b1,
-                            float b2, float eps, float c1, float c2, __nv_bfloat16* __restrict__ wb,
-                            __nv_bfloat16* __restrict__ wt, int ld_t) {
-  const int64_t total = rows * cols;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+// copy the GEMMs read. Vectorised by 4 (n a multiple of 4, 16-byte aligned
+// arrays): an HBM-bound stream of 16 bytes read and 14 written per value.
+__device__ __forceinline__ float adam_one(float& w, float g, float& m, float& v, float lr,
+                                          float b1, float b2, float eps, float c1, float c2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  w = w - lr * (m / c1) / (sqrtf(v / c2) + eps);
+  return w;
+}
+
+__global__ void adam_update_vec4(float4* __restrict__ w, const float4* __restrict__ g,
+                                 float4* __restrict__ m, float4* __restrict__ v, int64_t n4,
+                                 float lr, float b1, float b2, float eps, float c1, float c2,
+                                 uint2* __restrict__ wb) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    float4 wi = w[i], mi = m[i], vi = v[i];
+    const float4 gi = g[i];
+    adam_one(wi.x, gi.x, mi.x, vi.x, lr, b1, b2, eps, c1, c2);
+    adam_one(wi.y, gi.y, mi.y, vi.y, lr, b1, b2, eps, c1, c2);
+    adam_one(wi.z, gi.z, mi.z, vi.z, lr, b1, b2, eps, c1, c2);
+    adam_one(wi.w, gi.w, mi.w, vi.w, lr, b1, b2, eps, c1, c2);
+    w[i] = wi;
     m[i] = mi;
     v[i] = vi;
-    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    w[i] = wi;
     if (wb) {
-      const __nv_bfloat16 b = __float2bfloat16(wi);
-      wb[i] = b;
-      if (wt) wt[(int64_t)(i % cols) * ld_t + i / cols] = b;
+      __nv_bfloat162 lo = __floats2bfloat162_rn(wi.x, wi.y), hi = __floats2bfloat162_rn(wi.z, wi.w);
+      wb[i] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
     }
   }
+}
+
+// Scalar Adam for short vectors (biases).
+__global__ void adam_update(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float wi = w[i], mi = m[i], vi = v[i];
+    adam_one(wi, g[i], mi, vi, lr, b1, b2, eps, c1, c2);
+    w[i] = wi;
+    m[i] = mi;
+    v[i] = vi;
+  }
+}
+
+// Adam on a weight matrix [rows][cols] that also keeps a transposed bf16 copy
+// wt[col][row] (row stride ld_t): a block updates a 32 x 32 tile (32 x 8
+// threads) and writes the transposed copy through shared memory, coalesced.
+__global__ void __launch_bounds__(256) adam_update_tiled(
+    float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+    float* __restrict__ v, int rows, int cols, float lr, float b1, float b2, float eps, float c1,
+    float c2, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt, int ld_t) {
+  __shared__ __nv_bfloat16 tile[32][34];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx, r0 = blockIdx.y * 32;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = r0 + ty + 8 * k;
+    __nv_bfloat16 b = __float2bfloat16(0.f);
+    if (r < rows && c < cols) {
+      const int64_t i = (int64_t)r * cols + c;
+      float wi = w[i], mi = m[i], vi = v[i];
+      adam_one(wi, g[i], mi, vi, lr, b1, b2, eps, c1, c2);
+      w[i] = wi;
+      m[i] = mi;
+      v[i] = vi;
+      b = __float2bfloat16(wi);
+      wb[i] = b;
+    }
+    tile[ty + 8 * k][tx] = b;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int cc = blockIdx.x * 32 + ty + 8 * k, r = r0 + tx;
+    if (cc < cols && r < rows) wt[(int64_t)cc * ld_t + r] = tile[tx][ty + 8 * k];
+  }
+}
+
+// Hidden activations (bf16) to FP32, for inspection.
+__global__ void bf16_to_f32(const __nv_bfloat16* __restrict__ in, int64_t n, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __bfloat162float(in[i]);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- layout
-MlpLayout mlp_layout(int in_dim, int hidden, int out_dim, int max_batch) {
+MlpLayout mlp_layout(int in_dim, int hidden, int out_dim, int max_batch, size_t splitk_bytes) {
   MlpLayout L;
   L.dims[0] = in_dim;
   L.dims[1] = L.dims[2] = L.dims[3] = hidden;
@@ -191,6 +287,10 @@ MlpLayout mlp_layout(int in_dim, int hidden, int out_dim, int max_batch) {
   L.dzf = take(sizeof(float) * B * (hidden > L.out_pad ? hidden : L.out_pad));
   L.dh = take(sizeof(float) * B * hidden);
   L.loss = take(sizeof(float) * 4);
+  L.loss_part = take(sizeof(float) * (size_t)((max_batch * L.out_pad + 255) / 256));
+  L.loss_counter = take(sizeof(unsigned int));
+  L.splitk_bytes = splitk_bytes;
+  L.splitk = take(splitk_bytes);
   L.total = o;
   return L;
 }
@@ -236,7 +336,8 @@ cudaError_t mlp_forward(const MlpLayout& L, char* base, const __nv_bfloat16* x, 
       ep.ldc = out;
     }
     e = gemm_bf16(in, in_dim, reinterpret_cast<const __nv_bfloat16*>(base + L.wb[l]), in_dim, batch,
-                  out, in_dim, ep, err, st);
+                  out, in_dim, ep, err, st, reinterpret_cast<float*>(base + L.splitk),
+                  L.splitk_bytes);
     if (e != cudaSuccess) return e;
     in = reinterpret_cast<const __nv_bfloat16*>(base + L.h[l + 1 < 4 ? l + 1 : 3]);
     in_dim = out;
@@ -261,8 +362,10 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
   float* dzf = reinterpret_cast<float*>(base + L.dzf);
   float* loss = reinterpret_cast<float*>(base + L.loss);
   const int P = L.dims[4], Pp = L.out_pad;
-  mse_sigmoid_grad<<<1, 256, 0, st>>>(reinterpret_cast<const float*>(base + L.y), target, batch, P,
-                                      Pp, dz, dzt, dzf, loss);
+  mse_sigmoid_grad<<<(batch * Pp + 255) / 256, 256, 0, st>>>(
+      reinterpret_cast<const float*>(base + L.y), target, batch, P, Pp, dz, dzt, dzf,
+      reinterpret_cast<float*>(base + L.loss_part),
+      reinterpret_cast<unsigned int*>(base + L.loss_counter), loss);
   if (loss_out) cudaMemcpyAsync(loss_out, loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
   for (int l = 3; l >= 0; --l) {
     const int in = L.dims[l], out = L.dims[l + 1];
@@ -285,9 +388,10 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
       eh.out_f32 = dh;
       eh.ldc = in;
       if ((e = gemm_bf16(dz, ldz, reinterpret_cast<const __nv_bfloat16*>(base + L.wt[l]), ldz,
-                         batch, in, ldz, eh, err, st)) != cudaSuccess)
+                         batch, in, ldz, eh, err, st, reinterpret_cast<float*>(base + L.splitk),
+                         L.splitk_bytes)) != cudaSuccess)
         return e;
-      relu_grad<<<grid_of((int64_t)batch * in), 256, 0, st>>>(
+      relu_grad<<<dim3((in + 31) / 32, (batch + 31) / 32), 256, 0, st>>>(
           dh, reinterpret_cast<const __nv_bfloat16*>(base + L.h[l]), batch, in, dz, dzt, dzf);
     }
   }
@@ -296,17 +400,38 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
   for (int l = 0; l < 4; ++l) {
     const int in = L.dims[l], out = L.dims[l + 1];
-    const int outp = l == 3 ? Pp : out;
-    adam_update<<<grid_of((int64_t)in * out), 256, 0, st>>>(
-        reinterpret_cast<float*>(base + L.w[l]), reinterpret_cast<const float*>(base + L.gw[l]),
-        reinterpret_cast<float*>(base + L.mw[l]), reinterpret_cast<float*>(base + L.vw[l]), out, in,
-        lr, b1, b2, eps, c1, c2, reinterpret_cast<__nv_bfloat16*>(base + L.wb[l]),
-        l == 0 ? nullptr : reinterpret_cast<__nv_bfloat16*>(base + L.wt[l]), outp);
+    float* w = reinterpret_cast<float*>(base + L.w[l]);
+    const float* g = reinterpret_cast<const float*>(base + L.gw[l]);
+    float* mw = reinterpret_cast<float*>(base + L.mw[l]);
+    float* vw = reinterpret_cast<float*>(base + L.vw[l]);
+    __nv_bfloat16* wb = reinterpret_cast<__nv_bfloat16*>(base + L.wb[l]);
+    if (l == 0) {
+      // no transposed copy: a vectorised stream (in * out is a multiple of 4)
+      const int64_t n4 = (int64_t)in * out / 4;
+      adam_update_vec4<<<grid_of(n4), 256, 0, st>>>(
+          reinterpret_cast<float4*>(w), reinterpret_cast<const float4*>(g),
+          reinterpret_cast<float4*>(mw), reinterpret_cast<float4*>(vw), n4, lr, b1, b2, eps, c1,
+          c2, reinterpret_cast<uint2*>(wb));
+    } else {
+      const int outp = l == 3 ? Pp : out;
+      adam_update_tiled<<<dim3((in + 31) / 32, (out + 31) / 32), 256, 0, st>>>(
+          w, g, mw, vw, out, in, lr, b1, b2, eps, c1, c2, wb,
+          reinterpret_cast<__nv_bfloat16*>(base + L.wt[l]), outp);
+    }
     adam_update<<<grid_of(out), 256, 0, st>>>(
         reinterpret_cast<float*>(base + L.b[l]), reinterpret_cast<const float*>(base + L.gb[l]),
-        reinterpret_cast<float*>(base + L.mb[l]), reinterpret_cast<float*>(base + L.vb[l]), 1, out,
-        lr, b1, b2, eps, c1, c2, nullptr, nullptr, 0);
+        reinterpret_cast<float*>(base + L.mb[l]), reinterpret_cast<float*>(base + L.vb[l]), out,
+        lr, b1, b2, eps, c1, c2);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_hidden_f32(const MlpLayout& L, const char* base, int layer, int batch, float* dst,
+                           cudaStream_t st) {
+  if (layer < 1 || layer > 3 || batch < 1 || batch > L.max_batch) return cudaErrorInvalidValue;
+  const int64_t n = (int64_t)batch * L.dims[layer];
+  bf16_to_f32<<<grid_of(n), 256, 0, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(base + L.h[layer]), n, dst);
   return cudaGetLastError();
 }
 

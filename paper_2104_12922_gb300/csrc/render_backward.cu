@@ -45,7 +45,7 @@ BwdLayout bwd_layout(const VoiceConst& vc, int B, size_t base) {
   size_t o = base;
   auto take = [&](size_t bytes) { size_t at = o; o = al256(o + bytes); return at; };
   L.stat = take(sizeof(float) * B * K * kStat);
-  L.gpt = take(sizeof(double) * B * P * 5);
+  L.gpt = take(sizeof(double) * 2 * B * P * 5);
   L.vacc = take(sizeof(double) * B * 8);
   L.dtheta = take(sizeof(float) * B * 2 * P);
   L.denv = take(sizeof(float) * B * 6 * P);
@@ -219,7 +219,9 @@ __global__ void __launch_bounds__(kBT) bwd_samples(const __grid_constant__ Voice
 
 // ---------------------------------------------------------------------------
 // 3. reverse scan over intervals and the per-point pitch / amplitude adjoints.
-// One block per voice. gpt[v][k] = {dm_sine, dm_sq, dA_sine, dA_sq, dA_noise}.
+// One block per voice. gpt[half][v][k] = {dm_sine, dm_sq, dA_sine, dA_sq,
+// dA_noise}: half 0 from interval k (point k its left end), half 1 from
+// interval k - 1 (its right end); the point's adjoint is their sum.
 // vacc[v] = {dphase0_sine, dphase0_sq (cycles), dg0, dg1, dg2, dshape, 0, 0}.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBT) bwd_interval_scan(const __grid_constant__ VoiceConst vc,
@@ -257,13 +259,18 @@ __global__ void __launch_bounds__(kBT) bwd_interval_scan(const __grid_constant__
       double dk = 0.0;
       if (kap < (float)kBrightnessMax && !((s1.jc_flags >> 18) & 1))
         dk = (double)st[16] * (-(double)(kap - 1.f) * l12);
-      atomicAdd(&gv[(size_t)idx * 5 + 0], dl0);
-      atomicAdd(&gv[(size_t)(idx + 1) * 5 + 0], dr0);
-      atomicAdd(&gv[(size_t)idx * 5 + 1], dl1 + dk);
-      atomicAdd(&gv[(size_t)(idx + 1) * 5 + 1], dr1);
+      // interval idx reaches points idx (left end) and idx + 1 (right end):
+      // the left parts go to gv, the right parts to gr, one store each; the
+      // consumer adds the two halves of a point
+      double* gl = gv + (size_t)idx * 5;
+      double* gr = gv + (size_t)P * 5 * gridDim.x + (size_t)(idx + 1) * 5;
+      gl[0] = dl0;
+      gr[0] = dr0;
+      gl[1] = dl1 + dk;
+      gr[1] = dr1;
       for (int c = 0; c < 3; ++c) {
-        atomicAdd(&gv[(size_t)idx * 5 + 2 + c], (double)st[10 + c]);
-        atomicAdd(&gv[(size_t)(idx + 1) * 5 + 2 + c], (double)st[13 + c]);
+        gl[2 + c] = (double)st[10 + c];
+        gr[2 + c] = (double)st[13 + c];
       }
       for (int c = 0; c < 4; ++c) part[c] += (double)st[17 + c];
     }
@@ -373,10 +380,12 @@ __device__ __forceinline__ void lfo_shapes(float p, float sh[5], float dsh[5]) {
   sh[4] = p < 0.5f ? 1.f : -1.f; dsh[4] = 0.f;
 }
 
-// Adds a warp's values into one slot of the per-voice gradient.
-__device__ __forceinline__ void acc_y(float* gy, int slot, float val) {
+// Adds a warp's values into its own row of the per-voice gradient (one row
+// per warp, no atomics: the rows are summed in warp order at the end, so the
+// gradient is the same on every run).
+__device__ __forceinline__ void acc_y(float* gy_warp, int slot, float val) {
   const float w = warp_sum(val);
-  if ((threadIdx.x & 31) == 0 && w != 0.f) atomicAdd(&gy[slot], w);
+  if ((threadIdx.x & 31) == 0) gy_warp[slot] += w;
 }
 
 __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ VoiceConst vc,
@@ -390,13 +399,15 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
                                                    float* __restrict__ denv,
                                                    float* __restrict__ grad_params) {
   __shared__ float gy[kGY];
+  __shared__ float gyw_all[kBT / 32][kGY];  // per-warp partial gradients
   __shared__ float yv[kNumParams];
   __shared__ float warp_tot[2 * (kBT / 32)];
   const int v = blockIdx.x;
   const int P = vc.K + 1;
   const float inv_cr = (float)(1.0 / vc.control_rate);
   const float inv_2pi = 0.15915494309189533577f;
-  for (int i = threadIdx.x; i < kGY; i += kBT) gy[i] = 0.f;
+  float* gyw = gyw_all[threadIdx.x >> 5];
+  for (int i = threadIdx.x; i < kGY * (kBT / 32); i += kBT) (&gyw_all[0][0])[i] = 0.f;
   for (int i = threadIdx.x; i < kNumParams; i += kBT) yv[i] = (float)y[(size_t)v * kNumParams + i];
   __syncthreads();
   float inv_norm[5], wsum_col[5];
@@ -413,6 +424,7 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
     lfo_wsum[l] = ws;
   }
   const double* gv = gpt + (size_t)v * P * 5;
+  const double* gvr = gv + (size_t)P * 5 * gridDim.x;  // the right-end halves
   float* dth = dtheta + (size_t)v * 2 * P;
   float* de = denv + (size_t)v * 6 * P;
 
@@ -434,29 +446,32 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
     }
     const float src[4] = {e[0], e[1], lfo[0], lfo[1]};
     float dd[5] = {0, 0, 0, 0, 0}, dst[5];
+    float gk[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (ok)
+      for (int j = 0; j < 5; ++j) gk[j] = (float)(gv[(size_t)k * 5 + j] + gvr[(size_t)k * 5 + j]);
     if (ok) {
-      dd[0] = yv[kSine + 1] * (float)gv[(size_t)k * 5 + 0];
-      dd[2] = yv[kSqr + 1] * (float)gv[(size_t)k * 5 + 1];
-      dd[1] = (float)gv[(size_t)k * 5 + 2];
-      dd[3] = (float)gv[(size_t)k * 5 + 3];
-      dd[4] = (float)gv[(size_t)k * 5 + 4];
+      dd[0] = yv[kSine + 1] * gk[0];
+      dd[2] = yv[kSqr + 1] * gk[1];
+      dd[1] = gk[2];
+      dd[3] = gk[3];
+      dd[4] = gk[4];
     }
     for (int j = 0; j < 5; ++j) dst[j] = ff_to_float(dest[((size_t)v * 5 + j) * P + kk]);
     // pitch: m = midi + tune + depth * dest
-    const float dm0 = ok ? (float)gv[(size_t)k * 5 + 0] : 0.f;
-    const float dm1 = ok ? (float)gv[(size_t)k * 5 + 1] : 0.f;
-    acc_y(gy, kMidi, dm0 + dm1);
-    acc_y(gy, kSine, dm0);
-    acc_y(gy, kSqr, dm1);
-    acc_y(gy, kSine + 1, dm0 * dst[0]);
-    acc_y(gy, kSqr + 1, dm1 * dst[2]);
+    const float dm0 = gk[0];
+    const float dm1 = gk[1];
+    acc_y(gyw, kMidi, dm0 + dm1);
+    acc_y(gyw, kSine, dm0);
+    acc_y(gyw, kSqr, dm1);
+    acc_y(gyw, kSine + 1, dm0 * dst[0]);
+    acc_y(gyw, kSqr + 1, dm1 * dst[2]);
     // dest_j = (sum_i W_ij src_i) / max(1, sum_i W_ij)
     float dsrc[4] = {0, 0, 0, 0};
     for (int j = 0; j < 5; ++j) {
       const float over = wsum_col[j] > 1.f ? 1.f : 0.f;
       for (int i = 0; i < 4; ++i) {
         dsrc[i] += dd[j] * yv[kMod + 5 * i + j] * inv_norm[j];
-        acc_y(gy, kMod + 5 * i + j, dd[j] * (src[i] * inv_norm[j] - over * dst[j] * inv_norm[j]));
+        acc_y(gyw, kMod + 5 * i + j, dd[j] * (src[i] * inv_norm[j] - over * dst[j] * inv_norm[j]));
       }
     }
     float dea[6] = {dsrc[0], dsrc[1], 0.f, 0.f, 0.f, 0.f};
@@ -467,7 +482,7 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
       float dthv = 0.f;
       if (lfo_wsum[l] >= 1e-12f) {
         for (int s = 0; s < 5; ++s) {
-          acc_y(gy, kLfo + 8 * l + 3 + s, dmix * (sh[l][s] - mix[l]) / lfo_wsum[l]);
+          acc_y(gyw, kLfo + 8 * l + 3 + s, dmix * (sh[l][s] - mix[l]) / lfo_wsum[l]);
           dthv += yv[kLfo + 8 * l + 3 + s] * dsh[l][s];
         }
         dthv *= dmix / lfo_wsum[l];
@@ -496,16 +511,16 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
       }
       const bool inside = ok && rate_raw >= 0.f && rate_raw <= (float)kLfoMaxHz;
       const float dr = inside ? dinc * inv_cr : 0.f;
-      acc_y(gy, kLfo + 8 * l, dr);
-      acc_y(gy, kLfo + 8 * l + 1, dr * er);
+      acc_y(gyw, kLfo + 8 * l, dr);
+      acc_y(gyw, kLfo + 8 * l + 1, dr * er);
       if (ok) de[(size_t)(2 + 2 * l) * P + idx] = dr * yv[kLfo + 8 * l + 1];
     }
     carry0 += t0;
     carry1 += t1;
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&gy[kLfo + 2], carry0 * inv_2pi);       // theta_0 = frac(phase0 / 2 pi)
-    atomicAdd(&gy[kLfo + 8 + 2], carry1 * inv_2pi);
+    gyw[kLfo + 2] += carry0 * inv_2pi;  // theta_0 = frac(phase0 / 2 pi)
+    gyw[kLfo + 8 + 2] += carry1 * inv_2pi;
   }
   __syncthreads();
 
@@ -525,9 +540,15 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
       }
     }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) acc_y(gy, kAdsr + 5 * a + q, acc[q]);
+    for (int q = 0; q < 5; ++q) acc_y(gyw, kAdsr + 5 * a + q, acc[q]);
   }
-  acc_y(gy, kDuration, dur_acc);
+  acc_y(gyw, kDuration, dur_acc);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kGY; i += kBT) {
+    float t = 0.f;
+    for (int w = 0; w < kBT / 32; ++w) t += gyw_all[w][i];
+    gy[i] = t;
+  }
   __syncthreads();
 
   if (threadIdx.x == 0) {
@@ -587,7 +608,7 @@ cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t
   float* denv = reinterpret_cast<float*>(ws + L.denv);
   const int K = vc.K, P = K + 1;
   launch_control_pipeline(vc, seed, batch_index, batch, params, nullptr, cb, st);
-  cudaMemsetAsync(gpt, 0, sizeof(double) * (size_t)batch * P * 5, st);
+  cudaMemsetAsync(gpt, 0, sizeof(double) * 2 * (size_t)batch * P * 5, st);
   dim3 gs((K + kBT / 32 - 1) / (kBT / 32), batch);
   bwd_samples<<<gs, kBT, 0, st>>>(vc, seed, batch_index, batch, cb.y, cb.dest, cb.seg, cb.kappa,
                                   grad_audio, stat);

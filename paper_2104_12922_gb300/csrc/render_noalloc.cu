@@ -15,6 +15,7 @@
 // The paper has no counterpart to this entry point.
 
 #include <cmath>
+#include <cstddef>
 #include <mutex>
 
 #include "internal.h"
@@ -32,14 +33,29 @@ std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 int g_grid[kMaxDevices] = {};
 
-// One-time set-up on the current device: the device address of the scratch
-// array (host code cannot use the symbol itself) and the persistent grid.
-synth_status setup_current_device(int* device_out, void** addr_out, int* grid_out) {
+// Set-up on the current device: the device address of the scratch array
+// (host code cannot use the symbol itself) and the persistent grid, looked up
+// on the first call. Later calls outside stream capture look the address up
+// again and keep the new one if it moved: after cudaDeviceReset the runtime
+// loads the module afresh and the array may sit elsewhere. Under capture the
+// cached address is used (a lookup could load the module there).
+synth_status setup_current_device(cudaStream_t st, int* device_out, void** addr_out,
+                                  int* grid_out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SYNTH_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return SYNTH_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  if (g_scratch_addr[dev]) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+        return SYNTH_ERR_CUDA;
+      g_scratch_addr[dev] = ptr;
+    } else {
+      cudaGetLastError();  // a failed capture query leaves no sticky error
+    }
+  } else {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return SYNTH_ERR_CUDA;
     int sms = 0;
@@ -100,8 +116,8 @@ extern "C" synth_status synth_render_noalloc(const synth_config* cfg, uint64_t s
   if (need > kNoAllocScratchBytes) return SYNTH_ERR_ARG;  // beyond the fixed scratch
   int dev = 0, grid = 0;
   void* scratch = nullptr;
-  if ((s = setup_current_device(&dev, &scratch, &grid)) != SYNTH_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = setup_current_device(st, &dev, &scratch, &grid)) != SYNTH_OK) return s;
   // The scratch keeps the previous call's contents: clear the part this call
   // uses (counters, launch epoch, error word and look-back flags start at 0).
   if (cudaMemsetAsync(scratch, 0, need, st) != cudaSuccess) return SYNTH_ERR_CUDA;
@@ -111,4 +127,22 @@ extern "C" synth_status synth_render_noalloc(const synth_config* cfg, uint64_t s
                              params_out_dev, hdr, ts, grid, st) == cudaSuccess
              ? SYNTH_OK
              : SYNTH_ERR_CUDA;
+}
+
+// Waits for `stream`, then reads and clears the error word the last
+// synth_render_noalloc call left in the fixed scratch array (through the
+// symbol: no address, no allocation). Each call clears that word when it
+// starts, so this reports only the most recent call and must come before the
+// next one.
+extern "C" synth_status synth_noalloc_status(void* stream) {
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SYNTH_ERR_CUDA;
+  unsigned int err = 0;
+  const size_t at = offsetof(ScratchHeader, error);
+  if (cudaMemcpyFromSymbol(&err, g_noalloc_scratch, sizeof(err), at) != cudaSuccess)
+    return SYNTH_ERR_CUDA;
+  if (err == 0) return SYNTH_OK;
+  const unsigned int zero = 0;
+  if (cudaMemcpyToSymbol(g_noalloc_scratch, &zero, sizeof(zero), at) != cudaSuccess)
+    return SYNTH_ERR_CUDA;
+  return SYNTH_ERR_TIMEOUT;
 }

@@ -123,7 +123,7 @@ __device__ __forceinline__ void stage_segment(float* dst, const float* __restric
 template <int R>
 __global__ void __launch_bounds__(kThreadsMr, 2)
     mr_fft_kernel(const float* __restrict__ sig, int N, int F, int batch, MrTables t, float eps,
-                  float scale, int mode, float* __restrict__ logy, double* __restrict__ loss_voice,
+                  float scale, int mode, float* __restrict__ logy, double* __restrict__ loss_item,
                   float* __restrict__ part, unsigned int* __restrict__ err) {
   using C = MrCfg<R>;
   extern __shared__ __align__(16) unsigned char mr_raw[];
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(kThreadsMr, 2)
         double tot = 0.0;
 #pragma unroll
         for (int w = 0; w < kWarpsMr; ++w) tot += (double)S.red[w];
-        atomicAdd(loss_voice + v, tot * (double)scale);
+        loss_item[item] = tot * (double)scale;  // summed per voice in item order later
       }
     }
   }
@@ -548,7 +548,7 @@ int r_of(int n_fft) { return n_fft == 512 ? 8 : n_fft == 1024 ? 16 : n_fft == 20
 
 template <int R>
 cudaError_t mr_launch(const float* sig, int N, int F, int batch, const char* tables, float eps,
-                      float scale, int mode, float* logy, double* loss_voice, float* part,
+                      float scale, int mode, float* logy, double* loss_item, float* part,
                       unsigned int* err, cudaStream_t st) {
   const int smem = (int)sizeof(MrSmem<R>);
   static int grid_cap = 0;
@@ -569,14 +569,14 @@ cudaError_t mr_launch(const float* sig, int N, int F, int batch, const char* tab
   if (items >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const int grid = (int)std::min<int64_t>(items, grid_cap);
   mr_fft_kernel<R><<<grid, kThreadsMr, smem, st>>>(sig, N, F, batch, mr_tables(R, tables), eps,
-                                                   scale, mode, logy, loss_voice, part, err);
+                                                   scale, mode, logy, loss_item, part, err);
   return cudaGetLastError();
 }
 
 cudaError_t mr_pass(int n_fft, const float* sig, int N, int F, int batch, const char* tables,
-                    float eps, float scale, int mode, float* logy, double* loss_voice, float* part,
+                    float eps, float scale, int mode, float* logy, double* loss_item, float* part,
                     unsigned int* err, cudaStream_t st) {
-#define SYNTH_MR_ARGS sig, N, F, batch, tables, eps, scale, mode, logy, loss_voice, part, err, st
+#define SYNTH_MR_ARGS sig, N, F, batch, tables, eps, scale, mode, logy, loss_item, part, err, st
   switch (r_of(n_fft)) {
     case 8: return mr_launch<8>(SYNTH_MR_ARGS);
     case 16: return mr_launch<16>(SYNTH_MR_ARGS);
@@ -632,9 +632,29 @@ struct MrLayout {
   char* tables[8];
   float* part[8];
   float* logy[8];
+  double* loss_item[8];  // per work item (voice, frame group) of each resolution
+  int groups[8];
   double* loss_voice;
   size_t total;
 };
+
+// Per-voice loss: the work items' partial sums added in a fixed order
+// (resolution, then frame group), so the total does not depend on which
+// CTA finished first.
+struct MrLossItems {
+  const double* item[8];
+  int groups[8];
+  int n_res;
+};
+
+__global__ void mr_loss_reduce(MrLossItems li, int batch, double* __restrict__ loss_voice) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= batch) return;
+  double s = 0.0;
+  for (int r = 0; r < li.n_res; ++r)
+    for (int g = 0; g < li.groups[r]; ++g) s += li.item[r][(size_t)v * li.groups[r] + g];
+  loss_voice[v] = s;
+}
 
 MrLayout mr_layout(int64_t N, int batch, const int* n_ffts, int n_res, void* ws) {
   MrLayout L;
@@ -651,6 +671,8 @@ MrLayout mr_layout(int64_t N, int batch, const int* n_ffts, int n_res, void* ws)
     L.logy[r] = reinterpret_cast<float*>(take(sizeof(float) * batch * F * (n / 2 + 4)));
     const int64_t groups = (F + mr_group(n) - 1) / mr_group(n);
     L.part[r] = reinterpret_cast<float*>(take(sizeof(float) * batch * groups * mr_seg(n)));
+    L.loss_item[r] = reinterpret_cast<double*>(take(sizeof(double) * batch * groups));
+    L.groups[r] = (int)groups;
   }
   L.loss_voice = reinterpret_cast<double*>(take(sizeof(double) * batch));
   L.total = off;
@@ -682,16 +704,19 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
         return e;
     }
   }
-  if ((e = cudaMemsetAsync(L.loss_voice, 0, sizeof(double) * batch, st)) != cudaSuccess) return e;
   OlaArgs ola;
+  MrLossItems li;
+  li.n_res = n_res;
   ola.n_res = n_res;
   for (int r = 0; r < n_res; ++r) {
     const int n = n_ffts[r], F = stft_frames(N, n);
     const float scale = 1.0f / (float)((int64_t)F * (n / 2 + 1));
     if ((e = mr_pass(n, x, (int)N, F, batch, L.tables[r], eps, scale,
-                     grad_x ? kMrLossGrad : kMrLoss, L.logy[r], L.loss_voice, L.part[r], err, st)) !=
-        cudaSuccess)
+                     grad_x ? kMrLossGrad : kMrLoss, L.logy[r], L.loss_item[r], L.part[r], err,
+                     st)) != cudaSuccess)
       return e;
+    li.item[r] = L.loss_item[r];
+    li.groups[r] = L.groups[r];
     ola.r[r] = OlaRes{L.part[r], n, n / 4, mr_group(n), (F + mr_group(n) - 1) / mr_group(n),
                       mr_seg(n), F};
   }
@@ -701,9 +726,8 @@ cudaError_t mrstft_loss_grad(const float* x, const float* y, int64_t N, int batc
     dim3 go((unsigned)std::min<int64_t>((N / 4 + 255) / 256 + 1, 1024), (unsigned)batch);
     mr_ola_gather<<<go, 256, 0, st>>>(ola, (int)N, pad_max, grad_x);
   }
-  if (loss_voice_out)
-    cudaMemcpyAsync(loss_voice_out, L.loss_voice, sizeof(double) * batch, cudaMemcpyDeviceToDevice,
-                    st);
+  mr_loss_reduce<<<(batch + 127) / 128, 128, 0, st>>>(li, batch,
+                                                     loss_voice_out ? loss_voice_out : L.loss_voice);
   return cudaGetLastError();
 }
 

@@ -282,6 +282,37 @@ synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch
                                            static_cast<cudaStream_t>(stream)));
 }
 
+synth_status synth_gemm_bf16_workspace_size(synth_handle h, int32_t m, int32_t n, size_t* bytes) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!bytes || m < 1 || n < 1) return SYNTH_ERR_ARG;
+  *bytes = gemm_splitk_workspace_bytes(m, n);
+  return *bytes ? SYNTH_OK : SYNTH_ERR_CUDA;
+}
+
+synth_status synth_gemm_bf16_splitk(synth_handle h, const void* a_dev, int32_t lda,
+                                    const void* b_dev, int32_t ldb, float* c_dev, int32_t ldc,
+                                    int32_t m, int32_t n, int32_t k, float alpha,
+                                    void* workspace_dev, size_t workspace_bytes, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!a_dev || !b_dev || !c_dev || m < 1 || n < 1 || k < 8 || (k % 8) != 0 || lda < k ||
+      ldb < k || ldc < n || (lda % 8) != 0 || (ldb % 8) != 0)
+    return SYNTH_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(a_dev) & 15) || (reinterpret_cast<uintptr_t>(b_dev) & 15) ||
+      (reinterpret_cast<uintptr_t>(workspace_dev) & 15))
+    return SYNTH_ERR_ARG;
+  GemmEpilogue epi;
+  epi.kind = kEpiStoreF32;
+  epi.out_f32 = c_dev;
+  epi.ldc = ldc;
+  epi.alpha = alpha;
+  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  return check_cuda(gemm_bf16(static_cast<const __nv_bfloat16*>(a_dev), lda,
+                              static_cast<const __nv_bfloat16*>(b_dev), ldb, m, n, k, epi,
+                              &hdr->error, static_cast<cudaStream_t>(stream),
+                              static_cast<float*>(workspace_dev),
+                              workspace_dev ? workspace_bytes : 0));
+}
+
 synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, const void* b_dev,
                              int32_t ldb, float* c_dev, int32_t ldc, int32_t m, int32_t n,
                              int32_t k, float alpha, void* stream) {
@@ -300,6 +331,28 @@ synth_status synth_gemm_bf16(synth_handle h, const void* a_dev, int32_t lda, con
   return check_cuda(gemm_bf16(static_cast<const __nv_bfloat16*>(a_dev), lda,
                               static_cast<const __nv_bfloat16*>(b_dev), ldb, m, n, k, epi,
                               &hdr->error, static_cast<cudaStream_t>(stream)));
+}
+
+// ---------------------------------------------------------------- MMD
+synth_status synth_l1_distances(synth_handle h, const void* emb_dev, int64_t ld, int32_t m,
+                                int32_t dim, float* dist_dev, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (m < 0 || dim < 1 || ld < dim || (ld % 8) != 0 || (m > 0 && (!emb_dev || !dist_dev)) ||
+      (reinterpret_cast<uintptr_t>(emb_dev) & 15) || (int64_t)m * ld >= ((int64_t)1 << 40))
+    return SYNTH_ERR_ARG;
+  return check_cuda(launch_l1_distances(static_cast<const __nv_bfloat16*>(emb_dev), ld, m, dim,
+                                        dist_dev, static_cast<cudaStream_t>(stream)));
+}
+
+synth_status synth_mmd_trials(synth_handle h, const float* dist_dev, int32_t m,
+                              const int8_t* labels_dev, int32_t trials, double* mmd_dev,
+                              void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (m < 1 || m > 48 * 1024 || trials < 0 ||
+      (trials > 0 && (!dist_dev || !labels_dev || !mmd_dev)))
+    return SYNTH_ERR_ARG;
+  return check_cuda(launch_mmd_trials(dist_dev, m, labels_dev, trials, mmd_dev,
+                                      static_cast<cudaStream_t>(stream)));
 }
 
 // ---------------------------------------------------------------- MR-STFT
@@ -350,6 +403,7 @@ struct synth_model_s {
   int max_batch = 0;
   int frames = 0;
   int step = 0;
+  int last_batch = 0;  // batch of the last forward or training step
 };
 
 static const int kHidden = 1024;
@@ -364,7 +418,8 @@ synth_status synth_model_create(synth_handle h, int32_t max_batch, uint64_t seed
   m->synth = h;
   m->max_batch = max_batch;
   m->frames = stft_frames(h->vc.n_samples, kMelFFT);
-  m->L = mlp_layout(m->frames * kMelBands, kHidden, kNumParams, max_batch);
+  m->L = mlp_layout(m->frames * kMelBands, kHidden, kNumParams, max_batch,
+                    gemm_splitk_workspace_bytes(max_batch, kHidden));
   const size_t N = (size_t)h->vc.n_samples;
   const size_t a_bytes = (sizeof(float) * max_batch * N + 255) & ~size_t(255);
   const size_t p_bytes = (sizeof(float) * max_batch * kNumParams + 255) & ~size_t(255);
@@ -448,6 +503,7 @@ synth_status synth_model_forward(synth_model m, const void* features_dev, int32_
   if (!m) return SYNTH_ERR_STATE;
   if (!features_dev || !params_out_dev || batch < 1 || batch > m->max_batch) return SYNTH_ERR_ARG;
   ScratchHeader* hdr = static_cast<ScratchHeader*>(m->synth->scratch);
+  m->last_batch = batch;
   return check_cuda(mlp_forward(m->L, m->mem, static_cast<const __nv_bfloat16*>(features_dev), batch,
                                 false, params_out_dev, &hdr->error,
                                 static_cast<cudaStream_t>(stream)));
@@ -462,6 +518,7 @@ synth_status synth_model_train_features(synth_model m, const void* features_dev,
     return SYNTH_ERR_ARG;
   ScratchHeader* hdr = static_cast<ScratchHeader*>(m->synth->scratch);
   m->step += 1;
+  m->last_batch = batch;
   return check_cuda(mlp_train_step(m->L, m->mem, static_cast<const __nv_bfloat16*>(features_dev),
                                    target_dev, batch, lr, m->step, loss_dev, &hdr->error,
                                    static_cast<cudaStream_t>(stream)));
@@ -500,6 +557,14 @@ static float* model_tensor(synth_model m, int32_t which, int32_t layer, size_t* 
 
 synth_status synth_model_get_tensor(synth_model m, int32_t which, int32_t layer, float* dst_dev,
                                     size_t count, void* stream) {
+  if (m && which == 4) {
+    // hidden activations of the last forward / training step, bf16 -> FP32
+    if (layer < 1 || layer > 3 || !dst_dev || m->last_batch < 1 ||
+        count != (size_t)m->last_batch * kHidden)
+      return SYNTH_ERR_ARG;
+    return check_cuda(mlp_hidden_f32(m->L, m->mem, layer, m->last_batch, dst_dev,
+                                     static_cast<cudaStream_t>(stream)));
+  }
   size_t n = 0;
   float* src = model_tensor(m, which, layer, &n);
   if (!src || !dst_dev || count != n) return SYNTH_ERR_ARG;

@@ -43,20 +43,28 @@ def test_batches(batch: int):
 
 def train(model: pkg.ProposalModel, steps: int, batch: int = 128, seed: int = 0,
           lr: float = 3e-4, log_every: int = 100):
+    """On-the-fly training over consecutive training-split batches; returns
+    the loss history, wall seconds and GPU milliseconds (CUDA events around
+    the whole loop)."""
     import torch
     syn = model.synth
     loss = torch.zeros(1, device=syn.device)
     hist = []
     it = train_batches(batch)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
+    start.record()
     for s in range(steps):
         lr_s = lr * min(1.0, (s + 1) / 200) * (0.1 ** (s / max(1, steps)))
         model.train_step(seed, next(it), batch, lr_s, loss=loss)
         if s % log_every == 0 or s == steps - 1:
-            syn.sync()
-            hist.append((s, float(loss.item())))
+            hist.append((s, loss.clone()))
+    end.record()
+    end.synchronize()
     syn.sync()
-    return {"steps": steps, "batch": batch, "seconds": time.perf_counter() - t0, "loss": hist}
+    hist = [(s, float(l.item())) for s, l in hist]
+    return {"steps": steps, "batch": batch, "seconds": time.perf_counter() - t0,
+            "gpu_ms": start.elapsed_time(end), "loss": hist}
 
 
 def refine(syn: pkg.Synth, target, u0, steps: int, lr: float, seed: int, batch_index: int):
@@ -121,16 +129,21 @@ def evaluate(model: pkg.ProposalModel, voices: int, steps: int, lr: float = 0.02
     return results, finals
 
 
-def summarize(results):
+def summarize(results, goal: float | None = None):
+    """Mean distance per refinement step over all evaluated voices, the GPU
+    milliseconds spent up to each step (summed over batches; the proposal
+    arm includes the network's own inference), and for each arm the step
+    and GPU time at which the mean distance first reaches ``goal`` (default:
+    the random-start arm's final distance)."""
     out = {}
     for k, runs in results.items():
         steps = len(runs[0])
         dist = [sum(r[s][1] for r in runs) / len(runs) for s in range(steps)]
         ms = [sum(r[s][2] for r in runs) for s in range(steps)]
         out[k] = {"distance": dist, "gpu_ms": ms}
-    # GPU time for each method to reach the random-start method's final distance
-    goal = out["random"]["distance"][-1]
-    for k in out:
+    if goal is None:
+        goal = out["random"]["distance"][-1]
+    for k in list(out):
         hit = next((i for i, d in enumerate(out[k]["distance"]) if d <= goal), None)
         out[k]["steps_to_goal"] = hit
         out[k]["gpu_ms_to_goal"] = out[k]["gpu_ms"][hit] if hit is not None else None

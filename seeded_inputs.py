@@ -117,4 +117,24 @@ def sample_voices(seed: int, batch: int, count: int) -> np.ndarray:
     return np.sort(np.concatenate([[0, batch - 1], mid]).astype(np.int32))
 
 
+def mmd_labels(seed: int, trials: int, sizes, pair, n: int) -> np.ndarray:
+    """Trial labels over a pool of corpora laid end to end (corpus c holds
+    sizes[c] sounds): [trials][sum(sizes)] int8, 0 for X, 1 for Y, -1 left
+    out. pair = (a, b): with a == b, X and Y are a random split of n + n
+    sounds of corpus a (the paper's within-corpus diversity); otherwise n
+    sounds drawn from each corpus. Each trial draws afresh."""
+    rng = np.random.default_rng(seed)
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    out = np.full((trials, int(starts[-1])), -1, dtype=np.int8)
+    a, b = pair
+    for t in range(trials):
+        if a == b:
+            pick = rng.choice(sizes[a], size=2 * n, replace=False) + starts[a]
+            out[t, pick[:n]], out[t, pick[n:]] = 0, 1
+        else:
+            out[t, rng.choice(sizes[a], size=n, replace=False) + starts[a]] = 0
+            out[t, rng.choice(sizes[b], size=n, replace=False) + starts[b]] = 1
+    return out
+
+
 TWO_PI = 2.0 * math.pi

@@ -206,3 +206,36 @@ def test_log_mel_floor_and_power_scale():
     power[kbin - 1] = power[kbin + 1] = (A * n / 8) ** 2
     want = np.log(fb @ power + 1e-6)
     assert np.allclose(m1[10:30][:, loud], want[loud], atol=1e-9)
+
+
+def test_mlp_trace_matches_autograd():
+    """The written-out chain rule of mlp_trace gives autograd's loss and
+    gradients (which the finite-difference test pins), and its Y is
+    mlp_forward's output."""
+    rng = np.random.default_rng(8)
+    dims = [7, 6, 5, 4, 3]
+    ws = [rng.standard_normal((dims[i + 1], dims[i])) * 0.6 for i in range(4)]
+    bs = [rng.standard_normal(dims[i + 1]) * 0.2 for i in range(4)]
+    x = rng.standard_normal((5, 7))
+    tgt = rng.uniform(size=(5, 3))
+    tr = sp.mlp_trace(x, tgt, ws, bs)
+    loss, gw, gb = sp.mlp_loss_and_grads(x, tgt, ws, bs)
+    assert tr["loss"] == pytest.approx(loss, rel=1e-14)
+    assert np.allclose(tr["Y"], sp.mlp_forward(x, ws, bs).numpy(), rtol=1e-14, atol=0)
+    for l in range(4):
+        assert np.allclose(tr["gW"][l], gw[l], rtol=1e-12, atol=1e-15)
+        assert np.allclose(tr["gb"][l], gb[l], rtol=1e-12, atol=1e-15)
+    assert np.any(tr["Z"][1] < 0)  # the ReLU masks something in this case
+    # given ReLU decisions: the oracle's own reproduce the trace; flipping one
+    # entry moves the gradients below it by exactly that entry's dH term
+    own = [tr["Z"][l] > 0 for l in range(3)]
+    same = sp.mlp_trace(x, tgt, ws, bs, masks=own)
+    assert np.array_equal(same["gW"][0], tr["gW"][0])
+    flipped = [m.copy() for m in own]
+    b, j = np.argwhere(~own[1])[0]
+    flipped[1][b, j] = True
+    alt = sp.mlp_trace(x, tgt, ws, bs, masks=flipped)
+    extra = np.zeros_like(tr["dZ"][1])
+    extra[b, j] = tr["dH"][2][b, j]
+    assert np.allclose(alt["gW"][1] - tr["gW"][1], extra.T @ tr["H"][1], atol=1e-15)
+    assert np.array_equal(alt["gW"][2], tr["gW"][2])

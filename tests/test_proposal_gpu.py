@@ -4,7 +4,8 @@ Sec. 2.2 test split) are fitted by adjoint refinement on the MR-STFT
 distance, once from the network's proposal and once from random parameters.
 The FP64 oracle decides: it re-synthesizes both fitted parameter sets and
 measures their multi-resolution STFT distance to its own rendering of
-the target voices. Refinement renders with another noise seed than the
+the target voices. The proposal arm must also reach the random arm's final
+distance in less GPU time (CUDA events), its own inference counted. Refinement renders with another noise seed than the
 target, so the distance cannot reach 0 (the noise realisations differ)."""
 import numpy as np
 import pytest
@@ -36,7 +37,12 @@ def test_proposal_beats_random_starts_under_the_oracle(oracle_mod):
     assert all(pkg.synth_is_test(bi * batch + v) for v in range(batch))
     target_full, true_u = syn.render(seed, bi, batch)
     target = target_full[:VOICES].contiguous()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
     u_prop = model.propose(target)
+    end.record()
+    end.synchronize()
+    prop_ms = start.elapsed_time(end)  # the network's inference, charged to its arm
     gen = torch.Generator(device="cuda").manual_seed(7)
     u_rand = torch.rand((VOICES, 78), device="cuda", generator=gen)
     fit_p, curve_p = pr.refine(syn, target, u_prop, REFINE_STEPS, 0.02, seed + 1, bi)
@@ -63,8 +69,13 @@ def test_proposal_beats_random_starts_under_the_oracle(oracle_mod):
           f"random {curve_r[-1][1]:.3f}")
     assert np.all(np.isfinite(d_prop)) and np.all(np.isfinite(d_rand))
     assert d_prop.mean() < d_rand.mean()
-    # refinement from the proposal reaches the random starts' final distance
-    # (GPU measure) in fewer steps
+    # the stated distance: the random starts' final (GPU-measured) distance;
+    # the proposal arm reaches it in less GPU time, its inference included
     goal = curve_r[-1][1]
-    hit = next(i for i, (_, d, _) in enumerate(curve_p) if d <= goal)
-    assert hit < REFINE_STEPS
+    hit = next((i for i, (_, d, _) in enumerate(curve_p) if d <= goal), None)
+    assert hit is not None
+    gpu_ms_prop = prop_ms + curve_p[hit][2]
+    gpu_ms_rand = curve_r[-1][2]
+    print(f"PROPOSAL GPU ms to distance {goal:.3f}: proposal {gpu_ms_prop:.1f} "
+          f"({hit} steps), random starts {gpu_ms_rand:.1f} ({REFINE_STEPS} steps)")
+    assert gpu_ms_prop < gpu_ms_rand

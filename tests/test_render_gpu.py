@@ -241,3 +241,42 @@ def test_render_batches_full_size_sampled(torch_cuda, oracle_mod):
         err = float(np.max(np.abs(a - ref_a[rows])))
         assert err <= TOL, f"batch {k}: max-abs error {err:.3e}"
     syn.close()
+
+
+def _noise_only(u):
+    """Noise level 1, sine and square-saw levels 0; ADSR0 held at 1 for the
+    whole voice (attack and decay 0, sustain 1, note-on the full 4 s) and
+    routed alone, with weight 1, to the noise amplitude. The last control
+    point sits at t = 4 s = the note-off time: a release (5 s) that starts
+    there with alpha = 6 stays 1 - (tau / 5)^6 = 1 in FP32 for any tau the
+    two sides may round t - d to, so the tie at the note-off decides
+    nothing. The other parameters keep their drawn values."""
+    u = np.array(u, dtype=np.float64, copy=True)
+    u[:, si.MIX], u[:, si.MIX + 1], u[:, si.MIX + 2] = 0.0, 0.0, 1.0
+    u[:, si.DURATION] = 1.0
+    u[:, si.ADSR + 0], u[:, si.ADSR + 1], u[:, si.ADSR + 2], u[:, si.ADSR + 3] = 0.0, 0.0, 1.0, 1.0
+    u[:, si.ADSR + 4] = 1.0
+    for s in range(4):
+        u[:, si.mod_slot(s, 4)] = 0.0
+    u[:, si.mod_slot(0, 4)] = 1.0
+    return u
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_noise_stream_bit_exact(synth4, oracle_mod, torch_cuda, plain):
+    """The noise oscillator's Philox stream, bit for bit: with the patch of
+    _noise_only the output is exactly v = 2 u01(word) - 1 in FP32 (amplitude
+    1 + 0 x slope, gain 1, the other two terms 0 x finite), so the GPU audio
+    must equal the oracle's audio (FP64, rounded once to FP32) exactly, for
+    every sample of batch 16 x 4 s (voices g = 80..95, seed 5)."""
+    torch = torch_cuda
+    u = _noise_only(np.stack([oracle_mod.draw_params(5, 80 + v) for v in range(16)]))
+    pin = torch.tensor(u, dtype=torch.float32, device="cuda")
+    audio, params = synth4.render(5, 5, 16, params_in=pin, plain=plain)
+    synth4.sync()
+    ref_a, ref_p = _oracle_batch(oracle_mod, 4.0, 5, 5, 16, u_in=u.astype(np.float32).astype(np.float64))
+    a = audio.cpu().numpy()
+    assert np.all(np.abs(ref_a) <= 1.0) and np.std(ref_a) > 0.5
+    assert np.array_equal(a, ref_a), f"{np.count_nonzero(a != ref_a)} samples differ"
+    # params_out returns the caller's parameters as given
+    assert np.array_equal(params.cpu().numpy(), u.astype(np.float32))
