@@ -43,7 +43,8 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 64;          // one 128-byte swizzle row of bf16
 constexpr int kStages = 4;
-constexpr int kGemmThreads = 192;
+constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, each half the columns
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
 constexpr long long kWaitLimit = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -137,6 +138,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive accumulator columns of this thread's TMEM lane, one wait.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <int BN>
 struct __align__(1024) GemmSmem {
   __nv_bfloat16 a[kStages][BM * BK];
@@ -145,9 +164,12 @@ struct __align__(1024) GemmSmem {
   uint64_t empty[kStages];
   uint64_t acc_full[2];   // MMA -> epilogue: accumulator b holds a finished tile
   uint64_t acc_empty[2];  // epilogue -> MMA: accumulator b may be overwritten
+  float stage[kEpiWarps][32][33];  // per epilogue warp: a 32 x 32 chunk of its rows, padded
   uint32_t tmem_base;
   int failed;
 };
+
+static_assert(sizeof(GemmSmem<256>) + 1024 <= 232448, "GEMM shared memory within the 227 KB per CTA");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -176,7 +198,7 @@ __device__ __forceinline__ GemmItem gemm_item(int item, int n_tiles, int tiles_n
 // Otherwise (split-K, `splits` slices of kb_per k-blocks each) the raw
 // accumulator of slice s goes to part[s][M][N].
 template <int BN>
-__global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_tc(
     const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
     GemmEpilogue epi, int M, int N, int K, int splits, int kb_per, float* part,
     unsigned int* err) {
@@ -196,7 +218,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sm.acc_full[b], 1);
-      mbar_init(&sm.acc_empty[b], 4);  // one arrival per epilogue warp
+      mbar_init(&sm.acc_empty[b], kEpiWarps);  // one arrival per epilogue warp
     }
     sm.failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -253,8 +275,14 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
       umma_commit(&sm.acc_full[buf]);
     }
   } else if (warp >= 2) {
-    // epilogue
+    // epilogue: a warp owns 32 rows of the tile (its TMEM lane quarter). Per
+    // 32-column chunk it loads the accumulator (lane = row), applies the
+    // element-wise epilogue in registers, stages the chunk in shared memory
+    // and writes it back row by row (lane = column: 128-byte coalesced
+    // stores) and, for a transposed copy, column by column (lane = row)
     const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;  // which half of the tile's columns
+    float(*S)[33] = sm.stage[warp - 2];
     int t = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++t) {
       const GemmItem g = gemm_item(item, n_tiles, tiles_n, BN, kb_per, nk);
@@ -263,63 +291,69 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
       const bool ok = mbar_wait(&sm.acc_full[buf], use & 1u);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) { sm.failed = 1; break; }
-      const int row = g.m0 + 32 * q + lane;
+      const int row0 = g.m0 + 32 * q;
       const uint32_t acc = tmem + (uint32_t)(buf * BN) + ((uint32_t)(32 * q) << 16);
+      const bool act = !part && epi.kind == kEpiBiasActBF16;
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 16) {
-        float v[16];
-        tmem_ld16(acc + (uint32_t)c, v);
-        if (row >= M) continue;
+      for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+        float v[32];
+        tmem_ld32(acc + (uint32_t)c, v);
         const int col0 = g.n0 + c;
-        if (part) {
-          // split-K: the raw partial sums of this K-slice
-          float* out = part + ((size_t)g.split * M + row) * N;
-          if (col0 + 15 < N && (N & 3) == 0) {
-            float4* o4 = reinterpret_cast<float4*>(out + col0);
+        if (act) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-              o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (col0 + i < N) out[col0 + i] = v[i];
+          for (int i = 0; i < 32; ++i) {
+            const int col = min(col0 + i, N - 1);
+            float z = v[i] + (epi.bias ? epi.bias[col] : 0.f);
+            if (epi.act == kActRelu) z = fmaxf(z, 0.f);
+            else if (epi.act == kActSigmoid) z = sigmoidf(z);
+            v[i] = z;
           }
-          continue;
         }
-        switch (epi.kind) {
-          case kEpiStoreF32: {
-            float* out = epi.out_f32 + (size_t)row * epi.ldc;
-            if (col0 + 15 < N && ((reinterpret_cast<uintptr_t>(out + col0) & 15) == 0)) {
-              float4* o4 = reinterpret_cast<float4*>(out + col0);
+        __syncwarp();
 #pragma unroll
-              for (int i = 0; i < 4; ++i)
-                o4[i] = make_float4(v[4 * i] * epi.alpha, v[4 * i + 1] * epi.alpha,
-                                    v[4 * i + 2] * epi.alpha, v[4 * i + 3] * epi.alpha);
+        for (int i = 0; i < 32; ++i) S[lane][i] = v[i];
+        __syncwarp();
+        // FP32 rows: lane = (row within 4, 4-column group); one 16-byte store
+        // per lane covers four whole 128-byte row segments per instruction
+        float* f32 = part ? part + (size_t)g.split * M * N : epi.out_f32;
+        const size_t ld32 = part ? (size_t)N : (size_t)epi.ldc;
+        const float mul = part || act ? 1.f : epi.alpha;
+        const bool f32_out = part || epi.kind == kEpiStoreF32 || epi.out_f32;
+        const int c4 = 4 * (lane & 7), rs = lane >> 3;
+        const bool vec4 = col0 + 31 < N && (ld32 & 3) == 0 &&
+                          (reinterpret_cast<uintptr_t>(f32) & 15) == 0;
+        if (f32_out) {
+#pragma unroll 2
+          for (int r = 0; r < 32; r += 4) {
+            const int row = row0 + r + rs;
+            if (row >= M) continue;
+            float* o = f32 + (size_t)row * ld32 + col0 + c4;
+            const float* sr = S[r + rs] + c4;
+            if (vec4) {
+              *reinterpret_cast<float4*>(o) =
+                  make_float4(sr[0] * mul, sr[1] * mul, sr[2] * mul, sr[3] * mul);
             } else {
 #pragma unroll
-              for (int i = 0; i < 16; ++i)
-                if (col0 + i < N) out[col0 + i] = v[i] * epi.alpha;
+              for (int i = 0; i < 4; ++i)
+                if (col0 + c4 + i < N) o[i] = sr[i] * mul;
             }
-            break;
           }
-          case kEpiBiasActBF16: {
-            // y = act(acc + bias) in bf16 (and optionally the transposed copy)
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int col = col0 + i;
-              if (col >= N) continue;
-              float z = v[i] + (epi.bias ? epi.bias[col] : 0.f);
-              if (epi.act == kActRelu) z = fmaxf(z, 0.f);
-              else if (epi.act == kActSigmoid) z = sigmoidf(z);
-              const __nv_bfloat16 b = __float2bfloat16(z);
-              if (epi.out_bf16) epi.out_bf16[(size_t)row * epi.ldc + col] = b;
-              if (epi.out_bf16_t) epi.out_bf16_t[(size_t)col * epi.ldc_t + row] = b;
-              if (epi.out_f32) epi.out_f32[(size_t)row * epi.ldc + col] = z;
-            }
-            break;
+        }
+        if (act && epi.out_bf16 && col0 + lane < N) {
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            const int row = row0 + r;
+            if (row >= M) break;
+            epi.out_bf16[(size_t)row * epi.ldc + col0 + lane] = __float2bfloat16(S[r][lane]);
           }
-          default:
-            break;
+        }
+        if (act && epi.out_bf16_t && row0 + lane < M) {
+          const int row = row0 + lane;
+#pragma unroll 4
+          for (int cc = 0; cc < 32; ++cc) {
+            if (col0 + cc >= N) break;
+            epi.out_bf16_t[(size_t)(col0 + cc) * epi.ldc_t + row] = __float2bfloat16(S[lane][cc]);
+          }
         }
       }
       // the accumulator's values are all in registers or stored: release it
@@ -340,26 +374,51 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_tc(
 
 // Split-K reduction with the fused epilogue: C = sum over slices s = 0, 1, ...
 // of part[s] in that order, then the epilogue of `epi`. A block covers a
-// 32 x 32 output tile (32 x 8 threads, 4 rows each); the transposed bf16
-// copy goes through shared memory so both of its stores are coalesced.
+// 16 x 32 output tile (32 x 8 threads, 2 rows each: 256 blocks for a
+// 128 x 1024 output); the transposed bf16 copy goes through shared memory
+// so both of its stores are coalesced.
+constexpr int kRedRows = 16;
 __global__ void __launch_bounds__(256) splitk_reduce(const float* __restrict__ part, int splits,
                                                      int M, int N, GemmEpilogue epi) {
-  __shared__ float tile[32][33];
+  __shared__ float tile[kRedRows][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int c = blockIdx.x * 32 + tx, r0 = blockIdx.y * 32;
+  const int c = blockIdx.x * 32 + tx, r0 = blockIdx.y * kRedRows;
   const size_t slice = (size_t)M * N;
+  // the two rows' slices, eight at a time: 16 loads in flight per thread,
+  // added in slice order afterwards
+  const float* p[2];
+  bool ok[2];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
+    const int r = r0 + ty + 8 * i;
+    ok[i] = r < M && c < N;
+    p[i] = part + (size_t)(ok[i] ? r : 0) * N + (ok[i] ? c : 0);
+  }
+  float acc[2] = {0.f, 0.f};
+  int k = 0;
+  for (; k + 8 <= splits; k += 8) {
+    float t[2][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) t[i][u] = ok[i] ? p[i][(size_t)(k + u) * slice] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) acc[i] += t[i][u];
+  }
+  for (; k < splits; ++k)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) acc[i] += ok[i] ? p[i][(size_t)k * slice] : 0.f;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
     const int r = r0 + ty + 8 * i;
     float z = 0.f;
-    if (r < M && c < N) {
-      const float* p = part + (size_t)r * N + c;
-      float acc = 0.f;
-      for (int k = 0; k < splits; ++k) acc += p[(size_t)k * slice];
+    if (ok[i]) {
       if (epi.kind == kEpiStoreF32) {
-        epi.out_f32[(size_t)r * epi.ldc + c] = acc * epi.alpha;
+        epi.out_f32[(size_t)r * epi.ldc + c] = acc[i] * epi.alpha;
       } else {
-        z = acc + (epi.bias ? epi.bias[c] : 0.f);
+        z = acc[i] + (epi.bias ? epi.bias[c] : 0.f);
         if (epi.act == kActRelu) z = fmaxf(z, 0.f);
         else if (epi.act == kActSigmoid) z = sigmoidf(z);
         const __nv_bfloat16 b = __float2bfloat16(z);
@@ -372,11 +431,13 @@ __global__ void __launch_bounds__(256) splitk_reduce(const float* __restrict__ p
   }
   if (epi.kind != kEpiBiasActBF16 || !epi.out_bf16_t) return;
   __syncthreads();
+  // transposed: 16 rows of each of the 32 columns, lanes along the rows
+  const int rr = threadIdx.x & 15, cq = threadIdx.x >> 4;  // 16 rows x 16 column pairs
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int cc = blockIdx.x * 32 + ty + 8 * i, r = r0 + tx;
+  for (int j = 0; j < 2; ++j) {
+    const int cc = blockIdx.x * 32 + 2 * cq + j, r = r0 + rr;
     if (cc < N && r < M)
-      epi.out_bf16_t[(size_t)cc * epi.ldc_t + r] = __float2bfloat16(tile[tx][ty + 8 * i]);
+      epi.out_bf16_t[(size_t)cc * epi.ldc_t + r] = __float2bfloat16(tile[rr][2 * cq + j]);
   }
 }
 
@@ -481,7 +542,7 @@ cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEp
   gemm_bf16_tc<BN><<<grid, kGemmThreads, smem, st>>>(ma, mb, epi, M, N, K, splits, kb_per,
                                                      splits > 1 ? ws : nullptr, err);
   if ((e = cudaGetLastError()) != cudaSuccess || splits == 1) return e;
-  const dim3 rgrid((N + 31) / 32, (M + 31) / 32);
+  const dim3 rgrid((N + 31) / 32, (M + kRedRows - 1) / kRedRows);
   splitk_reduce<<<rgrid, 256, 0, st>>>(ws, splits, M, N, epi);
   return cudaGetLastError();
 }

@@ -150,14 +150,25 @@ __global__ void __launch_bounds__(256) relu_grad(const float* __restrict__ dh,
   }
 }
 
-// Bias gradient: db[c] = sum_b dZ[b][c] from the FP32 dZ (one thread per column).
-__global__ void bias_grad(const float* __restrict__ dz, int batch, int width, int ld,
-                          float* __restrict__ db) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= width) return;
+// Bias gradient: db[c] = sum_b dZ[b][c] from the FP32 dZ. A block covers 32
+// columns with 8 threads per column, each adding every 8th row; the eight
+// partial sums are then added in thread order (deterministic).
+__global__ void __launch_bounds__(256) bias_grad(const float* __restrict__ dz, int batch, int width,
+                                                 int ld, float* __restrict__ db) {
+  __shared__ float part[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx;
   float s = 0.f;
-  for (int b = 0; b < batch; ++b) s += dz[(int64_t)b * ld + c];
-  db[c] = s;
+  if (c < width)
+    for (int b = ty; b < batch; b += 8) s += dz[(int64_t)b * ld + c];
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && c < width) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += part[k][tx];
+    db[c] = t;
+  }
 }
 
 // Adam (Kingma & Ba, 2015) on FP32 master values; also refreshes the bf16
@@ -371,8 +382,8 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
     const int in = L.dims[l], out = L.dims[l + 1];
     const int ldz = l == 3 ? Pp : out;
     // bias and weight gradients: dW[out][in] = dZ^T[out][B] * H_{l}^T[in][B]^T
-    bias_grad<<<(out + 255) / 256, 256, 0, st>>>(dzf, batch, out, ldz,
-                                                 reinterpret_cast<float*>(base + L.gb[l]));
+    bias_grad<<<(out + 31) / 32, 256, 0, st>>>(dzf, batch, out, ldz,
+                                               reinterpret_cast<float*>(base + L.gb[l]));
     const __nv_bfloat16* hprev_t =
         l == 0 ? h0t : reinterpret_cast<const __nv_bfloat16*>(base + L.ht[l]);
     GemmEpilogue ew;

@@ -39,7 +39,11 @@ __global__ void __launch_bounds__(256) sfu_probe_kernel(int iters, float* __rest
   for (int c = 0; c < kChains; ++c) x[c] = 0.001f * (float)(threadIdx.x + c) + 0.5f;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) x[c] = mufu<OP>(x[c]);
+    for (int c = 0; c < kChains; ++c) {
+      // rcp(rcp(x)) is x: an FP32 add between reciprocals keeps every one
+      // of them (the add runs on the FP32 pipe, not the unit under test)
+      x[c] = OP == SYNTH_SFU_RCP ? mufu<OP>(x[c]) + 1.0f : mufu<OP>(x[c]);
+    }
   }
   float s = 0.f;
 #pragma unroll
