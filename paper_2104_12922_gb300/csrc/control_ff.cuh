@@ -239,6 +239,7 @@ __device__ inline ff vco_interval_ff(ff m_a, ff m_b, float R, int Rk, ff inv_R, 
   out->q2 = 2.f + e1;                 // 1 + r, r = 1 + e1
   out->q3 = fmaf(e1, e1 + 3.f, 3.f);  // 1 + r + r^2 = 3 + 3 e1 + e1^2
   out->invE = tiny ? 0.f : 1.0f / e1;
+  out->ih = tiny ? 1.f : xf * out->invE;
   out->jc_flags = jc | ((a_lin || tiny) ? 1 << 16 : 0) | ((b_lin || tiny) ? 1 << 17 : 0) |
                   (c_first ? 1 << 18 : 0) | (c_last ? 1 << 19 : 0);
   *inc_first = out->cA;

@@ -25,6 +25,7 @@ struct __align__(16) SegVco {
   float invE;    // 1 / expm1(x)
   float q2, q3;  // 1 + r and 1 + r + r^2 with r = e^x (a quad's phase steps, in units of
                  // its first increment)
+  float ih;      // x / expm1(x) (1 when x = 0)
   int jc_flags;  // jc | (A linear) << 16 | (B linear) << 17 | (A capped) << 18 | (B capped) << 19
 };
 
@@ -44,6 +45,20 @@ __device__ __forceinline__ float expm1_phase(float z) {
     return z * p;
   }
   return expm1f(z);
+}
+
+// expm1(z) / z (1 at z = 0): the same Taylor series for |z| < 1/4, one
+// division by z beyond.
+__device__ __forceinline__ float expm1_over_z(float z) {
+  if (fabsf(z) < 0.25f) {
+    float p = fmaf(z, 1.f / 5040.f, 1.f / 720.f);
+    p = fmaf(z, p, 1.f / 120.f);
+    p = fmaf(z, p, 1.f / 24.f);
+    p = fmaf(z, p, 1.f / 6.f);
+    p = fmaf(z, p, 0.5f);
+    return fmaf(z, p, 1.f);
+  }
+  return expm1f(z) / z;
 }
 
 // Per-sample phase increments (cycles/sample) of samples j0..j0+3 and whether
@@ -99,24 +114,18 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
     const float L = in_b ? s.LB : 0.f;
     const float c = in_b ? s.cB : s.cA;
     const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
-    const int d0 = j0 - (in_b ? jc : 0);
-    float base, g, e1, e2, e3;
-    if (lin) {
-      base = s.phase0 + fmaf(c, (float)d0, L);
-      g = c;
-      e1 = 1.f; e2 = 2.f; e3 = 3.f;
-    } else {
-      const float E0 = expm1_phase((float)d0 * s.x);
-      const float cE = c * s.invE;
-      base = s.phase0 + fmaf(cE, E0, L);
-      g = fmaf(c, E0, c);
-      e1 = 1.f;
-      e2 = s.q2;
-      e3 = s.q3;
-    }
+    const float d0 = (float)(j0 - (in_b ? jc : 0));
+    // one formula for both kinds of piece: a linear piece is the geometric
+    // one with x = 0 (expm1(z)/z = 1, steps 1, 2, 3), so no branch on the kind
+    const float x = lin ? 0.f : s.x;
+    const float z = d0 * x;
+    const float h = expm1_over_z(z);  // expm1(d0 x) = z h
+    float base = s.phase0 + fmaf(c * (lin ? 1.f : s.ih), d0 * h, L);
+    const float g = c * fmaf(z, h, 1.f);
+    const float e2 = lin ? 2.f : s.q2, e3 = lin ? 3.f : s.q3;
     base -= rintf(base);
     ph[0] = base;
-    const float p1 = fmaf(g, e1, base), p2 = fmaf(g, e2, base), p3 = fmaf(g, e3, base);
+    const float p1 = base + g, p2 = fmaf(g, e2, base), p3 = fmaf(g, e3, base);
     ph[1] = kWrap ? p1 - rintf(p1) : p1;
     ph[2] = kWrap ? p2 - rintf(p2) : p2;
     ph[3] = kWrap ? p3 - rintf(p3) : p3;
