@@ -241,8 +241,6 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
   const int R = vc.R, K = vc.K;
   const int64_t N = vc.n_samples;
   const int qps = R >> 2;             // quads per control interval
-  const int dq_s = NT / qps;          // a thread's quad stride NT as (intervals, quads)
-  const int dq_j = NT - dq_s * qps;
   const bool vec_ok = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(audio) & 15) == 0;
   const float invR = 1.0f / (float)R;
   load_tables(s.T, vc.T);
@@ -551,26 +549,44 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       float* out_t = audio + (size_t)v * (size_t)N + (size_t)t0;
       const int n_t = (int)min((int64_t)nseg * R, N - t0);   // samples in the tile
       const uint32_t q_t = (uint32_t)(t0 >> 2);               // its first quad (R % 4 == 0)
-      const int nq = nseg * qps;
+      // A work item is a run of G consecutive quads of one interval (G
+      // divides the interval's quads): the VCO phase description is
+      // evaluated for the run's first quad and stepped from quad to quad.
+      const int G = qps % 5 == 0 ? 5 : qps % 4 == 0 ? 4 : qps % 3 == 0 ? 3 : qps % 2 == 0 ? 2 : 1;
+      const int gpi = qps / G;
+      const int ngr = nseg * gpi;
       float vmax = 0.f;  // largest |sample| this thread wrote (kPeak)
-      int si = tid / qps;
-      int jq = tid - si * qps;
-      for (int q = tid; q < nq; q += NT) {
-        const int j0 = jq << 2;
-        const int off = si * R + j0;
-        if (off < n_t) {
-          float ps[4], pq[4];
-          // (the peak variant keeps the unrolled straddle code: measured faster there)
-          vco_quad<false, !kPeak>(s.seg[0][si], j0, ps);
-          vco_quad<false, !kPeak>(s.seg[1][si], j0, pq);
+      for (int gi = tid; gi < ngr; gi += NT) {
+        const int si = gi / gpi;
+        const int j0 = (gi - si * gpi) * (4 * G);  // the run's first sample in its interval
+        const int off0 = si * R + j0;
+        if (off0 >= n_t) continue;
+        const SegVco& sv0 = s.seg[0][si];
+        const SegVco& sv1 = s.seg[1][si];
+        VcoRun r0, r1;
+        // a run that meets a Nyquist-cap boundary evaluates each quad on its own
+        const bool run = vco_run_start(sv0, j0, 4 * G, r0) & vco_run_start(sv1, j0, 4 * G, r1);
+#pragma unroll 1
+        for (int q = 0; q < G; ++q) {
           const float4 sq = s.sq[si];
           const float4 A = s.ampv[si], D = s.aslope[si];
+          const int jq = j0 + 4 * q;
+          const int off = off0 + 4 * q;
+          if (off >= n_t) break;
+          float ps[4], pq[4];
+          if (run) {
+            vco_run_quad(sv0, r0, ps);
+            vco_run_quad(sv1, r1, pq);
+          } else {
+            vco_quad<false, true>(sv0, jq, ps);
+            vco_quad<false, true>(sv1, jq, pq);
+          }
           const uint4 nz = philox4x32_10(
               make_uint4((uint32_t)g, (uint32_t)(g >> 32), q_t + (uint32_t)(off >> 2), kStreamNoise),
               key);
           const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
           // amplitudes at the quad's first sample, then one step of the slope per sample
-          const float fj0 = (float)j0;
+          const float fj0 = (float)jq;
           const float a0x = fmaf(fj0, D.x, A.x), a0y = fmaf(fj0, D.y, A.y), a0z = fmaf(fj0, D.z, A.z);
           float out4[4];
 #pragma unroll
@@ -604,9 +620,6 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
               }
           }
         }
-        si += dq_s;
-        jq += dq_j;
-        if (jq >= qps) { jq -= qps; ++si; }
       }
       if (kPeak) publish_tile_peak(s, vt + w, vmax, epoch);
     }
