@@ -69,13 +69,17 @@ constexpr int kNormChunkSamples = 8192;  // samples per normalisation work item
 // Launches the fused persistent render of voices g = split_voice(split,
 // first + v), v < batch (with `norm`, also the peak normalisation); voice v
 // draws with seed + (v / sub_batch) seed_step (sub_batch 0: the whole batch
-// one seed). Returns the CUDA error of the launch.
+// one seed). With overlap_previous, the launch may start while the previous
+// kernel on the stream finishes (programmatic dependent launch): allowed only
+// when that kernel is a fused render on other scratch (hdr, tiles) or a
+// kernel that never releases its dependents early. Returns the CUDA error of
+// the launch.
 cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t first, int split,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
                                 int grid, cudaStream_t stream,
                                 const PeakNormArgs* norm = nullptr, uint64_t seed_step = 0,
-                                int sub_batch = 0);
+                                int sub_batch = 0, bool overlap_previous = false);
 int fused_max_active_blocks_per_sm();
 
 // The 4-operator FM voice (fm_voice.cu): voices g = batch_index * batch + v.

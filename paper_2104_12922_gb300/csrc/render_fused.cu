@@ -229,6 +229,21 @@ __device__ __noinline__ void normalize_chunk(Smem& s, float* __restrict__ audio,
   }
 }
 
+// Programmatic dependent launch. Once fewer work items remain than the grid
+// has CTAs (after the CTA's current item), the CTA waits for the previous
+// grid on the stream to complete (a no-op unless this launch may overlap it)
+// and then releases the next launch on the stream: when every CTA has done
+// so, the next launch's CTAs start in the SM slots that this launch's last
+// wave leaves idle. The wait comes first, so launch N + 2, which uses launch
+// N's scratch, can never overlap launch N. Neither grid ever waits on the
+// other's work.
+__device__ __forceinline__ void release_next_launch(bool& released) {
+  if (released) return;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  released = true;
+}
+
 template <bool kCarryF32, bool kPeak, bool kGenR>
 __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t first, int split, int batch,
@@ -245,6 +260,10 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
   const float invR = 1.0f / (float)R;
   load_tables(s.T, vc.T);
   if (tid == 0) s.epoch = *(volatile unsigned int*)&hdr->epoch;
+  // all work items of the launch: render tiles, then (peak variant) scaling chunks
+  const int total_items =
+      total_tiles + (kPeak ? (int)((N + kNormChunkSamples - 1) / kNormChunkSamples) * batch : 0);
+  bool released = false;
 
   for (;;) {
     if (tid == 0) s.tile = (int)atomicAdd(&hdr->work, 1u);
@@ -253,12 +272,13 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     if (t >= total_tiles) {
       // peak variant: the scaling chunks follow the render tiles, voice by
       // voice (window-major tiles finish their voices in that order)
-      if (!kPeak) break;
+      if (!kPeak) { release_next_launch(released); break; }
       const int chunks = (int)((N + kNormChunkSamples - 1) / kNormChunkSamples);
       const int j = t - total_tiles;
-      if (j >= chunks * batch) break;
+      if (j >= chunks * batch) { release_next_launch(released); break; }
       normalize_chunk(s, audio, N, tiles + (size_t)(j / chunks) * n_windows, n_windows,
                       j / chunks, j % chunks, vec_ok, norm, hdr, s.epoch);
+      if (t + (int)gridDim.x >= total_items) release_next_launch(released);
       continue;
     }
     const int v = t % batch, w = t / batch;
@@ -623,6 +643,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       }
       if (kPeak) publish_tile_peak(s, vt + w, vmax, epoch);
     }
+    if (t + (int)gridDim.x >= total_items) release_next_launch(released);
   }
   persistent_finish(hdr);
 }
@@ -639,25 +660,37 @@ cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t fi
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
                                 int grid, cudaStream_t stream, const PeakNormArgs* norm,
-                                uint64_t seed_step, int sub_batch) {
+                                uint64_t seed_step, int sub_batch, bool overlap_previous) {
   const int n_windows = windows_per_voice(vc.K);
   const int total = batch * n_windows;
   grid = grid < total ? grid : total;
   const PeakNormArgs nz = norm ? *norm : PeakNormArgs{0.f, nullptr, nullptr};
   if (sub_batch <= 0) sub_batch = batch;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap_previous ? 1 : 0;
 #define SYNTH_FUSED_ARGS vc, seed, first, split, batch, params_in, audio, params_out, hdr, tiles, \
                          n_windows, nz, seed_step, sub_batch
+  cudaError_t e;
   if (vc.general_r) {  // fractional R (never with FP32 carries)
-    if (norm) render_fused_kernel<false, true, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
-    else render_fused_kernel<false, false, true><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    if (norm) e = cudaLaunchKernelEx(&cfg, render_fused_kernel<false, true, true>, SYNTH_FUSED_ARGS);
+    else e = cudaLaunchKernelEx(&cfg, render_fused_kernel<false, false, true>, SYNTH_FUSED_ARGS);
   } else if (vc.carry_fp32) {
-    if (norm) render_fused_kernel<true, true, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
-    else render_fused_kernel<true, false, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    if (norm) e = cudaLaunchKernelEx(&cfg, render_fused_kernel<true, true, false>, SYNTH_FUSED_ARGS);
+    else e = cudaLaunchKernelEx(&cfg, render_fused_kernel<true, false, false>, SYNTH_FUSED_ARGS);
   } else {
-    if (norm) render_fused_kernel<false, true, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
-    else render_fused_kernel<false, false, false><<<grid, NT, 0, stream>>>(SYNTH_FUSED_ARGS);
+    if (norm) e = cudaLaunchKernelEx(&cfg, render_fused_kernel<false, true, false>, SYNTH_FUSED_ARGS);
+    else e = cudaLaunchKernelEx(&cfg, render_fused_kernel<false, false, false>, SYNTH_FUSED_ARGS);
   }
 #undef SYNTH_FUSED_ARGS
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -26,8 +26,9 @@ struct synth_handle_s {
   int num_sms = 0;
   int fused_grid = 0;
   int n_windows = 0;
-  void* scratch = nullptr;  // ScratchHeader + TileState[max_batch * n_windows]
-  size_t scratch_bytes = 0;
+  void* scratch = nullptr;  // two slots of ScratchHeader + TileState[max_batch * n_windows]
+  size_t scratch_bytes = 0;  // per slot (256-byte multiple)
+  int next_slot = 0;         // slot of the next overlappable fused launch
   bool plain_ready = false;
 };
 
@@ -85,6 +86,21 @@ double host_range_map(double u, double lo, double hi, double c, int sym) {
 synth_status check_cuda(cudaError_t e) { return e == cudaSuccess ? SYNTH_OK : SYNTH_ERR_CUDA; }
 
 bool valid_handle(synth_handle h) { return h != nullptr && h->scratch != nullptr; }
+
+// Scratch slot s (0 or 1): its header and tile states. Slot 0 also carries
+// the error word of every other kernel that reports one.
+ScratchHeader* slot_header(synth_handle h, int s) {
+  return reinterpret_cast<ScratchHeader*>(static_cast<char*>(h->scratch) + (size_t)s * h->scratch_bytes);
+}
+
+// The slot for the next fused launch that may overlap the previous one on
+// the stream: consecutive such launches alternate slots, so two that overlap
+// never share scratch.
+ScratchHeader* take_overlap_slot(synth_handle h) {
+  ScratchHeader* hdr = slot_header(h, h->next_slot);
+  h->next_slot ^= 1;
+  return hdr;
+}
 
 }  // namespace
 
@@ -146,13 +162,14 @@ synth_status synth_create(const synth_config* cfg, synth_handle* out) {
   h->n_windows = windows_per_voice(h->vc.K);
   const int per_sm = fused_max_active_blocks_per_sm();
   h->fused_grid = h->num_sms * (per_sm > 0 ? per_sm : 1);
-  h->scratch_bytes = sizeof(ScratchHeader) + sizeof(TileState) * (size_t)cfg->max_batch * h->n_windows;
-  if (cudaMalloc(&h->scratch, h->scratch_bytes) != cudaSuccess) {
+  h->scratch_bytes = (sizeof(ScratchHeader) + sizeof(TileState) * (size_t)cfg->max_batch * h->n_windows +
+                      255) & ~size_t(255);
+  if (cudaMalloc(&h->scratch, 2 * h->scratch_bytes) != cudaSuccess) {
     h->scratch = nullptr;
     delete h;
     return SYNTH_ERR_OOM;
   }
-  if (cudaMemset(h->scratch, 0, h->scratch_bytes) != cudaSuccess ||
+  if (cudaMemset(h->scratch, 0, 2 * h->scratch_bytes) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaFree(h->scratch);
     delete h;
@@ -180,11 +197,12 @@ synth_status synth_render(synth_handle h, uint64_t seed, uint64_t batch_index, i
   if (batch < 0 || batch > h->cfg.max_batch) return SYNTH_ERR_ARG;
   if (batch == 0) return SYNTH_OK;
   if (!audio_dev) return SYNTH_ERR_ARG;
-  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  ScratchHeader* hdr = take_overlap_slot(h);
   TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
   return check_cuda(launch_render_fused(h->vc, seed, batch_index * (uint64_t)batch, 0, batch,
                                         params_in_dev, audio_dev, params_out_dev, hdr, tiles,
-                                        h->fused_grid, static_cast<cudaStream_t>(stream)));
+                                        h->fused_grid, static_cast<cudaStream_t>(stream), nullptr,
+                                        0, 0, true));
 }
 
 synth_status synth_render_batches(synth_handle h, uint64_t seed, uint64_t seed_step,
@@ -195,13 +213,13 @@ synth_status synth_render_batches(synth_handle h, uint64_t seed, uint64_t seed_s
   if (batch < 0 || count < 0 || (int64_t)batch * count > h->cfg.max_batch) return SYNTH_ERR_ARG;
   if (batch == 0 || count == 0) return SYNTH_OK;
   if (!audio_dev) return SYNTH_ERR_ARG;
-  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  ScratchHeader* hdr = take_overlap_slot(h);
   TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
   return check_cuda(launch_render_fused(h->vc, seed, batch_index * (uint64_t)batch, 0,
                                         batch * count, params_in_dev, audio_dev, params_out_dev,
                                         hdr, tiles, h->fused_grid,
                                         static_cast<cudaStream_t>(stream), nullptr, seed_step,
-                                        batch));
+                                        batch, true));
 }
 
 synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t batch_index,
@@ -213,12 +231,13 @@ synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t bat
   if (!(threshold >= 0.f)) return SYNTH_ERR_ARG;
   if (batch == 0) return SYNTH_OK;
   if (!audio_dev) return SYNTH_ERR_ARG;
-  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
+  ScratchHeader* hdr = take_overlap_slot(h);
   TileState* tiles = reinterpret_cast<TileState*>(hdr + 1);
   const PeakNormArgs norm{threshold, peak_out_dev, silent_out_dev};
   return check_cuda(launch_render_fused(h->vc, seed, batch_index * (uint64_t)batch, 0, batch,
                                         params_in_dev, audio_dev, params_out_dev, hdr, tiles,
-                                        h->fused_grid, static_cast<cudaStream_t>(stream), &norm));
+                                        h->fused_grid, static_cast<cudaStream_t>(stream), &norm,
+                                        0, 0, true));
 }
 
 synth_status synth_fm_render(synth_handle h, uint64_t seed, uint64_t batch_index, int32_t batch,
@@ -609,17 +628,20 @@ synth_status synth_model_load(synth_model m, const char* path) {
 synth_status synth_sync(synth_handle h, void* stream) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SYNTH_ERR_CUDA;
-  ScratchHeader* hdr = static_cast<ScratchHeader*>(h->scratch);
-  unsigned int err = 0;
-  if (cudaMemcpy(&err, &hdr->error, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return SYNTH_ERR_CUDA;
-  if (err != 0) {
-    const unsigned int zero = 0;
-    if (cudaMemcpy(&hdr->error, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+  bool timeout = false;
+  for (int slot = 0; slot < 2; ++slot) {
+    ScratchHeader* hdr = slot_header(h, slot);
+    unsigned int err = 0;
+    if (cudaMemcpy(&err, &hdr->error, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
       return SYNTH_ERR_CUDA;
-    return SYNTH_ERR_TIMEOUT;
+    if (err != 0) {
+      const unsigned int zero = 0;
+      if (cudaMemcpy(&hdr->error, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SYNTH_ERR_CUDA;
+      timeout = true;
+    }
   }
-  return SYNTH_OK;
+  return timeout ? SYNTH_ERR_TIMEOUT : SYNTH_OK;
 }
 
 namespace {

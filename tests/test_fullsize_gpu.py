@@ -97,13 +97,16 @@ def _mlp_bars(tr, ws, t, vZ, vH):
     return NSIG * np.sqrt(vY), bars_w, bars_b
 
 
-@pytest.mark.parametrize("seconds,B", [(4.0, 128), (0.25, 16)])
+@pytest.mark.parametrize("seconds,B", [(4.0, 128), (0.25, 16), (0.05, 4864)])
 def test_mlp_elementwise(env, seconds, B):
     """Batch 128, 4 s voices (345 frames x 128 bands = 44160 inputs): the
     first layer's forward GEMM is 128 x 1024 x 44160 (split into 37 K-slices
     over the SMs), its weight gradient 1024 x 44160 x 128 (1,384 output
     tiles: every persistent CTA takes many). Batch 16 x 0.25 s (2816 inputs):
-    a batch that fills only part of a 128-row tile."""
+    a batch that fills only part of a 128-row tile. Batch 4864 x 0.05 s (640
+    inputs): the hidden layers' products have 38 x 4 = 152 output tiles, as
+    many as the GPU has SMs, so they are not split and their bias, ReLU, bf16
+    and transposed bf16 outputs come from the GEMM's own epilogue."""
     from oracle import spectral as sp
     torch, pkg = env
     syn = pkg.Synth(seconds=seconds, max_batch=B)
