@@ -231,19 +231,22 @@ __device__ inline ff vco_interval_ff(ff m_a, ff m_b, float R, int Rk, ff inv_R, 
   if (!c_first && !c_last) LB = ff_make(0.f);
   const float xf = x.hi;
   const bool tiny = fabsf(xf) < 1e-30f;
-  const float e1 = tiny ? 0.f : expm1f(xf);
+  // every piece linear: the quad steps (and the geometric constants, which
+  // no linear piece reads) are those of x = 0
+  const bool all_lin = tiny || (a_lin && b_lin);
+  const float e1 = all_lin ? 0.f : expm1f(xf);
   out->cA = cA.hi + cA.lo;
   out->cB = cB.hi + cB.lo;
   out->LB = LB.hi + LB.lo;
   out->x = xf;
   out->q2 = 2.f + e1;                 // 1 + r, r = 1 + e1
   out->q3 = fmaf(e1, e1 + 3.f, 3.f);  // 1 + r + r^2 = 3 + 3 e1 + e1^2
-  out->invE = tiny ? 0.f : 1.0f / e1;
-  out->ih = tiny ? 1.f : xf * out->invE;
+  out->invE = all_lin ? 0.f : 1.0f / e1;
+  out->ih = all_lin ? 1.f : xf * out->invE;
   out->q4 = fmaf(e1, fmaf(e1, e1 + 4.f, 6.f), 4.f);  // (r^4 - 1) / (r - 1) = 4 + 6 e1 + 4 e1^2 + e1^3
   out->r4m1 = e1 * out->q4;
   out->jc_flags = jc | ((a_lin || tiny) ? 1 << 16 : 0) | ((b_lin || tiny) ? 1 << 17 : 0) |
-                  (c_first ? 1 << 18 : 0) | (c_last ? 1 << 19 : 0);
+                  (c_first ? 1 << 18 : 0) | (c_last ? 1 << 19 : 0) | (all_lin ? 1 << 20 : 0);
   *inc_first = out->cA;
   return total;
 }

@@ -29,6 +29,7 @@ struct __align__(16) SegVco {
   float q4;      // 1 + r + r^2 + r^3: four samples' phase in units of the first increment
   float r4m1;    // r^4 - 1: a quad's change of the increment
   int jc_flags;  // jc | (A linear) << 16 | (B linear) << 17 | (A capped) << 18 | (B capped) << 19
+                 // | (every piece linear: the steps q2..r4m1 are those of x = 0) << 20
 };
 
 // expm1(z) for the in-interval phase of a geometric piece, z = d x (d samples
@@ -147,17 +148,23 @@ __device__ __forceinline__ void vco_quad(const SegVco& s, int j0, float ph[4]) {
 }
 
 // A run of consecutive quads inside one piece of an interval, stepped quad
-// to quad: the base phase (wrapped) and first increment of the current quad
-// and the piece's kind; the steps (e2, e3 inside a quad, q4 and r^4 - 1 from
-// quad to quad) are read from the interval's description at each quad.
+// to quad, in radians (the sine unit's argument, so no scaling per sample):
+// the base phase of the current quad (wrapped to [-pi, pi]) and its first
+// increment. The steps (q2, q3 inside a quad, q4 and r^4 - 1 from quad to
+// quad) are read from the interval's description at each quad; they are
+// those of the piece the run is in, since runs are only started in pieces of
+// the kind the steps describe.
+constexpr float kTwoPiRun = 6.28318530717958647692f;
+constexpr float kInvTwoPiRun = 0.159154943091895335769f;
 struct VcoRun {
   float base, g;
-  bool lin;
 };
 
 // Starts a run at sample j0 of the interval for `len` samples; false when
-// the samples straddle the piece boundary jc (the caller then evaluates each
-// quad on its own). The start is the quad formula of vco_quad.
+// the samples straddle the piece boundary jc, or lie in a piece of another
+// kind than the interval's steps describe (a linear piece beside a geometric
+// one): the caller then evaluates each quad on its own. The start is the
+// quad formula of vco_quad.
 __device__ __forceinline__ bool vco_run_start(const SegVco& s, int j0, int len, VcoRun& r) {
   const int jc = s.jc_flags & 0xffff;
   if (!(j0 + len - 1 < jc || j0 >= jc)) return false;
@@ -165,28 +172,28 @@ __device__ __forceinline__ bool vco_run_start(const SegVco& s, int j0, int len, 
   const float L = in_b ? s.LB : 0.f;
   const float c = in_b ? s.cB : s.cA;
   const bool lin = (s.jc_flags >> (in_b ? 17 : 16)) & 1;
+  if (lin != (bool)((s.jc_flags >> 20) & 1)) return false;
   const float d0 = (float)(j0 - (in_b ? jc : 0));
   const float z = d0 * (lin ? 0.f : s.x);
   const float h = expm1_over_z(z);
   const float base = s.phase0 + fmaf(c * (lin ? 1.f : s.ih), d0 * h, L);
-  r.base = base - rintf(base);
-  r.g = c * fmaf(z, h, 1.f);
-  r.lin = lin;
+  r.base = kTwoPiRun * (base - rintf(base));
+  r.g = kTwoPiRun * (c * fmaf(z, h, 1.f));
   return true;
 }
 
-// The current quad's four phases (left in (-1/2, 2), as vco_quad<false>),
-// then one quad on: base + g q4 wrapped, g r^4.
+// The current quad's four phases in radians (left in (-pi, 4 pi), as
+// vco_quad<false> in cycles), then one quad on: base + g q4 wrapped (the
+// float 2 pi differs from 2 pi by 1.7e-7, a drift of that much per wrapped
+// cycle that ends with the run, at most a few cycles), g r^4.
 __device__ __forceinline__ void vco_run_quad(const SegVco& s, VcoRun& r, float ph[4]) {
-  const float e2 = r.lin ? 2.f : s.q2, e3 = r.lin ? 3.f : s.q3;
-  const float q4 = r.lin ? 4.f : s.q4, r4m1 = r.lin ? 0.f : s.r4m1;
   ph[0] = r.base;
   ph[1] = r.base + r.g;
-  ph[2] = fmaf(r.g, e2, r.base);
-  ph[3] = fmaf(r.g, e3, r.base);
-  const float nb = fmaf(r.g, q4, r.base);
-  r.base = nb - rintf(nb);
-  r.g = fmaf(r.g, r4m1, r.g);
+  ph[2] = fmaf(r.g, s.q2, r.base);
+  ph[3] = fmaf(r.g, s.q3, r.base);
+  const float nb = fmaf(r.g, s.q4, r.base);
+  r.base = fmaf(-kTwoPiRun, rintf(nb * kInvTwoPiRun), nb);
+  r.g = fmaf(r.g, s.r4m1, r.g);
 }
 
 constexpr float kTwoPiF = 6.28318530717958647692f;

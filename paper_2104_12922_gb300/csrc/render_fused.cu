@@ -571,7 +571,10 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       const uint32_t q_t = (uint32_t)(t0 >> 2);               // its first quad (R % 4 == 0)
       // A work item is a run of G consecutive quads of one interval (G
       // divides the interval's quads): the VCO phase description is
-      // evaluated for the run's first quad and stepped from quad to quad.
+      // evaluated for the run's first quad and stepped from quad to quad, in
+      // radians. The interval's audio constants are read from shared memory
+      // at each quad (holding them across the run costs registers the loop
+      // has not got).
       const int G = qps % 5 == 0 ? 5 : qps % 4 == 0 ? 4 : qps % 3 == 0 ? 3 : qps % 2 == 0 ? 2 : 1;
       const int gpi = qps / G;
       const int ngr = nseg * gpi;
@@ -583,24 +586,12 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
         if (off0 >= n_t) continue;
         const SegVco& sv0 = s.seg[0][si];
         const SegVco& sv1 = s.seg[1][si];
-        VcoRun r0, r1;
-        // a run that meets a Nyquist-cap boundary evaluates each quad on its own
-        const bool run = vco_run_start(sv0, j0, 4 * G, r0) & vco_run_start(sv1, j0, 4 * G, r1);
-#pragma unroll 1
-        for (int q = 0; q < G; ++q) {
+        // one quad of audio from its VCO phases (radians)
+        auto emit = [&](int q, const float ps[4], const float pq[4]) {
           const float4 sq = s.sq[si];
           const float4 A = s.ampv[si], D = s.aslope[si];
           const int jq = j0 + 4 * q;
           const int off = off0 + 4 * q;
-          if (off >= n_t) break;
-          float ps[4], pq[4];
-          if (run) {
-            vco_run_quad(sv0, r0, ps);
-            vco_run_quad(sv1, r1, pq);
-          } else {
-            vco_quad<false, true>(sv0, jq, ps);
-            vco_quad<false, true>(sv1, jq, pq);
-          }
           const uint4 nz = philox4x32_10(
               make_uint4((uint32_t)g, (uint32_t)(g >> 32), q_t + (uint32_t)(off >> 2), kStreamNoise),
               key);
@@ -611,9 +602,9 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
           float out4[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const float x_sin = __sinf(kTwoPiF * ps[i]);
+            const float x_sin = __sinf(ps[i]);
             float sn, cs;
-            __sincosf(kTwoPiF * pq[i], &sn, &cs);
+            __sincosf(pq[i], &sn, &cs);
             const float x_sq = square_saw_sc(sn, cs, sq.x, sq.y, sq.z);
             const float x_nz = fmaf((float)(nw[i] >> 8), 0x1p-23f, -1.f);  // 2u - 1, exact
             const float fi = (float)i;
@@ -638,6 +629,47 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
                 out_t[off + i] = out4[i];
                 if (kPeak) vmax = fmaxf(vmax, fabsf(out4[i]));
               }
+          }
+        };
+        const int gq = min(G, (n_t - off0 + 3) >> 2);  // quads of the run inside the tile
+        VcoRun r0, r1;
+        // a run that meets a Nyquist-cap boundary evaluates each quad on its own
+        const bool run = vco_run_start(sv0, j0, 4 * G, r0) & vco_run_start(sv1, j0, 4 * G, r1);
+        if (kPeak) {
+          // one loop for both cases (the peak variant's extra state leaves no
+          // registers for two)
+#pragma unroll 1
+          for (int q = 0; q < gq; ++q) {
+            float ps[4], pq[4];
+            if (run) {
+              vco_run_quad(sv0, r0, ps);
+              vco_run_quad(sv1, r1, pq);
+            } else {
+              vco_quad<false, true>(sv0, j0 + 4 * q, ps);
+              vco_quad<false, true>(sv1, j0 + 4 * q, pq);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) { ps[i] *= kTwoPiF; pq[i] *= kTwoPiF; }
+            }
+            emit(q, ps, pq);
+          }
+        } else if (run) {
+          // two loops: the stepped one carries no state of the other
+#pragma unroll 1
+          for (int q = 0; q < gq; ++q) {
+            float ps[4], pq[4];
+            vco_run_quad(sv0, r0, ps);
+            vco_run_quad(sv1, r1, pq);
+            emit(q, ps, pq);
+          }
+        } else {
+#pragma unroll 1
+          for (int q = 0; q < gq; ++q) {
+            float ps[4], pq[4];
+            vco_quad<false, true>(sv0, j0 + 4 * q, ps);
+            vco_quad<false, true>(sv1, j0 + 4 * q, pq);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { ps[i] *= kTwoPiF; pq[i] *= kTwoPiF; }
+            emit(q, ps, pq);
           }
         }
       }
