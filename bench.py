@@ -594,11 +594,11 @@ def rates_leg(pkg, torch, stream, steps: int = 64):
     syn = pkg.Synth(seconds=seconds, max_batch=B, sample_rate=sr, control_rate=441.0)
     n = syn.num_samples
     outs = [torch.empty((B, n), dtype=torch.float32, device=syn.device) for _ in range(4)]
-    pout = torch.empty((B, 78), dtype=torch.float32, device=syn.device)
+    pouts = [torch.empty((B, 78), dtype=torch.float32, device=syn.device) for _ in range(4)]
 
     def record(k):
         for s in range(k):
-            syn.render(s, s, B, out=outs[s % 4], params_out=pout, stream=stream)
+            syn.render(s, s, B, out=outs[s % 4], params_out=pouts[s % 4], stream=stream)
     with torch.cuda.stream(stream):
         record(3)
     stream.synchronize()
@@ -871,15 +871,16 @@ def run_ours(args):
     normalized = None
     if not args.no_normalized:
         Kn = min(K, 64)
-        peak_b = torch.empty(BATCH, dtype=torch.float32, device=dev)
-        silent_b = torch.empty(BATCH, dtype=torch.int32, device=dev)
+        # every buffer rotates, so consecutive launches share none and overlap
+        peak_b = [torch.empty(BATCH, dtype=torch.float32, device=dev) for _ in range(n_buf)]
+        silent_b = [torch.empty(BATCH, dtype=torch.int32, device=dev) for _ in range(n_buf)]
 
         def record_norm(g_steps):
             for s in range(g_steps):
                 bi = batch_index(s)
                 syn.render_normalized(bi, bi, BATCH, threshold=1e-3, out=outs[s % n_buf],
-                                      params_out=pouts[s % n_buf], peak=peak_b, silent=silent_b,
-                                      stream=stream)
+                                      params_out=pouts[s % n_buf], peak=peak_b[s % n_buf],
+                                      silent=silent_b[s % n_buf], stream=stream)
         with torch.cuda.stream(stream):
             record_norm(2)
         stream.synchronize()

@@ -23,6 +23,13 @@
  *    up) is recorded in the handle and returned by synth_sync.
  *  - One handle renders one batch at a time: calls on one handle must be
  *    ordered on one stream (they share the handle's scratch).
+ *  - Consecutive fused renders on a stream (synth_render,
+ *    synth_render_batches, synth_render_normalized) may run partly at the
+ *    same time: the next launch's CTAs start while the previous one's last
+ *    wave finishes (programmatic dependent launch; the handle alternates two
+ *    scratch slots). This is done only when neither launch writes a buffer
+ *    the other reads or writes; otherwise, and between a render and any
+ *    other kernel, copy or event, stream order holds as usual.
  */
 #ifndef SYNTH_H
 #define SYNTH_H

@@ -70,10 +70,13 @@ constexpr int kNormChunkSamples = 8192;  // samples per normalisation work item
 // first + v), v < batch (with `norm`, also the peak normalisation); voice v
 // draws with seed + (v / sub_batch) seed_step (sub_batch 0: the whole batch
 // one seed). With overlap_previous, the launch may start while the previous
-// kernel on the stream finishes (programmatic dependent launch): allowed only
-// when that kernel is a fused render on other scratch (hdr, tiles) or a
-// kernel that never releases its dependents early. Returns the CUDA error of
-// the launch.
+// kernel on the stream finishes (programmatic dependent launch). A fused
+// render releases its dependents before it completes, so the request is
+// granted only when the previous fused launch on the stream used other
+// scratch (hdr) and none of the two launches writes a buffer the other reads
+// or writes (params_in, audio, params_out, peak, silent); otherwise the
+// launch waits for the previous kernel as usual. Every launch is recorded for
+// that check. Returns the CUDA error of the launch.
 cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t first, int split,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,

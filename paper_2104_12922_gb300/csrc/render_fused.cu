@@ -27,6 +27,9 @@
 // mode). Nothing but the audio, the parameters and a 48-byte look-back record
 // per tile is written to device memory, and no FP64 instruction runs.
 
+#include <mutex>
+#include <unordered_map>
+
 #include "control_ff.cuh"
 #include "internal.h"
 #include "render_common.cuh"
@@ -682,6 +685,41 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
 
 }  // namespace
 
+namespace {
+
+// The buffers and scratch of one fused launch, for the overlap check: the
+// CTAs of a launch that overlaps its predecessor run their work items while
+// the predecessor's last wave is still running (they wait for it only before
+// releasing their own dependents), so the two must share no scratch and no
+// buffer that either of them writes.
+struct FusedLaunchRecord {
+  const void* hdr = nullptr;
+  uintptr_t lo[5] = {}, hi[5] = {};  // params_in, audio, params_out, peak, silent
+  bool writes[5] = {};
+};
+
+bool launches_conflict(const FusedLaunchRecord& a, const FusedLaunchRecord& b) {
+  if (a.hdr == b.hdr) return true;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j)
+      if ((a.writes[i] || b.writes[j]) && a.lo[i] < a.hi[i] && b.lo[j] < b.hi[j] &&
+          a.lo[i] < b.hi[j] && b.lo[j] < a.hi[i])
+        return true;
+  return false;
+}
+
+std::mutex g_fused_launch_mu;
+std::unordered_map<cudaStream_t, FusedLaunchRecord> g_last_fused_launch;  // per stream
+
+void set_range(FusedLaunchRecord& r, int k, const void* p, size_t bytes, bool writes) {
+  if (!p || bytes == 0) return;
+  r.lo[k] = reinterpret_cast<uintptr_t>(p);
+  r.hi[k] = r.lo[k] + bytes;
+  r.writes[k] = writes;
+}
+
+}  // namespace
+
 int fused_max_active_blocks_per_sm() {
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false, false, false>, NT, 0);
@@ -703,11 +741,27 @@ cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t fi
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = stream;
+  FusedLaunchRecord rec;
+  rec.hdr = hdr;
+  const size_t nv = (size_t)batch;
+  set_range(rec, 0, params_in, nv * kNumParams * sizeof(float), false);
+  set_range(rec, 1, audio, nv * (size_t)vc.n_samples * sizeof(float), true);
+  set_range(rec, 2, params_out, nv * kNumParams * sizeof(float), true);
+  set_range(rec, 3, nz.peak_out, nv * sizeof(float), true);
+  set_range(rec, 4, nz.silent_out, nv * sizeof(int32_t), true);
+  bool overlap = false;
+  {
+    std::lock_guard<std::mutex> lock(g_fused_launch_mu);
+    auto it = g_last_fused_launch.find(stream);
+    overlap = overlap_previous &&
+              (it == g_last_fused_launch.end() || !launches_conflict(it->second, rec));
+    g_last_fused_launch[stream] = rec;
+  }
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = overlap_previous ? 1 : 0;
+  cfg.numAttrs = overlap ? 1 : 0;
 #define SYNTH_FUSED_ARGS vc, seed, first, split, batch, params_in, audio, params_out, hdr, tiles, \
                          n_windows, nz, seed_step, sub_batch
   cudaError_t e;

@@ -335,3 +335,67 @@ def test_back_to_back_launches_equal_separate_renders(torch_cuda):
         assert torch.equal(on, ref_n)
     del g
     syn.close()
+
+
+def test_back_to_back_launches_sharing_buffers_keep_stream_order(torch_cuda):
+    """A launch that writes what the previous launch on the stream reads or
+    writes, or reads what it writes, is not overlapped with it. Chains that
+    depend on that order: the parameters written by one render fed back as
+    the next render's input (read after write), two renders into the same
+    output (write after write: the second wins), and a render into the
+    buffer the previous render took its parameters from (write after read),
+    eagerly and from a replayed CUDA graph; each must equal the same calls
+    with the stream synchronised between them."""
+    import paper_2104_12922_gb300 as pkg
+    torch = torch_cuda
+    B, secs = 32, 1.0
+    syn = pkg.Synth(seconds=secs, max_batch=B)
+    n = syn.num_samples
+    st = torch.cuda.Stream()
+    # references, one call at a time
+    a0, p0 = syn.render(11, 3, B)
+    syn.sync()
+    a0, p0 = a0.clone(), p0.clone()
+    a1, _ = syn.render(0, 0, B, params_in=p0)
+    syn.sync()
+    a1 = a1.clone()
+    a2, _ = syn.render(12, 4, B)
+    syn.sync()
+    a2 = a2.clone()
+    pq = torch.empty((B, 78), device="cuda")
+    out = torch.empty((B, n), device="cuda")
+    out2 = torch.empty((B, n), device="cuda")
+    pw = torch.empty((B, 78), device="cuda")
+
+    def issue():
+        # read after write: params written, then read by the next launch
+        syn.render(11, 3, B, out=out2, params_out=pq, stream=st)
+        syn.render(0, 0, B, params_in=pq, out=out, params_out=pw, stream=st)
+        # write after read: the next launch writes the parameters just read
+        syn.render(12, 4, B, out=out2, params_out=pq, stream=st)
+        # write after write: the same output twice, the second wins
+        syn.render(11, 3, B, out=out, stream=st)
+        syn.render(0, 0, B, params_in=p0, out=out, stream=st)
+
+    with torch.cuda.stream(st):
+        issue()
+    st.synchronize()
+    syn.sync(st)
+    assert torch.equal(pw, p0)
+    assert torch.equal(out, a1)
+    assert torch.equal(out2, a2)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        issue()
+    for _ in range(2):
+        for o in (out, out2, pq, pw):
+            o.fill_(float("nan"))
+        with torch.cuda.stream(st):
+            g.replay()
+        st.synchronize()
+        syn.sync(st)
+        assert torch.equal(pw, p0)
+        assert torch.equal(out, a1)
+        assert torch.equal(out2, a2)
+    del g
+    syn.close()
