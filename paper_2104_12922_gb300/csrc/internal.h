@@ -76,13 +76,20 @@ constexpr int kNormChunkSamples = 8192;  // samples per normalisation work item
 // scratch (hdr) and none of the two launches writes a buffer the other reads
 // or writes (params_in, audio, params_out, peak, silent); otherwise the
 // launch waits for the previous kernel as usual. Every launch is recorded for
-// that check. Returns the CUDA error of the launch.
+// that check. voice_setups: NULL, or room for `batch` records of
+// fused_voice_setup_bytes() each (16-byte aligned) in the same scratch as
+// hdr, zeroed before its first use: a voice's first window publishes its
+// parameter set-up there and its later windows copy it (epoch-tagged, so
+// the records need no clearing between launches). Returns the CUDA error of
+// the launch.
 cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t first, int split,
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
                                 int grid, cudaStream_t stream,
                                 const PeakNormArgs* norm = nullptr, uint64_t seed_step = 0,
-                                int sub_batch = 0, bool overlap_previous = false);
+                                int sub_batch = 0, bool overlap_previous = false,
+                                void* voice_setups = nullptr);
+size_t fused_voice_setup_bytes();
 int fused_max_active_blocks_per_sm();
 
 // The 4-operator FM voice (fm_voice.cu): voices g = batch_index * batch + v.

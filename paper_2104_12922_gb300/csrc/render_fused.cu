@@ -46,6 +46,26 @@ static_assert(NT == P, "one thread per control point");
 
 using u64 = unsigned long long;
 
+// What a tile derives from its voice's parameters before its control points
+// (step 1): the same for every window of the voice.
+struct __align__(16) VoiceSetup {
+  VoiceFF V;
+  u64 lfo_p0[2], vco_p0[2];    // initial phases
+  float gain[3];               // mixer gains (sine, square-saw, noise)
+  float shape, inv_1p_shape;   // square-saw shape and 1 / (1 + shape)
+};
+static_assert(sizeof(VoiceSetup) % 16 == 0, "voice set-up copies as 16-byte vectors");
+
+// A voice's set-up as its first window published it: windows after the
+// first copy it instead of deriving it again when it is there (flag = this
+// launch's epoch tag); when it is not yet, they derive it themselves, with
+// the same arithmetic, so the result does not depend on which happened.
+struct __align__(16) VoiceSetupRecord {
+  unsigned int flag;  // (epoch << 2) | 1 once vs is written in this launch
+  unsigned int pad[3];
+  VoiceSetup vs;
+};
+
 struct __align__(16) Smem {
   FFTables T;
   union {
@@ -68,17 +88,15 @@ struct __align__(16) Smem {
                              // folded into sq), noise
   ff m[2][P];                // VCO pitch (midi) at the control points
   ff y[kNumParams];          // human-range parameters
-  VoiceFF V;
+  VoiceSetup vs;
   float u[80];
   u64 warp_tot[2][2][kWarps];  // [scan][chain][warp]
   float warp_tot_f[2][kWarps];
   float warp_max[kWarps];      // peak variant: per-warp largest |sample|
   u64 prefix[2][2];            // [scan][chain]: phase carried in from earlier windows
   float prefix_f[2];
-  u64 lfo_p0[2], vco_p0[2];    // initial phases
-  float gain[3];
-  float shape, inv_1p_shape;
   int tile;
+  int setup_ready;             // this tile copies its voice's published set-up
   unsigned int epoch;
 };
 // static shared memory is capped at 48 KB per block; 4 blocks per SM fit
@@ -252,7 +270,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t first, int split, int batch,
     const float* __restrict__ params_in, float* __restrict__ audio, float* __restrict__ params_out,
     ScratchHeader* hdr, TileState* tiles, int n_windows, const PeakNormArgs norm,
-    uint64_t seed_step, int sub_batch) {
+    uint64_t seed_step, int sub_batch, VoiceSetupRecord* setups) {
   __shared__ Smem s;
   const int tid = threadIdx.x;
   const int total_tiles = batch * n_windows;
@@ -269,7 +287,17 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
   bool released = false;
 
   for (;;) {
-    if (tid == 0) s.tile = (int)atomicAdd(&hdr->work, 1u);
+    if (tid == 0) {
+      const int tc = (int)atomicAdd(&hdr->work, 1u);
+      s.tile = tc;
+      // a later window of a voice whose first window has published its set-up
+      int ready = 0;
+      if (setups && tc < total_tiles && tc >= batch) {
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(setups[tc % batch].flag);
+        ready = f.load(cuda::memory_order_acquire) == (((s.epoch & 0x3fffffffu) << 2) | 1u);
+      }
+      s.setup_ready = ready;
+    }
     __syncthreads();  // also: the previous tile's audio is done with the shared buffers
     const int t = s.tile;
     if (t >= total_tiles) {
@@ -296,48 +324,64 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     const unsigned int epoch = s.epoch;
 
     // ---- 1. parameters (Sec. 2.1 draw, Sec. 3.3 range map) ---------------
-    if (params_in == nullptr) {
-      if (tid < 20) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)tid,
-                                                 kStreamParam), key);
-        s.u[4 * tid + 0] = u01f(r.x);
-        s.u[4 * tid + 1] = u01f(r.y);
-        s.u[4 * tid + 2] = u01f(r.z);
-        s.u[4 * tid + 3] = u01f(r.w);
+    const VoiceFF& V = s.vs.V;
+    constexpr int kSetupVec = (int)(sizeof(VoiceSetup) / 16);
+    static_assert(kSetupVec <= NT, "one 16-byte vector of the set-up per thread");
+    if (s.setup_ready) {
+      // a later window: the set-up its voice's first window published
+      const float4* src = reinterpret_cast<const float4*>(&setups[v].vs);
+      float4* dst = reinterpret_cast<float4*>(&s.vs);
+      for (int i = tid; i < kSetupVec; i += NT) dst[i] = __ldcg(src + i);
+      __syncthreads();
+    } else {
+      if (params_in == nullptr) {
+        if (tid < 20) {
+          const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)tid,
+                                                   kStreamParam), key);
+          s.u[4 * tid + 0] = u01f(r.x);
+          s.u[4 * tid + 1] = u01f(r.y);
+          s.u[4 * tid + 2] = u01f(r.z);
+          s.u[4 * tid + 3] = u01f(r.w);
+        }
+      } else if (tid < kNumParams) {
+        s.u[tid] = fminf(fmaxf(params_in[(size_t)v * kNumParams + tid], 0.f), 1.f);
       }
-    } else if (tid < kNumParams) {
-      s.u[tid] = fminf(fmaxf(params_in[(size_t)v * kNumParams + tid], 0.f), 1.f);
+      __syncthreads();
+      if (tid < kNumParams) {
+        const float u = s.u[tid];
+        if (w == 0 && params_out) params_out[(size_t)v * kNumParams + tid] = u;
+        s.y[tid] = range_map_ff(u, vc.map_base[tid], vc.map_scale[tid], vc.map_curve[tid],
+                                vc.map_code[tid], vc.sym[tid], s.T);
+      }
+      __syncthreads();
+      if (tid < 16) {
+        voice_ff_fill(s.vs.V, s.y, tid);
+      } else if (tid == 32) {
+        const float l0 = ff_to_float(s.y[kMix]), l1 = ff_to_float(s.y[kMix + 1]),
+                    l2 = ff_to_float(s.y[kMix + 2]);
+        const float inv = 1.f / fmaxf(1.f, l0 + l1 + l2);
+        s.vs.gain[0] = l0 * inv;
+        s.vs.gain[1] = l1 * inv;
+        s.vs.gain[2] = l2 * inv;
+        const float sh = ff_to_float(s.y[kSqr + 3]);
+        s.vs.shape = sh;
+        s.vs.inv_1p_shape = 1.f / (1.f + sh);
+      } else if (tid == 64) {
+        s.vs.lfo_p0[0] = ff_to_fix64(ff_mul(s.y[kLfo + 2], vc.inv_2pi));
+        s.vs.lfo_p0[1] = ff_to_fix64(ff_mul(s.y[kLfo + 8 + 2], vc.inv_2pi));
+        s.vs.vco_p0[0] = ff_to_fix64(ff_mul(s.y[kSine + 2], vc.inv_2pi));
+        s.vs.vco_p0[1] = ff_to_fix64(ff_mul(s.y[kSqr + 2], vc.inv_2pi));
+      }
+      __syncthreads();
+      if (tid < 6) s.vs.V.level_d[tid] = gate_level_ff(tid, V, s.T);
+      __syncthreads();
+      if (w == 0 && setups && n_windows > 1 && tid < kSetupVec) {
+        // published for the voice's later windows; the flag follows after
+        // the barrier that ends step 3
+        reinterpret_cast<float4*>(&setups[v].vs)[tid] = reinterpret_cast<const float4*>(&s.vs)[tid];
+        __threadfence();
+      }
     }
-    __syncthreads();
-    if (tid < kNumParams) {
-      const float u = s.u[tid];
-      if (w == 0 && params_out) params_out[(size_t)v * kNumParams + tid] = u;
-      s.y[tid] = range_map_ff(u, vc.map_base[tid], vc.map_scale[tid], vc.map_curve[tid],
-                              vc.map_code[tid], vc.sym[tid], s.T);
-    }
-    __syncthreads();
-    if (tid < 16) {
-      voice_ff_fill(s.V, s.y, tid);
-    } else if (tid == 32) {
-      const float l0 = ff_to_float(s.y[kMix]), l1 = ff_to_float(s.y[kMix + 1]),
-                  l2 = ff_to_float(s.y[kMix + 2]);
-      const float inv = 1.f / fmaxf(1.f, l0 + l1 + l2);
-      s.gain[0] = l0 * inv;
-      s.gain[1] = l1 * inv;
-      s.gain[2] = l2 * inv;
-      const float sh = ff_to_float(s.y[kSqr + 3]);
-      s.shape = sh;
-      s.inv_1p_shape = 1.f / (1.f + sh);
-    } else if (tid == 64) {
-      s.lfo_p0[0] = ff_to_fix64(ff_mul(s.y[kLfo + 2], vc.inv_2pi));
-      s.lfo_p0[1] = ff_to_fix64(ff_mul(s.y[kLfo + 8 + 2], vc.inv_2pi));
-      s.vco_p0[0] = ff_to_fix64(ff_mul(s.y[kSine + 2], vc.inv_2pi));
-      s.vco_p0[1] = ff_to_fix64(ff_mul(s.y[kSqr + 2], vc.inv_2pi));
-    }
-    __syncthreads();
-    const VoiceFF& V = s.V;
-    if (tid < 6) s.V.level_d[tid] = gate_level_ff(tid, V, s.T);
-    __syncthreads();
 
     // ---- 2. rate envelopes at point k0 + tid; LFO increments over interval tid
     const bool has_pt = tid <= nseg;
@@ -383,7 +427,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       ff lfo0, lfo1;
 #pragma unroll 1
       for (int l = 0; l < 2; ++l) {
-        const ff th = fix64_to_ff(s.lfo_p0[l] + s.prefix[0][l] + (l == 0 ? r0 : r1));
+        const ff th = fix64_to_ff(s.vs.lfo_p0[l] + s.prefix[0][l] + (l == 0 ? r0 : r1));
         const ff val = lfo_ff(th, l, s.env[3 + 2 * l][tid], V, s.T);
         if (l == 0) lfo0 = val; else lfo1 = val;
       }
@@ -406,9 +450,14 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
         for (int q = 1; q < 4; ++q) acc = fmaf(V.amp_w[k][q], srcf[q], acc);
         amp[k] = acc;
       }
-      s.ampv[tid] = make_float4(s.gain[0] * amp[0], amp[1], s.gain[2] * amp[2], 0.f);
+      s.ampv[tid] = make_float4(s.vs.gain[0] * amp[0], amp[1], s.vs.gain[2] * amp[2], 0.f);
     }
     __syncthreads();
+    if (w == 0 && setups && n_windows > 1 && tid == 0) {
+      // every part of the voice's set-up record is stored and fenced
+      cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(setups[v].flag);
+      f.store(((epoch & 0x3fffffffu) << 2) | 1u, cuda::memory_order_release);
+    }
 
     // ---- 4. VCO phase over each control interval, scanned -----------------
     ff tot[2] = {ff_make(0.f), ff_make(0.f)};
@@ -462,8 +511,8 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       // square-saw drive from the (capped) frequency at the interval start:
       // kappa = 1 + SR / (8 f) = 1 + 1 / (8 inc), at most 50
       const float kap = fminf((float)kBrightnessMax, 1.f + 0.125f / inc1);
-      const float c1 = s.gain[1] * s.inv_1p_shape / tanhf(kap);
-      s.sq[tid] = make_float4(kTwoLog2e * kap, c1, c1 * s.shape, 0.f);
+      const float c1 = s.vs.gain[1] * s.vs.inv_1p_shape / tanhf(kap);
+      s.sq[tid] = make_float4(kTwoLog2e * kap, c1, c1 * s.vs.shape, 0.f);
     }
     if constexpr (!kCarryF32) {
       u64 c0 = tid < nseg ? ff_to_fix64(tot[0]) : 0ull;
@@ -477,8 +526,8 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       }
       __syncthreads();
       if (tid < nseg) {
-        s.seg[0][tid].phase0 = fix64_to_float(s.vco_p0[0] + s.prefix[1][0] + c0);
-        s.seg[1][tid].phase0 = fix64_to_float(s.vco_p0[1] + s.prefix[1][1] + c1);
+        s.seg[0][tid].phase0 = fix64_to_float(s.vs.vco_p0[0] + s.prefix[1][0] + c0);
+        s.seg[1][tid].phase0 = fix64_to_float(s.vs.vco_p0[1] + s.prefix[1][1] + c1);
       }
     } else {
       // FP32 carries (precision study): the interval phases are summed in
@@ -494,8 +543,8 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       }
       __syncthreads();
       if (tid < nseg) {
-        s.seg[0][tid].phase0 = carry_wrap(fix64_to_float(s.vco_p0[0]) + s.prefix_f[0] + c0);
-        s.seg[1][tid].phase0 = carry_wrap(fix64_to_float(s.vco_p0[1]) + s.prefix_f[1] + c1);
+        s.seg[0][tid].phase0 = carry_wrap(fix64_to_float(s.vs.vco_p0[0]) + s.prefix_f[0] + c0);
+        s.seg[1][tid].phase0 = carry_wrap(fix64_to_float(s.vs.vco_p0[1]) + s.prefix_f[1] + c1);
       }
     }
     __syncthreads();
@@ -720,6 +769,8 @@ void set_range(FusedLaunchRecord& r, int k, const void* p, size_t bytes, bool wr
 
 }  // namespace
 
+size_t fused_voice_setup_bytes() { return sizeof(VoiceSetupRecord); }
+
 int fused_max_active_blocks_per_sm() {
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_fused_kernel<false, false, false>, NT, 0);
@@ -730,7 +781,8 @@ cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t fi
                                 int batch, const float* params_in, float* audio,
                                 float* params_out, ScratchHeader* hdr, TileState* tiles,
                                 int grid, cudaStream_t stream, const PeakNormArgs* norm,
-                                uint64_t seed_step, int sub_batch, bool overlap_previous) {
+                                uint64_t seed_step, int sub_batch, bool overlap_previous,
+                                void* voice_setups) {
   const int n_windows = windows_per_voice(vc.K);
   const int total = batch * n_windows;
   grid = grid < total ? grid : total;
@@ -762,8 +814,9 @@ cudaError_t launch_render_fused(const VoiceConst& vc, uint64_t seed, uint64_t fi
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = overlap ? 1 : 0;
+  VoiceSetupRecord* setups = static_cast<VoiceSetupRecord*>(voice_setups);
 #define SYNTH_FUSED_ARGS vc, seed, first, split, batch, params_in, audio, params_out, hdr, tiles, \
-                         n_windows, nz, seed_step, sub_batch
+                         n_windows, nz, seed_step, sub_batch, setups
   cudaError_t e;
   if (vc.general_r) {  // fractional R (never with FP32 carries)
     if (norm) e = cudaLaunchKernelEx(&cfg, render_fused_kernel<false, true, true>, SYNTH_FUSED_ARGS);

@@ -27,7 +27,9 @@ struct synth_handle_s {
   int fused_grid = 0;
   int n_windows = 0;
   void* scratch = nullptr;  // two slots of ScratchHeader + TileState[max_batch * n_windows]
+                            // + the voices' set-up records [max_batch]
   size_t scratch_bytes = 0;  // per slot (256-byte multiple)
+  size_t setup_offset = 0;   // of the set-up records within a slot (16-byte multiple)
   int next_slot = 0;         // slot of the next overlappable fused launch
   bool plain_ready = false;
 };
@@ -102,6 +104,11 @@ ScratchHeader* take_overlap_slot(synth_handle h) {
   return hdr;
 }
 
+// The voice set-up records of the slot whose header is hdr.
+void* slot_voice_setups(synth_handle h, ScratchHeader* hdr) {
+  return reinterpret_cast<char*>(hdr) + h->setup_offset;
+}
+
 }  // namespace
 
 extern "C" {
@@ -162,8 +169,10 @@ synth_status synth_create(const synth_config* cfg, synth_handle* out) {
   h->n_windows = windows_per_voice(h->vc.K);
   const int per_sm = fused_max_active_blocks_per_sm();
   h->fused_grid = h->num_sms * (per_sm > 0 ? per_sm : 1);
-  h->scratch_bytes = (sizeof(ScratchHeader) + sizeof(TileState) * (size_t)cfg->max_batch * h->n_windows +
-                      255) & ~size_t(255);
+  h->setup_offset = (sizeof(ScratchHeader) + sizeof(TileState) * (size_t)cfg->max_batch * h->n_windows +
+                     15) & ~size_t(15);
+  h->scratch_bytes = (h->setup_offset + fused_voice_setup_bytes() * (size_t)cfg->max_batch + 255) &
+                     ~size_t(255);
   if (cudaMalloc(&h->scratch, 2 * h->scratch_bytes) != cudaSuccess) {
     h->scratch = nullptr;
     delete h;
@@ -202,7 +211,7 @@ synth_status synth_render(synth_handle h, uint64_t seed, uint64_t batch_index, i
   return check_cuda(launch_render_fused(h->vc, seed, batch_index * (uint64_t)batch, 0, batch,
                                         params_in_dev, audio_dev, params_out_dev, hdr, tiles,
                                         h->fused_grid, static_cast<cudaStream_t>(stream), nullptr,
-                                        0, 0, true));
+                                        0, 0, true, slot_voice_setups(h, hdr)));
 }
 
 synth_status synth_render_batches(synth_handle h, uint64_t seed, uint64_t seed_step,
@@ -219,7 +228,7 @@ synth_status synth_render_batches(synth_handle h, uint64_t seed, uint64_t seed_s
                                         batch * count, params_in_dev, audio_dev, params_out_dev,
                                         hdr, tiles, h->fused_grid,
                                         static_cast<cudaStream_t>(stream), nullptr, seed_step,
-                                        batch, true));
+                                        batch, true, slot_voice_setups(h, hdr)));
 }
 
 synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t batch_index,
@@ -237,7 +246,7 @@ synth_status synth_render_normalized(synth_handle h, uint64_t seed, uint64_t bat
   return check_cuda(launch_render_fused(h->vc, seed, batch_index * (uint64_t)batch, 0, batch,
                                         params_in_dev, audio_dev, params_out_dev, hdr, tiles,
                                         h->fused_grid, static_cast<cudaStream_t>(stream), &norm,
-                                        0, 0, true));
+                                        0, 0, true, slot_voice_setups(h, hdr)));
 }
 
 synth_status synth_fm_render(synth_handle h, uint64_t seed, uint64_t batch_index, int32_t batch,
@@ -509,7 +518,8 @@ synth_status synth_stream_features(synth_model m, uint64_t seed, int32_t split, 
     const int c = (int)std::min<int64_t>(c_max, count - off);
     cudaError_t e = launch_render_fused(h->vc, seed, first + (uint64_t)off, split, c, nullptr,
                                         m->audio, params_dev ? params_dev + off * kNumParams : nullptr,
-                                        hdr, tiles, h->fused_grid, st);
+                                        hdr, tiles, h->fused_grid, st, nullptr, 0, 0, false,
+                                        slot_voice_setups(h, hdr));
     if (e != cudaSuccess) return SYNTH_ERR_CUDA;
     e = logmel_features_fft(m->audio, h->vc.n_samples, c, m->mel_ws, feats + off * fdim, st);
     if (e != cudaSuccess) return SYNTH_ERR_CUDA;

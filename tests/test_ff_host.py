@@ -141,6 +141,21 @@ def test_division_reciprocal_products_sums(lib):
         assert float(abs(call(lib.h_add, ah, al, bh, bl) - s)) <= 4e-14 * float(abs(ax) + abs(bx))
 
 
+def test_fixed_point_phase_across_magnitudes_and_signs(lib):
+    """Values from 2^-40 to 2^20 of either sign, with the low word of either
+    sign: 2^32 hi below and above 2^31, negative remainders."""
+    rng = np.random.default_rng(11)
+    two64 = mp.mpf(2) ** 64
+    for e in range(-40, 21, 3):
+        for v in rng.uniform(-1.0, 1.0, 40) * 2.0 ** e:
+            hi, lo, vx = split(float(v))
+            for l, x in ((lo, vx), (-lo, mp.mpf(hi) - mp.mpf(lo))):
+                u = lib.h_to_fix64(hi, l)
+                frac = x - mp.floor(x)
+                d = abs(mp.mpf(u) / two64 - frac)
+                assert min(d, 1 - d) < 2.0 ** -50, (v, e, float(d))
+
+
 def test_fixed_point_phase_roundtrip_and_exact_sums(lib):
     rng = np.random.default_rng(7)
     two64 = mp.mpf(2) ** 64
