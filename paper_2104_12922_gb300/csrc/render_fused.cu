@@ -250,12 +250,14 @@ __device__ __noinline__ void normalize_chunk(Smem& s, float* __restrict__ audio,
   }
 }
 
-// Programmatic dependent launch. Once fewer work items remain than the grid
-// has CTAs (after the CTA's current item), the CTA waits for the previous
-// grid on the stream to complete (a no-op unless this launch may overlap it)
-// and then releases the next launch on the stream: when every CTA has done
-// so, the next launch's CTAs start in the SM slots that this launch's last
-// wave leaves idle. The wait comes first, so launch N + 2, which uses launch
+// Programmatic dependent launch. When a CTA takes a render tile that is
+// likely its last (fewer items remain after it than the grid has CTAs), and
+// after a scaling item that is, it waits for the previous grid on the stream
+// to complete (a no-op unless this launch may overlap it) and then releases
+// the next launch on the stream: when every CTA has done so, the next
+// launch's CTAs start in the SM slots that this launch's last wave leaves
+// idle. Releasing before the last tile rather than after it lets the next
+// launch in while that tile runs. The wait comes first, so launch N + 2, which uses launch
 // N's scratch, can never overlap launch N. Neither grid ever waits on the
 // other's work.
 __device__ __forceinline__ void release_next_launch(bool& released) {
@@ -312,6 +314,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       if (t + (int)gridDim.x >= total_items) release_next_launch(released);
       continue;
     }
+    if (t + (int)gridDim.x >= total_items) release_next_launch(released);  // likely the last tile
     const int v = t % batch, w = t / batch;
     const uint64_t g = split_voice(split, first + (uint64_t)v);
     // consecutive sub-batches of sub_batch voices may each have their own
@@ -727,7 +730,6 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       }
       if (kPeak) publish_tile_peak(s, vt + w, vmax, epoch);
     }
-    if (t + (int)gridDim.x >= total_items) release_next_launch(released);
   }
   persistent_finish(hdr);
 }
