@@ -399,3 +399,36 @@ def test_back_to_back_launches_sharing_buffers_keep_stream_order(torch_cuda):
         assert torch.equal(out2, a2)
     del g
     syn.close()
+
+
+def test_two_handles_interleaved_on_one_stream(torch_cuda):
+    """Renders of two handles (each with its own scratch and voice set-up
+    records) interleaved on one stream overlap each other's tails; each
+    result must equal the same render done alone."""
+    import paper_2104_12922_gb300 as pkg
+    torch = torch_cuda
+    B = 48
+    sa = pkg.Synth(seconds=1.0, max_batch=B)
+    sb = pkg.Synth(seconds=1.5, max_batch=B)
+    refs = []
+    for k in range(4):
+        s = sa if k % 2 == 0 else sb
+        a, _ = s.render(30 + k, k, B)
+        s.sync()
+        refs.append(a.clone())
+    st = torch.cuda.Stream()
+    outs = [torch.empty((B, (sa if k % 2 == 0 else sb).num_samples), device="cuda") for k in range(4)]
+    pouts = [torch.empty((B, 78), device="cuda") for _ in range(4)]
+    with torch.cuda.stream(st):
+        for rep in range(2):
+            for k in range(4):
+                s = sa if k % 2 == 0 else sb
+                s.render(30 + k, k, B, out=outs[k], params_out=pouts[k], stream=st)
+            st.synchronize()
+            for k in range(4):
+                assert torch.equal(outs[k], refs[k]), (rep, k)
+                outs[k].fill_(float("nan"))
+    sa.sync(st)
+    sb.sync(st)
+    sa.close()
+    sb.close()
