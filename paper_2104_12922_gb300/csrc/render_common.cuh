@@ -23,14 +23,16 @@ struct __align__(16) SegVco {
   float LB;      // phase advanced over piece A (cycles) = local phase where B starts
   float x;       // log of the per-sample increment ratio
   float invE;    // 1 / expm1(x)
-  float q2, q3;  // 1 + r and 1 + r + r^2 with r = e^x (a quad's phase steps, in units of
-                 // its first increment)
   float ih;      // x / expm1(x) (1 when x = 0)
-  float q4;      // 1 + r + r^2 + r^3: four samples' phase in units of the first increment
-  float r4m1;    // r^4 - 1: a quad's change of the increment
   int jc_flags;  // jc | (A linear) << 16 | (B linear) << 17 | (A capped) << 18 | (B capped) << 19
                  // | (every piece linear: the steps q2..r4m1 are those of x = 0) << 20
+  // the four steps of a run, one 16-byte vector:
+  float q2, q3;  // 1 + r and 1 + r + r^2 with r = e^x (a quad's phase steps, in units of
+                 // its first increment)
+  float q4;      // 1 + r + r^2 + r^3: four samples' phase in units of the first increment
+  float r4m1;    // r^4 - 1: a quad's change of the increment
 };
+static_assert(sizeof(SegVco) == 48, "interval description: three 16-byte vectors");
 
 // expm1(z) for the in-interval phase of a geometric piece, z = d x (d samples
 // into the piece, x the log of the per-sample increment ratio). |z| < 1/4
@@ -187,13 +189,14 @@ __device__ __forceinline__ bool vco_run_start(const SegVco& s, int j0, int len, 
 // float 2 pi differs from 2 pi by 1.7e-7, a drift of that much per wrapped
 // cycle that ends with the run, at most a few cycles), g r^4.
 __device__ __forceinline__ void vco_run_quad(const SegVco& s, VcoRun& r, float ph[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(&s.q2);  // q2, q3, q4, r4m1
   ph[0] = r.base;
   ph[1] = r.base + r.g;
-  ph[2] = fmaf(r.g, s.q2, r.base);
-  ph[3] = fmaf(r.g, s.q3, r.base);
-  const float nb = fmaf(r.g, s.q4, r.base);
+  ph[2] = fmaf(r.g, q.x, r.base);
+  ph[3] = fmaf(r.g, q.y, r.base);
+  const float nb = fmaf(r.g, q.z, r.base);
   r.base = fmaf(-kTwoPiRun, rintf(nb * kInvTwoPiRun), nb);
-  r.g = fmaf(r.g, s.r4m1, r.g);
+  r.g = fmaf(r.g, q.w, r.g);
 }
 
 constexpr float kTwoPiF = 6.28318530717958647692f;
