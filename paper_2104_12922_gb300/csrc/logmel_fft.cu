@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "fft_warp.cuh"
+#include "launch_config.h"
 #include "spectral.h"
 
 namespace synth {
@@ -289,20 +290,10 @@ cudaError_t logmel_features_fft(const float* audio, int64_t N, int batch, const 
   t.band = reinterpret_cast<const int2*>(b + L.band);
   t.line = reinterpret_cast<const float4*>(b + L.line);
   const int smem = (int)sizeof(LmSmem);
-  static int grid_cap = 0;  // resident CTAs on the device
-  if (grid_cap == 0) {
-    cudaError_t e =
-        cudaFuncSetAttribute(logmel_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-      return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, logmel_fft_kernel, kThreadsLm,
-                                                           smem)) != cudaSuccess)
-      return e;
-    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
-  }
+  int grid_cap = 0;  // resident CTAs on the current device
+  const cudaError_t ge =
+      resident_grid(reinterpret_cast<const void*>(logmel_fft_kernel), kThreadsLm, smem, &grid_cap);
+  if (ge != cudaSuccess) return ge;
   const int64_t items = (int64_t)((F + kGroup - 1) / kGroup) * batch;
   if (items >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const int grid = (int)(items < grid_cap ? items : grid_cap);

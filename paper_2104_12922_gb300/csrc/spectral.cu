@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "fft_warp.cuh"
+#include "launch_config.h"
 #include "mbarrier.cuh"
 #include "spectral.h"
 
@@ -551,20 +552,10 @@ cudaError_t mr_launch(const float* sig, int N, int F, int batch, const char* tab
                       float scale, int mode, float* logy, double* loss_item, float* part,
                       unsigned int* err, cudaStream_t st) {
   const int smem = (int)sizeof(MrSmem<R>);
-  static int grid_cap = 0;
-  if (grid_cap == 0) {
-    cudaError_t e =
-        cudaFuncSetAttribute(mr_fft_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-      return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mr_fft_kernel<R>, kThreadsMr,
-                                                           smem)) != cudaSuccess)
-      return e;
-    grid_cap = sms * (per_sm > 0 ? per_sm : 1);
-  }
+  int grid_cap = 0;  // resident CTAs on the current device
+  const cudaError_t ge =
+      resident_grid(reinterpret_cast<const void*>(mr_fft_kernel<R>), kThreadsMr, smem, &grid_cap);
+  if (ge != cudaSuccess) return ge;
   const int64_t items = (int64_t)((F + MrCfg<R>::G - 1) / MrCfg<R>::G) * batch;
   if (items >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const int grid = (int)std::min<int64_t>(items, grid_cap);
