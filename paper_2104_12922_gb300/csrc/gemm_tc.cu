@@ -35,6 +35,7 @@
 #include <mutex>
 
 #include "gemm_tc.h"
+#include "pdl.cuh"
 
 namespace synth {
 
@@ -234,6 +235,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_tc(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sm.tmem_base;
+  // the set-up above reads and writes no global memory: only now wait for
+  // the kernels ahead, and let the next one be scheduled
+  pdl_wait();
+  pdl_release();
 
   if (warp == 0 && lane == 0) {
     // producer: the stage ring runs on across this CTA's tiles
@@ -380,6 +385,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_tc(
 constexpr int kRedRows = 16;
 __global__ void __launch_bounds__(256) splitk_reduce(const float* __restrict__ part, int splits,
                                                      int M, int N, GemmEpilogue epi) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   __shared__ float tile[kRedRows][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + tx, r0 = blockIdx.y * kRedRows;
@@ -539,11 +546,13 @@ cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEp
          : 1;
   const long long items = tiles * splits;
   const int grid = (int)(items < sms ? items : sms);  // persistent: one CTA per SM
-  gemm_bf16_tc<BN><<<grid, kGemmThreads, smem, st>>>(ma, mb, epi, M, N, K, splits, kb_per,
-                                                     splits > 1 ? ws : nullptr, err);
-  if ((e = cudaGetLastError()) != cudaSuccess || splits == 1) return e;
+  float* part = splits > 1 ? ws : nullptr;
+  e = launch_pdl(gemm_bf16_tc<BN>, dim3((unsigned)grid), dim3(kGemmThreads), smem, st, ma, mb, epi,
+                 M, N, K, splits, kb_per, part, err);
+  if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess || splits == 1) return e;
   const dim3 rgrid((N + 31) / 32, (M + kRedRows - 1) / kRedRows);
-  splitk_reduce<<<rgrid, 256, 0, st>>>(ws, splits, M, N, epi);
+  e = launch_pdl(splitk_reduce, rgrid, dim3(256), 0, st, (const float*)ws, splits, M, N, epi);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@
 
 #include "fft_warp.cuh"
 #include "launch_config.h"
+#include "pdl.cuh"
 #include "spectral.h"
 
 namespace synth {
@@ -71,6 +72,8 @@ __global__ void __launch_bounds__(kThreadsLm, 2)
     logmel_fft_kernel(const float* __restrict__ audio, int N, int F, int batch, LmTables t,
                       float eps, float shift, float inv_scale,
                       __nv_bfloat16* __restrict__ features) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   extern __shared__ __align__(16) unsigned char lm_raw[];
   LmSmem& S = *reinterpret_cast<LmSmem*>(lm_raw);
   for (int j = threadIdx.x; j < kHalf; j += kThreadsLm) {
@@ -297,8 +300,10 @@ cudaError_t logmel_features_fft(const float* audio, int64_t N, int batch, const 
   const int64_t items = (int64_t)((F + kGroup - 1) / kGroup) * batch;
   if (items >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const int grid = (int)(items < grid_cap ? items : grid_cap);
-  logmel_fft_kernel<<<grid, kThreadsLm, smem, st>>>(audio, (int)N, F, batch, t, 1e-6f,
-                                                    kFeatureShift, 1.0f / kFeatureScale, features);
+  const cudaError_t le = launch_pdl(logmel_fft_kernel, dim3((unsigned)grid), dim3(kThreadsLm),
+                                    (size_t)smem, st, audio, (int)N, F, batch, t, 1e-6f,
+                                    kFeatureShift, 1.0f / kFeatureScale, features);
+  if (le != cudaSuccess) return le;
   return cudaGetLastError();
 }
 

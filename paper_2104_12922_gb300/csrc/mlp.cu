@@ -18,6 +18,7 @@
 
 #include "gemm_tc.h"
 #include "mlp.h"
+#include "pdl.cuh"
 #include "voice_device.cuh"
 
 namespace synth {
@@ -57,6 +58,8 @@ __global__ void to_bf16(const float* __restrict__ w, int rows, int cols, __nv_bf
 // out[c][r] = in[r][c] (bf16), for the input features of the first layer.
 __global__ void transpose_bf16(const __nv_bfloat16* __restrict__ in, int rows, int cols,
                                __nv_bfloat16* __restrict__ out) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   __shared__ __nv_bfloat16 tile[32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
@@ -81,6 +84,8 @@ __global__ void __launch_bounds__(256) mse_sigmoid_grad(
     const float* __restrict__ y, const float* __restrict__ target, int batch, int P, int P_pad,
     __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt, float* __restrict__ dzf,
     float* __restrict__ part, unsigned int* __restrict__ counter, float* __restrict__ loss) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   __shared__ float red[8];
   __shared__ bool last;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -126,6 +131,8 @@ __global__ void __launch_bounds__(256) relu_grad(const float* __restrict__ dh,
                                                  int width, __nv_bfloat16* __restrict__ dz,
                                                  __nv_bfloat16* __restrict__ dzt,
                                                  float* __restrict__ dzf) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   __shared__ __nv_bfloat16 tile[32][34];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + tx, b0 = blockIdx.y * 32;
@@ -155,6 +162,8 @@ __global__ void __launch_bounds__(256) relu_grad(const float* __restrict__ dh,
 // partial sums are then added in thread order (deterministic).
 __global__ void __launch_bounds__(256) bias_grad(const float* __restrict__ dz, int batch, int width,
                                                  int ld, float* __restrict__ db) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   __shared__ float part[8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + tx;
@@ -186,6 +195,8 @@ __global__ void adam_update_vec4(float4* __restrict__ w, const float4* __restric
                                  float4* __restrict__ m, float4* __restrict__ v, int64_t n4,
                                  float lr, float b1, float b2, float eps, float c1, float c2,
                                  uint2* __restrict__ wb) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
     float4 wi = w[i], mi = m[i], vi = v[i];
@@ -208,6 +219,8 @@ __global__ void adam_update_vec4(float4* __restrict__ w, const float4* __restric
 __global__ void adam_update(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, int64_t n, float lr, float b1, float b2,
                             float eps, float c1, float c2) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float wi = w[i], mi = m[i], vi = v[i];
@@ -225,6 +238,8 @@ __global__ void __launch_bounds__(256) adam_update_tiled(
     float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
     float* __restrict__ v, int rows, int cols, float lr, float b1, float b2, float eps, float c1,
     float c2, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt, int ld_t) {
+  pdl_wait();     // earlier kernels' writes are visible
+  pdl_release();  // the next kernel may be scheduled
   __shared__ __nv_bfloat16 tile[32][34];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + tx, r0 = blockIdx.y * 32;
@@ -365,7 +380,8 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
   __nv_bfloat16* h0t = reinterpret_cast<__nv_bfloat16*>(base + L.h0t);
   {
     dim3 g((L.dims[0] + 31) / 32, (batch + 31) / 32), b(32, 8);
-    transpose_bf16<<<g, b, 0, st>>>(x, batch, L.dims[0], h0t);
+    if ((e = launch_pdl(transpose_bf16, g, b, 0, st, x, batch, L.dims[0], h0t)) != cudaSuccess)
+      return e;
   }
   __nv_bfloat16* dz = reinterpret_cast<__nv_bfloat16*>(base + L.dz);
   __nv_bfloat16* dzt = reinterpret_cast<__nv_bfloat16*>(base + L.dzt);
@@ -373,17 +389,18 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
   float* dzf = reinterpret_cast<float*>(base + L.dzf);
   float* loss = reinterpret_cast<float*>(base + L.loss);
   const int P = L.dims[4], Pp = L.out_pad;
-  mse_sigmoid_grad<<<(batch * Pp + 255) / 256, 256, 0, st>>>(
-      reinterpret_cast<const float*>(base + L.y), target, batch, P, Pp, dz, dzt, dzf,
-      reinterpret_cast<float*>(base + L.loss_part),
-      reinterpret_cast<unsigned int*>(base + L.loss_counter), loss);
-  if (loss_out) cudaMemcpyAsync(loss_out, loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if ((e = launch_pdl(mse_sigmoid_grad, dim3((batch * Pp + 255) / 256), dim3(256), 0, st,
+                      reinterpret_cast<const float*>(base + L.y), target, batch, P, Pp, dz, dzt,
+                      dzf, reinterpret_cast<float*>(base + L.loss_part),
+                      reinterpret_cast<unsigned int*>(base + L.loss_counter), loss)) != cudaSuccess)
+    return e;
   for (int l = 3; l >= 0; --l) {
     const int in = L.dims[l], out = L.dims[l + 1];
     const int ldz = l == 3 ? Pp : out;
     // bias and weight gradients: dW[out][in] = dZ^T[out][B] * H_{l}^T[in][B]^T
-    bias_grad<<<(out + 31) / 32, 256, 0, st>>>(dzf, batch, out, ldz,
-                                               reinterpret_cast<float*>(base + L.gb[l]));
+    if ((e = launch_pdl(bias_grad, dim3((out + 31) / 32), dim3(256), 0, st, (const float*)dzf,
+                        batch, out, ldz, reinterpret_cast<float*>(base + L.gb[l]))) != cudaSuccess)
+      return e;
     const __nv_bfloat16* hprev_t =
         l == 0 ? h0t : reinterpret_cast<const __nv_bfloat16*>(base + L.ht[l]);
     GemmEpilogue ew;
@@ -402,8 +419,10 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
                          batch, in, ldz, eh, err, st, reinterpret_cast<float*>(base + L.splitk),
                          L.splitk_bytes)) != cudaSuccess)
         return e;
-      relu_grad<<<dim3((in + 31) / 32, (batch + 31) / 32), 256, 0, st>>>(
-          dh, reinterpret_cast<const __nv_bfloat16*>(base + L.h[l]), batch, in, dz, dzt, dzf);
+      if ((e = launch_pdl(relu_grad, dim3((in + 31) / 32, (batch + 31) / 32), dim3(256), 0, st,
+                          (const float*)dh, reinterpret_cast<const __nv_bfloat16*>(base + L.h[l]),
+                          batch, in, dz, dzt, dzf)) != cudaSuccess)
+        return e;
     }
   }
   // Adam
@@ -419,21 +438,30 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
     if (l == 0) {
       // no transposed copy: a vectorised stream (in * out is a multiple of 4)
       const int64_t n4 = (int64_t)in * out / 4;
-      adam_update_vec4<<<grid_of(n4), 256, 0, st>>>(
-          reinterpret_cast<float4*>(w), reinterpret_cast<const float4*>(g),
-          reinterpret_cast<float4*>(mw), reinterpret_cast<float4*>(vw), n4, lr, b1, b2, eps, c1,
-          c2, reinterpret_cast<uint2*>(wb));
+      if ((e = launch_pdl(adam_update_vec4, dim3(grid_of(n4)), dim3(256), 0, st,
+                          reinterpret_cast<float4*>(w), reinterpret_cast<const float4*>(g),
+                          reinterpret_cast<float4*>(mw), reinterpret_cast<float4*>(vw), n4, lr, b1,
+                          b2, eps, c1, c2, reinterpret_cast<uint2*>(wb))) != cudaSuccess)
+        return e;
     } else {
       const int outp = l == 3 ? Pp : out;
-      adam_update_tiled<<<dim3((in + 31) / 32, (out + 31) / 32), 256, 0, st>>>(
-          w, g, mw, vw, out, in, lr, b1, b2, eps, c1, c2, wb,
-          reinterpret_cast<__nv_bfloat16*>(base + L.wt[l]), outp);
+      if ((e = launch_pdl(adam_update_tiled, dim3((in + 31) / 32, (out + 31) / 32), dim3(256), 0,
+                          st, w, g, mw, vw, out, in, lr, b1, b2, eps, c1, c2, wb,
+                          reinterpret_cast<__nv_bfloat16*>(base + L.wt[l]), outp)) != cudaSuccess)
+        return e;
     }
-    adam_update<<<grid_of(out), 256, 0, st>>>(
-        reinterpret_cast<float*>(base + L.b[l]), reinterpret_cast<const float*>(base + L.gb[l]),
-        reinterpret_cast<float*>(base + L.mb[l]), reinterpret_cast<float*>(base + L.vb[l]), out,
-        lr, b1, b2, eps, c1, c2);
+    if ((e = launch_pdl(adam_update, dim3(grid_of(out)), dim3(256), 0, st,
+                        reinterpret_cast<float*>(base + L.b[l]),
+                        reinterpret_cast<const float*>(base + L.gb[l]),
+                        reinterpret_cast<float*>(base + L.mb[l]),
+                        reinterpret_cast<float*>(base + L.vb[l]), (int64_t)out, lr, b1, b2, eps, c1,
+                        c2)) != cudaSuccess)
+      return e;
   }
+  // the loss last, so that no copy splits the chain of kernels above
+  if (loss_out &&
+      (e = cudaMemcpyAsync(loss_out, loss, sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
   return cudaGetLastError();
 }
 

@@ -747,10 +747,11 @@ struct FusedLaunchRecord {
   const void* hdr = nullptr;
   uintptr_t lo[5] = {}, hi[5] = {};  // params_in, audio, params_out, peak, silent
   bool writes[5] = {};
+  bool other = false;  // the last launch was another kernel that releases its successor early
 };
 
 bool launches_conflict(const FusedLaunchRecord& a, const FusedLaunchRecord& b) {
-  if (a.hdr == b.hdr) return true;
+  if (a.other || b.other || a.hdr == b.hdr) return true;
   for (int i = 0; i < 5; ++i)
     for (int j = 0; j < 5; ++j)
       if ((a.writes[i] || b.writes[j]) && a.lo[i] < a.hi[i] && b.lo[j] < b.hi[j] &&
@@ -772,6 +773,13 @@ void set_range(FusedLaunchRecord& r, int k, const void* p, size_t bytes, bool wr
 }  // namespace
 
 size_t fused_voice_setup_bytes() { return sizeof(VoiceSetupRecord); }
+
+void note_early_release_launch(cudaStream_t st) {
+  FusedLaunchRecord rec;
+  rec.other = true;
+  std::lock_guard<std::mutex> lock(g_fused_launch_mu);
+  g_last_fused_launch[st] = rec;
+}
 
 int fused_max_active_blocks_per_sm() {
   int n = 0;
