@@ -432,3 +432,37 @@ def test_two_handles_interleaved_on_one_stream(torch_cuda):
     sb.sync(st)
     sa.close()
     sb.close()
+
+
+def test_render_right_after_the_network_reads_its_output(torch_cuda):
+    """The network's kernels let their successor be scheduled early (each
+    waits for its predecessor at its start); a fused render does not wait at
+    its start, so after such a kernel it must be launched the plain way. The
+    proposal network's parameters fed straight into a render on one stream,
+    with no synchronisation between them, must give the render of the same
+    parameters done after a synchronisation."""
+    import paper_2104_12922_gb300 as pkg
+    torch = torch_cuda
+    B = 16
+    syn = pkg.Synth(seconds=1.0, max_batch=B)
+    model = pkg.ProposalModel(syn, max_batch=B, seed=3)
+    audio, _ = syn.render(5, 0, B)
+    syn.sync()
+    feats = model.features(audio)
+    ref_p = model.forward(feats)
+    torch.cuda.synchronize()
+    ref_a, _ = syn.render(0, 0, B, params_in=ref_p)
+    syn.sync()
+    ref_a = ref_a.clone()
+    st = torch.cuda.Stream()
+    for _ in range(3):
+        with torch.cuda.stream(st):
+            f2 = model.features(audio, stream=st)
+            p2 = model.forward(f2, stream=st)
+            a2, _ = syn.render(0, 0, B, params_in=p2, stream=st)
+        st.synchronize()
+        syn.sync(st)
+        assert torch.equal(p2, ref_p)
+        assert torch.equal(a2, ref_a)
+    model.close()
+    syn.close()
