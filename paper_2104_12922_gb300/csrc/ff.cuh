@@ -88,8 +88,6 @@ FF_HD ff ff_mul_f(ff a, float b) {
   p.lo = fmaf(a.lo, b, p.lo);
   return quick_two_sum(p.hi, p.lo);
 }
-// Scale by a power of two (exact barring under/overflow).
-FF_HD ff ff_ldexp(ff a, int e) { return {ldexpf(a.hi, e), ldexpf(a.lo, e)}; }
 // a / b: long division, two quotient digits and a correction.
 FF_HD ff ff_div(ff a, ff b) {
   const float q1 = a.hi / b.hi;
@@ -141,6 +139,9 @@ FF_HD ff ff_scale2i(ff a, int n) {
   }
   return {ldexpf(a.hi, n), ldexpf(a.lo, n)};
 }
+// Scale by a power of two (exact barring under/overflow): a product by the
+// constant 2^e for the small exponents the control chain uses.
+FF_HD ff ff_ldexp(ff a, int e) { return ff_scale2i(a, e); }
 
 // Tables for argument reduction. They are computed on the host from FP64
 // values (ff_tables_fill) and handed to the kernels with the configuration:
@@ -277,14 +278,14 @@ FF_HD ff ff_sin2pi(ff p, const FFTables& T) {
   const float sg = m < 0.0f ? -1.0f : 1.0f;
   const ff sm = {sg * T.sin_tab[mi].hi, sg * T.sin_tab[mi].lo};  // sin(2 pi m/128), odd
   const ff cm = T.cos_tab[mi];                                    // cos, even
-  // sin(x) and cos(x) of x = 2 pi r
-  const ff sx = ff_add(ff_mul(sm, cos_a), ff_mul(cm, sin_a));
-  const ff cx = ff_sub(ff_mul(cm, cos_a), ff_mul(sm, sin_a));
+  // sin(2 pi p) = sin(q pi/2 + x) with x = 2 pi r: sin x, cos x, -sin x,
+  // -cos x for q mod 4 = 0..3; sin x = sm cos a + cm sin a and
+  // cos x = cm cos a - sm sin a, so one u cos a + w sin a with the pair
+  // chosen (and negated) first
   const int qi = ((int)q) & 3;
-  if (qi == 0) return sx;
-  if (qi == 1) return cx;
-  if (qi == 2) return ff_neg(sx);
-  return ff_neg(cx);
+  const float sgn = qi >= 2 ? -1.0f : 1.0f;
+  const ff u = (qi & 1) ? cm : sm, w = (qi & 1) ? ff_neg(sm) : cm;
+  return ff_add(ff_mul({sgn * u.hi, sgn * u.lo}, cos_a), ff_mul({sgn * w.hi, sgn * w.lo}, sin_a));
 }
 
 // ---------------------------------------------------------------------------
