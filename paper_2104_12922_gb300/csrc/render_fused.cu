@@ -579,8 +579,8 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
           vco_quad<false, false>(s.seg[0][si + 1], rel0 - b1, psB);
           vco_quad<false, false>(s.seg[1][si + 1], rel0 - b1, pqB);
         }
-        const uint4 nz = philox4x32_10(
-            make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(q_lo + q), kStreamNoise), key);
+        const uint4 nc = make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(q_lo + q), kStreamNoise);
+        const uint4 nz = kPeak ? philox4x32_10_wide(nc, key) : philox4x32_10(nc, key);
         const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
         float out4[4];
 #pragma unroll
@@ -647,9 +647,10 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
           const float4 A = s.ampv[si], D = s.aslope[si];
           const int jq = j0 + 4 * q;
           const int off = off0 + 4 * q;
-          const uint4 nz = philox4x32_10(
-              make_uint4((uint32_t)g, (uint32_t)(g >> 32), q_t + (uint32_t)(off >> 2), kStreamNoise),
-              key);
+          const uint4 nc =
+              make_uint4((uint32_t)g, (uint32_t)(g >> 32), q_t + (uint32_t)(off >> 2), kStreamNoise);
+          // the peak variant: the wide-product form, which leaves it no spills
+          const uint4 nz = kPeak ? philox4x32_10_wide(nc, key) : philox4x32_10(nc, key);
           const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
           // amplitudes at the quad's first sample, then one step of the slope per sample
           const float fj0 = (float)jq;

@@ -155,6 +155,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// The same generator with each 32 x 32 -> 64-bit product as one wide
+// multiply (bit-identical). It issues more slowly than the split high and low
+// products, but holds fewer registers across the rounds: the peak-normalising
+// render, whose audio loop otherwise spills, runs faster with it.
+__device__ __forceinline__ uint4 philox4x32_10_wide(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y,
+                   (uint32_t)p0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
 // Top 24 bits of a draw, times 2^-24: exact in float, in [0,1).
 __device__ __forceinline__ float u01f(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
