@@ -554,18 +554,46 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
 
     // ---- 5. audio ----------------------------------------------------------
     if constexpr (kGenR) {
-      // fractional R: quads of the voice's own 4-sample grid, each sample in
-      // the interval whose start it has passed (a quad meets at most two
-      // intervals since R >= 4); the tile writes only its own samples
+      // fractional R: quads of the voice's own 4-sample grid. A work item is
+      // (interval, chunk): the quad that straddles the interval's start is
+      // evaluated on its own (each sample in the interval whose start it has
+      // passed; a quad meets at most two intervals since R >= 4), the quads
+      // inside the interval in runs of kGenG, their VCO phases stepped from
+      // quad to quad as on the default path. The tile writes only its own
+      // samples.
       const int n_t = s.sst[nseg];
       float* out_v = audio + (size_t)v * (size_t)N;
-      const int64_t q_lo = s_tile >> 2;
-      const int nq = (int)(((s_tile + n_t + 3) >> 2) - q_lo);
       const float invRg = ff_to_float(vc.inv_R);
       float vmax = 0.f;
-      for (int q = tid; q < nq; q += NT) {
-        const int64_t n0 = (q_lo + q) << 2;
-        const int rel0 = (int)(n0 - s_tile);  // -3 .. 0 on the first quad
+      // a quad's four samples at tile-relative sample rel0: 16-byte stores
+      // inside the tile, else the samples in [0, n_t) one by one
+      auto store_quad = [&](int rel0, const float out4[4]) {
+        const int64_t n0 = s_tile + rel0;
+        if (vec_ok && rel0 >= 0 && rel0 + 3 < n_t) {
+          if (kPeak) {
+            *reinterpret_cast<float4*>(out_v + n0) = make_float4(out4[0], out4[1], out4[2], out4[3]);
+            vmax = fmaxf(fmaxf(vmax, fmaxf(fabsf(out4[0]), fabsf(out4[1]))),
+                         fmaxf(fabsf(out4[2]), fabsf(out4[3])));
+          } else {
+            __stcs(reinterpret_cast<float4*>(out_v + n0),
+                   make_float4(out4[0], out4[1], out4[2], out4[3]));
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (rel0 + i >= 0 && rel0 + i < n_t) {
+              out_v[n0 + i] = out4[i];
+              if (kPeak) vmax = fmaxf(vmax, fabsf(out4[i]));
+            }
+        }
+      };
+      auto noise_quad = [&](int rel0) {
+        const uint4 nc = make_uint4((uint32_t)g, (uint32_t)(g >> 32),
+                                    (uint32_t)((s_tile + rel0) >> 2), kStreamNoise);
+        return kPeak ? philox4x32_10_wide(nc, key) : philox4x32_10(nc, key);
+      };
+      // a quad on its own, its interval found from a float estimate
+      auto single_quad = [&](int rel0) {
         const int r0 = max(rel0, 0);
         int si = min((int)((float)r0 * invRg), nseg - 1);
         while (si + 1 < nseg && s.sst[si + 1] <= r0) ++si;
@@ -579,8 +607,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
           vco_quad<false, false>(s.seg[0][si + 1], rel0 - b1, psB);
           vco_quad<false, false>(s.seg[1][si + 1], rel0 - b1, pqB);
         }
-        const uint4 nc = make_uint4((uint32_t)g, (uint32_t)(g >> 32), (uint32_t)(q_lo + q), kStreamNoise);
-        const uint4 nz = kPeak ? philox4x32_10_wide(nc, key) : philox4x32_10(nc, key);
+        const uint4 nz = noise_quad(rel0);
         const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
         float out4[4];
 #pragma unroll
@@ -600,22 +627,81 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
           out4[i] = fmaf(fmaf(fj, Bn.x - A.x, A.x), x_sin,
                          fmaf(fmaf(fj, Bn.y - A.y, A.y), x_sq, fmaf(fj, Bn.z - A.z, A.z) * x_nz));
         }
-        if (vec_ok && rel0 >= 0 && rel0 + 3 < n_t) {
-          if (kPeak) {
-            *reinterpret_cast<float4*>(out_v + n0) = make_float4(out4[0], out4[1], out4[2], out4[3]);
-            vmax = fmaxf(fmaxf(vmax, fmaxf(fabsf(out4[0]), fabsf(out4[1]))),
-                         fmaxf(fabsf(out4[2]), fabsf(out4[3])));
-          } else {
-            __stcs(reinterpret_cast<float4*>(out_v + n0),
-                   make_float4(out4[0], out4[1], out4[2], out4[3]));
+        store_quad(rel0, out4);
+      };
+      // first the quads that straddle an interval's start (or the tile's
+      // start or end), one loop of their own so that the run loop below
+      // carries none of their state
+      for (int si = tid; si < nseg; si += NT) {
+        const int a = s.sst[si], b = s.sst[si + 1];
+        const int f = a + (int)((-(s_tile + a)) & 3);  // first grid quad at or after a
+        const int nf = b - f >= 4 ? (b - f) >> 2 : 0;   // quads wholly inside [a, b)
+        const int tail = f + 4 * nf;
+        const int n_single = (f > a ? 1 : 0) + (si == nseg - 1 && tail < b ? 1 : 0);
+#pragma unroll 1
+        for (int k = 0; k < n_single; ++k) single_quad(k == 0 && f > a ? f - 4 : tail);
+      }
+      // then the whole quads: work items of kGenG quads of one interval
+      constexpr int kGenG = 5;
+      const int full_max = (int)(vc.r_f * 0.25f) + 2;  // bound on an interval's whole quads
+      const int cpi = (full_max + kGenG - 1) / kGenG;   // chunks per interval
+      for (int it = tid; it < nseg * cpi; it += NT) {
+        const int si = it / cpi, c = it - si * cpi;
+        const int a = s.sst[si], b = s.sst[si + 1];
+        const int f = a + (int)((-(s_tile + a)) & 3);
+        const int nf = b - f >= 4 ? (b - f) >> 2 : 0;
+        const int q0 = c * kGenG, q1 = min(nf, q0 + kGenG);
+        if (q0 >= q1) continue;
+        const SegVco& sv0 = s.seg[0][si];
+        const SegVco& sv1 = s.seg[1][si];
+        // one whole quad from its VCO phases (radians)
+        auto emit = [&](int rel0, const float ps[4], const float pq[4]) {
+          const float4 sq = s.sq[si];
+          const float4 A = s.ampv[si], Bn = s.ampv[si + 1];
+          const float u0 = s.u0f[si];
+          // amplitudes: A + (Bn - A) ((rel - a) / R + u0), linear in rel
+          const float dx = (Bn.x - A.x) * invRg, dy = (Bn.y - A.y) * invRg, dz = (Bn.z - A.z) * invRg;
+          const float fj0 = (float)(rel0 - a);
+          const float a0x = fmaf(fj0, dx, fmaf(u0, Bn.x - A.x, A.x));
+          const float a0y = fmaf(fj0, dy, fmaf(u0, Bn.y - A.y, A.y));
+          const float a0z = fmaf(fj0, dz, fmaf(u0, Bn.z - A.z, A.z));
+          const uint4 nz = noise_quad(rel0);
+          const uint32_t nw[4] = {nz.x, nz.y, nz.z, nz.w};
+          float out4[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float x_sin = __sinf(ps[i]);
+            float sn, cs;
+            __sincosf(pq[i], &sn, &cs);
+            const float x_sq = square_saw_sc(sn, cs, sq.x, sq.y, sq.z);
+            const float x_nz = fmaf((float)(nw[i] >> 8), 0x1p-23f, -1.f);  // 2u - 1, exact
+            const float fi = (float)i;
+            out4[i] = fmaf(fmaf(fi, dx, a0x), x_sin,
+                           fmaf(fmaf(fi, dy, a0y), x_sq, fmaf(fi, dz, a0z) * x_nz));
+          }
+          store_quad(rel0, out4);
+        };
+        VcoRun r0, r1;
+        const int j0 = f + 4 * q0 - a;  // the chunk's first sample in its interval
+        if (vco_run_start(sv0, j0, 4 * (q1 - q0), r0) & vco_run_start(sv1, j0, 4 * (q1 - q0), r1)) {
+#pragma unroll 1
+          for (int q = q0; q < q1; ++q) {
+            float ps[4], pq[4];
+            vco_run_quad(sv0, r0, ps);
+            vco_run_quad(sv1, r1, pq);
+            emit(f + 4 * q, ps, pq);
           }
         } else {
+          // a chunk that meets a Nyquist-cap boundary evaluates each quad on its own
+#pragma unroll 1
+          for (int q = q0; q < q1; ++q) {
+            float ps[4], pq[4];
+            vco_quad<false, true>(sv0, f + 4 * q - a, ps);
+            vco_quad<false, true>(sv1, f + 4 * q - a, pq);
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (rel0 + i >= 0 && rel0 + i < n_t) {
-              out_v[n0 + i] = out4[i];
-              if (kPeak) vmax = fmaxf(vmax, fabsf(out4[i]));
-            }
+            for (int i = 0; i < 4; ++i) { ps[i] *= kTwoPiF; pq[i] *= kTwoPiF; }
+            emit(f + 4 * q, ps, pq);
+          }
         }
       }
       if (kPeak) publish_tile_peak(s, vt + w, vmax, epoch);
