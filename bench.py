@@ -9,7 +9,7 @@ Our arm (default) times the fused persistent kernel (and, beside it, the
 plain unfused module-by-module form on the same GPU). ``--impl reference``
 times the FP64 CPU oracle as it stands on the host cores.
 
-The timed loop renders 8 consecutive batches per launch
+The timed loop renders 16 consecutive batches per launch
 (synth_render_batches, each batch with seed = its index); the same render
 with one launch per batch is reported beside it.
 
@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BATCH = 128
-GROUP = 8  # consecutive batches per launch of the timed loop
+GROUP = 16  # consecutive batches per launch of the timed loop
 SECONDS = 4.0
 SR = 44100.0
 N_SAMPLES = int(SECONDS * SR)
@@ -179,7 +179,7 @@ def profiled_traffic():
 
 
 def profiled_instructions():
-    """Warp instructions per launch of the fused kernel (8 batches) from the
+    """Warp instructions per launch of the fused kernel (GROUP batches) from the
     committed ncu summary, or None when it was taken on other sources."""
     try:
         text = open(PROFILE_SUMMARY).read()
@@ -742,7 +742,7 @@ def run_ours(args):
     n_buf = 4  # 4 x 90.3 MB rotating outputs: > L2 (129 MB), writes reach HBM
     outs = [torch.empty((BATCH, N_SAMPLES), dtype=torch.float32, device=dev) for _ in range(n_buf)]
     pouts = [torch.empty((BATCH, 78), dtype=torch.float32, device=dev) for _ in range(n_buf)]
-    # GROUP consecutive batches per launch into 2 rotating 723 MB outputs
+    # GROUP consecutive batches per launch into 2 rotating outputs of GROUP x 90.3 MB
     outs_g = [torch.empty((BATCH * GROUP, N_SAMPLES), dtype=torch.float32, device=dev)
               for _ in range(2)]
     pouts_g = [torch.empty((BATCH * GROUP, 78), dtype=torch.float32, device=dev) for _ in range(2)]
@@ -752,13 +752,17 @@ def run_ours(args):
         return rank_batch_index(step, ws, rank, K)
 
     def record(g_steps):
-        """g_steps batches, GROUP per launch (seed = batch index)"""
-        for s0 in range(0, g_steps, GROUP):
-            c = min(GROUP, g_steps - s0)
+        """g_steps batches in launches of at most GROUP, as even as possible
+        (20 steps: two of 10, not 16 + 4; seed = batch index)"""
+        n_launch = (g_steps + GROUP - 1) // GROUP
+        s0 = 0
+        for l in range(n_launch):
+            c = g_steps // n_launch + (1 if l < g_steps % n_launch else 0)
             bi = batch_index(s0)
-            i = (s0 // GROUP) % 2
+            i = l % 2
             syn.render_batches(bi, 1, bi, BATCH, c, out=outs_g[i][:c * BATCH],
                                params_out=pouts_g[i][:c * BATCH], stream=stream)
+            s0 += c
 
     def record_single(g_steps, plain=False):
         """one launch per batch"""
@@ -1003,10 +1007,12 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (synth1B1 workload: parameters drawn per voice from seed and voice index)",
             "config": {"workload": "Voice batch 128 x 4 s @ 44.1 kHz, FP32 out, seed = batch index, "
-                                   f"{K} batches per CUDA graph, {GROUP} per launch "
-                                   "(synth_render_batches)", "global_batch": BATCH * ws,
+                                   f"{K} batches per CUDA graph in {(K + GROUP - 1) // GROUP} launches "
+                                   f"of at most {GROUP} (synth_render_batches)",
+                       "global_batch": BATCH * ws,
                        "seconds": SECONDS, "sample_rate": SR,
-                       "l2": "2 rotating 723 MB outputs of 8 batches (> 129 MB L2)",
+                       "l2": f"2 rotating {GROUP * BATCH * N_SAMPLES * 4 / 1e6:.0f} MB outputs of "
+                             f"{GROUP} batches (> 129 MB L2)",
                        "parallelism": f"replicas x{ws} (disjoint batch indices)"},
             "x_realtime": value * 1e6 / SR,
             "paper_context": {"value": PAPER_MHZ, "unit": "MHz", "hardware": "single V100 (Sec. 2.2)"},
