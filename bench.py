@@ -9,7 +9,7 @@ Our arm (default) times the fused persistent kernel (and, beside it, the
 plain unfused module-by-module form on the same GPU). ``--impl reference``
 times the FP64 CPU oracle as it stands on the host cores.
 
-The timed loop renders 16 consecutive batches per launch
+The timed loop renders up to 20 consecutive batches per launch
 (synth_render_batches, each batch with seed = its index); the same render
 with one launch per batch is reported beside it.
 
@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BATCH = 128
-GROUP = 16  # consecutive batches per launch of the timed loop
+GROUP = 20  # at most this many consecutive batches per launch of the timed loop
 SECONDS = 4.0
 SR = 44100.0
 N_SAMPLES = int(SECONDS * SR)
@@ -753,7 +753,7 @@ def run_ours(args):
 
     def record(g_steps):
         """g_steps batches in launches of at most GROUP, as even as possible
-        (20 steps: two of 10, not 16 + 4; seed = batch index)"""
+        (24 steps: two of 12, not 20 + 4; seed = batch index)"""
         n_launch = (g_steps + GROUP - 1) // GROUP
         s0 = 0
         for l in range(n_launch):

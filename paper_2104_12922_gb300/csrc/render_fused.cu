@@ -1,4 +1,5 @@
-// render_fused.cu -- the fused persistent Voice render (one launch per batch).
+// render_fused.cu -- the fused persistent Voice render (one launch per batch
+// or per several consecutive batches).
 //
 // Work unit: a tile = (voice v, window w) of kFusedTilePoints = 256 control
 // points, i.e. the 255 control intervals between them; window w starts at
@@ -10,7 +11,8 @@
 // One CTA of 256 threads takes a tile through these steps, one thread per
 // control point (Sec. 3.1 control rate) and then all threads on the audio:
 //  1. parameters: Philox draw (Sec. 2.1) or the caller's values, Sec. 3.3
-//     range map (float-float), the per-voice constants;
+//     range map (float-float), the per-voice constants -- derived by the
+//     voice's first window and published, copied by its later windows;
 //  2. the 6 ADSRs at the thread's control point, the two LFO rates and their
 //     phase increments over the interval that starts there;
 //  3. a block scan of those increments plus a look-back over the voice's
@@ -19,13 +21,16 @@
 //  4. per interval and VCO the closed-form description of the phase (SegVco)
 //     and the phase advanced over it; a second scan + look-back gives each
 //     interval's starting phase;
-//  5. the audio (Sec. 3.2): each thread takes quads of 4 consecutive samples
-//     -- VCO phases from the interval description, sine, square-saw, Philox
-//     noise, VCAs, mixer -- written with one 16-byte streaming store.
+//  5. the audio (Sec. 3.2): each thread takes runs of quads of 4 consecutive
+//     samples of one interval -- VCO phases from the interval description,
+//     stepped from quad to quad, sine, square-saw, Philox noise, VCAs,
+//     mixer -- each quad written with one 16-byte streaming store.
 // The control chain is float-float (control_ff.cuh); running phase sums are
 // 64-bit fixed point, exact and order-independent (FP32 in the precision-study
-// mode). Nothing but the audio, the parameters and a 48-byte look-back record
-// per tile is written to device memory, and no FP64 instruction runs.
+// mode). Nothing but the audio, the parameters, a 48-byte look-back record
+// per tile and a set-up record per voice is written to device memory, and no
+// FP64 arithmetic runs. Consecutive launches on a stream may overlap (see
+// release_next_launch and the launch record at the end of this file).
 
 #include <mutex>
 #include <unordered_map>
@@ -257,9 +262,9 @@ __device__ __noinline__ void normalize_chunk(Smem& s, float* __restrict__ audio,
 // the next launch on the stream: when every CTA has done so, the next
 // launch's CTAs start in the SM slots that this launch's last wave leaves
 // idle. Releasing before the last tile rather than after it lets the next
-// launch in while that tile runs. The wait comes first, so launch N + 2, which uses launch
-// N's scratch, can never overlap launch N. Neither grid ever waits on the
-// other's work.
+// launch in while that tile runs. The wait comes first, so launch N + 2,
+// which uses launch N's scratch, can never overlap launch N. Neither grid
+// ever waits on the other's work.
 __device__ __forceinline__ void release_next_launch(bool& released) {
   if (released) return;
   asm volatile("griddepcontrol.wait;" ::: "memory");

@@ -219,18 +219,18 @@ def test_render_batches_equals_separate_renders(torch_cuda):
 
 
 def test_render_batches_full_size_sampled(torch_cuda, oracle_mod):
-    """The throughput launch itself: 16 consecutive batches of 128 x 4 s in
+    """The throughput launch itself: 20 consecutive batches of 128 x 4 s in
     one synth_render_batches call, batch k with seed = batch index = 16 + k.
     A sample of voices of the first, a middle and the last batch is checked
     against the oracle (parameters bit-exact, audio within the 2e-4 bar)."""
     import paper_2104_12922_gb300 as pkg
     torch = torch_cuda
-    syn = pkg.Synth(seconds=4.0, max_batch=2048)
+    syn = pkg.Synth(seconds=4.0, max_batch=2560)
     bi = 16
-    audio, params = syn.render_batches(bi, 1, bi, 128, 16)
+    audio, params = syn.render_batches(bi, 1, bi, 128, 20)
     syn.sync()
-    assert audio.shape == (2048, syn.num_samples)
-    for k in (0, 7, 15):
+    assert audio.shape == (2560, syn.num_samples)
+    for k in (0, 9, 19):
         rows = si.sample_voices(bi + k, 128, 6)
         idx = torch.as_tensor(k * 128 + rows, device=audio.device, dtype=torch.long)
         a = audio.index_select(0, idx).cpu().numpy()
