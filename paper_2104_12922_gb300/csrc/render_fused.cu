@@ -37,6 +37,7 @@
 
 #include "control_ff.cuh"
 #include "internal.h"
+#include "philox_noise.cuh"
 #include "render_common.cuh"
 
 namespace synth {
@@ -592,10 +593,19 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
             }
         }
       };
+      // the noise generator's key schedule and the products the voice fixes,
+      // once per tile (the peak variant keeps the wide-product form)
+      const PhiloxNoise pn =
+          philox_noise_setup((uint32_t)g, (uint32_t)(g >> 32), kStreamNoise, key.x, key.y);
       auto noise_quad = [&](int rel0) {
-        const uint4 nc = make_uint4((uint32_t)g, (uint32_t)(g >> 32),
-                                    (uint32_t)((s_tile + rel0) >> 2), kStreamNoise);
-        return kPeak ? philox4x32_10_wide(nc, key) : philox4x32_10(nc, key);
+        const uint32_t q = (uint32_t)((s_tile + rel0) >> 2);
+        if constexpr (kPeak) {
+          return philox4x32_10_wide(make_uint4((uint32_t)g, (uint32_t)(g >> 32), q, kStreamNoise), key);
+        } else {
+          uint32_t o[4];
+          philox_noise(pn, q, o);
+          return make_uint4(o[0], o[1], o[2], o[3]);
+        }
       };
       // a quad on its own, its interval found from a float estimate
       auto single_quad = [&](int rel0) {
