@@ -145,7 +145,7 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
-FUSED_SOURCES = ["render_fused.cu", "render_common.cuh", "control_ff.cuh", "ff.cuh",
+FUSED_SOURCES = ["render_fused.cu", "render_common.cuh", "control_ff.cuh", "ff.cuh", "philox_noise.cuh",
                  "voice_device.cuh", "internal.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "render_fused_batch128x4s.md")
 
