@@ -50,7 +50,9 @@ typedef enum {
   SYNTH_ERR_OOM = 3,         /* device or pinned allocation failed (create only) */
   SYNTH_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (output invalid) */
   SYNTH_ERR_STATE = 5,       /* handle not usable (destroyed / earlier failure) */
-  SYNTH_ERR_UNSUPPORTED = 6  /* configuration the kernels do not implement */
+  SYNTH_ERR_UNSUPPORTED = 6, /* configuration the kernels do not implement */
+  SYNTH_ERR_BOUNDS = 7       /* bounds-checked build only: a kernel index left its
+                                range; the access was skipped (output invalid) */
 } synth_status;
 
 typedef struct synth_handle_s* synth_handle;
@@ -393,14 +395,17 @@ synth_status synth_render_noalloc(const synth_config* cfg, uint64_t seed, uint64
 /* Status of the last synth_render_noalloc call on the current device: waits
  * for `stream`, then returns SYNTH_ERR_TIMEOUT (and clears the record) if a
  * bounded device-side wait of that render gave up (its audio is invalid),
+ * SYNTH_ERR_BOUNDS (bounds-checked build) if an index left its range,
  * SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. Allocates nothing; call it
  * after the render and before the next synth_render_noalloc. The paper has
  * no counterpart to this call either. */
 synth_status synth_noalloc_status(void* stream);
 
 /* Waits for the stream, then reports (and clears) a device-side error
- * recorded by any earlier call on this handle: SYNTH_ERR_TIMEOUT if a bounded
- * wait gave up, SYNTH_ERR_CUDA on a CUDA error, else SYNTH_OK. */
+ * recorded by any earlier call on this handle: SYNTH_ERR_BOUNDS if, in the
+ * bounds-checked build, a kernel index left its range; else
+ * SYNTH_ERR_TIMEOUT if a bounded wait gave up; SYNTH_ERR_CUDA on a CUDA
+ * error; else SYNTH_OK. */
 synth_status synth_sync(synth_handle h, void* stream);
 
 /* Special-function-unit (MUFU) throughput probe, for the render's
@@ -433,6 +438,24 @@ synth_status synth_sfu_probe(int32_t op, int32_t blocks, int32_t iters, float* s
  * Allocates and frees a 2-record device buffer. Errors: SYNTH_ERR_STATE
  * (invalid handle), SYNTH_ERR_CUDA. */
 synth_status synth_selftest_wait_timeout(synth_handle h, void* stream);
+
+/* The bounds-checked build (the library's own debugging aid; the paper has
+ * none): the same sources compiled with -DSYNTH_CHECKS into
+ * libsynth_checked.so, with the same calls and results. Its fused render
+ * tests every index it derives -- audio and parameter offsets, the voice's
+ * set-up and tile records, the tile's interval arrays in shared memory --
+ * against the range it addresses; an index outside it is not used, and the
+ * next synth_sync (synth_noalloc_status) returns SYNTH_ERR_BOUNDS. It takes
+ * the place of a memory checker where none can run.
+ * synth_checked_build: 1 in that library, 0 in the release build.
+ * synth_selftest_bounds: runs, on `stream`, a kernel whose 32 threads each
+ * derive an index past a 4-element array; the check refuses them, and the
+ * next synth_sync(h, stream) returns SYNTH_ERR_BOUNDS and clears the record.
+ * Returns after the stream is idle. Errors: SYNTH_ERR_STATE (invalid
+ * handle), SYNTH_ERR_UNSUPPORTED (the release build, which launches
+ * nothing), SYNTH_ERR_CUDA. */
+int32_t synth_checked_build(void);
+synth_status synth_selftest_bounds(synth_handle h, void* stream);
 
 /* Host-side range map of normalized parameters (Sec. 3.3): y[count][78]
  * from u[count][78] under the handle's nebula. Host pointers. */

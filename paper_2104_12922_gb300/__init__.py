@@ -15,10 +15,13 @@ import os
 
 NUM_PARAMS = 78
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsynth.so")
+# SYNTH_CHECKED=1 in the environment selects, for the whole process, the
+# bounds-checked build libsynth_checked.so (build.build(checks=True)).
+LIB_PATH = os.path.join(_HERE, "libsynth_checked.so" if os.environ.get("SYNTH_CHECKED") == "1"
+                        else "libsynth.so")
 
 SYNTH_OK, SYNTH_ERR_ARG, SYNTH_ERR_CUDA, SYNTH_ERR_OOM = 0, 1, 2, 3
-SYNTH_ERR_TIMEOUT, SYNTH_ERR_STATE, SYNTH_ERR_UNSUPPORTED = 4, 5, 6
+SYNTH_ERR_TIMEOUT, SYNTH_ERR_STATE, SYNTH_ERR_UNSUPPORTED, SYNTH_ERR_BOUNDS = 4, 5, 6, 7
 SYNTH_CARRY_FIXED64, SYNTH_CARRY_FP32 = 0, 1
 # Network input features = (log(mel + 1e-6) - FEATURE_SHIFT) / FEATURE_SCALE
 # (the affine map synth_model_features applies; see include/synth.h).
@@ -120,6 +123,10 @@ def lib() -> ctypes.CDLL:
         L.synth_mmd_trials.restype = ctypes.c_int
         L.synth_selftest_wait_timeout.argtypes = [vp, vp]
         L.synth_selftest_wait_timeout.restype = ctypes.c_int
+        L.synth_selftest_bounds.argtypes = [vp, vp]
+        L.synth_selftest_bounds.restype = ctypes.c_int
+        L.synth_checked_build.argtypes = []
+        L.synth_checked_build.restype = i32
         L.synth_status_string.argtypes = [ctypes.c_int]
         L.synth_status_string.restype = ctypes.c_char_p
         for name in ("synth_create", "synth_destroy", "synth_render", "synth_render_normalized",

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "synth.h"
 #include "voice_device.cuh"
 
 namespace synth {
@@ -18,7 +19,7 @@ struct ScratchHeader {
   unsigned int work;
   unsigned int done;
   unsigned int epoch;
-  unsigned int error;   // bit 0: a bounded look-back wait gave up
+  unsigned int error;   // kErr* bits: a bounded wait gave up, an index left its range
   unsigned int pad[60];
 };
 static_assert(sizeof(ScratchHeader) == 256, "header is one 256-byte block");
@@ -36,6 +37,38 @@ static_assert(sizeof(TileState) == 48, "tile state layout");
 
 constexpr unsigned int kErrLookbackTimeout = 1u;
 constexpr unsigned int kErrTileWaitTimeout = 2u;
+constexpr unsigned int kErrBounds = 4u;  // bounds-checked build: an index left its range
+
+// The bounds-checked build (compiled with -DSYNTH_CHECKS into
+// libsynth_checked.so; the stand-in for a memory checker, which this
+// library's GPUs do not offer): the fused render tests each index it derives
+// against the extent of the range it addresses, global (audio, parameters,
+// set-up and tile records) or shared (the tile's interval arrays). An index
+// outside [0, n) records kErrBounds in the launch's error word and the
+// access is skipped, so a wrong index shows up as SYNTH_ERR_BOUNDS from
+// synth_sync instead of a fault. In the release build in_bounds is the
+// constant true and the checks compile to nothing.
+// The status a launch's error word reports: an index out of its range
+// first, then a bounded wait that gave up.
+inline synth_status status_of_error_word(unsigned int err) {
+  if (err & kErrBounds) return SYNTH_ERR_BOUNDS;
+  return err ? SYNTH_ERR_TIMEOUT : SYNTH_OK;
+}
+
+#if defined(SYNTH_CHECKS)
+constexpr bool kBoundsChecks = true;
+#else
+constexpr bool kBoundsChecks = false;
+#endif
+__device__ __forceinline__ bool in_bounds(ScratchHeader* hdr, long long i, long long n) {
+  if constexpr (!kBoundsChecks) {
+    return true;
+  } else {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&hdr->error, kErrBounds);
+    return false;
+  }
+}
 
 constexpr int kFusedThreads = 256;     // one thread per control point of a tile
 constexpr int kFusedTilePoints = 256;  // control points per tile of the fused kernel

@@ -233,6 +233,8 @@ __device__ __noinline__ void normalize_chunk(Smem& s, float* __restrict__ audio,
   const float g = 1.0f / peak;
   const int64_t a0 = (int64_t)c * kNormChunkSamples;
   const int n = (int)min((int64_t)kNormChunkSamples, N - a0);
+  // the chunk's samples lie in the voice's [0, N)
+  if (!in_bounds(hdr, a0, N) || !in_bounds(hdr, a0 + n - 1, N)) return;
   float* x = audio + (size_t)v * N + a0;
   if (vec_ok) {  // N % 4 == 0 and a 16-byte aligned buffer: whole quads
     float4* x4 = reinterpret_cast<float4*>(x);
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       s.tile = tc;
       // a later window of a voice whose first window has published its set-up
       int ready = 0;
-      if (setups && tc < total_tiles && tc >= batch) {
+      if (setups && tc < total_tiles && tc >= batch && in_bounds(hdr, tc % batch, batch)) {
         cuda::atomic_ref<unsigned int, cuda::thread_scope_device> f(setups[tc % batch].flag);
         ready = f.load(cuda::memory_order_acquire) == (((s.epoch & 0x3fffffffu) << 2) | 1u);
       }
@@ -315,6 +317,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       const int chunks = (int)((N + kNormChunkSamples - 1) / kNormChunkSamples);
       const int j = t - total_tiles;
       if (j >= chunks * batch) { release_next_launch(released); break; }
+      if (!in_bounds(hdr, j / chunks, batch)) continue;
       normalize_chunk(s, audio, N, tiles + (size_t)(j / chunks) * n_windows, n_windows,
                       j / chunks, j % chunks, vec_ok, norm, hdr, s.epoch);
       if (t + (int)gridDim.x >= total_items) release_next_launch(released);
@@ -322,6 +325,8 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     }
     if (t + (int)gridDim.x >= total_items) release_next_launch(released);  // likely the last tile
     const int v = t % batch, w = t / batch;
+    // the tile's voice and window address its set-up, tile and output records
+    if (!in_bounds(hdr, v, batch) || !in_bounds(hdr, w, n_windows)) continue;
     const uint64_t g = split_voice(split, first + (uint64_t)v);
     // consecutive sub-batches of sub_batch voices may each have their own
     // seed: seed + (v / sub_batch) seed_step
@@ -329,6 +334,9 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
     const uint2 key = make_uint2((uint32_t)sd, (uint32_t)(sd >> 32));
     const int k0 = w * TI;
     const int nseg = min(TI, K - k0);
+    // 1 <= nseg <= TI: every per-interval index below (tid, si < nseg; the
+    // point after an interval, <= nseg < P) stays inside the shared arrays
+    if (!in_bounds(hdr, nseg - 1, TI)) continue;
     TileState* vt = tiles + (size_t)v * n_windows;
     const unsigned int epoch = s.epoch;
 
@@ -352,13 +360,16 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
           s.u[4 * tid + 2] = u01f(r.z);
           s.u[4 * tid + 3] = u01f(r.w);
         }
-      } else if (tid < kNumParams) {
+      } else if (tid < kNumParams &&
+                 in_bounds(hdr, (long long)v * kNumParams + tid, (long long)batch * kNumParams)) {
         s.u[tid] = fminf(fmaxf(params_in[(size_t)v * kNumParams + tid], 0.f), 1.f);
       }
       __syncthreads();
       if (tid < kNumParams) {
         const float u = s.u[tid];
-        if (w == 0 && params_out) params_out[(size_t)v * kNumParams + tid] = u;
+        if (w == 0 && params_out &&
+            in_bounds(hdr, (long long)v * kNumParams + tid, (long long)batch * kNumParams))
+          params_out[(size_t)v * kNumParams + tid] = u;
         s.y[tid] = range_map_ff(u, vc.map_base[tid], vc.map_scale[tid], vc.map_curve[tid],
                                 vc.map_code[tid], vc.sym[tid], s.T);
       }
@@ -576,6 +587,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
       auto store_quad = [&](int rel0, const float out4[4]) {
         const int64_t n0 = s_tile + rel0;
         if (vec_ok && rel0 >= 0 && rel0 + 3 < n_t) {
+          if (!in_bounds(hdr, n0, N) || !in_bounds(hdr, n0 + 3, N)) return;
           if (kPeak) {
             *reinterpret_cast<float4*>(out_v + n0) = make_float4(out4[0], out4[1], out4[2], out4[3]);
             vmax = fmaxf(fmaxf(vmax, fmaxf(fabsf(out4[0]), fabsf(out4[1]))),
@@ -587,7 +599,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
         } else {
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (rel0 + i >= 0 && rel0 + i < n_t) {
+            if (rel0 + i >= 0 && rel0 + i < n_t && in_bounds(hdr, n0 + i, N)) {
               out_v[n0 + i] = out4[i];
               if (kPeak) vmax = fmaxf(vmax, fabsf(out4[i]));
             }
@@ -768,7 +780,8 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
             out4[i] = fmaf(fmaf(fi, D.x, a0x), x_sin,
                            fmaf(fmaf(fi, D.y, a0y), x_sq, fmaf(fi, D.z, a0z) * x_nz));
           }
-          if (vec_ok && off + 3 < n_t) {
+          if (vec_ok && off + 3 < n_t &&
+              in_bounds(hdr, t0 + off, N) && in_bounds(hdr, t0 + off + 3, N)) {
             // streaming stores, except when the scaling pass reads the audio
             // back: then it stays in L2 for that pass
             if (kPeak)
@@ -782,7 +795,7 @@ __global__ void __launch_bounds__(NT, 4) render_fused_kernel(
           } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              if (off + i < n_t) {
+              if (off + i < n_t && in_bounds(hdr, t0 + off + i, N)) {
                 out_t[off + i] = out4[i];
                 if (kPeak) vmax = fmaxf(vmax, fabsf(out4[i]));
               }

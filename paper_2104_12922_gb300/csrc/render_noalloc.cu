@@ -144,5 +144,5 @@ extern "C" synth_status synth_noalloc_status(void* stream) {
   const unsigned int zero = 0;
   if (cudaMemcpyToSymbol(g_noalloc_scratch, &zero, sizeof(zero), at) != cudaSuccess)
     return SYNTH_ERR_CUDA;
-  return SYNTH_ERR_TIMEOUT;
+  return status_of_error_word(err);
 }

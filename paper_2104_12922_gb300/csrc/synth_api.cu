@@ -638,7 +638,7 @@ synth_status synth_model_load(synth_model m, const char* path) {
 synth_status synth_sync(synth_handle h, void* stream) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return SYNTH_ERR_CUDA;
-  bool timeout = false;
+  unsigned int all = 0;
   for (int slot = 0; slot < 2; ++slot) {
     ScratchHeader* hdr = slot_header(h, slot);
     unsigned int err = 0;
@@ -648,10 +648,10 @@ synth_status synth_sync(synth_handle h, void* stream) {
       const unsigned int zero = 0;
       if (cudaMemcpy(&hdr->error, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
         return SYNTH_ERR_CUDA;
-      timeout = true;
+      all |= err;
     }
   }
-  return timeout ? SYNTH_ERR_TIMEOUT : SYNTH_OK;
+  return status_of_error_word(all);
 }
 
 namespace {
@@ -669,6 +669,34 @@ __global__ void wait_probe_kernel(TileState* probe, ScratchHeader* hdr) {
   }
 }
 }  // namespace
+
+namespace {
+// The bounds-checked build's self-test: each of 32 threads derives an index
+// one range past a 4-element shared array; in_bounds records kErrBounds and
+// the store is skipped. The release build has no such kernel body.
+__global__ void bounds_probe_kernel(ScratchHeader* hdr, float* sink) {
+  if constexpr (kBoundsChecks) {
+    __shared__ float a[4];
+    if (threadIdx.x < 4) a[threadIdx.x] = 0.f;
+    __syncthreads();
+    const int i = 4 + (int)threadIdx.x;
+    if (in_bounds(hdr, i, 4)) a[i] = 1.f;
+    __syncthreads();
+    if (threadIdx.x == 0 && sink) *sink = a[0];
+  }
+}
+}  // namespace
+
+int32_t synth_checked_build(void) { return kBoundsChecks ? 1 : 0; }
+
+synth_status synth_selftest_bounds(synth_handle h, void* stream) {
+  if (!valid_handle(h)) return SYNTH_ERR_STATE;
+  if (!kBoundsChecks) return SYNTH_ERR_UNSUPPORTED;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bounds_probe_kernel<<<1, 32, 0, st>>>(static_cast<ScratchHeader*>(h->scratch), nullptr);
+  if (cudaGetLastError() != cudaSuccess) return SYNTH_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? SYNTH_OK : SYNTH_ERR_CUDA;
+}
 
 synth_status synth_selftest_wait_timeout(synth_handle h, void* stream) {
   if (!valid_handle(h)) return SYNTH_ERR_STATE;
@@ -713,6 +741,7 @@ const char* synth_status_string(synth_status s) {
     case SYNTH_ERR_TIMEOUT: return "device-side wait timed out";
     case SYNTH_ERR_STATE: return "invalid handle state";
     case SYNTH_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SYNTH_ERR_BOUNDS: return "an index left its range (bounds-checked build)";
   }
   return "unknown status";
 }

@@ -121,3 +121,20 @@ def test_default_nebula_matches_oracle(pkg, oracle_mod):
     ora_nb = oracle_mod.default_nebula()
     for k in ("lo", "hi", "curve", "symmetric"):
         assert np.array_equal(lib_nb[k], ora_nb[k]), k
+
+
+def test_checked_build_exports_the_same_calls(pkg):
+    """The bounds-checked library (build(checks=True): the same sources with
+    -DSYNTH_CHECKS) builds, exports every declared call, says it is the
+    checked build, and validates its arguments like the release build."""
+    from paper_2104_12922_gb300 import build as b
+    path = b.build(checks=True)
+    C = ctypes.CDLL(path)
+    for name in _declared_functions():
+        assert hasattr(C, name), name
+    C.synth_checked_build.restype = ctypes.c_int32
+    C.synth_selftest_bounds.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert C.synth_checked_build() == 1
+    assert pkg.lib().synth_checked_build() == 0
+    assert C.synth_selftest_bounds(None, None) == pkg.SYNTH_ERR_STATE
+    assert pkg.lib().synth_selftest_bounds(None, None) == pkg.SYNTH_ERR_STATE
