@@ -7,8 +7,9 @@
 // square LFO) the derivative is that of the branch taken.
 //
 // Passes (all on the caller's stream, buffers in the caller's workspace):
-//  1. forward recomputation of the control rate (control_pipeline.cuh);
-//     its per-interval phase descriptions are the checkpoints from which the
+//  1. forward recomputation of the control rate (control_pipeline.cuh: the
+//     plain form's module steps in one kernel, one CTA per voice); its
+//     per-interval phase descriptions are the checkpoints from which the
 //     audio-rate values are rebuilt;
 //  2. audio-rate reverse pass, one warp per control interval: rebuilds every
 //     sample, forms d/d(phase) of both VCOs, the amplitude, drive, shape and
@@ -607,7 +608,7 @@ cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t
   float* dtheta = reinterpret_cast<float*>(ws + L.dtheta);
   float* denv = reinterpret_cast<float*>(ws + L.denv);
   const int K = vc.K, P = K + 1;
-  launch_control_pipeline(vc, seed, batch_index, batch, params, nullptr, cb, st);
+  launch_control_fused(vc, seed, batch_index, batch, params, nullptr, cb, st);
   cudaMemsetAsync(gpt, 0, sizeof(double) * 2 * (size_t)batch * P * 5, st);
   dim3 gs((K + kBT / 32 - 1) / (kBT / 32), batch);
   bwd_samples<<<gs, kBT, 0, st>>>(vc, seed, batch_index, batch, cb.y, cb.dest, cb.seg, cb.kappa,

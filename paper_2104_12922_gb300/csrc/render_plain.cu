@@ -42,12 +42,14 @@ AudioLayout audio_layout(const VoiceConst& vc, int B, size_t base) {
   return L;
 }
 
-// Parameter module: draw (or read) and range-map.
-__global__ void plain_params(const __grid_constant__ VoiceConst vc, uint64_t seed,
-                             uint64_t batch_index, int batch, const float* params_in,
-                             float* params_out, double* y) {
-  const int v = blockIdx.x, p = threadIdx.x;
-  if (p >= kNumParams) return;
+// The control modules' work per element, shared by the module kernels below
+// (one element per thread of a grid) and by control_fused_kernel (one CTA
+// per voice looping over the voice's elements), so both write the same bits.
+
+// Parameter module: draw (or read) and range-map parameter p of voice v.
+__device__ __forceinline__ void params_elem(const VoiceConst& vc, uint64_t seed,
+                                            uint64_t batch_index, int batch, const float* params_in,
+                                            float* params_out, double* y, int v, int p) {
   const uint64_t g = batch_index * (uint64_t)batch + (uint64_t)v;
   float u;
   if (params_in) {
@@ -63,13 +65,10 @@ __global__ void plain_params(const __grid_constant__ VoiceConst vc, uint64_t see
   y[(size_t)v * kNumParams + p] = range_map((double)u, vc.lo[p], vc.hi[p], vc.curve[p], vc.sym[p]);
 }
 
-// Per-voice constants of the control modules (float-float).
-__global__ void plain_voice_consts(const __grid_constant__ VoiceConst vc, const double* y,
-                                   VoiceFF* vff, float* mixc) {
-  __shared__ FFTables T;
-  __shared__ ff yff[kNumParams];
-  const int v = blockIdx.x;
-  load_tables(T, vc.T);
+// Per-voice constants of the control modules (float-float), by the threads
+// of one block (at least 33): yff and T in shared memory, T loaded.
+__device__ __forceinline__ void voice_consts_block(const double* y, VoiceFF* vff, float* mixc,
+                                                   int v, ff* yff, const FFTables& T) {
   for (int p = threadIdx.x; p < kNumParams; p += blockDim.x)
     yff[p] = ff_from_double(y[(size_t)v * kNumParams + p]);
   __syncthreads();
@@ -88,28 +87,19 @@ __global__ void plain_voice_consts(const __grid_constant__ VoiceConst vc, const 
   if (threadIdx.x < 6) V.level_d[threadIdx.x] = gate_level_ff(threadIdx.x, V, T);
 }
 
-// ADSR modules (6 per voice) at the control points.
-__global__ void plain_adsr(const __grid_constant__ VoiceConst vc, const VoiceFF* vff, ff* env) {
-  __shared__ FFTables T;
-  load_tables(T, vc.T);
-  __syncthreads();
+// ADSR a = i / P of voice v at control point k = i mod P.
+__device__ __forceinline__ void adsr_elem(const VoiceConst& vc, const VoiceFF& V,
+                                          const FFTables& T, ff* env, int v, int i) {
   const int P = vc.K + 1;
-  const int v = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 6 * P) return;
   const int a = i / P, k = i - a * P;
   const ff tk = ff_mul_f(vc.inv_cr, (float)k);
-  env[((size_t)v * 6 + a) * P + k] = adsr_ff(tk, a, vff[v], T);
+  env[((size_t)v * 6 + a) * P + k] = adsr_ff(tk, a, V, T);
 }
 
 // LFO rate: phase increment per control interval (rate / CR, FP64 for the scan).
-__global__ void plain_lfo_rate(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
-                               const ff* env, double* lfo_inc) {
+__device__ __forceinline__ void lfo_rate_elem(const VoiceConst& vc, const VoiceFF& V,
+                                              const ff* env, double* lfo_inc, int v, int k) {
   const int P = vc.K + 1;
-  const int v = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= P) return;
-  const VoiceFF& V = vff[v];
   const ff inv_cr = vc.inv_cr;
   for (int l = 0; l < 2; ++l) {
     const ff e = env[((size_t)v * 6 + 2 + 2 * l) * P + k];
@@ -120,11 +110,11 @@ __global__ void plain_lfo_rate(const __grid_constant__ VoiceConst vc, const Voic
 }
 
 // Exclusive running sum of per-step phase increments, wrapped to [0,1),
-// starting from an initial phase; one block scans two sequences of a voice.
-__global__ void plain_phase_scan(const double* inc, double* phase, int len, int stride_seq,
-                                 const double* y, int init_slot0, int init_slot1) {
-  __shared__ double warp_tot[2 * (kPT / 32)];
-  const int v = blockIdx.x;
+// starting from an initial phase: the two sequences of voice v, by one block
+// of kPT threads.
+__device__ __forceinline__ void phase_scan_block(const double* inc, double* phase, int len,
+                                                 int stride_seq, const double* y, int init_slot0,
+                                                 int init_slot1, int v, double* warp_tot) {
   const double two_pi = 6.28318530717958647692;
   const double* yv = y + (size_t)v * kNumParams;
   double carry0 = wrap01(yv[init_slot0] / two_pi);
@@ -147,17 +137,11 @@ __global__ void plain_phase_scan(const double* inc, double* phase, int len, int 
   }
 }
 
-// LFO outputs and modulation mixer at the control points.
-__global__ void plain_modmix(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
-                             const ff* env, const double* lfo_phase, ff* dest) {
-  __shared__ FFTables T;
-  load_tables(T, vc.T);
-  __syncthreads();
+// LFO outputs and modulation mixer at control point k of voice v.
+__device__ __forceinline__ void modmix_elem(const VoiceConst& vc, const VoiceFF& V,
+                                            const FFTables& T, const ff* env,
+                                            const double* lfo_phase, ff* dest, int v, int k) {
   const int P = vc.K + 1;
-  const int v = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= P) return;
-  const VoiceFF& V = vff[v];
   ff lfo[2];
   for (int l = 0; l < 2; ++l) {
     const double th = lfo_phase[((size_t)v * 2 + l) * P + k];
@@ -172,17 +156,11 @@ __global__ void plain_modmix(const __grid_constant__ VoiceConst vc, const VoiceF
   }
 }
 
-// VCO interval descriptions and the phase each interval advances.
-__global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
-                                    const ff* dest, SegVco* seg, double* seg_sum, float* kappa) {
-  __shared__ FFTables T;
-  load_tables(T, vc.T);
-  __syncthreads();
+// VCO interval k of voice v: descriptions and the phase each VCO advances.
+__device__ __forceinline__ void vco_interval_elem(const VoiceConst& vc, const VoiceFF& V,
+                                                  const FFTables& T, const ff* dest, SegVco* seg,
+                                                  double* seg_sum, float* kappa, int v, int k) {
   const int P = vc.K + 1, K = vc.K;
-  const int v = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const VoiceFF& V = vff[v];
   const int64_t rem = vc.n_samples - (int64_t)k * vc.R;
   const int Rk = rem < vc.R ? (int)rem : vc.R;
   for (int o = 0; o < 2; ++o) {
@@ -201,12 +179,120 @@ __global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const
   }
 }
 
+// Parameter module.
+__global__ void plain_params(const __grid_constant__ VoiceConst vc, uint64_t seed,
+                             uint64_t batch_index, int batch, const float* params_in,
+                             float* params_out, double* y) {
+  if (threadIdx.x >= kNumParams) return;
+  params_elem(vc, seed, batch_index, batch, params_in, params_out, y, blockIdx.x, threadIdx.x);
+}
+
+// Per-voice constants of the control modules (float-float).
+__global__ void plain_voice_consts(const __grid_constant__ VoiceConst vc, const double* y,
+                                   VoiceFF* vff, float* mixc) {
+  __shared__ FFTables T;
+  __shared__ ff yff[kNumParams];
+  load_tables(T, vc.T);
+  voice_consts_block(y, vff, mixc, blockIdx.x, yff, T);
+}
+
+// ADSR modules (6 per voice) at the control points.
+__global__ void plain_adsr(const __grid_constant__ VoiceConst vc, const VoiceFF* vff, ff* env) {
+  __shared__ FFTables T;
+  load_tables(T, vc.T);
+  __syncthreads();
+  const int P = vc.K + 1;
+  const int v = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * P) return;
+  adsr_elem(vc, vff[v], T, env, v, i);
+}
+
+// LFO rate: phase increment per control interval.
+__global__ void plain_lfo_rate(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
+                               const ff* env, double* lfo_inc) {
+  const int P = vc.K + 1;
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P) return;
+  lfo_rate_elem(vc, vff[v], env, lfo_inc, v, k);
+}
+
+// Running phase sums; one block scans the two sequences of a voice.
+__global__ void plain_phase_scan(const double* inc, double* phase, int len, int stride_seq,
+                                 const double* y, int init_slot0, int init_slot1) {
+  __shared__ double warp_tot[2 * (kPT / 32)];
+  phase_scan_block(inc, phase, len, stride_seq, y, init_slot0, init_slot1, blockIdx.x, warp_tot);
+}
+
+// LFO outputs and modulation mixer at the control points.
+__global__ void plain_modmix(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
+                             const ff* env, const double* lfo_phase, ff* dest) {
+  __shared__ FFTables T;
+  load_tables(T, vc.T);
+  __syncthreads();
+  const int P = vc.K + 1;
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P) return;
+  modmix_elem(vc, vff[v], T, env, lfo_phase, dest, v, k);
+}
+
+// VCO interval descriptions and the phase each interval advances.
+__global__ void plain_vco_intervals(const __grid_constant__ VoiceConst vc, const VoiceFF* vff,
+                                    const ff* dest, SegVco* seg, double* seg_sum, float* kappa) {
+  __shared__ FFTables T;
+  load_tables(T, vc.T);
+  __syncthreads();
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= vc.K) return;
+  vco_interval_elem(vc, vff[v], T, dest, seg, seg_sum, kappa, v, k);
+}
+
 // Writes the scanned interval start phases into the interval descriptions.
 __global__ void plain_seg_phase(const __grid_constant__ VoiceConst vc, const double* seg_phase,
                                 SegVco* seg, int batch) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)batch * 2 * vc.K) return;
   seg[i].phase0 = (float)seg_phase[i];
+}
+
+// The whole control pipeline of one voice per CTA (kPT threads): the same
+// steps and per-element code as the module kernels above, in the same
+// order, separated by barriers instead of launches. The adjoint's forward
+// recomputation runs it: at its batch sizes the nine module launches are
+// each a few microseconds of mostly idle GPU.
+__global__ void __launch_bounds__(kPT) control_fused_kernel(
+    const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t batch_index, int batch,
+    const float* params_in, float* params_out, const ControlBuffers cb) {
+  __shared__ FFTables T;
+  __shared__ ff yff[kNumParams];
+  __shared__ double warp_tot[2 * (kPT / 32)];
+  const int v = blockIdx.x, tid = threadIdx.x;
+  const int P = vc.K + 1, K = vc.K;
+  load_tables(T, vc.T);
+  if (tid < kNumParams)
+    params_elem(vc, seed, batch_index, batch, params_in, params_out, cb.y, v, tid);
+  __syncthreads();
+  voice_consts_block(cb.y, cb.vff, cb.mixc, v, yff, T);
+  __syncthreads();
+  const VoiceFF& V = cb.vff[v];
+  for (int i = tid; i < 6 * P; i += kPT) adsr_elem(vc, V, T, cb.env, v, i);
+  __syncthreads();
+  for (int k = tid; k < P; k += kPT) lfo_rate_elem(vc, V, cb.env, cb.lfo_inc, v, k);
+  __syncthreads();
+  phase_scan_block(cb.lfo_inc, cb.lfo_phase, P, P, cb.y, kLfo + 2, kLfo + 8 + 2, v, warp_tot);
+  __syncthreads();
+  for (int k = tid; k < P; k += kPT) modmix_elem(vc, V, T, cb.env, cb.lfo_phase, cb.dest, v, k);
+  __syncthreads();
+  for (int k = tid; k < K; k += kPT)
+    vco_interval_elem(vc, V, T, cb.dest, cb.seg, cb.seg_sum, cb.kappa, v, k);
+  __syncthreads();
+  phase_scan_block(cb.seg_sum, cb.seg_start, K, K, cb.y, kSine + 2, kSqr + 2, v, warp_tot);
+  __syncthreads();
+  for (int i = tid; i < 2 * K; i += kPT)
+    cb.seg[(size_t)v * 2 * K + i].phase0 = (float)cb.seg_start[(size_t)v * 2 * K + i];
 }
 
 // Upsampled amplitudes (VCA control inputs) at audio rate.
@@ -375,6 +461,13 @@ void launch_control_pipeline(const VoiceConst& vc, uint64_t seed, uint64_t batch
                                           kSqr + 2);
   plain_seg_phase<<<(int)(((size_t)batch * 2 * K + kPT - 1) / kPT), kPT, 0, st>>>(
       vc, cb.seg_start, cb.seg, batch);
+}
+
+void launch_control_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index, int batch,
+                          const float* params_in, float* params_out, const ControlBuffers& cb,
+                          cudaStream_t st) {
+  control_fused_kernel<<<batch, kPT, 0, st>>>(vc, seed, batch_index, batch, params_in, params_out,
+                                              cb);
 }
 
 size_t plain_workspace_bytes(const VoiceConst& vc, int batch) {
