@@ -71,7 +71,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBT) bwd_samples(const __grid_constant__ VoiceConst vc,
                                                    uint64_t seed, uint64_t batch_index, int batch,
-                                                   const double* __restrict__ y,
+                                                   const float* __restrict__ mixc,
                                                    const ff* __restrict__ dest,
                                                    const SegVco* __restrict__ seg,
                                                    const float* __restrict__ kappa,
@@ -83,11 +83,11 @@ __global__ void __launch_bounds__(kBT) bwd_samples(const __grid_constant__ Voice
   const int k = blockIdx.x * (kBT / 32) + warp;
   if (k >= K) return;
   const int64_t N = vc.n_samples;
-  const double* yv = y + (size_t)v * kNumParams;
-  const double norm = fmax(1.0, yv[kMix] + yv[kMix + 1] + yv[kMix + 2]);
-  const float g[3] = {(float)(yv[kMix] / norm), (float)(yv[kMix + 1] / norm),
-                      (float)(yv[kMix + 2] / norm)};
-  const float sigma = (float)yv[kSqr + 3];
+  // mixer gains and square-saw shape as the control pass stored them (the
+  // FP64 quotients rounded to float: no FP64 arithmetic in this kernel)
+  const float* mc = mixc + (size_t)v * 5;
+  const float g[3] = {mc[0], mc[1], mc[2]};
+  const float sigma = mc[3];
   const float ip = 1.f / (1.f + sigma);
   const int dj[3] = {1, 3, 4};
   float a0[3], a1[3];
@@ -534,7 +534,9 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
       const float g = de[(size_t)a * P + k];
       if (g != 0.f) {
         float out[6];
-        adsr_d((float)((double)k / vc.control_rate), yv + kAdsr + 5 * a, yv[kDuration], out);
+        // t_k = k / CR: the float-float product the forward pass uses,
+        // rounded to float (no FP64 division per point and envelope)
+        adsr_d(ff_to_float(ff_mul_f(vc.inv_cr, (float)k)), yv + kAdsr + 5 * a, yv[kDuration], out);
 #pragma unroll
         for (int q = 0; q < 5; ++q) acc[q] += g * out[q];
         dur_acc += g * out[5];
@@ -611,7 +613,7 @@ cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t
   launch_control_fused(vc, seed, batch_index, batch, params, nullptr, cb, st);
   cudaMemsetAsync(gpt, 0, sizeof(double) * 2 * (size_t)batch * P * 5, st);
   dim3 gs((K + kBT / 32 - 1) / (kBT / 32), batch);
-  bwd_samples<<<gs, kBT, 0, st>>>(vc, seed, batch_index, batch, cb.y, cb.dest, cb.seg, cb.kappa,
+  bwd_samples<<<gs, kBT, 0, st>>>(vc, seed, batch_index, batch, cb.mixc, cb.dest, cb.seg, cb.kappa,
                                   grad_audio, stat);
   bwd_interval_scan<<<batch, kBT, 0, st>>>(vc, stat, cb.seg, cb.kappa, gpt, vacc);
   bwd_control<<<batch, kBT, 0, st>>>(vc, cb.y, cb.env, cb.lfo_phase, cb.dest, gpt, vacc, dtheta,
