@@ -109,12 +109,62 @@ __device__ __forceinline__ void lfo_rate_elem(const VoiceConst& vc, const VoiceF
   }
 }
 
+// Synchronises the first kPT threads (warps 0 .. kPT/32 - 1) of a larger
+// block on named barrier 1: the phase scans of control_fused_kernel run on
+// those warps alone, with the module kernel's width and summation order.
+__device__ __forceinline__ void sync_scan_warps() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kPT) : "memory");
+}
+
+// Exclusive block scan of two values over kPT threads (block_exclusive_scan2
+// of render_common.cuh, the same arithmetic and order), synchronised by
+// `sync`: __syncthreads in a block of kPT threads, sync_scan_warps in a
+// larger one.
+template <class Sync>
+__device__ __forceinline__ void scan2_kpt(double& a, double& b, double* warp_tot, double& tot_a,
+                                          double& tot_b, Sync sync) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double na = __shfl_up_sync(0xffffffffu, ia, o);
+    double nb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) { ia += na; ib += nb; }
+  }
+  if (lane == 31) { warp_tot[warp] = ia; warp_tot[kPT / 32 + warp] = ib; }
+  sync();
+  if (warp == 0) {
+    double wa = lane < kPT / 32 ? warp_tot[lane] : 0.0;
+    double wb = lane < kPT / 32 ? warp_tot[kPT / 32 + lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < kPT / 32; o <<= 1) {
+      double na = __shfl_up_sync(0xffffffffu, wa, o);
+      double nb = __shfl_up_sync(0xffffffffu, wb, o);
+      if (lane >= o) { wa += na; wb += nb; }
+    }
+    if (lane < kPT / 32) { warp_tot[lane] = wa; warp_tot[kPT / 32 + lane] = wb; }
+  }
+  sync();
+  const double pa = warp > 0 ? warp_tot[warp - 1] : 0.0;
+  const double pb = warp > 0 ? warp_tot[kPT / 32 + warp - 1] : 0.0;
+  tot_a = warp_tot[kPT / 32 - 1];
+  tot_b = warp_tot[2 * (kPT / 32) - 1];
+  double ea = __shfl_up_sync(0xffffffffu, ia, 1);
+  double eb = __shfl_up_sync(0xffffffffu, ib, 1);
+  if (lane == 0) { ea = 0.0; eb = 0.0; }
+  a = pa + ea;
+  b = pb + eb;
+  sync();
+}
+
 // Exclusive running sum of per-step phase increments, wrapped to [0,1),
-// starting from an initial phase: the two sequences of voice v, by one block
-// of kPT threads.
+// starting from an initial phase: the two sequences of voice v, by kPT
+// threads (see scan2_kpt for `sync`).
+template <class Sync>
 __device__ __forceinline__ void phase_scan_block(const double* inc, double* phase, int len,
                                                  int stride_seq, const double* y, int init_slot0,
-                                                 int init_slot1, int v, double* warp_tot) {
+                                                 int init_slot1, int v, double* warp_tot,
+                                                 Sync sync) {
   const double two_pi = 6.28318530717958647692;
   const double* yv = y + (size_t)v * kNumParams;
   double carry0 = wrap01(yv[init_slot0] / two_pi);
@@ -127,7 +177,7 @@ __device__ __forceinline__ void phase_scan_block(const double* inc, double* phas
     const int i = base + threadIdx.x;
     double a = i < len ? in0[i] : 0.0, b = i < len ? in1[i] : 0.0;
     double ta, tb;
-    block_exclusive_scan2<double, kPT>(a, b, warp_tot, ta, tb);
+    scan2_kpt(a, b, warp_tot, ta, tb, sync);
     if (i < len) {
       out0[i] = wrap01(carry0 + a);
       out1[i] = wrap01(carry1 + b);
@@ -222,7 +272,8 @@ __global__ void plain_lfo_rate(const __grid_constant__ VoiceConst vc, const Voic
 __global__ void plain_phase_scan(const double* inc, double* phase, int len, int stride_seq,
                                  const double* y, int init_slot0, int init_slot1) {
   __shared__ double warp_tot[2 * (kPT / 32)];
-  phase_scan_block(inc, phase, len, stride_seq, y, init_slot0, init_slot1, blockIdx.x, warp_tot);
+  phase_scan_block(inc, phase, len, stride_seq, y, init_slot0, init_slot1, blockIdx.x, warp_tot,
+                   [] { __syncthreads(); });
 }
 
 // LFO outputs and modulation mixer at the control points.
@@ -258,12 +309,15 @@ __global__ void plain_seg_phase(const __grid_constant__ VoiceConst vc, const dou
   seg[i].phase0 = (float)seg_phase[i];
 }
 
-// The whole control pipeline of one voice per CTA (kPT threads): the same
-// steps and per-element code as the module kernels above, in the same
-// order, separated by barriers instead of launches. The adjoint's forward
-// recomputation runs it: at its batch sizes the nine module launches are
-// each a few microseconds of mostly idle GPU.
-__global__ void __launch_bounds__(kPT) control_fused_kernel(
+// The whole control pipeline of one voice per CTA (kFusedCtl threads): the
+// same steps and per-element code as the module kernels above, in the same
+// order, separated by barriers instead of launches; the two phase scans run
+// on the first kPT threads, as wide as the module kernel's and in its order,
+// so every buffer gets the same bits. The adjoint's forward recomputation
+// runs it: at its batch sizes the nine module launches are each a few
+// microseconds of mostly idle GPU.
+constexpr int kFusedCtl = 1024;
+__global__ void __launch_bounds__(kFusedCtl) control_fused_kernel(
     const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t batch_index, int batch,
     const float* params_in, float* params_out, const ControlBuffers cb) {
   __shared__ FFTables T;
@@ -278,20 +332,25 @@ __global__ void __launch_bounds__(kPT) control_fused_kernel(
   voice_consts_block(cb.y, cb.vff, cb.mixc, v, yff, T);
   __syncthreads();
   const VoiceFF& V = cb.vff[v];
-  for (int i = tid; i < 6 * P; i += kPT) adsr_elem(vc, V, T, cb.env, v, i);
+  for (int i = tid; i < 6 * P; i += kFusedCtl) adsr_elem(vc, V, T, cb.env, v, i);
   __syncthreads();
-  for (int k = tid; k < P; k += kPT) lfo_rate_elem(vc, V, cb.env, cb.lfo_inc, v, k);
+  for (int k = tid; k < P; k += kFusedCtl) lfo_rate_elem(vc, V, cb.env, cb.lfo_inc, v, k);
   __syncthreads();
-  phase_scan_block(cb.lfo_inc, cb.lfo_phase, P, P, cb.y, kLfo + 2, kLfo + 8 + 2, v, warp_tot);
+  if (tid < kPT)
+    phase_scan_block(cb.lfo_inc, cb.lfo_phase, P, P, cb.y, kLfo + 2, kLfo + 8 + 2, v, warp_tot,
+                     sync_scan_warps);
   __syncthreads();
-  for (int k = tid; k < P; k += kPT) modmix_elem(vc, V, T, cb.env, cb.lfo_phase, cb.dest, v, k);
+  for (int k = tid; k < P; k += kFusedCtl)
+    modmix_elem(vc, V, T, cb.env, cb.lfo_phase, cb.dest, v, k);
   __syncthreads();
-  for (int k = tid; k < K; k += kPT)
+  for (int k = tid; k < K; k += kFusedCtl)
     vco_interval_elem(vc, V, T, cb.dest, cb.seg, cb.seg_sum, cb.kappa, v, k);
   __syncthreads();
-  phase_scan_block(cb.seg_sum, cb.seg_start, K, K, cb.y, kSine + 2, kSqr + 2, v, warp_tot);
+  if (tid < kPT)
+    phase_scan_block(cb.seg_sum, cb.seg_start, K, K, cb.y, kSine + 2, kSqr + 2, v, warp_tot,
+                     sync_scan_warps);
   __syncthreads();
-  for (int i = tid; i < 2 * K; i += kPT)
+  for (int i = tid; i < 2 * K; i += kFusedCtl)
     cb.seg[(size_t)v * 2 * K + i].phase0 = (float)cb.seg_start[(size_t)v * 2 * K + i];
 }
 
@@ -466,8 +525,8 @@ void launch_control_pipeline(const VoiceConst& vc, uint64_t seed, uint64_t batch
 void launch_control_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index, int batch,
                           const float* params_in, float* params_out, const ControlBuffers& cb,
                           cudaStream_t st) {
-  control_fused_kernel<<<batch, kPT, 0, st>>>(vc, seed, batch_index, batch, params_in, params_out,
-                                              cb);
+  control_fused_kernel<<<batch, kFusedCtl, 0, st>>>(vc, seed, batch_index, batch, params_in,
+                                                    params_out, cb);
 }
 
 size_t plain_workspace_bytes(const VoiceConst& vc, int batch) {
