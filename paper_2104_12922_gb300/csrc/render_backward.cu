@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(kBT) bwd_interval_scan(const __grid_constant__
 // and rounded to float here).
 // ---------------------------------------------------------------------------
 constexpr int kGY = 80;  // slots of the per-voice human-range gradient d/dy (78 used)
+constexpr int kBC = 512;  // threads of the control-rate reverse sweep (one block per voice)
 
 // x^a for x >= 0 and its partials (0 at x <= 0, as the forward's convention).
 __device__ __forceinline__ void pow_d(float x, float a, float& p, float& dpx, float& dpa) {
@@ -389,7 +390,7 @@ __device__ __forceinline__ void acc_y(float* gy_warp, int slot, float val) {
   if ((threadIdx.x & 31) == 0) gy_warp[slot] += w;
 }
 
-__global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ VoiceConst vc,
+__global__ void __launch_bounds__(kBC) bwd_control(const __grid_constant__ VoiceConst vc,
                                                    const double* __restrict__ y,
                                                    const ff* __restrict__ env,
                                                    const double* __restrict__ lfo_phase,
@@ -400,16 +401,16 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
                                                    float* __restrict__ denv,
                                                    float* __restrict__ grad_params) {
   __shared__ float gy[kGY];
-  __shared__ float gyw_all[kBT / 32][kGY];  // per-warp partial gradients
+  __shared__ float gyw_all[kBC / 32][kGY];  // per-warp partial gradients
   __shared__ float yv[kNumParams];
-  __shared__ float warp_tot[2 * (kBT / 32)];
+  __shared__ float warp_tot[2 * (kBC / 32)];
   const int v = blockIdx.x;
   const int P = vc.K + 1;
   const float inv_cr = (float)(1.0 / vc.control_rate);
   const float inv_2pi = 0.15915494309189533577f;
   float* gyw = gyw_all[threadIdx.x >> 5];
-  for (int i = threadIdx.x; i < kGY * (kBT / 32); i += kBT) (&gyw_all[0][0])[i] = 0.f;
-  for (int i = threadIdx.x; i < kNumParams; i += kBT) yv[i] = (float)y[(size_t)v * kNumParams + i];
+  for (int i = threadIdx.x; i < kGY * (kBC / 32); i += kBC) (&gyw_all[0][0])[i] = 0.f;
+  for (int i = threadIdx.x; i < kNumParams; i += kBC) yv[i] = (float)y[(size_t)v * kNumParams + i];
   __syncthreads();
   float inv_norm[5], wsum_col[5];
   for (int j = 0; j < 5; ++j) {
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
   float* de = denv + (size_t)v * 6 * P;
 
   // pass A: modulation mixer, LFO outputs, pitch
-  for (int base = 0; base < P; base += kBT) {
+  for (int base = 0; base < P; base += kBC) {
     const int k = base + threadIdx.x;
     const bool ok = k < P;
     const int kk = ok ? k : 0;
@@ -498,11 +499,11 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
   // pass B: reverse scan of the LFO phase adjoint -> d/d(phase increment);
   // increments rate_k / CR with rate = clamp(freq + depth * env_rate, 0, 20)
   float carry0 = 0.f, carry1 = 0.f;
-  for (int base = 0; base < P; base += kBT) {
+  for (int base = 0; base < P; base += kBC) {
     const int idx = P - 1 - (base + (int)threadIdx.x);
     const bool ok = idx >= 0;
     float a0 = ok ? dth[idx] : 0.f, a1 = ok ? dth[(size_t)P + idx] : 0.f, t0, t1;
-    block_exclusive_scan2<float, kBT>(a0, a1, warp_tot, t0, t1);
+    block_exclusive_scan2<float, kBC>(a0, a1, warp_tot, t0, t1);
     for (int l = 0; l < 2; ++l) {
       float dinc = 0.f, er = 0.f, rate_raw = 0.f;
       if (ok) {
@@ -525,31 +526,41 @@ __global__ void __launch_bounds__(kBT) bwd_control(const __grid_constant__ Voice
   }
   __syncthreads();
 
-  // pass C: ADSRs, one at a time: each thread sums its points' partials,
-  // then one block-wide sum per partial
+  // pass C: the ADSRs' partials, the (envelope, point) pairs spread over
+  // the block; each thread sums its pairs' partials per envelope, then one
+  // block-wide sum per partial
   float dur_acc = 0.f;
-  for (int a = 0; a < 6; ++a) {
-    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int k = threadIdx.x; k < P; k += kBT) {
-      const float g = de[(size_t)a * P + k];
-      if (g != 0.f) {
-        float out[6];
-        // t_k = k / CR: the float-float product the forward pass uses,
-        // rounded to float (no FP64 division per point and envelope)
-        adsr_d(ff_to_float(ff_mul_f(vc.inv_cr, (float)k)), yv + kAdsr + 5 * a, yv[kDuration], out);
+  float acc[6][5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) acc[q] += g * out[q];
-        dur_acc += g * out[5];
-      }
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[a][q] = 0.f;
+  for (int i = threadIdx.x; i < 6 * P; i += kBC) {
+    const int a = i / P, k = i - a * P;
+    const float g = de[(size_t)a * P + k];
+    if (g != 0.f) {
+      float out[6];
+      // t_k = k / CR: the float-float product the forward pass uses,
+      // rounded to float (no FP64 division per point and envelope)
+      adsr_d(ff_to_float(ff_mul_f(vc.inv_cr, (float)k)), yv + kAdsr + 5 * a, yv[kDuration], out);
+#pragma unroll
+      for (int b = 0; b < 6; ++b)
+        if (b == a) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q) acc[b][q] += g * out[q];
+        }
+      dur_acc += g * out[5];
     }
-#pragma unroll
-    for (int q = 0; q < 5; ++q) acc_y(gyw, kAdsr + 5 * a + q, acc[q]);
   }
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc_y(gyw, kAdsr + 5 * a + q, acc[a][q]);
   acc_y(gyw, kDuration, dur_acc);
   __syncthreads();
-  for (int i = threadIdx.x; i < kGY; i += kBT) {
+  for (int i = threadIdx.x; i < kGY; i += kBC) {
     float t = 0.f;
-    for (int w = 0; w < kBT / 32; ++w) t += gyw_all[w][i];
+    for (int w = 0; w < kBC / 32; ++w) t += gyw_all[w][i];
     gy[i] = t;
   }
   __syncthreads();
@@ -616,7 +627,7 @@ cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t
   bwd_samples<<<gs, kBT, 0, st>>>(vc, seed, batch_index, batch, cb.mixc, cb.dest, cb.seg, cb.kappa,
                                   grad_audio, stat);
   bwd_interval_scan<<<batch, kBT, 0, st>>>(vc, stat, cb.seg, cb.kappa, gpt, vacc);
-  bwd_control<<<batch, kBT, 0, st>>>(vc, cb.y, cb.env, cb.lfo_phase, cb.dest, gpt, vacc, dtheta,
+  bwd_control<<<batch, kBC, 0, st>>>(vc, cb.y, cb.env, cb.lfo_phase, cb.dest, gpt, vacc, dtheta,
                                      denv, grad_params);
   bwd_range_map<<<(batch * kNumParams + 255) / 256, 256, 0, st>>>(vc, params, batch, grad_params);
   return cudaGetLastError();
