@@ -390,6 +390,17 @@ __device__ __forceinline__ void acc_y(float* gy_warp, int slot, float val) {
   if ((threadIdx.x & 31) == 0) gy_warp[slot] += w;
 }
 
+// d y / d u of the range map for parameter p at u (FP32: the FP64 pipe is
+// narrow on this GPU, and the gradient needs ~1e-6).
+__device__ __forceinline__ float range_map_dydu(const VoiceConst& vc, int p, float u_raw) {
+  const float u = fminf(fmaxf(u_raw, 0.f), 1.f);
+  const float c = ff_to_float(vc.map_curve[p]);
+  const float span = vc.sym[p] ? 2.f * ff_to_float(vc.map_scale[p]) : ff_to_float(vc.map_scale[p]);
+  if (!vc.sym[p]) return u <= 0.f ? 0.f : span * c * powf(u, c - 1.f);
+  const float s = fabsf(2.f * u - 1.f);
+  return s <= 0.f ? 0.f : span * c * powf(s, c - 1.f);
+}
+
 __global__ void __launch_bounds__(kBC) bwd_control(const __grid_constant__ VoiceConst vc,
                                                    const double* __restrict__ y,
                                                    const ff* __restrict__ env,
@@ -399,6 +410,7 @@ __global__ void __launch_bounds__(kBC) bwd_control(const __grid_constant__ Voice
                                                    const double* __restrict__ vacc,
                                                    float* __restrict__ dtheta,
                                                    float* __restrict__ denv,
+                                                   const float* __restrict__ u_in,
                                                    float* __restrict__ grad_params) {
   __shared__ float gy[kGY];
   __shared__ float gyw_all[kBC / 32][kGY];  // per-warp partial gradients
@@ -578,29 +590,13 @@ __global__ void __launch_bounds__(kBC) bwd_control(const __grid_constant__ Voice
       gy[kMix + c] += (float)va[2 + c] / norm - (sum > 1.f ? dotg / (norm * norm) : 0.f);
   }
   __syncthreads();
-  // range map: dy/du
-  if (threadIdx.x < kNumParams) grad_params[(size_t)v * kNumParams + threadIdx.x] = gy[threadIdx.x];
+  // through the range map: d/du = d/dy dy/du
+  if (threadIdx.x < kNumParams) {
+    const size_t i = (size_t)v * kNumParams + threadIdx.x;
+    grad_params[i] = gy[threadIdx.x] * range_map_dydu(vc, threadIdx.x, u_in[i]);
+  }
 }
 
-// d y / d u of the range map, applied in place to grad (which holds d/dy).
-__global__ void bwd_range_map(const __grid_constant__ VoiceConst vc, const float* __restrict__ u_in,
-                              int batch, float* __restrict__ grad) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= batch * kNumParams) return;
-  const int p = i % kNumParams;
-  // FP32 (the FP64 pipe is narrow on this GPU; the gradient needs ~1e-6)
-  const float u = fminf(fmaxf(u_in[i], 0.f), 1.f);
-  const float c = ff_to_float(vc.map_curve[p]);
-  const float span = vc.sym[p] ? 2.f * ff_to_float(vc.map_scale[p]) : ff_to_float(vc.map_scale[p]);
-  float dydu;
-  if (!vc.sym[p]) {
-    dydu = u <= 0.f ? 0.f : span * c * powf(u, c - 1.f);
-  } else {
-    const float s = fabsf(2.f * u - 1.f);
-    dydu = s <= 0.f ? 0.f : span * c * powf(s, c - 1.f);
-  }
-  grad[i] *= dydu;
-}
 
 }  // namespace
 
@@ -628,8 +624,7 @@ cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t
                                   grad_audio, stat);
   bwd_interval_scan<<<batch, kBT, 0, st>>>(vc, stat, cb.seg, cb.kappa, gpt, vacc);
   bwd_control<<<batch, kBC, 0, st>>>(vc, cb.y, cb.env, cb.lfo_phase, cb.dest, gpt, vacc, dtheta,
-                                     denv, grad_params);
-  bwd_range_map<<<(batch * kNumParams + 255) / 256, 256, 0, st>>>(vc, params, batch, grad_params);
+                                     denv, params, grad_params);
   return cudaGetLastError();
 }
 
