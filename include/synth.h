@@ -444,7 +444,7 @@ synth_status synth_selftest_wait_timeout(synth_handle h, void* stream);
  * libsynth_checked.so, with the same calls and results. Its fused render
  * tests every index it derives -- audio and parameter offsets, the voice's
  * set-up and tile records, the tile's interval arrays in shared memory --
- * against the range it addresses; an index outside it is not used, and the
+ * against the range it addresses, as do the adjoint's kernels; an index outside it is not used, and the
  * next synth_sync (synth_noalloc_status) returns SYNTH_ERR_BOUNDS. It takes
  * the place of a memory checker where none can run.
  * synth_checked_build: 1 in that library, 0 in the release build.

@@ -31,9 +31,9 @@ void launch_control_pipeline(const VoiceConst& vc, uint64_t seed, uint64_t batch
                              const float* params_in, float* params_out, const ControlBuffers& cb,
                              cudaStream_t st);
 // The same buffers, bit for bit, from one kernel (one CTA per voice, the
-// steps separated by barriers).
+// steps separated by barriers); hdr takes the bounds-checked build's errors.
 void launch_control_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index, int batch,
                           const float* params_in, float* params_out, const ControlBuffers& cb,
-                          cudaStream_t st);
+                          ScratchHeader* hdr, cudaStream_t st);
 
 }  // namespace synth

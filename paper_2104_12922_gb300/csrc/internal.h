@@ -146,8 +146,11 @@ cudaError_t launch_mmd_trials(const float* dist, int m, const int8_t* labels, in
 
 // Adjoint.
 size_t backward_workspace_bytes(const VoiceConst& vc, int batch);
+// hdr: the handle's scratch header, whose error word the bounds-checked
+// build's checks write.
 cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
                                    int batch, const float* params, const float* grad_audio,
-                                   float* grad_params, void* workspace, cudaStream_t stream);
+                                   float* grad_params, void* workspace, ScratchHeader* hdr,
+                                   cudaStream_t stream);
 
 }  // namespace synth

@@ -76,12 +76,15 @@ __global__ void __launch_bounds__(kBT) bwd_samples(const __grid_constant__ Voice
                                                    const SegVco* __restrict__ seg,
                                                    const float* __restrict__ kappa,
                                                    const float* __restrict__ grad_audio,
-                                                   float* __restrict__ stat) {
+                                                   float* __restrict__ stat, ScratchHeader* hdr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int v = blockIdx.y;
   const int K = vc.K, P = K + 1, R = vc.R;
   const int k = blockIdx.x * (kBT / 32) + warp;
   if (k >= K) return;
+  // the interval's control points k and k + 1, its descriptions and its row
+  // of statistics belong to voice v of this batch
+  if (!in_bounds(hdr, v, batch) || !in_bounds(hdr, k + 1, P)) return;
   const int64_t N = vc.n_samples;
   // mixer gains and square-saw shape as the control pass stored them (the
   // FP64 quotients rounded to float: no FP64 arithmetic in this kernel)
@@ -131,7 +134,9 @@ __global__ void __launch_bounds__(kBT) bwd_samples(const __grid_constant__ Voice
         inc[0][i] = inc[1][i] = 0.f;
         continue;
       }
-      const float go = grad_audio[(size_t)v * N + n0 + i];
+      const float go = in_bounds(hdr, (long long)v * N + n0 + i, (long long)batch * N)
+                           ? grad_audio[(size_t)v * N + n0 + i]
+                           : 0.f;
       const float fj = (float)j * invR;
       float A[3];
 #pragma unroll
@@ -230,7 +235,8 @@ __global__ void __launch_bounds__(kBT) bwd_interval_scan(const __grid_constant__
                                                          const SegVco* __restrict__ seg,
                                                          const float* __restrict__ kappa,
                                                          double* __restrict__ gpt,
-                                                         double* __restrict__ vacc) {
+                                                         double* __restrict__ vacc,
+                                                         ScratchHeader* hdr) {
   __shared__ double warp_tot[2 * (kBT / 32)];
   __shared__ double red[8][kBT / 32];
   const int v = blockIdx.x;
@@ -265,13 +271,15 @@ __global__ void __launch_bounds__(kBT) bwd_interval_scan(const __grid_constant__
       // consumer adds the two halves of a point
       double* gl = gv + (size_t)idx * 5;
       double* gr = gv + (size_t)P * 5 * gridDim.x + (size_t)(idx + 1) * 5;
-      gl[0] = dl0;
-      gr[0] = dr0;
-      gl[1] = dl1 + dk;
-      gr[1] = dr1;
-      for (int c = 0; c < 3; ++c) {
-        gl[2 + c] = (double)st[10 + c];
-        gr[2 + c] = (double)st[13 + c];
+      if (in_bounds(hdr, idx + 1, P)) {  // both halves stay in the voice's P points
+        gl[0] = dl0;
+        gr[0] = dr0;
+        gl[1] = dl1 + dk;
+        gr[1] = dr1;
+        for (int c = 0; c < 3; ++c) {
+          gl[2 + c] = (double)st[10 + c];
+          gr[2 + c] = (double)st[13 + c];
+        }
       }
       for (int c = 0; c < 4; ++c) part[c] += (double)st[17 + c];
     }
@@ -411,7 +419,8 @@ __global__ void __launch_bounds__(kBC) bwd_control(const __grid_constant__ Voice
                                                    float* __restrict__ dtheta,
                                                    float* __restrict__ denv,
                                                    const float* __restrict__ u_in,
-                                                   float* __restrict__ grad_params) {
+                                                   float* __restrict__ grad_params,
+                                                   int batch, ScratchHeader* hdr) {
   __shared__ float gy[kGY];
   __shared__ float gyw_all[kBC / 32][kGY];  // per-warp partial gradients
   __shared__ float yv[kNumParams];
@@ -591,7 +600,8 @@ __global__ void __launch_bounds__(kBC) bwd_control(const __grid_constant__ Voice
   }
   __syncthreads();
   // through the range map: d/du = d/dy dy/du
-  if (threadIdx.x < kNumParams) {
+  if (threadIdx.x < kNumParams &&
+      in_bounds(hdr, (long long)v * kNumParams + threadIdx.x, (long long)batch * kNumParams)) {
     const size_t i = (size_t)v * kNumParams + threadIdx.x;
     grad_params[i] = gy[threadIdx.x] * range_map_dydu(vc, threadIdx.x, u_in[i]);
   }
@@ -606,7 +616,8 @@ size_t backward_workspace_bytes(const VoiceConst& vc, int batch) {
 
 cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t batch_index,
                                    int batch, const float* params, const float* grad_audio,
-                                   float* grad_params, void* workspace, cudaStream_t st) {
+                                   float* grad_params, void* workspace, ScratchHeader* hdr,
+                                   cudaStream_t st) {
   if (vc.R > 128) return cudaErrorInvalidValue;
   const ControlBuffers cb = control_carve(vc, batch, workspace);
   const BwdLayout L = bwd_layout(vc, batch, control_bytes(vc, batch));
@@ -617,14 +628,14 @@ cudaError_t launch_render_backward(const VoiceConst& vc, uint64_t seed, uint64_t
   float* dtheta = reinterpret_cast<float*>(ws + L.dtheta);
   float* denv = reinterpret_cast<float*>(ws + L.denv);
   const int K = vc.K, P = K + 1;
-  launch_control_fused(vc, seed, batch_index, batch, params, nullptr, cb, st);
+  launch_control_fused(vc, seed, batch_index, batch, params, nullptr, cb, hdr, st);
   cudaMemsetAsync(gpt, 0, sizeof(double) * 2 * (size_t)batch * P * 5, st);
   dim3 gs((K + kBT / 32 - 1) / (kBT / 32), batch);
   bwd_samples<<<gs, kBT, 0, st>>>(vc, seed, batch_index, batch, cb.mixc, cb.dest, cb.seg, cb.kappa,
-                                  grad_audio, stat);
-  bwd_interval_scan<<<batch, kBT, 0, st>>>(vc, stat, cb.seg, cb.kappa, gpt, vacc);
+                                  grad_audio, stat, hdr);
+  bwd_interval_scan<<<batch, kBT, 0, st>>>(vc, stat, cb.seg, cb.kappa, gpt, vacc, hdr);
   bwd_control<<<batch, kBC, 0, st>>>(vc, cb.y, cb.env, cb.lfo_phase, cb.dest, gpt, vacc, dtheta,
-                                     denv, params, grad_params);
+                                     denv, params, grad_params, batch, hdr);
   return cudaGetLastError();
 }
 

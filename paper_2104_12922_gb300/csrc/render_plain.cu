@@ -319,12 +319,14 @@ __global__ void plain_seg_phase(const __grid_constant__ VoiceConst vc, const dou
 constexpr int kFusedCtl = 1024;
 __global__ void __launch_bounds__(kFusedCtl) control_fused_kernel(
     const __grid_constant__ VoiceConst vc, uint64_t seed, uint64_t batch_index, int batch,
-    const float* params_in, float* params_out, const ControlBuffers cb) {
+    const float* params_in, float* params_out, const ControlBuffers cb, ScratchHeader* hdr) {
   __shared__ FFTables T;
   __shared__ ff yff[kNumParams];
   __shared__ double warp_tot[2 * (kPT / 32)];
   const int v = blockIdx.x, tid = threadIdx.x;
   const int P = vc.K + 1, K = vc.K;
+  // every buffer below is addressed at voice v of this batch
+  if (!in_bounds(hdr, v, batch)) return;
   load_tables(T, vc.T);
   if (tid < kNumParams)
     params_elem(vc, seed, batch_index, batch, params_in, params_out, cb.y, v, tid);
@@ -344,7 +346,8 @@ __global__ void __launch_bounds__(kFusedCtl) control_fused_kernel(
     modmix_elem(vc, V, T, cb.env, cb.lfo_phase, cb.dest, v, k);
   __syncthreads();
   for (int k = tid; k < K; k += kFusedCtl)
-    vco_interval_elem(vc, V, T, cb.dest, cb.seg, cb.seg_sum, cb.kappa, v, k);
+    if (in_bounds(hdr, k + 1, P))  // the interval's end point
+      vco_interval_elem(vc, V, T, cb.dest, cb.seg, cb.seg_sum, cb.kappa, v, k);
   __syncthreads();
   if (tid < kPT)
     phase_scan_block(cb.seg_sum, cb.seg_start, K, K, cb.y, kSine + 2, kSqr + 2, v, warp_tot,
@@ -524,9 +527,9 @@ void launch_control_pipeline(const VoiceConst& vc, uint64_t seed, uint64_t batch
 
 void launch_control_fused(const VoiceConst& vc, uint64_t seed, uint64_t batch_index, int batch,
                           const float* params_in, float* params_out, const ControlBuffers& cb,
-                          cudaStream_t st) {
+                          ScratchHeader* hdr, cudaStream_t st) {
   control_fused_kernel<<<batch, kFusedCtl, 0, st>>>(vc, seed, batch_index, batch, params_in,
-                                                    params_out, cb);
+                                                    params_out, cb, hdr);
 }
 
 size_t plain_workspace_bytes(const VoiceConst& vc, int batch) {

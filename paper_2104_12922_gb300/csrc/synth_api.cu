@@ -307,6 +307,7 @@ synth_status synth_render_backward(synth_handle h, uint64_t seed, uint64_t batch
   if (h->vc.R > 128) return SYNTH_ERR_UNSUPPORTED;
   return check_cuda(launch_render_backward(h->vc, seed, batch_index, batch, params_dev,
                                            grad_audio_dev, grad_params_dev, workspace_dev,
+                                           static_cast<ScratchHeader*>(h->scratch),
                                            static_cast<cudaStream_t>(stream)));
 }
 

@@ -3,8 +3,8 @@ with SYNTH_CHECKED=1, which selects libsynth_checked.so) and once through the
 release library: every path of the fused render -- several windows per
 voice, a ragged length (scalar stores), several batches in one launch, peak
 normalisation, a fractional rate, FP32 carries, caller parameters at the
-corners, the allocation-free entry point -- with the device status read
-after each. Used by tests/test_checked_gpu.py."""
+corners, the allocation-free entry point -- and the adjoint, with the device
+status read after each. Used by tests/test_checked_gpu.py."""
 import ctypes
 
 import numpy as np
@@ -74,6 +74,12 @@ def run_cases(pkg, torch):
     s.sync()
     s.close()
     keep("noalloc", *_noalloc(pkg, torch, 0.3, 17, 5, 2))
+    s = pkg.Synth(seconds=1.0, max_batch=8)  # the adjoint: 441 intervals, both scans chunked
+    u = torch.tensor(si.uniform_params(19, 8), dtype=torch.float32, device="cuda")
+    ga = torch.tensor(si.upstream_grad(20, (8, s.num_samples)), dtype=torch.float32, device="cuda")
+    keep("adjoint", s.backward(19, 0, u, ga))
+    s.sync()
+    s.close()
     return res
 
 

@@ -1,7 +1,7 @@
 """The bounds-checked build (libsynth_checked.so, -DSYNTH_CHECKS) on the GPU:
-no index of the fused render leaves its range on any render path (every
-device status is SYNTH_OK), its outputs equal the release library's bit for
-bit (the checks only add tests, never change a value), and its self-test
+no index of the fused render or of the adjoint leaves its range on any path
+(every device status is SYNTH_OK), its outputs equal the release library's
+bit for bit (the checks only add tests, never change a value), and its self-test
 shows an out-of-range index refused and reported as SYNTH_ERR_BOUNDS once,
 the handle rendering unchanged afterwards. The checked library runs in a
 child process (SYNTH_CHECKED=1 selects it for a whole process); this process
