@@ -67,9 +67,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---------------------------------------------------------------------------
 // 2. audio-rate reverse pass. Warp w of a block takes control interval k; lane
-// l takes samples 4l..4l+3 of it (R <= 128).
+// l takes samples 4l..4l+3 of it (R <= 128). Four blocks per SM (64
+// registers, a small spill) run it faster than three with no spill.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBT) bwd_samples(const __grid_constant__ VoiceConst vc,
+__global__ void __launch_bounds__(kBT, 4) bwd_samples(const __grid_constant__ VoiceConst vc,
                                                    uint64_t seed, uint64_t batch_index, int batch,
                                                    const float* __restrict__ mixc,
                                                    const ff* __restrict__ dest,
