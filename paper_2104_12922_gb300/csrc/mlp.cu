@@ -191,14 +191,37 @@ __device__ __forceinline__ float adam_one(float& w, float g, float& m, float& v,
   return w;
 }
 
+// A layer's bias vector, updated by the same launch as its weights.
+struct BiasAdam {
+  float* w;
+  const float* g;
+  float* m;
+  float* v;
+  int n;
+};
+
+__device__ __forceinline__ void bias_adam_one(const BiasAdam& b, int j, float lr, float b1,
+                                              float b2, float eps, float c1, float c2) {
+  float wi = b.w[j], mi = b.m[j], vi = b.v[j];
+  adam_one(wi, b.g[j], mi, vi, lr, b1, b2, eps, c1, c2);
+  b.w[j] = wi;
+  b.m[j] = mi;
+  b.v[j] = vi;
+}
+
 __global__ void adam_update_vec4(float4* __restrict__ w, const float4* __restrict__ g,
                                  float4* __restrict__ m, float4* __restrict__ v, int64_t n4,
                                  float lr, float b1, float b2, float eps, float c1, float c2,
-                                 uint2* __restrict__ wb) {
+                                 uint2* __restrict__ wb, const BiasAdam bias) {
   pdl_wait();     // earlier kernels' writes are visible
   pdl_release();  // the next kernel may be scheduled
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+  // indices n4 .. n4 + bias.n - 1 are the bias entries
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4 + bias.n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (i >= n4) {
+      bias_adam_one(bias, (int)(i - n4), lr, b1, b2, eps, c1, c2);
+      continue;
+    }
     float4 wi = w[i], mi = m[i], vi = v[i];
     const float4 gi = g[i];
     adam_one(wi.x, gi.x, mi.x, vi.x, lr, b1, b2, eps, c1, c2);
@@ -215,34 +238,22 @@ __global__ void adam_update_vec4(float4* __restrict__ w, const float4* __restric
   }
 }
 
-// Scalar Adam for short vectors (biases).
-__global__ void adam_update(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int64_t n, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
-  pdl_wait();     // earlier kernels' writes are visible
-  pdl_release();  // the next kernel may be scheduled
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float wi = w[i], mi = m[i], vi = v[i];
-    adam_one(wi, g[i], mi, vi, lr, b1, b2, eps, c1, c2);
-    w[i] = wi;
-    m[i] = mi;
-    v[i] = vi;
-  }
-}
-
 // Adam on a weight matrix [rows][cols] that also keeps a transposed bf16 copy
 // wt[col][row] (row stride ld_t): a block updates a 32 x 32 tile (32 x 8
-// threads) and writes the transposed copy through shared memory, coalesced.
+// threads) and writes the transposed copy through shared memory, coalesced;
+// the blocks of the first tile column also update the bias of their rows.
 __global__ void __launch_bounds__(256) adam_update_tiled(
     float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
     float* __restrict__ v, int rows, int cols, float lr, float b1, float b2, float eps, float c1,
-    float c2, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt, int ld_t) {
+    float c2, __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wt, int ld_t,
+    const BiasAdam bias) {
   pdl_wait();     // earlier kernels' writes are visible
   pdl_release();  // the next kernel may be scheduled
   __shared__ __nv_bfloat16 tile[32][34];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + tx, r0 = blockIdx.y * 32;
+  if (blockIdx.x == 0 && ty == 0 && r0 + tx < bias.n)
+    bias_adam_one(bias, r0 + tx, lr, b1, b2, eps, c1, c2);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int r = r0 + ty + 8 * k;
@@ -425,7 +436,7 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
         return e;
     }
   }
-  // Adam
+  // Adam: each layer's weights and bias in one launch
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
   for (int l = 0; l < 4; ++l) {
@@ -435,28 +446,26 @@ cudaError_t mlp_train_step(const MlpLayout& L, char* base, const __nv_bfloat16* 
     float* mw = reinterpret_cast<float*>(base + L.mw[l]);
     float* vw = reinterpret_cast<float*>(base + L.vw[l]);
     __nv_bfloat16* wb = reinterpret_cast<__nv_bfloat16*>(base + L.wb[l]);
+    const BiasAdam bias{reinterpret_cast<float*>(base + L.b[l]),
+                        reinterpret_cast<const float*>(base + L.gb[l]),
+                        reinterpret_cast<float*>(base + L.mb[l]),
+                        reinterpret_cast<float*>(base + L.vb[l]), out};
     if (l == 0) {
       // no transposed copy: a vectorised stream (in * out is a multiple of 4)
       const int64_t n4 = (int64_t)in * out / 4;
-      if ((e = launch_pdl(adam_update_vec4, dim3(grid_of(n4)), dim3(256), 0, st,
+      if ((e = launch_pdl(adam_update_vec4, dim3(grid_of(n4 + out)), dim3(256), 0, st,
                           reinterpret_cast<float4*>(w), reinterpret_cast<const float4*>(g),
                           reinterpret_cast<float4*>(mw), reinterpret_cast<float4*>(vw), n4, lr, b1,
-                          b2, eps, c1, c2, reinterpret_cast<uint2*>(wb))) != cudaSuccess)
+                          b2, eps, c1, c2, reinterpret_cast<uint2*>(wb), bias)) != cudaSuccess)
         return e;
     } else {
       const int outp = l == 3 ? Pp : out;
       if ((e = launch_pdl(adam_update_tiled, dim3((in + 31) / 32, (out + 31) / 32), dim3(256), 0,
                           st, w, g, mw, vw, out, in, lr, b1, b2, eps, c1, c2, wb,
-                          reinterpret_cast<__nv_bfloat16*>(base + L.wt[l]), outp)) != cudaSuccess)
+                          reinterpret_cast<__nv_bfloat16*>(base + L.wt[l]), outp, bias)) !=
+          cudaSuccess)
         return e;
     }
-    if ((e = launch_pdl(adam_update, dim3(grid_of(out)), dim3(256), 0, st,
-                        reinterpret_cast<float*>(base + L.b[l]),
-                        reinterpret_cast<const float*>(base + L.gb[l]),
-                        reinterpret_cast<float*>(base + L.mb[l]),
-                        reinterpret_cast<float*>(base + L.vb[l]), (int64_t)out, lr, b1, b2, eps, c1,
-                        c2)) != cudaSuccess)
-      return e;
   }
   // the loss last, so that no copy splits the chain of kernels above
   if (loss_out &&
