@@ -502,9 +502,14 @@ class ProposalModel:
         except Exception:
             pass
 
-    def features(self, audio, stream=None):
+    def features(self, audio, stream=None, out=None):
         import torch
-        f = torch.empty((audio.shape[0], self.feature_dim), dtype=torch.bfloat16, device=audio.device)
+        f = out if out is not None else torch.empty((audio.shape[0], self.feature_dim),
+                                                    dtype=torch.bfloat16, device=audio.device)
+        if f.dtype != torch.bfloat16 or not f.is_contiguous() or \
+                tuple(f.shape) != (audio.shape[0], self.feature_dim):
+            raise ValueError(f"out must be a contiguous bf16 tensor of shape "
+                             f"({audio.shape[0]}, {self.feature_dim})")
         _check(lib().synth_model_features(self.handle, _ptr(audio), audio.shape[0], _ptr(f),
                                           _stream_ptr(stream)), "synth_model_features")
         return f

@@ -42,24 +42,65 @@ def test_batches(batch: int):
 
 
 def train(model: pkg.ProposalModel, steps: int, batch: int = 128, seed: int = 0,
-          lr: float = 3e-4, log_every: int = 100):
+          lr: float = 3e-4, log_every: int = 100, pipeline: bool = True):
     """On-the-fly training over consecutive training-split batches; returns
     the loss history, wall seconds and GPU milliseconds (CUDA events around
-    the whole loop)."""
+    the whole loop).
+
+    pipeline: the next batch is rendered and turned into features on a
+    second stream while the network trains on this one (two sets of
+    buffers, events between the streams); the same calls on the same
+    inputs as the one-stream loop (synth_model_train_step), so the model
+    ends bit-identical to it."""
     import torch
     syn = model.synth
     loss = torch.zeros(1, device=syn.device)
     hist = []
     it = train_batches(batch)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def lr_at(s):
+        return lr * min(1.0, (s + 1) / 200) * (0.1 ** (s / max(1, steps)))
+
     t0 = time.perf_counter()
-    start.record()
-    for s in range(steps):
-        lr_s = lr * min(1.0, (s + 1) / 200) * (0.1 ** (s / max(1, steps)))
-        model.train_step(seed, next(it), batch, lr_s, loss=loss)
-        if s % log_every == 0 or s == steps - 1:
-            hist.append((s, loss.clone()))
-    end.record()
+    main = torch.cuda.current_stream()
+    start.record(main)
+    if not pipeline:
+        for s in range(steps):
+            model.train_step(seed, next(it), batch, lr_at(s), loss=loss)
+            if s % log_every == 0 or s == steps - 1:
+                hist.append((s, loss.clone()))
+    else:
+        dev = syn.device
+        side = torch.cuda.Stream(device=dev)
+        audio = [torch.empty((batch, syn.num_samples), device=dev) for _ in range(2)]
+        params = [torch.empty((batch, pkg.NUM_PARAMS), device=dev) for _ in range(2)]
+        feats = [torch.empty((batch, model.feature_dim), dtype=torch.bfloat16, device=dev)
+                 for _ in range(2)]
+        ready = [torch.cuda.Event(), torch.cuda.Event()]  # batch in buffer i is prepared
+        done = [torch.cuda.Event(), torch.cuda.Event()]   # buffer i has been trained on
+
+        def prepare(i, b):
+            syn.render(seed, b, batch, out=audio[i], params_out=params[i], stream=side)
+            model.features(audio[i], stream=side, out=feats[i])
+            ready[i].record(side)
+
+        side.wait_stream(main)
+        if steps > 0:
+            prepare(0, next(it))
+        for s in range(steps):
+            i, j = s % 2, 1 - s % 2
+            if s + 1 < steps:
+                if s >= 1:
+                    side.wait_event(done[j])
+                prepare(j, next(it))
+            main.wait_event(ready[i])
+            model.train_features(feats[i], params[i], lr_at(s), loss=loss, stream=main)
+            done[i].record(main)
+            if s % log_every == 0 or s == steps - 1:
+                hist.append((s, loss.clone()))
+        main.wait_stream(side)
+    end.record(main)
     end.synchronize()
     syn.sync()
     hist = [(s, float(l.item())) for s, l in hist]

@@ -148,3 +148,23 @@ def test_param_adam_descends_and_stays_in_range(env):
     assert float(u.min()) >= 0.0 and float(u.max()) <= 1.0
     assert float(u[0]) > 0.99 and float(u[-1]) < 0.01
     syn.close()
+
+
+def test_pipelined_training_equals_one_stream_training(env):
+    """proposal.train renders and transforms the next batch on a second
+    stream while the network trains on this one; the model it leaves is the
+    one the one-stream loop of synth_model_train_step leaves, bit for bit."""
+    torch, pkg = env
+    from paper_2104_12922_gb300 import proposal as pr
+    syn = pkg.Synth(seconds=0.25, max_batch=16)
+    one = pkg.ProposalModel(syn, max_batch=16, seed=4)
+    two = pkg.ProposalModel(syn, max_batch=16, seed=4)
+    r1 = pr.train(one, 7, batch=16, lr=1e-3, log_every=3, pipeline=False)
+    r2 = pr.train(two, 7, batch=16, lr=1e-3, log_every=3, pipeline=True)
+    assert r1["loss"] == r2["loss"]
+    for l in range(4):
+        assert torch.equal(one.tensor(0, l), two.tensor(0, l)), l
+        assert torch.equal(one.tensor(1, l), two.tensor(1, l)), l
+    one.close()
+    two.close()
+    syn.close()
